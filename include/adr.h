@@ -1,0 +1,178 @@
+/*
+ * adr.h — C ABI of libadr.so, a GB300 (sm_103a) implementation of the
+ * AdR-Gaussian rasterization path (Wang, Yi, Ma: "AdR-Gaussian: Accelerating
+ * Gaussian Splatting with Adaptive Radius", SIGGRAPH Asia 2024, arXiv 2409.08669).
+ *
+ * The path is the paper's six-stage tile rasterizer (Sec. 3.2.1: Preprocess,
+ * InclusiveSum, DuplicateWithKeys, SortPairs, IdentifyTileRanges, Render) with
+ * the early culling of Gaussian-tile pairs whose splatting opacity cannot reach
+ * alpha_low = 1/255: the adaptive radius (Sec. 4.2, Eq. 5-8) and the
+ * axis-aligned bounding box (Sec. 4.3, Eq. 9-11).  Render also counts the
+ * per-pixel load l_i (Sec. 4.4, Eq. 12) that the load-balancing loss uses.
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is caller-owned memory.  Unless an entry point says
+ *     HOST, it is device memory on the context's device, C-contiguous float32
+ *     (or the stated integer type), and it is only read/written during the
+ *     stream-ordered work the call enqueues.  The library never frees it.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls enqueue asynchronously and return without waiting unless
+ *     the entry point says it synchronises.
+ *   - A context holds one frame's intermediates; calls that use the same
+ *     context must be ordered on one stream (or externally synchronised).
+ *   - Parameters are activated: positive scales, opacity in (0, 1), rotation
+ *     quaternions (w, x, y, z) of any non-zero norm (normalised internally).
+ *   - On failure an entry point returns a non-zero adr_status and
+ *     adr_last_error() describes it (thread-local, valid until the next call
+ *     on that thread).  Invalid arguments are rejected before any work is
+ *     enqueued.
+ */
+#ifndef ADR_H
+#define ADR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADR_TILE 16            /* tile edge in pixels (Sec. 3.2) */
+#define ADR_CAMERA_FLOATS 24   /* view[16], fx, fy, cx, cy, near, cam_pos[3] */
+#define ADR_GEOM_FLOATS 12     /* see adr_read_gaussians */
+
+typedef enum adr_status {
+    ADR_OK = 0,
+    ADR_ERR_INVALID = 1,    /* bad argument (NULL, size out of range, bad mode) */
+    ADR_ERR_CAPACITY = 2,   /* more pairs than pair_capacity; nothing written out of bounds */
+    ADR_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    ADR_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (output not valid) */
+    ADR_PENDING = 5,        /* serving: request not finished yet */
+    ADR_ERR_ADMISSION = 6   /* serving: request can never fit the memory budget */
+} adr_status;
+
+/* Pair-culling mode of Preprocess.
+ *   ADR_PLAIN  : 3DGS tile range, square of radius r_o = ceil(3 sqrt(lambda'_max))
+ *                (the "99% confidence" range the paper compares against, Sec. 4.2).
+ *   ADR_CIRCLE : adaptive radius r = min(sqrt(2 lambda'_max ln(sigma/alpha_low)), r_o)
+ *                (Eq. 7-8); no pairs when sigma < alpha_low.
+ *   ADR_AABB   : r_x = min(sqrt(2 Sigma'_X ln(sigma/alpha_low)), r_o),
+ *                r_y = min(sqrt(2 Sigma'_Y ln(sigma/alpha_low)), r_o) (Eq. 10-11).
+ * All modes produce the same image (the culled pairs have alpha < alpha_low at
+ * every pixel of the culled tile, Sec. 5.2 and 5.3). */
+typedef enum adr_mode { ADR_PLAIN = 0, ADR_CIRCLE = 1, ADR_AABB = 2 } adr_mode;
+
+/* Pinhole camera.  view: row-major world->camera matrix with OpenCV axes
+ * (x right, y down, z forward).  A pixel (i, j) has its centre at integer
+ * coordinates.  near: Gaussians with view depth <= near are culled. */
+typedef struct adr_camera {
+    float view[16];
+    float fx, fy, cx, cy;
+    float near_z;
+    float cam_pos[3];
+    int32_t width, height;
+} adr_camera;
+
+/* Render settings.  alpha_low: minimum splatting opacity (paper: 1/255,
+ * Sec. 5.1.2); t_min: blending stops before a Gaussian that would take the
+ * transmittance below it; lowpass: added to the diagonal of Sigma';
+ * jac_clamp: the projection Jacobian uses x/z, y/z clamped to
+ * +-jac_clamp*tan(fov/2); bg: background colour; sh_degree: 0..3. */
+typedef struct adr_settings {
+    int32_t mode;
+    float alpha_low, t_min, lowpass, jac_clamp;
+    float bg[3];
+    int32_t sh_degree;
+} adr_settings;
+
+typedef struct adr_ctx adr_ctx;
+
+/* Create a context on `device` with workspace for up to `max_gaussians`
+ * Gaussians, `pair_capacity` Gaussian-tile pairs (at most 2^30) and images
+ * up to max_width x max_height (at most 2^16 tiles, e.g. 4096 x 4096).  All
+ * workspace is allocated here (cudaMalloc); no later call allocates, except
+ * the first adr_render_host, which allocates its staging buffers.  Returns ADR_ERR_INVALID for sizes <= 0 or too
+ * large, ADR_ERR_CUDA if allocation fails (nothing leaks). */
+adr_status adr_create(adr_ctx **ctx, int64_t max_gaussians, int64_t pair_capacity,
+                      int32_t max_width, int32_t max_height, int32_t device);
+
+/* Synchronise the context's device and free its workspace.  NULL is a no-op. */
+void adr_destroy(adr_ctx *ctx);
+
+/* Stages 1-3 (Sec. 3.2.1): Preprocess each Gaussian (projection, EWA
+ * covariance Sigma', conic, SH colour of degree sh_degree, early cull by
+ * settings->mode), order the Gaussians by view depth, scan their tile counts
+ * and emit one (tile, Gaussian) pair per overlapped tile.
+ *   means [n,3], scales [n,3], rots [n,4] (w,x,y,z), opac [n], sh [n,16,3]
+ *   (coefficient index l*l+l+m, channel last; only (sh_degree+1)^2 used).
+ * 0 <= n <= max_gaussians; camera size within the context's maximum.
+ * The pair count stays on the device (see adr_num_pairs).  If it exceeds
+ * pair_capacity the excess pairs are dropped and a device flag is set; the
+ * next adr_num_pairs / adr_sync_status returns ADR_ERR_CAPACITY. */
+adr_status adr_preprocess(adr_ctx *ctx, const float *means, const float *scales,
+                          const float *rots, const float *opac, const float *sh, int64_t n,
+                          const adr_camera *camera, const adr_settings *settings, void *stream);
+
+/* Stages 4-5: stable sort of the pairs by tile (the Gaussians are already in
+ * depth order, so the result is ordered by (tile, depth, index)) and the
+ * per-tile ranges [start, end) into the sorted list. */
+adr_status adr_sort(adr_ctx *ctx, void *stream);
+
+/* Stage 6: per-tile front-to-back alpha blending (Eq. 2-3) of the sorted
+ * Gaussians; pairs with alpha < alpha_low are skipped and a pixel stops
+ * before the Gaussian that would take its transmittance below t_min.
+ *   img [3,H,W] = sum_k c_k alpha_k T_k + T_final * bg
+ *   t_final [H,W] final transmittance (may be NULL)
+ *   load [H,W] int32 Gaussians blended per pixel, l_i of Eq. 12 (may be NULL). */
+adr_status adr_render(adr_ctx *ctx, float *img, float *t_final, int32_t *load, void *stream);
+
+/* Waits for the context's last stream and returns the pair count P (the sum
+ * of tiles over Gaussians, which may exceed pair_capacity).  Returns
+ * ADR_ERR_CAPACITY if P > pair_capacity, ADR_ERR_TIMEOUT if a bounded device
+ * wait gave up (device flags are cleared).  SYNCHRONISES that stream. */
+adr_status adr_num_pairs(adr_ctx *ctx, int64_t *num_pairs);
+
+/* Inspection (tests, debugging).  Copy the sorted pairs as 64-bit keys
+ * (tile << 32) | bits(depth) and Gaussian indices into caller device buffers
+ * of `capacity` entries (at most min(P, capacity) written).  Enqueued on
+ * `stream` after adr_sort. */
+adr_status adr_read_pairs(adr_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t capacity,
+                          void *stream);
+
+/* Inspection: per-Gaussian Preprocess results for the last adr_preprocess.
+ *   geom [n, ADR_GEOM_FLOATS]: px, py, conic_a, conic_b, conic_c, opacity,
+ *        r_x, r_y, red, green, blue, depth
+ *   rect [n,4] int32 tile rectangle tx0, ty0, tx1, ty1 (exclusive ends)
+ *   tiles [n] int32 number of tiles (0 = culled) */
+adr_status adr_read_gaussians(adr_ctx *ctx, float *geom, int32_t *rect, int32_t *tiles,
+                              void *stream);
+
+/* Inspection: per-tile ranges [start, end) as uint32 pairs, tiles_x*tiles_y rows. */
+adr_status adr_read_ranges(adr_ctx *ctx, uint32_t *ranges, void *stream);
+
+/* Waits for the context's work and reports device-side flags as a status
+ * (ADR_ERR_CAPACITY, ADR_ERR_TIMEOUT or ADR_OK); clears them.  SYNCHRONISES. */
+adr_status adr_sync_status(adr_ctx *ctx);
+
+/* End-to-end frame from HOST memory: copies the scene arrays (HOST pointers,
+ * ideally pinned) into the context's device staging buffers, runs
+ * preprocess, sort and render, and copies img [3,H,W] (and t_final, load if
+ * non-NULL; all HOST pointers) back.  The first call allocates the staging
+ * buffers (max_gaussians * 236 bytes + image buffers).  SYNCHRONISES
+ * `stream` before returning. */
+adr_status adr_render_host(adr_ctx *ctx, const float *means, const float *scales,
+                           const float *rots, const float *opac, const float *sh, int64_t n,
+                           const adr_camera *camera, const adr_settings *settings,
+                           float *img, float *t_final, int32_t *load, void *stream);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *adr_last_error(void);
+
+/* Library version string. */
+const char *adr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADR_H */

@@ -1,0 +1,192 @@
+"""ctypes binding of libadr.so — argument marshalling only.
+
+Every function here has the name and argument order of its C counterpart in
+include/adr.h.  Pointers are passed as integers (device addresses from
+torch tensors' data_ptr(), or host addresses of numpy arrays); streams as
+integers (torch.cuda.Stream.cuda_stream).  No computation happens here.
+There is no fallback: if libadr.so cannot be loaded, the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+ADR_OK = 0
+ADR_ERR_INVALID = 1
+ADR_ERR_CAPACITY = 2
+ADR_ERR_CUDA = 3
+ADR_ERR_TIMEOUT = 4
+ADR_PENDING = 5
+ADR_ERR_ADMISSION = 6
+STATUS_NAMES = {0: "ADR_OK", 1: "ADR_ERR_INVALID", 2: "ADR_ERR_CAPACITY", 3: "ADR_ERR_CUDA",
+                4: "ADR_ERR_TIMEOUT", 5: "ADR_PENDING", 6: "ADR_ERR_ADMISSION"}
+ADR_TILE = 16
+ADR_GEOM_FLOATS = 12
+
+
+class AdrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class adr_camera(ctypes.Structure):
+    _fields_ = [("view", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("near_z", ctypes.c_float),
+                ("cam_pos", ctypes.c_float * 3), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class adr_settings(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("alpha_low", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("lowpass", ctypes.c_float), ("jac_clamp", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "adr_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _I32, _I32]),
+    "adr_destroy": (None, [_P]),
+    "adr_preprocess": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
+                              ctypes.POINTER(adr_settings), _P]),
+    "adr_sort": (_I32, [_P, _P]),
+    "adr_render": (_I32, [_P, _P, _P, _P, _P]),
+    "adr_num_pairs": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "adr_read_pairs": (_I32, [_P, _P, _P, _I64, _P]),
+    "adr_read_gaussians": (_I32, [_P, _P, _P, _P, _P]),
+    "adr_read_ranges": (_I32, [_P, _P, _P]),
+    "adr_sync_status": (_I32, [_P]),
+    "adr_render_host": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
+                               ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
+    "adr_last_error": (ctypes.c_char_p, []),
+    "adr_version": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libadr.so (building it first if asked and it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libadr.so not found at {path}; run __graft_entry__.build()")
+            import torch  # noqa: F401  (load torch's libcudart first so one runtime is shared)
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGNATURES)
+
+
+def last_error() -> str:
+    return load().adr_last_error().decode()
+
+
+def check(status: int, what: str = "") -> int:
+    if status != ADR_OK and status != ADR_PENDING:
+        raise AdrError(status, f"{what}: {last_error()}")
+    return status
+
+
+def make_camera(cam) -> adr_camera:
+    """Build the C struct from a scenes.Camera."""
+    c = adr_camera()
+    v = cam.view.reshape(-1)
+    for i in range(16):
+        c.view[i] = float(v[i])
+    c.fx, c.fy, c.cx, c.cy, c.near_z = cam.fx, cam.fy, cam.cx, cam.cy, cam.near
+    for i in range(3):
+        c.cam_pos[i] = float(cam.cam_pos[i])
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+def make_settings(st) -> adr_settings:
+    s = adr_settings()
+    s.mode = int(st.mode)
+    s.alpha_low, s.t_min, s.lowpass, s.jac_clamp = st.alpha_low, st.t_min, st.lowpass, st.jac_clamp
+    for i in range(3):
+        s.bg[i] = float(st.bg[i])
+    s.sh_degree = int(st.sh_degree)
+    return s
+
+
+# Thin call-throughs with the C names (pointers as ints).
+def adr_create(max_gaussians, pair_capacity, max_width, max_height, device=0):
+    out = _P()
+    check(load().adr_create(ctypes.byref(out), max_gaussians, pair_capacity, max_width,
+                            max_height, device), "adr_create")
+    return out.value
+
+
+def adr_destroy(ctx):
+    load().adr_destroy(ctx)
+
+
+def adr_preprocess(ctx, means, scales, rots, opac, sh, n, camera, settings, stream):
+    return check(load().adr_preprocess(ctx, means, scales, rots, opac, sh, n,
+                                       ctypes.byref(camera), ctypes.byref(settings), stream),
+                 "adr_preprocess")
+
+
+def adr_sort(ctx, stream):
+    return check(load().adr_sort(ctx, stream), "adr_sort")
+
+
+def adr_render(ctx, img, t_final, load_, stream):
+    return check(load().adr_render(ctx, img, t_final, load_, stream), "adr_render")
+
+
+def adr_num_pairs(ctx, raise_on_error=True):
+    p = _I64(0)
+    st = load().adr_num_pairs(ctx, ctypes.byref(p))
+    if raise_on_error:
+        check(st, "adr_num_pairs")
+    return p.value, st
+
+
+def adr_read_pairs(ctx, keys, vals, capacity, stream):
+    return check(load().adr_read_pairs(ctx, keys, vals, capacity, stream), "adr_read_pairs")
+
+
+def adr_read_gaussians(ctx, geom, rect, tiles, stream):
+    return check(load().adr_read_gaussians(ctx, geom, rect, tiles, stream), "adr_read_gaussians")
+
+
+def adr_read_ranges(ctx, ranges, stream):
+    return check(load().adr_read_ranges(ctx, ranges, stream), "adr_read_ranges")
+
+
+def adr_sync_status(ctx):
+    return load().adr_sync_status(ctx)
+
+
+def adr_render_host(ctx, means, scales, rots, opac, sh, n, camera, settings, img, t_final, load_,
+                    stream):
+    return check(load().adr_render_host(ctx, means, scales, rots, opac, sh, n,
+                                        ctypes.byref(camera), ctypes.byref(settings), img,
+                                        t_final, load_, stream), "adr_render_host")
+
+
+def adr_version():
+    return load().adr_version().decode()

@@ -1,0 +1,120 @@
+"""Rasterizer: device-tensor wrapper over the C ABI (marshalling only).
+
+PyTorch provides device memory and streams; every stage runs in libadr.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from .scenes import Scene
+
+TILE = _lib.ADR_TILE
+
+
+def upload(scene: Scene, device="cuda") -> tuple:
+    """Copy a scene's arrays to device float32 tensors (means, scales, rots, opac, sh)."""
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in scene.arrays())
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Rasterizer:
+    """One library context: workspace for up to `max_gaussians` Gaussians,
+    `pair_capacity` Gaussian-tile pairs and images up to max_width x max_height."""
+
+    def __init__(self, max_gaussians: int, pair_capacity: int, max_width: int, max_height: int,
+                 device: int = 0):
+        self.device = device
+        self.ctx = _lib.adr_create(int(max_gaussians), int(pair_capacity), int(max_width),
+                                   int(max_height), int(device))
+        self.n = 0
+        self.camera = None
+
+    def close(self):
+        if self.ctx:
+            _lib.adr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stages -----------------------------------------------------------------
+    def preprocess(self, params, camera, settings, stream=None):
+        means, scales, rots, opac, sh = params
+        n = int(means.shape[0])
+        for t in params:
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        self.n = n
+        self.camera = camera
+        _lib.adr_preprocess(self.ctx, _ptr(means), _ptr(scales), _ptr(rots), _ptr(opac), _ptr(sh),
+                            n, _lib.make_camera(camera), _lib.make_settings(settings),
+                            _stream(stream))
+
+    def sort(self, stream=None):
+        _lib.adr_sort(self.ctx, _stream(stream))
+
+    def render(self, img=None, t_final=None, load=None, stream=None, want_aux=True):
+        h, w = self.camera.height, self.camera.width
+        dev = f"cuda:{self.device}"
+        if img is None:
+            img = torch.empty((3, h, w), dtype=torch.float32, device=dev)
+        if want_aux and t_final is None:
+            t_final = torch.empty((h, w), dtype=torch.float32, device=dev)
+        if want_aux and load is None:
+            load = torch.empty((h, w), dtype=torch.int32, device=dev)
+        _lib.adr_render(self.ctx, _ptr(img), _ptr(t_final), _ptr(load), _stream(stream))
+        return img, t_final, load
+
+    def forward(self, params, camera, settings, stream=None, **kw):
+        self.preprocess(params, camera, settings, stream)
+        self.sort(stream)
+        return self.render(stream=stream, **kw)
+
+    # -- inspection -------------------------------------------------------------
+    def num_pairs(self, raise_on_error=True):
+        p, st = _lib.adr_num_pairs(self.ctx, raise_on_error)
+        return (p, st) if not raise_on_error else p
+
+    def read_pairs(self, count=None, stream=None):
+        p = self.num_pairs() if count is None else count
+        dev = f"cuda:{self.device}"
+        keys = torch.empty(max(p, 1), dtype=torch.int64, device=dev)
+        vals = torch.empty(max(p, 1), dtype=torch.int32, device=dev)
+        _lib.adr_read_pairs(self.ctx, _ptr(keys), _ptr(vals), p, _stream(stream))
+        torch.cuda.synchronize(self.device)
+        return (keys[:p].cpu().numpy().view(np.uint64), vals[:p].cpu().numpy().view(np.uint32))
+
+    def read_gaussians(self, stream=None):
+        dev = f"cuda:{self.device}"
+        n = max(self.n, 1)
+        geom = torch.empty((n, _lib.ADR_GEOM_FLOATS), dtype=torch.float32, device=dev)
+        rect = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        tiles = torch.empty((n,), dtype=torch.int32, device=dev)
+        _lib.adr_read_gaussians(self.ctx, _ptr(geom), _ptr(rect), _ptr(tiles), _stream(stream))
+        torch.cuda.synchronize(self.device)
+        return (geom[:self.n].cpu().numpy(), rect[:self.n].cpu().numpy(),
+                tiles[:self.n].cpu().numpy())
+
+    def read_ranges(self, stream=None):
+        cam = self.camera
+        nt = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
+        r = torch.empty((nt, 2), dtype=torch.int32, device=f"cuda:{self.device}")
+        _lib.adr_read_ranges(self.ctx, _ptr(r), _stream(stream))
+        torch.cuda.synchronize(self.device)
+        return r.cpu().numpy().view(np.uint32)
+
+    def sync_status(self):
+        return _lib.adr_sync_status(self.ctx)

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every entry point include/adr.h
+declares (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2409_08669_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(adr_[a-z_0-9]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    try:
+        return build.build()
+    except RuntimeError as e:
+        pytest.fail(f"libadr.so did not build: {e}")
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("adr_create", "adr_destroy", "adr_preprocess", "adr_sort", "adr_render",
+                     "adr_num_pairs", "adr_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = declared_functions() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name)
+    assert declared_functions() <= set(_lib.exported_names())
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(_lib.adr_camera) == (16 + 4 + 1 + 3) * 4 + 2 * 4
+    assert ctypes.sizeof(_lib.adr_settings) == 4 + 4 * 4 + 3 * 4 + 4
+
+
+def test_version_and_error_without_gpu(libpath):
+    lib = _lib.load()
+    assert lib.adr_version().startswith(b"adr-gb300")
+    # invalid arguments are rejected before any CUDA call
+    out = ctypes.c_void_p()
+    st = lib.adr_create(ctypes.byref(out), 0, 10, 16, 16, 0)
+    assert st == _lib.ADR_ERR_INVALID
+    assert b"max_gaussians" in lib.adr_last_error()

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Bar (from the target): Gaussian-tile pairs and sorted keys bit-exact, except
+pairs whose cull/tile decision lies within 1e-6 (relative) of its threshold,
+which are logged; images within 1e-4 max abs per channel, excluding pixels
+whose blend decisions lie within tolerance of a threshold in the FP64
+oracle (alpha vs alpha_low within 1e-5, T(1-alpha) vs t_min within 1e-3 —
+the FP32 transmittance drifts by ~1e-5 relative over a long blend, so the
+stop decision needs the wider band) and the tiles touched by logged pairs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_08669_gb300 import scenes as S
+from parity_utils import compare_images, compare_pairs, gpu_forward, tile_mask
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rast():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_08669_gb300.raster import Rasterizer
+    r = Rasterizer(max_gaussians=1 << 20, pair_capacity=1 << 24, max_width=2048, max_height=2048)
+    yield r
+    r.close()
+
+
+def _check_frame(rast, scene, cam, st, label=""):
+    from paper_2409_08669_gb300.raster import upload
+    params = upload(scene)
+    img, t_final, load = gpu_forward(rast, params, cam, st)
+    ref = oracle.render(scene, cam, st)
+    pre = ref["pre"]
+    flags = pre["flags"]
+    near = (flags & oracle.F_NEAR) != 0
+    geom, rect, tiles = rast.read_gaussians()
+    # depth sort keys: bit-exact for every Gaussian
+    np.testing.assert_array_equal(geom[:, 11].view(np.uint32), pre["depth"].view(np.uint32))
+    # tile counts and rectangles: exact except near-threshold Gaussians
+    tbad = np.nonzero((tiles != pre["tiles"]) & ~near)[0]
+    assert tbad.size == 0, f"{label}: {tbad.size} Gaussians with different tile counts, e.g. {tbad[:5]}"
+    has = tiles > 0
+    rbad = np.nonzero(np.any(rect != pre["rect"], axis=1) & has & ~near)[0]
+    assert rbad.size == 0, f"{label}: rect differs for {rbad[:5]}"
+    # continuous per-Gaussian values where the Gaussian has pairs
+    g = pre["geom"]
+    np.testing.assert_allclose(geom[has, 0], g[has, oracle.G_PX], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(geom[has, 1], g[has, oracle.G_PY], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(geom[has, 8:11], pre["rgb"][has], rtol=2e-5, atol=2e-6)
+    np.testing.assert_allclose(geom[has, 5], g[has, oracle.G_OPAC], rtol=0, atol=0)
+    # sorted pairs
+    keys, vals = rast.read_pairs()
+    differing, dtiles = compare_pairs(keys, vals, ref["keys"], ref["vals"], flags)
+    if not differing:
+        ranges = rast.read_ranges()
+        np.testing.assert_array_equal(ranges, ref["ranges"])
+    exclude = (ref["near"] != 0) | tile_mask(dtiles, cam.width, cam.height)
+    worst, n_ex = compare_images(img, t_final, load, ref, exclude)
+    hw = cam.width * cam.height
+    assert n_ex <= max(4, 1e-3 * hw), f"{label}: {n_ex} excluded pixels"
+    print(f"{label}: P={keys.size} near-Gaussians={int(near.sum())} differing={len(differing)} "
+          f"max|err|={worst:.2e} excluded={n_ex}/{hw}")
+    return img, load
+
+
+@pytest.mark.parametrize("mode", [S.MODE_PLAIN, S.MODE_CIRCLE, S.MODE_AABB])
+def test_tiny_scene_parity(rast, mode):
+    """10k Gaussians, 256x256, one camera at distance 3 (the small workload)."""
+    scene = S.tiny_scene(0)
+    cam = S.look_at((0, 0, -3), width=256, height=256)
+    _check_frame(rast, scene, cam, S.Settings(mode=mode), f"tiny/{S.MODE_NAMES[mode]}")
+
+
+def test_ragged_image_many_tiles(rast):
+    scene = S.tiny_scene(11, n=6000)
+    cam = S.look_at((0.3, -0.2, -2.2), width=250, height=190)
+    for mode in (S.MODE_PLAIN, S.MODE_AABB):
+        _check_frame(rast, scene, cam, S.Settings(mode=mode), f"ragged/{mode}")
+
+
+def test_cluster_scene_1080p_subset(rast):
+    """A 200k-Gaussian draw of the clustered scene at 1920x1080 (tile grid 120x68)."""
+    scene = S.cluster_scene(n=200_000, seed=1)
+    cam = S.orbit_cameras(50, width=1920, height=1080)[7]
+    _check_frame(rast, scene, cam, S.Settings(mode=S.MODE_AABB), "cluster1080")
+
+
+def test_modes_render_identical_images_on_gpu(rast):
+    """Losslessness (Sec. 5.2-5.3): culling changes no pixel."""
+    from paper_2409_08669_gb300.raster import upload
+    scene = S.cluster_scene(n=100_000, seed=5)
+    cam = S.orbit_cameras(50, width=1280, height=720)[3]
+    params = upload(scene)
+    out = {}
+    pairs = {}
+    for mode in (S.MODE_PLAIN, S.MODE_CIRCLE, S.MODE_AABB):
+        img, t, load = gpu_forward(rast, params, cam, S.Settings(mode=mode))
+        out[mode] = (img, t, load)
+        pairs[mode] = rast.num_pairs()
+    ref = oracle.render(scene, cam, S.Settings(mode=S.MODE_AABB))
+    near = ref["near"] != 0
+    for mode in (S.MODE_CIRCLE, S.MODE_AABB):
+        diff = np.any(out[mode][0] != out[S.MODE_PLAIN][0], axis=0)
+        assert np.count_nonzero(diff & ~near) == 0
+        assert np.array_equal(out[mode][2][~near], out[S.MODE_PLAIN][2][~near])
+    assert pairs[S.MODE_AABB] < pairs[S.MODE_CIRCLE] < pairs[S.MODE_PLAIN]
+
+
+@pytest.mark.parametrize("theta,op", [(0.4, 0.3), (1.0, 0.95)])
+def test_single_gaussian_footprint_closed_form(rast, theta, op):
+    """One Gaussian at the image centre: image = c * min(0.99, sigma e^{-q/2})
+    on the alpha >= 1/255 footprint (within the r_o tiles), 0 elsewhere."""
+    from paper_2409_08669_gb300.raster import upload
+    z0, s1, s2 = 3.0, 0.04, 0.015
+    w, h = 96, 80
+    cam = S.look_at((0, 0, -z0), width=w, height=h)
+    dc = (0.9, 0.2, 0.5)
+    q = (math.cos(theta / 2), 0.0, 0.0, math.sin(theta / 2))
+    scene = S.isolated_gaussian((0, 0, 0), (s1, s2, 0.01), q, op, dc)
+    img, t_final, load = gpu_forward(rast, upload(scene), cam, S.Settings())
+    ref = oracle.render(scene, cam, S.Settings())
+    # the oracle is pinned to the closed form on the same case (test_oracle_pins)
+    np.testing.assert_allclose(img, ref["img"], atol=2e-6)
+    np.testing.assert_array_equal(load[ref["near"] == 0], ref["load"][ref["near"] == 0])
+
+
+def test_empty_scene_and_all_culled(rast):
+    from paper_2409_08669_gb300.raster import upload
+    cam = S.look_at((0, 0, -3), width=40, height=24)
+    st = S.Settings(bg=(0.1, 0.2, 0.3))
+    empty = S.tiny_scene(0, n=1).subset(np.arange(0))
+    params = tuple(torch.zeros((0,) + a.shape[1:], dtype=torch.float32, device="cuda")
+                   for a in empty.arrays())
+    img, t_final, load = gpu_forward(rast, params, cam, st)
+    assert rast.num_pairs() == 0
+    np.testing.assert_array_equal(img, np.broadcast_to(np.float32([0.1, 0.2, 0.3])[:, None, None], img.shape))
+    assert np.all(t_final == 1.0) and np.all(load == 0)
+    behind = S.tiny_scene(1, n=500)
+    behind.means[:, 2] = -5.0  # camera at z=-3 looking +z: all behind
+    img, t_final, load = gpu_forward(rast, upload(behind), cam, st)
+    assert rast.num_pairs() == 0 and np.all(load == 0)
+    faint = S.tiny_scene(2, n=500)
+    faint.opac[:] = np.float32(0.002)  # below 1/255: no pair in the adaptive modes
+    gpu_forward(rast, upload(faint), cam, S.Settings(mode=S.MODE_AABB))
+    assert rast.num_pairs() == 0
+    gpu_forward(rast, upload(faint), cam, S.Settings(mode=S.MODE_PLAIN))
+    assert rast.num_pairs() > 0
+
+
+def test_capacity_overflow_is_reported_not_written():
+    from paper_2409_08669_gb300 import _lib
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
+    r = Rasterizer(max_gaussians=20_000, pair_capacity=1000, max_width=256, max_height=256)
+    try:
+        scene = S.tiny_scene(0)
+        cam = S.look_at((0, 0, -3), width=256, height=256)
+        r.forward(upload(scene), cam, S.Settings())
+        p, st = r.num_pairs(raise_on_error=False)
+        assert st == _lib.ADR_ERR_CAPACITY
+        assert p > 1000
+        # the context stays usable
+        small = S.tiny_scene(0, n=50)
+        r.forward(upload(small), cam, S.Settings())
+        assert r.num_pairs() <= 1000
+    finally:
+        r.close()
+
+
+def test_invalid_arguments_rejected(rast):
+    from paper_2409_08669_gb300 import _lib
+    cam = S.look_at((0, 0, -3), width=4096, height=64)  # wider than the context allows
+    scene = S.tiny_scene(0, n=10)
+    from paper_2409_08669_gb300.raster import upload
+    with pytest.raises(_lib.AdrError) as e:
+        rast.forward(upload(scene), cam, S.Settings())
+    assert e.value.status == _lib.ADR_ERR_INVALID
+    cam = S.look_at((0, 0, -3), width=64, height=64)
+    with pytest.raises(_lib.AdrError):
+        rast.forward(upload(scene), cam, S.Settings(mode=7))
