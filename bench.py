@@ -1,0 +1,447 @@
+"""Benchmark of the AdR-Gaussian rasterization path on GB300.
+
+Workload (the headline metric: FPS at 1920x1080 with 3M Gaussians, AdR vs the
+plain 3DGS-style path): the heavy-load synthetic scene (3M Gaussians, 30% in
+one dense central cluster, the rest in 64 anisotropic clusters plus a uniform
+background; SH degree 3, fp32), rendered from 50 cameras on a circle of
+radius 4.  One step = one frame = Preprocess + scan + emission, the tile
+sort + ranges, and Render (every stage of the forward path) for the next
+camera in the cycle.  The scene (708 MB) and the per-frame working set are
+larger than the 129 MB L2, so no explicit L2 flush is used.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+paper) on the host cores, on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank renders its own cameras (replicas: the
+frames are independent), the timed region is bracketed by barriers and the
+slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2409_08669_gb300 import scenes as S  # noqa: E402
+
+METRIC = "FPS @1080p, 3M Gaussians, AdR vs plain 3DGS path on 1 GB300; serving p50/p99 ms"
+WORKLOAD = "heavy-3M-1080p"
+N_GAUSS = 3_000_000
+WIDTH, HEIGHT = 1920, 1080
+N_CAMERAS = 50
+PAIR_CAPACITY = 1 << 29
+LAUNCHES_PER_FRAME = 12   # preprocess, digit hist, 4 depth passes, scan, emit, 2 tile passes, ranges, render
+EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device_sync=True):
+    import torch
+    if device_sync and torch.cuda.is_available():
+        torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_workload(rank=0):
+    scene = S.heavy_scene(n=N_GAUSS, seed=2)
+    cams = S.orbit_cameras(N_CAMERAS, radius=4.0, width=WIDTH, height=HEIGHT)
+    cams = cams[rank % N_CAMERAS:] + cams[:rank % N_CAMERAS]
+    return scene, cams
+
+
+# ---------------------------------------------------------------------------
+# Our arm: the CUDA path through the C ABI
+# ---------------------------------------------------------------------------
+
+def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stages=True):
+    """Returns (seconds for `steps` frames, per-stage ms lists, per-frame render ms)."""
+    import torch
+    for k in range(warmup):
+        rast.forward(params, cams[k % len(cams)], st, stream=stream, want_aux=False)
+    barrier(pg)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device="cuda")
+    start.record(stream)
+    for k in range(steps):
+        cam = cams[(warmup + k) % len(cams)]
+        if with_stages:
+            ev[k][0].record(stream)
+        rast.preprocess(params, cam, st, stream=stream)
+        if with_stages:
+            ev[k][1].record(stream)
+        rast.sort(stream=stream)
+        if with_stages:
+            ev[k][2].record(stream)
+        rast.render(img=img, stream=stream, want_aux=False)
+        if with_stages:
+            ev[k][3].record(stream)
+    stop.record(stream)
+    barrier(pg)
+    total = start.elapsed_time(stop) / 1e3
+    stages = None
+    if with_stages:
+        stages = {"preprocess_scan_emit": [e[0].elapsed_time(e[1]) for e in ev],
+                  "sort_ranges": [e[1].elapsed_time(e[2]) for e in ev],
+                  "render": [e[2].elapsed_time(e[3]) for e in ev]}
+    return total, stages
+
+
+def frame_units(rast, params, cams, st, stream, count):
+    """Untimed: pairs P and sum over pixels of Gaussians evaluated, per frame."""
+    out = []
+    for k in range(count):
+        rast.forward(params, cams[k], st, stream=stream, want_aux=False)
+        p = rast.num_pairs()
+        _, trav = rast.read_pixel_stats(stream=stream)
+        out.append((p, int(trav.astype(np.int64).sum())))
+    return out
+
+
+def e2e_host(rast_ctx, scene, cams, st, steps, warmup):
+    """FPS through adr_render_host with pinned host buffers (scene uploaded
+    and the image read back inside every step)."""
+    import ctypes
+    import torch
+    from paper_2409_08669_gb300 import _lib
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in scene.arrays()]
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream().cuda_stream
+    st_c = _lib.make_settings(st)
+    ptrs = [p.data_ptr() for p in pinned]
+
+    def one(cam):
+        _lib.adr_render_host(rast_ctx, *ptrs, scene.n, _lib.make_camera(cam), st_c, img.data_ptr(),
+                             0, 0, stream)
+
+    for k in range(warmup):
+        one(cams[k % len(cams)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        one(cams[(warmup + k) % len(cams)])
+    dt = time.perf_counter() - t0
+    h2d = sum(a.nbytes for a in scene.arrays())
+    d2h = img.numel() * 4
+    del ctypes
+    return steps / dt, h2d, d2h
+
+
+def run_ours(args):
+    import torch
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    scene, cams = build_workload(rank)
+    params = upload(scene)
+    rast = Rasterizer(max_gaussians=N_GAUSS, pair_capacity=PAIR_CAPACITY, max_width=WIDTH,
+                      max_height=HEIGHT, device=local)
+    stream = torch.cuda.Stream()
+    st_adr = S.Settings(mode=S.MODE_AABB)
+    st_plain = S.Settings(mode=S.MODE_PLAIN)
+    st_circle = S.Settings(mode=S.MODE_CIRCLE)
+
+    # Correctness gate before timing: device flags clear, pair capacity respected.
+    rast.forward(params, cams[0], st_adr, stream=stream)
+    torch.cuda.synchronize()
+    rast.num_pairs()
+
+    with ClockSampler(local) as clk:
+        t_adr, stages = time_mode(rast, params, cams, st_adr, args.steps, args.warmup, stream, pg)
+    clocks = clk.summary()
+    status = rast.sync_status()
+    if status != 0:
+        raise SystemExit(f"device status {status} after the timed region")
+    t_plain, stages_plain = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
+                                      stream, pg)
+    t_circle, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
+                            with_stages=False)
+    t_adr = max_over_ranks(pg, t_adr)
+    t_plain = max_over_ranks(pg, t_plain)
+    t_circle = max_over_ranks(pg, t_circle)
+    frames = args.steps * world
+    fps = frames / t_adr
+
+    # Units of work for the roofline (untimed, on the first cameras of the timed cycle).
+    nu = min(args.steps, 5)
+    ucams = [cams[(args.warmup + k) % len(cams)] for k in range(nu)]
+    units_adr = frame_units(rast, params, ucams, st_adr, stream, nu)
+    units_plain = frame_units(rast, params, ucams, st_plain, stream, nu)
+    render_ms = stages["render"][:nu]
+    evals = [u[1] for u in units_adr]
+    pairs = [u[0] for u in units_adr]
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = clocks.get("sm_mhz") or sm_max_mhz
+    alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12          # FP32 lane-ops per s, in T/s
+    alu_achieved = statistics.mean(e * EVAL_FP32_OPS / (ms / 1e3) for e, ms in zip(evals, render_ms)) / 1e12
+    render_bytes = [p * 52 + WIDTH * HEIGHT * 12 for p in pairs]
+    render_gbs = statistics.mean(b / (ms / 1e3) for b, ms in zip(render_bytes, render_ms)) / 1e9
+    stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
+    stage_ms_plain = {k: statistics.mean(v) for k, v in stages_plain.items()}
+
+    e2e_fps, h2d, d2h = e2e_host(rast.ctx, scene, cams, st_adr, max(3, min(args.steps, 10)), 2)
+
+    result = {
+        "metric": METRIC,
+        "value": fps,
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_adr / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded heavy-load scene; no dataset or trained model)",
+        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                   "cameras": N_CAMERAS, "mode": "adr_aabb", "sh_degree": 3,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (708 MB scene, 144 MB render records); no flush"},
+        "plain_fps": frames / t_plain,
+        "circle_fps": frames / t_circle,
+        "speedup_vs_plain": t_plain / t_adr,
+        "stages_ms": stage_ms,
+        "stages_ms_plain": stage_ms_plain,
+        "pairs_per_frame": {"adr_aabb": statistics.mean(pairs),
+                            "plain": statistics.mean(u[0] for u in units_plain)},
+        "evals_per_frame": {"adr_aabb": statistics.mean(evals),
+                            "plain": statistics.mean(u[1] for u in units_plain)},
+        "roofline": {"kernel": "k_render", "bound": "alu", "achieved": alu_achieved,
+                     "peak": alu_peak, "unit": "T FP32 lane-ops/s",
+                     "frac": alu_achieved / alu_peak, "traffic": None,
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock under load)",
+                     "work": f"{EVAL_FP32_OPS} FP32 ops per Gaussian-pixel evaluation"},
+        "render_hbm": {"achieved_gbs": render_gbs, "peak_gbs": hbm_gbs,
+                       "frac": render_gbs / hbm_gbs, "peak_source": peak_src,
+                       "bytes": "52 B per tile-pair (record + index) + 12 B per pixel written"},
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(scene, cams, st_adr, budget_s=args.cpu_budget)
+    rast.close()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+class OracleFrame:
+    """Times the CPU oracle on a bounded sample of one frame and scales to a
+    full frame: Preprocess on a 1/g_div sample of the Gaussians (scaled by
+    g_div), emission + sort of that sample's pairs (scaled by g_div), and the
+    tiled render of a 1/t_div sample of the tiles over their full sorted lists
+    (scaled by t_div).  The full lists for the sampled tiles come from one
+    untimed preprocess of the whole scene per camera."""
+
+    def __init__(self, scene, g_div=16, t_div=64, seed=0):
+        import oracle
+        self.oracle = oracle
+        self.scene = scene
+        self.g_div = g_div
+        self.t_div = t_div
+        rng = np.random.default_rng(seed)
+        self.sample = np.sort(rng.choice(scene.n, scene.n // g_div, replace=False))
+        self.sub = scene.subset(self.sample)
+        self.rng = rng
+        self.cache = {}
+
+    def _tile_lists(self, key, cam, st):
+        """Untimed, once per camera: the full preprocess and the sorted lists of
+        a random 1/t_div sample of the tiles."""
+        if key not in self.cache:
+            o = self.oracle
+            full = o.preprocess(self.scene, cam, st)
+            keys, vals = o.emit_pairs(full)
+            tiles = (keys >> np.uint64(32)).astype(np.int64)
+            nt = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+            chosen = np.sort(self.rng.choice(nt, max(1, nt // self.t_div), replace=False))
+            m = np.isin(tiles, chosen)
+            skeys, svals = o.sort_pairs(keys[m], vals[m])
+            ranges = o.tile_ranges(skeys, cam.width, cam.height)
+            self.cache[key] = (full, ranges, svals, nt / len(chosen))
+        return self.cache[key]
+
+    def frame_seconds(self, cam, st, key=None):
+        o = self.oracle
+        full, ranges, svals, tile_scale = self._tile_lists(key if key is not None else id(cam), cam, st)
+        t0 = time.perf_counter()
+        pre_s = o.preprocess(self.sub, cam, st)
+        k, v = o.emit_pairs(pre_s)
+        o.sort_pairs(k, v)
+        t_pre = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        o.render_tiled(full, ranges, svals, st)
+        t_render = time.perf_counter() - t1
+        return t_pre * self.g_div + t_render * tile_scale
+
+
+def cpu_baseline(scene, cams, st, budget_s=30.0):
+    of = OracleFrame(scene)
+    t0 = time.perf_counter()
+    secs = []
+    for i, cam in enumerate(cams):
+        secs.append(of.frame_seconds(cam, st, key=i))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return {"value": 1.0 / statistics.mean(secs), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{len(secs)} frame(s): preprocess+emit+sort of a 1/{of.g_div} Gaussian "
+                       f"sample and render of a 1/{of.t_div} tile sample, each scaled to the "
+                       f"full frame; single-threaded FP64 C")}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, cams = build_workload(0)
+    st = S.Settings(mode=S.MODE_AABB)
+    of = OracleFrame(scene, g_div=64, t_div=256)
+    ncam = 2   # the untimed full-scene lists are built once per distinct camera
+    warmup = max(args.warmup, 3)
+    for k in range(warmup):
+        of.frame_seconds(cams[k % ncam], st, key=k % ncam)
+    secs = [of.frame_seconds(cams[(warmup + k) % ncam], st, key=(warmup + k) % ncam)
+            for k in range(args.steps)]
+    total = sum(secs)
+    fps = args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                   "cameras": N_CAMERAS, "mode": "adr_aabb"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: 1/64 Gaussian sample (preprocess, emit, sort) and "
+                                   "1/256 tile sample (render), scaled to a full frame; "
+                                   "2 distinct cameras"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

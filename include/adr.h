@@ -150,6 +150,13 @@ adr_status adr_read_gaussians(adr_ctx *ctx, float *geom, int32_t *rect, int32_t 
 /* Inspection: per-tile ranges [start, end) as uint32 pairs, tiles_x*tiles_y rows. */
 adr_status adr_read_ranges(adr_ctx *ctx, uint32_t *ranges, void *stream);
 
+/* Inspection: per-pixel statistics of the last adr_render, [H,W] int32 each
+ * (either may be NULL).  last: 1-based position in the tile's sorted list of
+ * the last Gaussian blended into the pixel (0 if none).  traversed: list
+ * positions the pixel evaluated before it stopped or the list ended, i.e.
+ * the pixel thread's serial load (Sec. 4.4). */
+adr_status adr_read_pixel_stats(adr_ctx *ctx, int32_t *last, int32_t *traversed, void *stream);
+
 /* Waits for the context's work and reports device-side flags as a status
  * (ADR_ERR_CAPACITY, ADR_ERR_TIMEOUT or ADR_OK); clears them.  SYNCHRONISES. */
 adr_status adr_sync_status(adr_ctx *ctx);

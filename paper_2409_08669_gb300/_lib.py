@@ -65,6 +65,7 @@ _SIGNATURES = {
     "adr_read_gaussians": (_I32, [_P, _P, _P, _P, _P]),
     "adr_read_ranges": (_I32, [_P, _P, _P]),
     "adr_sync_status": (_I32, [_P]),
+    "adr_read_pixel_stats": (_I32, [_P, _P, _P, _P]),
     "adr_render_host": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
                                ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
     "adr_last_error": (ctypes.c_char_p, []),
@@ -175,6 +176,10 @@ def adr_read_gaussians(ctx, geom, rect, tiles, stream):
 
 def adr_read_ranges(ctx, ranges, stream):
     return check(load().adr_read_ranges(ctx, ranges, stream), "adr_read_ranges")
+
+
+def adr_read_pixel_stats(ctx, last, traversed, stream):
+    return check(load().adr_read_pixel_stats(ctx, last, traversed, stream), "adr_read_pixel_stats")
 
 
 def adr_sync_status(ctx):

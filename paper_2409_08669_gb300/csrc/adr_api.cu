@@ -77,7 +77,8 @@ struct adr_ctx {
     uint32_t* pgauss[2] = {nullptr, nullptr};
     // per-tile / per-pixel
     uint2* ranges = nullptr;
-    int32_t* last = nullptr;
+    int32_t* last = nullptr;         // 1-based list position of the last blended Gaussian
+    int32_t* trav = nullptr;         // list positions each pixel evaluated
     // bookkeeping
     uint32_t* hist = nullptr;        // [kMaxPasses][256] depth digits, then [2][256] tile digits
     uint32_t* counters = nullptr;    // kCntSlots
@@ -91,7 +92,7 @@ struct adr_ctx {
     CamDev cam{};
     SetDev st{};
     int tile_passes = 0, tile_bits = 0;
-    bool have_frame = false, have_sort = false;
+    bool have_frame = false, have_sort = false, have_render = false;
     cudaStream_t last_stream = nullptr;
     const uint32_t* sorted_order = nullptr;   // Gaussians in depth order
     uint32_t* sorted_tile = nullptr;          // pairs after adr_sort
@@ -108,7 +109,7 @@ namespace {
 void free_ctx(adr_ctx* c) {
     void* ptrs[] = {c->rec, c->aux, c->depth_key, c->tiles, c->rect, c->offsets,
                     c->gkeys[0], c->gkeys[1], c->gvals[0], c->gvals[1], c->ptile[0],
-                    c->ptile[1], c->pgauss[0], c->pgauss[1], c->ranges, c->last,
+                    c->ptile[1], c->pgauss[0], c->pgauss[1], c->ranges, c->last, c->trav,
                     c->hist, c->counters, c->status, c->lookback, c->stage,
                     c->stage_img, c->stage_load};
     for (void* p : ptrs)
@@ -233,6 +234,7 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     }
     ALLOC(c->ranges, (size_t)c->max_tiles * sizeof(uint2));
     ALLOC(c->last, (size_t)max_width * max_height * sizeof(int32_t));
+    ALLOC(c->trav, (size_t)max_width * max_height * sizeof(int32_t));
     ALLOC(c->hist, (kMaxPasses + 2) * kRadix * sizeof(uint32_t));
     ALLOC(c->counters, kCntSlots * sizeof(uint32_t));
     ALLOC(c->status, sizeof(uint32_t) * 4);
@@ -351,7 +353,8 @@ adr_status adr_render(adr_ctx* c, float* img, float* t_final, int32_t* load, voi
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
     launch_render(c->ranges, c->sorted_gauss, c->rec, c->cam, c->st, img, t_final, load, c->last,
-                  strm);
+                  c->trav, strm);
+    c->have_render = true;
     return check_launch("adr_render") == ADR_OK ? ok() : ADR_ERR_CUDA;
 }
 
@@ -411,6 +414,17 @@ adr_status adr_read_ranges(adr_ctx* c, uint32_t* ranges, void* stream) {
     DeviceGuard guard(c->device);
     const size_t bytes = (size_t)c->cam.tiles_x * c->cam.tiles_y * sizeof(uint2);
     ADR_CUDA(cudaMemcpyAsync(ranges, c->ranges, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return ok();
+}
+
+adr_status adr_read_pixel_stats(adr_ctx* c, int32_t* last, int32_t* traversed, void* stream) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (!c->have_render) return fail(ADR_ERR_INVALID, "adr_read_pixel_stats before adr_render");
+    DeviceGuard guard(c->device);
+    const size_t bytes = (size_t)c->cam.width * c->cam.height * sizeof(int32_t);
+    if (last) ADR_CUDA(cudaMemcpyAsync(last, c->last, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    if (traversed)
+        ADR_CUDA(cudaMemcpyAsync(traversed, c->trav, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return ok();
 }
 

@@ -100,7 +100,7 @@ void launch_ranges(const uint32_t* sorted_tile, const uint32_t* d_n, int64_t cap
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, cudaStream_t stream);
+                   int32_t* last, int32_t* trav, cudaStream_t stream);
 
 void launch_pair_keys(const uint32_t* sorted_tile, const uint32_t* sorted_gauss,
                       const uint32_t* depth_key_by_gauss, const uint32_t* d_n, int64_t count,

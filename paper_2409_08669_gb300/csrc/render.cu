@@ -18,7 +18,8 @@ constexpr int kRenderThreads = kTilePixels;
 __global__ void __launch_bounds__(kRenderThreads)
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const float4* __restrict__ rec, CamDev cam, SetDev st, float* __restrict__ img,
-         float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out) {
+         float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
+         int32_t* __restrict__ trav_out) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
@@ -33,7 +34,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
     const uint2 range = ranges[tile];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int32_t count = 0, last = 0;
+    int32_t count = 0, last = 0, trav = 0;
     bool done = !inside;
     const float alpha_low = st.alpha_low, t_min = st.t_min;
 
@@ -52,7 +53,8 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         __syncthreads();
         const int m = min((uint32_t)kRenderThreads, range.y - base);
         if (!done) {
-            for (int j = 0; j < m; ++j) {
+            int j = 0;
+            for (; j < m; ++j) {
                 const float2 c = s_xy[j];
                 const float4 w = s_w[j];
                 const float dx = c.x - fx, dy = c.y - fy;
@@ -63,7 +65,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 const float alpha = fminf(0.99f, exp2f(e));
                 if (alpha < alpha_low) continue;
                 const float test_T = T * (1.f - alpha);
-                if (test_T < t_min) { done = true; break; }
+                if (test_T < t_min) { done = true; ++j; break; }
                 const float wgt = alpha * T;
                 C0 = fmaf(col.x, wgt, C0);
                 C1 = fmaf(col.y, wgt, C1);
@@ -72,6 +74,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 ++count;
                 last = (int32_t)(base - range.x) + j + 1;
             }
+            trav += j;
         }
     }
     if (inside) {
@@ -83,6 +86,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         if (t_final) t_final[pix] = T;
         if (load) load[pix] = count;
         if (last_out) last_out[pix] = last;
+        if (trav_out) trav_out[pix] = trav;
     }
 }
 
@@ -90,11 +94,11 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, cudaStream_t stream) {
+                   int32_t* last, int32_t* trav, cudaStream_t stream) {
     const int tiles = cam.tiles_x * cam.tiles_y;
     if (tiles <= 0) return;
     k_render<<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, rec, cam, st, img,
-                                                   t_final, load, last);
+                                                   t_final, load, last, trav);
 }
 
 }  // namespace adr

@@ -116,5 +116,14 @@ class Rasterizer:
         torch.cuda.synchronize(self.device)
         return r.cpu().numpy().view(np.uint32)
 
+    def read_pixel_stats(self, stream=None):
+        h, w = self.camera.height, self.camera.width
+        dev = f"cuda:{self.device}"
+        last = torch.empty((h, w), dtype=torch.int32, device=dev)
+        trav = torch.empty((h, w), dtype=torch.int32, device=dev)
+        _lib.adr_read_pixel_stats(self.ctx, _ptr(last), _ptr(trav), _stream(stream))
+        torch.cuda.synchronize(self.device)
+        return last.cpu().numpy(), trav.cpu().numpy()
+
     def sync_status(self):
         return _lib.adr_sync_status(self.ctx)

@@ -59,19 +59,25 @@ def tile_mask(tiles, width, height):
     return m
 
 
-def compare_images(img, t_final, load, ref, exclude, atol=1e-4):
-    """Max abs error per channel within atol on every pixel not excluded.
-    Returns (max error, number of excluded pixels)."""
+def compare_images(img, t_final, load, ref, exclude, atol=1e-4, max_logged_frac=1e-4):
+    """Every pixel where the GPU and the oracle disagree (any channel or the
+    final transmittance off by more than atol, or a different load l_i) must
+    be an excluded (near-threshold) pixel, and the number of such logged
+    pixels must stay within max_logged_frac of the image.
+    Returns (max error over kept pixels, logged pixels, excluded pixels)."""
+    err = np.abs(img.astype(np.float64) - ref["img"]).max(axis=0)
+    terr = np.abs(t_final.astype(np.float64) - ref["t_final"])
+    mism = (err > atol) | (terr > atol) | (load != ref["load"])
+    bad = mism & ~exclude
+    if bad.any():
+        y, x = np.argwhere(bad)[0]
+        raise AssertionError(
+            f"{int(bad.sum())} non-excluded pixels differ; first ({x},{y}): gpu "
+            f"{img[:, y, x]} T={t_final[y, x]} l={load[y, x]} oracle {ref['img'][:, y, x]} "
+            f"T={ref['t_final'][y, x]} l={ref['load'][y, x]}")
+    logged = int(mism.sum())
+    hw = img.shape[1] * img.shape[2]
+    assert logged <= max(4, max_logged_frac * hw), f"{logged} near-threshold pixels differ"
     keep = ~exclude
-    err = np.abs(img.astype(np.float64) - ref["img"])
-    worst = float(err[:, keep].max()) if keep.any() else 0.0
-    if worst > atol:
-        c, y, x = np.unravel_index(np.argmax(np.where(keep[None], err, 0)), err.shape)
-        raise AssertionError(f"image error {worst:.3e} > {atol} at channel {c} pixel ({x},{y}): "
-                             f"gpu {img[c, y, x]!r} oracle {ref['img'][c, y, x]!r}")
-    terr = np.abs(t_final.astype(np.float64) - ref["t_final"])[keep]
-    assert terr.size == 0 or terr.max() <= atol, f"t_final error {terr.max():.3e}"
-    # the per-pixel load is an integer decision: exact except at excluded pixels
-    lbad = np.count_nonzero((load != ref["load"]) & keep)
-    assert lbad == 0, f"{lbad} pixels with a different load l_i"
-    return worst, int(exclude.sum())
+    worst = float(err[keep].max()) if keep.any() else 0.0
+    return worst, logged, int(exclude.sum())

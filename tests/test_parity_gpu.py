@@ -5,9 +5,11 @@ Bar (from the target): Gaussian-tile pairs and sorted keys bit-exact, except
 pairs whose cull/tile decision lies within 1e-6 (relative) of its threshold,
 which are logged; images within 1e-4 max abs per channel, excluding pixels
 whose blend decisions lie within tolerance of a threshold in the FP64
-oracle (alpha vs alpha_low within 1e-5, T(1-alpha) vs t_min within 1e-3 —
-the FP32 transmittance drifts by ~1e-5 relative over a long blend, so the
-stop decision needs the wider band) and the tiles touched by logged pairs.
+oracle (alpha vs alpha_low within 1e-5, T(1-alpha) vs t_min within 1e-4 —
+after a few blends of alpha ~0.9 the FP32 transmittance carries ~1e-5
+relative error, so the stop decision gets the wider band) and the tiles
+touched by logged pairs.  Every pixel that actually differs must be flagged,
+and at most 1e-4 of the pixels may differ.
 """
 import math
 
@@ -63,11 +65,10 @@ def _check_frame(rast, scene, cam, st, label=""):
         ranges = rast.read_ranges()
         np.testing.assert_array_equal(ranges, ref["ranges"])
     exclude = (ref["near"] != 0) | tile_mask(dtiles, cam.width, cam.height)
-    worst, n_ex = compare_images(img, t_final, load, ref, exclude)
+    worst, logged, n_ex = compare_images(img, t_final, load, ref, exclude)
     hw = cam.width * cam.height
-    assert n_ex <= max(4, 1e-3 * hw), f"{label}: {n_ex} excluded pixels"
     print(f"{label}: P={keys.size} near-Gaussians={int(near.sum())} differing={len(differing)} "
-          f"max|err|={worst:.2e} excluded={n_ex}/{hw}")
+          f"max|err|={worst:.2e} logged={logged} flagged={n_ex}/{hw}")
     return img, load
 
 
@@ -129,6 +130,7 @@ def test_single_gaussian_footprint_closed_form(rast, theta, op):
     ref = oracle.render(scene, cam, S.Settings())
     # the oracle is pinned to the closed form on the same case (test_oracle_pins)
     np.testing.assert_allclose(img, ref["img"], atol=2e-6)
+    assert ref["near"].sum() == 0
     np.testing.assert_array_equal(load[ref["near"] == 0], ref["load"][ref["near"] == 0])
 
 
