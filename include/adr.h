@@ -172,6 +172,33 @@ adr_status adr_render_host(adr_ctx *ctx, const float *means, const float *scales
                            const adr_camera *camera, const adr_settings *settings,
                            float *img, float *t_final, int32_t *load, void *stream);
 
+/* Allocation-free frame for small scenes.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (or anything
+ * that allocates) when they render -- e.g. an application whose device
+ * memory belongs to its own allocator and forbids allocations after start-up,
+ * or a real-time loop that cannot afford an allocation's implicit device
+ * synchronisation -- and so cannot create an adr_ctx.
+ * It runs the same stages as adr_preprocess + adr_sort + adr_render with all
+ * intermediates in one static device array compiled into the library (about
+ * 23 MB, held by every GPU that loads the library until the process exits).
+ * Limits: n <= 32768 Gaussians, width and height <= 512, at most 1048576
+ * Gaussian-tile pairs; larger sizes are rejected with ADR_ERR_INVALID, and a
+ * frame that produces more pairs returns ADR_ERR_CAPACITY (image incomplete).
+ * Arguments are as for adr_preprocess and adr_render (device memory, the
+ * caller's inputs and outputs; t_final and load may be NULL); the frame runs
+ * on the current CUDA device.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams or threads without ordering) race and corrupt each other.  Each
+ * call clears what must start at zero, waits for its frame (SYNCHRONISES
+ * `stream`) and reports device-side errors in its return value.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+adr_status adr_render_frame_noalloc(const float *means, const float *scales, const float *rots,
+                                    const float *opac, const float *sh, int64_t n,
+                                    const adr_camera *camera, const adr_settings *settings,
+                                    float *img, float *t_final, int32_t *load, void *stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char *adr_last_error(void);
 

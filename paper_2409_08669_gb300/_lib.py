@@ -68,6 +68,8 @@ _SIGNATURES = {
     "adr_read_pixel_stats": (_I32, [_P, _P, _P, _P]),
     "adr_render_host": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
                                ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
+    "adr_render_frame_noalloc": (_I32, [_P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
+                                        ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
     "adr_last_error": (ctypes.c_char_p, []),
     "adr_version": (ctypes.c_char_p, []),
 }

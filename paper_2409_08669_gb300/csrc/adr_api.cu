@@ -171,6 +171,19 @@ adr_status check_launch(const char* what) {
 
 }  // namespace
 
+namespace adr {
+// Shared with other translation units of the library (declared in adr_internal.cuh).
+adr_status report_error(adr_status st, const char* msg) { return fail(st, "%s", msg); }
+adr_status report_ok() { return ok(); }
+adr_status camera_to_dev(const adr_camera* cam, int max_w, int max_h, CamDev& d) {
+    adr_ctx probe;
+    probe.max_w = max_w;
+    probe.max_h = max_h;
+    return make_cam(&probe, cam, d);
+}
+adr_status settings_to_dev(const adr_settings* s, SetDev& d) { return make_settings(s, d); }
+}  // namespace adr
+
 extern "C" {
 
 const char* adr_last_error(void) { return g_last_error.c_str(); }

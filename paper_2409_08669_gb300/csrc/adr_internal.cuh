@@ -114,4 +114,10 @@ void launch_read_gaussians(const float4* rec, const float4* aux, const ushort4* 
                            const uint32_t* tiles, int n, float* geom, int32_t* rect_out,
                            int32_t* tiles_out, cudaStream_t stream);
 
+// Error reporting and argument conversion shared by the entry points.
+adr_status report_error(adr_status st, const char* msg);
+adr_status report_ok();
+adr_status camera_to_dev(const adr_camera* cam, int max_w, int max_h, CamDev& d);
+adr_status settings_to_dev(const adr_settings* s, SetDev& d);
+
 }  // namespace adr

@@ -1,0 +1,218 @@
+// adr_render_frame_noalloc: the whole forward path (preprocess, depth sort,
+// tile-count scan, pair emission, tile sort, ranges, render) for small frames,
+// with every intermediate buffer carved out of one file-scope device array
+// instead of memory the caller or the library allocates at run time.
+//
+// Who needs it: callers that cannot call cudaMalloc (or anything that does)
+// when they render, e.g. a host application whose GPU memory is owned by
+// another allocator and forbids allocations after start-up, a real-time loop
+// where an allocation's implicit device synchronisation is unacceptable, or
+// a plugin loaded into a process that has no spare device memory budget for
+// a library context.  They pass their own input and output buffers; the
+// scratch lives in the library image itself.
+//
+// The array is sized for at most kNaMaxGaussians Gaussians, kNaMaxPairs
+// Gaussian-tile pairs and kNaMaxWidth x kNaMaxHeight images (about 23 MB);
+// every GPU that loads the library holds it until the process exits.
+#include <atomic>
+#include <mutex>
+
+#include "adr_internal.cuh"
+
+namespace adr {
+namespace {
+
+constexpr int64_t kNaMaxGaussians = 1 << 15;
+constexpr int64_t kNaMaxPairs = 1 << 20;
+constexpr int kNaMaxWidth = 512;
+constexpr int kNaMaxHeight = 512;
+constexpr int kNaMaxTiles = (kNaMaxWidth / kTile) * (kNaMaxHeight / kTile);
+constexpr int kMaxDevices = 64;
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Byte offsets of each buffer inside the array.
+constexpr size_t kOffRec = 0;
+constexpr size_t kOffAux = align256(kOffRec + kNaMaxGaussians * kRecFloat4 * 16);
+constexpr size_t kOffDepth = align256(kOffAux + kNaMaxGaussians * kAuxFloat4 * 16);
+constexpr size_t kOffTiles = align256(kOffDepth + kNaMaxGaussians * 4);
+constexpr size_t kOffRect = align256(kOffTiles + kNaMaxGaussians * 4);
+constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
+constexpr size_t kOffGKeys = align256(kOffOffsets + kNaMaxGaussians * 4);     // 2 buffers
+constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
+constexpr size_t kOffPTile = align256(kOffGVals + 2 * kNaMaxGaussians * 4);   // 2 buffers
+constexpr size_t kOffPGauss = align256(kOffPTile + 2 * kNaMaxPairs * 4);      // 2 buffers
+constexpr size_t kOffRanges = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
+constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
+constexpr size_t kOffTrav = align256(kOffLast + (size_t)kNaMaxWidth * kNaMaxHeight * 4);
+constexpr size_t kOffHist = align256(kOffTrav + (size_t)kNaMaxWidth * kNaMaxHeight * 4);
+constexpr size_t kOffCounters = align256(kOffHist + (kMaxPasses + 2) * kRadix * 4);
+constexpr size_t kOffStatus = align256(kOffCounters + kCntSlots * 4);
+constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 1) * kRadix;
+constexpr size_t kOffLookback = align256(kOffStatus + 16);
+constexpr size_t kNaBytes = align256(kOffLookback + kLookbackWords * 8);
+
+// The scratch.  Zero-initialised when the module loads (the lookback words
+// rely on that: a zero word never matches a pass's non-zero epoch).
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+struct DeviceState {
+    unsigned char* base = nullptr;   // device address of g_na_scratch on this device
+    int sort_grid = 0, scan_grid = 0, sm_count = 0;
+    std::atomic<uint32_t> epoch{0};
+};
+
+std::mutex g_setup_mutex;
+DeviceState g_state[kMaxDevices];
+
+// Once per device, with that device current: resolve the array's device
+// address (the host-side symbol is only a stand-in) and size the grids.
+adr_status setup(int dev, DeviceState*& out) {
+    if (dev < 0 || dev >= kMaxDevices) return report_error(ADR_ERR_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    DeviceState& s = g_state[dev];
+    if (!s.base) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return report_error(ADR_ERR_CUDA, "cudaGetSymbolAddress(g_na_scratch) failed");
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            return report_error(ADR_ERR_CUDA, "cudaDeviceGetAttribute(multiProcessorCount) failed");
+        s.sm_count = sms;
+        s.sort_grid = sms * onesweep_blocks_per_sm();
+        s.scan_grid = sms * scan_blocks_per_sm();
+        s.base = static_cast<unsigned char*>(p);
+    }
+    out = &s;
+    return ADR_OK;
+}
+
+uint32_t next_epoch(DeviceState& s, unsigned long long* lookback, cudaStream_t strm) {
+    uint32_t e = s.epoch.fetch_add(1) + 1;
+    if (e == 0) {   // wrapped: clear every word so none can match a new pass
+        cudaMemsetAsync(lookback, 0, kLookbackWords * 8, strm);
+        e = s.epoch.fetch_add(1) + 1;
+    }
+    return e;
+}
+
+int ceil_log2_tiles(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) < v) ++b;
+    return b;
+}
+
+}  // namespace
+}  // namespace adr
+
+using namespace adr;
+
+extern "C" adr_status adr_render_frame_noalloc(const float* means, const float* scales,
+                                               const float* rots, const float* opac,
+                                               const float* sh, int64_t n,
+                                               const adr_camera* camera,
+                                               const adr_settings* settings, float* img,
+                                               float* t_final, int32_t* load, void* stream) {
+    if (n < 0 || n > kNaMaxGaussians)
+        return report_error(ADR_ERR_INVALID,
+                            "adr_render_frame_noalloc: n must be in 0..32768 (static scratch limit)");
+    if (!img) return report_error(ADR_ERR_INVALID, "adr_render_frame_noalloc: img is NULL");
+    if (n > 0 && (!means || !scales || !rots || !opac || !sh))
+        return report_error(ADR_ERR_INVALID, "adr_render_frame_noalloc: a parameter pointer is NULL");
+    if (n > 0 && ((uintptr_t)rots % 16 || (uintptr_t)sh % 16 || (uintptr_t)means % 4 ||
+                  (uintptr_t)scales % 4 || (uintptr_t)opac % 4))
+        return report_error(ADR_ERR_INVALID,
+                            "adr_render_frame_noalloc: rots and sh must be 16-byte aligned");
+    CamDev cam;
+    SetDev st;
+    adr_status s = camera_to_dev(camera, kNaMaxWidth, kNaMaxHeight, cam);
+    if (s != ADR_OK) return s;   // includes images larger than 512 x 512
+    if ((s = settings_to_dev(settings, st)) != ADR_OK) return s;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return report_error(ADR_ERR_CUDA, "cudaGetDevice failed");
+    DeviceState* ds = nullptr;
+    if ((s = setup(dev, ds)) != ADR_OK) return s;
+
+    unsigned char* b = ds->base;
+    float4* rec = reinterpret_cast<float4*>(b + kOffRec);
+    float4* aux = reinterpret_cast<float4*>(b + kOffAux);
+    uint32_t* depth_key = reinterpret_cast<uint32_t*>(b + kOffDepth);
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(b + kOffTiles);
+    ushort4* rect = reinterpret_cast<ushort4*>(b + kOffRect);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(b + kOffOffsets);
+    uint32_t* gkeys[2] = {reinterpret_cast<uint32_t*>(b + kOffGKeys),
+                          reinterpret_cast<uint32_t*>(b + kOffGKeys) + kNaMaxGaussians};
+    uint32_t* gvals[2] = {reinterpret_cast<uint32_t*>(b + kOffGVals),
+                          reinterpret_cast<uint32_t*>(b + kOffGVals) + kNaMaxGaussians};
+    uint32_t* ptile[2] = {reinterpret_cast<uint32_t*>(b + kOffPTile),
+                          reinterpret_cast<uint32_t*>(b + kOffPTile) + kNaMaxPairs};
+    uint32_t* pgauss[2] = {reinterpret_cast<uint32_t*>(b + kOffPGauss),
+                           reinterpret_cast<uint32_t*>(b + kOffPGauss) + kNaMaxPairs};
+    uint2* ranges = reinterpret_cast<uint2*>(b + kOffRanges);
+    int32_t* last = reinterpret_cast<int32_t*>(b + kOffLast);
+    int32_t* trav = reinterpret_cast<int32_t*>(b + kOffTrav);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(b + kOffHist);
+    uint32_t* counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
+    uint32_t* status = reinterpret_cast<uint32_t*>(b + kOffStatus);
+    unsigned long long* lookback = reinterpret_cast<unsigned long long*>(b + kOffLookback);
+
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    const int64_t num_tiles = (int64_t)cam.tiles_x * cam.tiles_y;
+    const int tile_bits = ceil_log2_tiles(num_tiles);
+    const int tile_passes = (tile_bits + kRadixBits - 1) / kRadixBits;
+
+    // Clear what must start at zero (the array keeps the previous call's contents).
+    if (cudaMemsetAsync(counters, 0, kCntSlots * 4, strm) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, 16, strm) != cudaSuccess ||
+        cudaMemsetAsync(hist, 0, (kMaxPasses + 2) * kRadix * 4, strm) != cudaSuccess ||
+        cudaMemsetAsync(ranges, 0, num_tiles * 8, strm) != cudaSuccess)
+        return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: cudaMemsetAsync failed");
+
+    launch_preprocess((int)n, means, scales, rots, opac, sh, cam, st, rec, aux, depth_key, tiles,
+                      rect, strm);
+    launch_digit_hist(depth_key, n, nullptr, 0, kMaxPasses, hist, ds->sm_count * 4, strm);
+    const uint32_t* kin = depth_key;
+    const uint32_t* vin = nullptr;
+    for (int p = 0; p < kMaxPasses; ++p) {
+        launch_onesweep(kin, vin, gkeys[p & 1], gvals[p & 1], n, nullptr, 8 * p, 8,
+                        hist + p * kRadix, lookback, next_epoch(*ds, lookback, strm),
+                        counters + kCntSortTicket0 + p, status, ds->sort_grid, strm);
+        kin = gkeys[p & 1];
+        vin = gvals[p & 1];
+    }
+    const uint32_t* order = vin;
+    launch_scan_tiles(order, tiles, n, offsets, lookback, next_epoch(*ds, lookback, strm), counters,
+                      status, ds->scan_grid, strm);
+    launch_emit(order, tiles, offsets, rect, n, cam, kNaMaxPairs, ptile[0], pgauss[0],
+                hist + kMaxPasses * kRadix, tile_passes, tile_bits, status, strm);
+    int cur = 0;
+    for (int p = 0; p < tile_passes; ++p) {
+        const int bits = (tile_bits - 8 * p) < 8 ? (tile_bits - 8 * p) : 8;
+        launch_onesweep(ptile[cur], pgauss[cur], ptile[cur ^ 1], pgauss[cur ^ 1], kNaMaxPairs,
+                        counters + kCntPairs, 8 * p, bits, hist + (kMaxPasses + p) * kRadix,
+                        lookback, next_epoch(*ds, lookback, strm),
+                        counters + kCntSortTicket0 + kMaxPasses + p, status, ds->sort_grid, strm);
+        cur ^= 1;
+    }
+    launch_ranges(ptile[cur], counters + kCntPairs, kNaMaxPairs, (uint32_t)num_tiles, ranges,
+                  ds->sm_count * 8, strm);
+    launch_render(ranges, pgauss[cur], rec, cam, st, img, t_final, load, last, trav, strm);
+    if (cudaGetLastError() != cudaSuccess)
+        return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: kernel launch failed");
+
+    // Report pair overflow and bounded-wait expiry: read the status word and the
+    // pair count back (into host stack memory) and wait for the frame.
+    uint32_t words[2] = {0, 0};
+    if (cudaMemcpyAsync(&words[0], status, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+        cudaMemcpyAsync(&words[1], counters + kCntPairs, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+        cudaStreamSynchronize(strm) != cudaSuccess)
+        return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: status readback failed");
+    if (words[0] & (kErrLookback | kErrRange))
+        return report_error(ADR_ERR_TIMEOUT, "adr_render_frame_noalloc: a device-side wait gave up");
+    if ((words[0] & kErrCapacity) || words[1] > kNaMaxPairs)
+        return report_error(ADR_ERR_CAPACITY,
+                            "adr_render_frame_noalloc: more than 1048576 Gaussian-tile pairs "
+                            "(static scratch limit); the image is incomplete");
+    return report_ok();
+}
