@@ -37,11 +37,25 @@ if ROOT not in sys.path:
 from paper_2409_08669_gb300 import scenes as S  # noqa: E402
 
 METRIC = "FPS @1080p, 3M Gaussians, AdR vs plain 3DGS path on 1 GB300; serving p50/p99 ms"
+# name -> (scene builder, gaussians, width, height, pair capacity)
+WORKLOADS = {
+    "heavy-3M-1080p": ("heavy", 3_000_000, 1920, 1080, 1 << 29),
+    "heavy-3M-4k": ("heavy", 3_000_000, 3840, 2160, 1 << 30),
+    "cluster-1M-1080p": ("cluster", 1_000_000, 1920, 1080, 1 << 27),
+    "heavy-600k-1080p": ("heavy", 600_000, 1920, 1080, 1 << 26),
+}
 WORKLOAD = "heavy-3M-1080p"
 N_GAUSS = 3_000_000
 WIDTH, HEIGHT = 1920, 1080
 N_CAMERAS = 50
 PAIR_CAPACITY = 1 << 29
+
+
+def select_workload(name):
+    global WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY
+    kind, n, w, h, cap = WORKLOADS[name]
+    WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
+    return kind
 LAUNCHES_PER_FRAME = 12   # preprocess, digit hist, 4 depth passes, scan, emit, 2 tile passes, ranges, render
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
 
@@ -141,7 +155,8 @@ def max_over_ranks(pg, value):
 
 
 def build_workload(rank=0):
-    scene = S.heavy_scene(n=N_GAUSS, seed=2)
+    kind = WORKLOADS[WORKLOAD][0]
+    scene = S.heavy_scene(n=N_GAUSS, seed=2) if kind == "heavy" else S.cluster_scene(n=N_GAUSS, seed=1)
     cams = S.orbit_cameras(N_CAMERAS, radius=4.0, width=WIDTH, height=HEIGHT)
     cams = cams[rank % N_CAMERAS:] + cams[:rank % N_CAMERAS]
     return scene, cams
@@ -251,6 +266,12 @@ def run_ours(args):
     status = rast.sync_status()
     if status != 0:
         raise SystemExit(f"device status {status} after the timed region")
+    if args.quick:
+        rast.close()
+        if rank == 0:
+            print(json.dumps({"workload": WORKLOAD, "fps": args.steps * world / t_adr,
+                              "stages_ms": {k: statistics.mean(v) for k, v in stages.items()}}))
+        return
     t_plain, stages_plain = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
                                       stream, pg)
     t_circle, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
@@ -430,12 +451,16 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heavy-3M-1080p")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the AdR mode only (no plain/circle arms, e2e or baselines)")
     args = ap.parse_args()
+    select_workload(args.workload)
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
