@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "adr.h"
 
 namespace adr {
@@ -55,56 +57,134 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;                           // up to 32 key bits
 constexpr int kMaxTiles = 1 << 16;                      // tile ids sort in two 8-bit passes
 
-// Per-call counters kept on the device (ctx->d_counters).
+// Per-call counters kept on the device.
 enum Counter : int {
-    kCntPairs = 0,        // number of pairs P (sum of tiles over Gaussians)
-    kCntVisible = 1,      // Gaussians with at least one tile
+    kCntPairs = 0,        // number of pairs P (sum of tiles over Gaussians), saturating
+    kCntVisible = 1,      // Gaussians with at least one tile (they sort first by depth)
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
-    kCntSortTicket0 = 4,  // chunk tickets of the sort passes (kMaxPasses * 2 slots)
+    kCntSortTicket0 = 4,  // chunk tickets of the sort passes (depth: 4, tiles: 2)
     kCntSlots = 16
 };
 
-// Launchers (each enqueues on `stream`; all pointers are device memory).
+// Device buffers one frame needs.  The context path allocates them with
+// cudaMalloc; the allocation-free path carves them out of a static array.
+struct Workspace {
+    int64_t max_n = 0, capacity = 0;       // Gaussians, Gaussian-tile pairs
+    int max_tiles = 0;
+    int sm_count = 0, sort_grid = 0, scan_grid = 0;
+    float4* rec = nullptr;                 // [max_n * kRecFloat4]
+    float4* aux = nullptr;                 // [max_n * kAuxFloat4]
+    uint32_t* depth_key = nullptr;         // [max_n]
+    uint32_t* tiles = nullptr;             // [max_n]
+    ushort4* rect = nullptr;               // [max_n]
+    uint32_t* offsets = nullptr;           // [max_n]
+    uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
+    uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
+    uint32_t* ptile = nullptr;             // [capacity]  pair tiles after the first tile pass
+    uint32_t* pgauss[2] = {nullptr, nullptr};  // [capacity] each
+    uint32_t* chunk_first = nullptr;       // [capacity / kSortChunk + 2]
+    uint2* ranges = nullptr;               // [max_tiles]
+    int32_t* last = nullptr;               // [max pixels]
+    int32_t* trav = nullptr;               // [max pixels]
+    uint32_t* hist = nullptr;              // [kHistWords]
+    uint32_t* counters = nullptr;          // [kCntSlots]
+    uint32_t* status = nullptr;            // [4]
+    unsigned long long* lookback = nullptr;
+    size_t lookback_words = 0;             // (max(max_n, capacity) / kSortChunk + 2) * kRadix
+};
+
+// hist layout: 4 x 256 depth digits, then 2 x 256 tile digits.
+constexpr int kHistWords = (kMaxPasses + 2) * kRadix;
+
+// What one frame's stages hand to the next.
+struct FrameState {
+    int64_t n = 0;
+    CamDev cam{};
+    SetDev st{};
+    int num_tiles = 0, tile_bits = 0, bits1 = 0, bits2 = 0, tile_passes = 0;
+    const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
+    const uint32_t* sorted_gauss = nullptr;  // pairs' Gaussians by (tile, depth)
+};
+
+// Monotone pass tag for the lookback words; on wrap-around clears them.
+uint32_t next_epoch(std::atomic<uint32_t>& epoch, const Workspace& ws, cudaStream_t stream);
+
+// Stage orchestration shared by every entry point (pipeline.cu).
+void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                        const float* means, const float* scales, const float* rots,
+                        const float* opac, const float* sh, cudaStream_t stream);
+void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                  cudaStream_t stream);
+void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
+                    int32_t* load, cudaStream_t stream);
+void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st);
+
+// Kernel launchers (each enqueues on `stream`; all pointers are device memory).
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
                        const float* opac, const float* sh, const CamDev& cam, const SetDev& st,
                        float4* rec, float4* aux, uint32_t* depth_key, uint32_t* tiles,
                        ushort4* rect, cudaStream_t stream);
 
-// Histogram of `passes` 8-bit digits of u32 keys (count read from *d_n if
-// d_n != nullptr, else n).  hist must hold passes*256 zeroed u32.
-void launch_digit_hist(const uint32_t* keys, int64_t n, const uint32_t* d_n, int shift0, int passes,
-                       uint32_t* hist, int grid, cudaStream_t stream);
+// Histogram of `passes` 8-bit digits of u32 keys.  hist must hold passes*256 zeroed u32.
+void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, uint32_t* hist,
+                       int grid, cudaStream_t stream);
 
-// One stable onesweep pass of 8-bit digit at `shift`.  vals_in == nullptr
-// means the values are the indices 0..n-1.  lookback holds chunks*256 u64.
+// Stable onesweep pass over u32 keys in memory: digit (key >> shift) &
+// (2^digit_bits - 1).  vals_in == nullptr means the values are 0..n-1.
 void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                     uint32_t* vals_out, int64_t n, const uint32_t* d_n, int shift, int digit_bits,
+                     uint32_t* vals_out, int64_t n, int shift, int digit_bits,
                      const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
                      uint32_t* ticket, uint32_t* status, int grid, cudaStream_t stream);
 
-// Exclusive scan of tiles[order[i]] with decoupled lookback; writes offsets,
-// the total to counters[kCntPairs] and the non-empty count to kCntVisible.
-void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, int64_t n, uint32_t* offsets,
-                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
-                       uint32_t* status, int grid, cudaStream_t stream);
+// Inputs of the tile passes.
+struct PairSource {
+    const uint32_t* order = nullptr;       // Gaussians by depth
+    const uint32_t* offsets = nullptr;     // exclusive scan of their tile counts
+    const ushort4* rect = nullptr;         // tile rectangle per Gaussian index
+    const uint32_t* chunk_first = nullptr; // sorted position holding each chunk's first pair
+    const uint32_t* counters = nullptr;    // kCntPairs, kCntVisible
+    int64_t capacity = 0;
+    int tiles_x = 0;
+};
 
-// Emit (tile, Gaussian) pairs in depth order; accumulates the tile-digit
-// histogram for the pair sort.
-void launch_emit(const uint32_t* order, const uint32_t* tiles, const uint32_t* offsets,
-                 const ushort4* rect, int64_t n, const CamDev& cam, int64_t capacity,
-                 uint32_t* pair_tile, uint32_t* pair_gauss, uint32_t* tile_hist, int hist_passes,
-                 int hist_bits, uint32_t* status, cudaStream_t stream);
+// First tile pass: the pairs are generated on chip from the depth-ordered
+// Gaussians (no pair list in memory) and scattered by the low tile digit.
+// With final = true (single pass) it writes only Gaussian ids and the ranges.
+void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t* gauss_out,
+                            int digit_bits, bool final, uint2* ranges, const uint32_t* hist,
+                            unsigned long long* lookback, uint32_t epoch, uint32_t* ticket,
+                            uint32_t* status, int grid, cudaStream_t stream);
+// Second tile pass: scatter by the high digit, write only Gaussian ids, and
+// derive each tile's [start, end) from the digit runs.
+void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, uint32_t* gauss_out,
+                           const uint32_t* counters, int64_t capacity, int shift, int digit_bits,
+                           uint2* ranges, const uint32_t* hist, unsigned long long* lookback,
+                           uint32_t epoch, uint32_t* ticket, uint32_t* status, int grid,
+                           cudaStream_t stream);
 
-void launch_ranges(const uint32_t* sorted_tile, const uint32_t* d_n, int64_t capacity,
-                   uint32_t num_tiles, uint2* ranges, int grid, cudaStream_t stream);
+// Exclusive scan of tiles[order[i]] with decoupled lookback.  Also writes the
+// pair total and visible count to counters, the tile-digit histograms of the
+// two tile passes (hist_tiles[0..255] low digit of bits1 bits, [256..511]
+// high digit) and chunk_first[c] = position of the Gaussian holding pair
+// c * kSortChunk.
+void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
+                       int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
+                       uint32_t* chunk_first, uint32_t* hist_tiles, unsigned long long* lookback,
+                       uint32_t epoch, uint32_t* counters, uint32_t* status, int grid,
+                       cudaStream_t stream);
+
+void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
                    int32_t* last, int32_t* trav, cudaStream_t stream);
 
-void launch_pair_keys(const uint32_t* sorted_tile, const uint32_t* sorted_gauss,
-                      const uint32_t* depth_key_by_gauss, const uint32_t* d_n, int64_t count,
+// Inspection: sorted pairs as (tile << 32 | depth bits, Gaussian) from the ranges.
+void launch_pair_keys(const uint2* ranges, int num_tiles, const uint32_t* sorted_gauss,
+                      const uint32_t* depth_key_by_gauss, int64_t count,
                       unsigned long long* keys_out, uint32_t* vals_out, cudaStream_t stream);
+// Inspection: ranges with empty tiles as [0, 0).
+void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream);
 
 // Occupancy of the persistent kernels (CTAs per SM), for grid sizing.
 int onesweep_blocks_per_sm();

@@ -1,10 +1,13 @@
-// Stages 2-3 and 5 of the rasterization pipeline (Sec. 3.2.1):
-//   InclusiveSum      scan of per-Gaussian tile counts (decoupled lookback)
-//   DuplicateWithKeys one (tile, Gaussian) pair per overlapped tile, emitted
-//                     cooperatively by a warp (warp-aggregated emission)
-//   IdentifyTileRanges [start, end) of each tile in the sorted pair list
-// The Gaussians are visited in view-depth order, so the pair list is already
-// depth-ordered and only needs a stable sort by tile.
+// Stages 2-3 of the rasterization pipeline (Sec. 3.2.1), InclusiveSum and the
+// bookkeeping DuplicateWithKeys needs, over the Gaussians in view-depth order:
+//   * offsets[i] = exclusive prefix sum of the tile counts (decoupled lookback),
+//     the pair total P and the number of Gaussians with tiles;
+//   * chunk_first[c] = depth-order position of the Gaussian that holds pair
+//     c * 4096, so each chunk of the first tile-sort pass can generate its
+//     pairs on chip without an emitted pair list;
+//   * the histograms of the two tile-sort digits, counted per rectangle row
+//     (a row of a tile rectangle is a contiguous range of tile ids).
+// Plus small helpers for the tile ranges.
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -23,13 +26,24 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles, int64_t n,
-             uint32_t* __restrict__ offsets, unsigned long long* __restrict__ lookback,
+k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
+             const ushort4* __restrict__ rect, int64_t n, int tiles_x, int bits1,
+             int64_t capacity, uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
+             uint32_t* __restrict__ hist_tiles, unsigned long long* __restrict__ lookback,
              uint32_t epoch, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
+    __shared__ uint32_t s_lo_diff[kRadix + 1];   // circular difference array of the low digit
+    __shared__ uint32_t s_hi[kRadix];
+    __shared__ uint32_t s_full;                  // full cycles of the low digit (every bin + 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long tag = (unsigned long long)epoch << 32;
+    const uint32_t R1 = 1u << bits1, M1 = R1 - 1u;
+    for (int i = tid; i <= kRadix; i += kScanThreads) s_lo_diff[i] = 0;
+    for (int i = tid; i < kRadix; i += kScanThreads) s_hi[i] = 0;
+    if (tid == 0) s_full = 0;
+    uint32_t my_full = 0;
+
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(counters + kCntScanTicket, 1u);
         __syncthreads();
@@ -74,7 +88,7 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
                 while (j >= 0) {
                     const unsigned long long w =
                         *reinterpret_cast<volatile unsigned long long*>(lookback + j);
-                    if ((w >> 32) != epoch) {
+                    if ((uint32_t)(w >> 32) != epoch) {
                         if (++spins > kSpinLimit) { atomicOr(status, kErrLookback); break; }
                         __nanosleep(32);
                         continue;
@@ -87,120 +101,97 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
                     tag | kScanInc | sat_add(excl, total);
             }
             s_prefix = excl;
-            if (base + kScanChunk >= n) counters[kCntPairs] = sat_add(excl, total);
+            if (base + kScanChunk >= n) {
+                const uint32_t p = sat_add(excl, total);
+                counters[kCntPairs] = p;
+                if ((int64_t)p > capacity) atomicOr(status, kErrCapacity);
+            }
         }
-        // Visible (non-empty) count.
-        uint32_t nz = __reduce_add_sync(0xffffffffu, nonzero);
+        const uint32_t nz = __reduce_add_sync(0xffffffffu, nonzero);
         if (lane == 0 && nz) atomicAdd(counters + kCntVisible, nz);
         __syncthreads();
         uint32_t run = sat_add(s_prefix, texcl);
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + tid * kScanItems + k;
+            const uint32_t t = v[k];
             if (i < n) offsets[i] = run;
-            run = sat_add(run, v[k]);
+            if (t != 0 && (int64_t)run < capacity) {
+                // chunk starts inside [run, run + t)
+                const uint64_t c_lo = ((uint64_t)run + kSortChunk - 1) / kSortChunk;
+                uint64_t c_hi = ((uint64_t)run + t - 1) / kSortChunk;
+                const uint64_t c_max = ((uint64_t)capacity - 1) / kSortChunk;
+                if (c_hi > c_max) c_hi = c_max;
+                for (uint64_t c = c_lo; c <= c_hi; ++c) chunk_first[c] = (uint32_t)i;
+                // digit histograms of this Gaussian's pairs, row by row
+                const ushort4 r = rect[order[i]];
+                const uint32_t w = (uint32_t)(r.z - r.x);
+                for (uint32_t ty = r.y; ty < r.w; ++ty) {
+                    const uint32_t a0 = ty * (uint32_t)tiles_x + r.x;   // tile ids a0 .. a0+w-1
+                    my_full += w >> bits1;
+                    const uint32_t rem = w & M1, s0 = a0 & M1;
+                    if (rem) {
+                        atomicAdd(&s_lo_diff[s0], 1u);
+                        if (s0 + rem <= R1) {
+                            atomicAdd(&s_lo_diff[s0 + rem], 0xFFFFFFFFu);
+                        } else {
+                            atomicAdd(&s_lo_diff[0], 1u);
+                            atomicAdd(&s_lo_diff[s0 + rem - R1], 0xFFFFFFFFu);
+                        }
+                    }
+                    const uint32_t h0 = a0 >> bits1, h1 = (a0 + w - 1) >> bits1;
+                    for (uint32_t hd = h0; hd <= h1; ++hd) {
+                        const uint32_t lo = max(a0, hd << bits1);
+                        const uint32_t hi = min(a0 + w, (hd + 1) << bits1);
+                        atomicAdd(&s_hi[hd & 0xFF], hi - lo);
+                    }
+                }
+            }
+            run = sat_add(run, t);
         }
         __syncthreads();
     }
-}
-
-__global__ void __launch_bounds__(256)
-k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
-       const uint32_t* __restrict__ offsets, const ushort4* __restrict__ rect, int64_t n,
-       int tiles_x, int64_t capacity, uint32_t* __restrict__ pair_tile,
-       uint32_t* __restrict__ pair_gauss, uint32_t* __restrict__ tile_hist, int hist_passes,
-       uint32_t* __restrict__ status) {
-    __shared__ uint32_t s_hist[2][kRadix];
-    for (int i = threadIdx.x; i < 2 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    // Flush this CTA's digit histograms.
+    const uint32_t fw = __reduce_add_sync(0xffffffffu, my_full);
+    if (lane == 0 && fw) atomicAdd(&s_full, fw);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x / 32);
-    bool overflow = false;
-    for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32;
-         wbase < n; wbase += warps_total * 32) {
-        const int64_t pos = wbase + lane;
-        uint32_t g = 0, t = 0, off = 0;
-        ushort4 r = make_ushort4(0, 0, 1, 1);
-        if (pos < n) {
-            g = order[pos];
-            t = tiles[g];
-            if (t) {
-                off = offsets[pos];
-                r = rect[g];
-            }
-        }
-        // Inclusive warp scan of the tile counts.
-        uint32_t incl = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t excl = incl - t;
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t rx0 = r.x, ry0 = r.y, rw = (uint32_t)(r.z - r.x);
-        for (uint32_t j = 0; j < total; j += 32) {
-            const uint32_t p = j + lane;
-            // Source lane: the largest s with excl[s] <= p.
-            int s = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t e = __shfl_sync(0xffffffffu, excl, s + step);
-                if (e <= p) s += step;
-            }
-            const uint32_t e_s = __shfl_sync(0xffffffffu, excl, s);
-            const uint32_t off_s = __shfl_sync(0xffffffffu, off, s);
-            const uint32_t g_s = __shfl_sync(0xffffffffu, g, s);
-            const uint32_t x0 = __shfl_sync(0xffffffffu, rx0, s);
-            const uint32_t y0 = __shfl_sync(0xffffffffu, ry0, s);
-            const uint32_t w = __shfl_sync(0xffffffffu, rw, s);
-            if (p < total) {
-                const uint32_t k = p - e_s;
-                const uint32_t dy = k / w, dx = k - dy * w;
-                const uint32_t tile = (y0 + dy) * (uint32_t)tiles_x + (x0 + dx);
-                const uint64_t gp = (uint64_t)off_s + k;
-                if (gp < (uint64_t)capacity) {
-                    pair_tile[gp] = tile;
-                    pair_gauss[gp] = g_s;
-                    atomicAdd(&s_hist[0][tile & 0xFF], 1u);
-                    if (hist_passes > 1) atomicAdd(&s_hist[1][(tile >> 8) & 0xFF], 1u);
-                } else {
-                    overflow = true;
-                }
-            }
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (uint32_t d = 0; d < R1; ++d) {
+            acc += s_lo_diff[d];
+            s_lo_diff[d] = acc + s_full;
         }
     }
-    if (overflow) atomicOr(status, kErrCapacity);
     __syncthreads();
-    for (int i = threadIdx.x; i < hist_passes * kRadix; i += blockDim.x) {
-        const uint32_t v = (&s_hist[0][0])[i];
-        if (v) atomicAdd(tile_hist + i, v);
+    for (uint32_t d = tid; d < R1; d += kScanThreads)
+        if (s_lo_diff[d]) atomicAdd(hist_tiles + d, s_lo_diff[d]);
+    for (int d = tid; d < kRadix; d += kScanThreads)
+        if (s_hi[d]) atomicAdd(hist_tiles + kRadix + d, s_hi[d]);
+}
+
+__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x)
+        ranges[t] = make_uint2(0xFFFFFFFFu, 0u);
+}
+
+__global__ void k_copy_ranges(const uint2* __restrict__ ranges, int num_tiles, uint2* __restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        out[t] = r.x < r.y ? r : make_uint2(0u, 0u);
     }
 }
 
+// One CTA per tile writes that tile's slice of the inspection output.
 __global__ void __launch_bounds__(256)
-k_ranges(const uint32_t* __restrict__ sorted_tile, const uint32_t* __restrict__ d_n,
-         int64_t capacity, uint32_t num_tiles, uint2* __restrict__ ranges) {
-    const int64_t n = (int64_t)min((uint64_t)*d_n, (uint64_t)capacity);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = sorted_tile[i];
-        if (t >= num_tiles) continue;   // only after a failed (flagged) sort
-        if (i == 0 || sorted_tile[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == n - 1 || sorted_tile[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
-    }
-}
-
-__global__ void __launch_bounds__(256)
-k_pair_keys(const uint32_t* __restrict__ sorted_tile, const uint32_t* __restrict__ sorted_gauss,
-            const uint32_t* __restrict__ depth_key, const uint32_t* __restrict__ d_n,
-            int64_t count, unsigned long long* __restrict__ keys_out,
-            uint32_t* __restrict__ vals_out) {
-    const int64_t n = (int64_t)min((uint64_t)*d_n, (uint64_t)count);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+k_pair_keys(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
+            const uint32_t* __restrict__ depth_key, int64_t count,
+            unsigned long long* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+    const uint32_t t = blockIdx.x;
+    const uint2 r = ranges[t];
+    if (!(r.x < r.y)) return;
+    for (uint32_t i = r.x + threadIdx.x; i < r.y && (int64_t)i < count; i += blockDim.x) {
         const uint32_t g = sorted_gauss[i];
-        keys_out[i] = ((unsigned long long)sorted_tile[i] << 32) | depth_key[g];
+        keys_out[i] = ((unsigned long long)t << 32) | depth_key[g];
         vals_out[i] = g;
     }
 }
@@ -236,38 +227,33 @@ int scan_blocks_per_sm() {
     return b > 0 ? b : 1;
 }
 
-void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, int64_t n, uint32_t* offsets,
-                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
-                       uint32_t* status, int grid, cudaStream_t stream) {
+void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
+                       int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
+                       uint32_t* chunk_first, uint32_t* hist_tiles, unsigned long long* lookback,
+                       uint32_t epoch, uint32_t* counters, uint32_t* status, int grid,
+                       cudaStream_t stream) {
     if (n <= 0) return;
-    k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, n, offsets, lookback, epoch,
-                                                    counters, status);
+    k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, tiles_x, bits1, capacity,
+                                                    offsets, chunk_first, hist_tiles, lookback,
+                                                    epoch, counters, status);
 }
 
-void launch_emit(const uint32_t* order, const uint32_t* tiles, const uint32_t* offsets,
-                 const ushort4* rect, int64_t n, const CamDev& cam, int64_t capacity,
-                 uint32_t* pair_tile, uint32_t* pair_gauss, uint32_t* tile_hist, int hist_passes,
-                 int hist_bits, uint32_t* status, cudaStream_t stream) {
-    (void)hist_bits;
-    if (n <= 0) return;
-    const int64_t warps = (n + 31) / 32;
-    const int64_t blocks = (warps + 7) / 8;
-    const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
-    k_emit<<<grid, 256, 0, stream>>>(order, tiles, offsets, rect, n, cam.tiles_x, capacity,
-                                     pair_tile, pair_gauss, tile_hist, hist_passes, status);
+void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream) {
+    if (num_tiles <= 0) return;
+    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles);
 }
 
-void launch_ranges(const uint32_t* sorted_tile, const uint32_t* d_n, int64_t capacity,
-                   uint32_t num_tiles, uint2* ranges, int grid, cudaStream_t stream) {
-    k_ranges<<<grid, 256, 0, stream>>>(sorted_tile, d_n, capacity, num_tiles, ranges);
+void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream) {
+    if (num_tiles <= 0) return;
+    k_copy_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles, out);
 }
 
-void launch_pair_keys(const uint32_t* sorted_tile, const uint32_t* sorted_gauss,
-                      const uint32_t* depth_key_by_gauss, const uint32_t* d_n, int64_t count,
+void launch_pair_keys(const uint2* ranges, int num_tiles, const uint32_t* sorted_gauss,
+                      const uint32_t* depth_key_by_gauss, int64_t count,
                       unsigned long long* keys_out, uint32_t* vals_out, cudaStream_t stream) {
-    if (count <= 0) return;
-    k_pair_keys<<<152 * 4, 256, 0, stream>>>(sorted_tile, sorted_gauss, depth_key_by_gauss, d_n,
-                                             count, keys_out, vals_out);
+    if (count <= 0 || num_tiles <= 0) return;
+    k_pair_keys<<<num_tiles, 256, 0, stream>>>(ranges, sorted_gauss, depth_key_by_gauss, count,
+                                               keys_out, vals_out);
 }
 
 void launch_read_gaussians(const float4* rec, const float4* aux, const ushort4* rect,

@@ -32,6 +32,7 @@ constexpr int kMaxDevices = 64;
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Byte offsets of each buffer inside the array.
+constexpr size_t kPixels = (size_t)kNaMaxWidth * kNaMaxHeight;
 constexpr size_t kOffRec = 0;
 constexpr size_t kOffAux = align256(kOffRec + kNaMaxGaussians * kRecFloat4 * 16);
 constexpr size_t kOffDepth = align256(kOffAux + kNaMaxGaussians * kAuxFloat4 * 16);
@@ -40,15 +41,16 @@ constexpr size_t kOffRect = align256(kOffTiles + kNaMaxGaussians * 4);
 constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
 constexpr size_t kOffGKeys = align256(kOffOffsets + kNaMaxGaussians * 4);     // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
-constexpr size_t kOffPTile = align256(kOffGVals + 2 * kNaMaxGaussians * 4);   // 2 buffers
-constexpr size_t kOffPGauss = align256(kOffPTile + 2 * kNaMaxPairs * 4);      // 2 buffers
-constexpr size_t kOffRanges = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
+constexpr size_t kOffPTile = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
+constexpr size_t kOffPGauss = align256(kOffPTile + kNaMaxPairs * 4);          // 2 buffers
+constexpr size_t kOffChunkFirst = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
+constexpr size_t kOffRanges = align256(kOffChunkFirst + (kNaMaxPairs / kSortChunk + 2) * 4);
 constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
-constexpr size_t kOffTrav = align256(kOffLast + (size_t)kNaMaxWidth * kNaMaxHeight * 4);
-constexpr size_t kOffHist = align256(kOffTrav + (size_t)kNaMaxWidth * kNaMaxHeight * 4);
-constexpr size_t kOffCounters = align256(kOffHist + (kMaxPasses + 2) * kRadix * 4);
+constexpr size_t kOffTrav = align256(kOffLast + kPixels * 4);
+constexpr size_t kOffHist = align256(kOffTrav + kPixels * 4);
+constexpr size_t kOffCounters = align256(kOffHist + kHistWords * 4);
 constexpr size_t kOffStatus = align256(kOffCounters + kCntSlots * 4);
-constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 1) * kRadix;
+constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 2) * kRadix;
 constexpr size_t kOffLookback = align256(kOffStatus + 16);
 constexpr size_t kNaBytes = align256(kOffLookback + kLookbackWords * 8);
 
@@ -58,7 +60,7 @@ static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
 struct DeviceState {
     unsigned char* base = nullptr;   // device address of g_na_scratch on this device
-    int sort_grid = 0, scan_grid = 0, sm_count = 0;
+    Workspace ws;                    // buffers inside the array
     std::atomic<uint32_t> epoch{0};
 };
 
@@ -79,28 +81,39 @@ adr_status setup(int dev, DeviceState*& out) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             return report_error(ADR_ERR_CUDA, "cudaDeviceGetAttribute(multiProcessorCount) failed");
-        s.sm_count = sms;
-        s.sort_grid = sms * onesweep_blocks_per_sm();
-        s.scan_grid = sms * scan_blocks_per_sm();
-        s.base = static_cast<unsigned char*>(p);
+        unsigned char* b = static_cast<unsigned char*>(p);
+        Workspace& w = s.ws;
+        w.max_n = kNaMaxGaussians;
+        w.capacity = kNaMaxPairs;
+        w.max_tiles = kNaMaxTiles;
+        w.sm_count = sms;
+        w.sort_grid = sms * onesweep_blocks_per_sm();
+        w.scan_grid = sms * scan_blocks_per_sm();
+        w.rec = reinterpret_cast<float4*>(b + kOffRec);
+        w.aux = reinterpret_cast<float4*>(b + kOffAux);
+        w.depth_key = reinterpret_cast<uint32_t*>(b + kOffDepth);
+        w.tiles = reinterpret_cast<uint32_t*>(b + kOffTiles);
+        w.rect = reinterpret_cast<ushort4*>(b + kOffRect);
+        w.offsets = reinterpret_cast<uint32_t*>(b + kOffOffsets);
+        for (int k = 0; k < 2; ++k) {
+            w.gkeys[k] = reinterpret_cast<uint32_t*>(b + kOffGKeys) + k * kNaMaxGaussians;
+            w.gvals[k] = reinterpret_cast<uint32_t*>(b + kOffGVals) + k * kNaMaxGaussians;
+            w.pgauss[k] = reinterpret_cast<uint32_t*>(b + kOffPGauss) + k * kNaMaxPairs;
+        }
+        w.ptile = reinterpret_cast<uint32_t*>(b + kOffPTile);
+        w.chunk_first = reinterpret_cast<uint32_t*>(b + kOffChunkFirst);
+        w.ranges = reinterpret_cast<uint2*>(b + kOffRanges);
+        w.last = reinterpret_cast<int32_t*>(b + kOffLast);
+        w.trav = reinterpret_cast<int32_t*>(b + kOffTrav);
+        w.hist = reinterpret_cast<uint32_t*>(b + kOffHist);
+        w.counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
+        w.status = reinterpret_cast<uint32_t*>(b + kOffStatus);
+        w.lookback = reinterpret_cast<unsigned long long*>(b + kOffLookback);
+        w.lookback_words = kLookbackWords;
+        s.base = b;
     }
     out = &s;
     return ADR_OK;
-}
-
-uint32_t next_epoch(DeviceState& s, unsigned long long* lookback, cudaStream_t strm) {
-    uint32_t e = s.epoch.fetch_add(1) + 1;
-    if (e == 0) {   // wrapped: clear every word so none can match a new pass
-        cudaMemsetAsync(lookback, 0, kLookbackWords * 8, strm);
-        e = s.epoch.fetch_add(1) + 1;
-    }
-    return e;
-}
-
-int ceil_log2_tiles(int64_t v) {
-    int b = 0;
-    while ((int64_t(1) << b) < v) ++b;
-    return b;
 }
 
 }  // namespace
@@ -134,78 +147,24 @@ extern "C" adr_status adr_render_frame_noalloc(const float* means, const float* 
     DeviceState* ds = nullptr;
     if ((s = setup(dev, ds)) != ADR_OK) return s;
 
-    unsigned char* b = ds->base;
-    float4* rec = reinterpret_cast<float4*>(b + kOffRec);
-    float4* aux = reinterpret_cast<float4*>(b + kOffAux);
-    uint32_t* depth_key = reinterpret_cast<uint32_t*>(b + kOffDepth);
-    uint32_t* tiles = reinterpret_cast<uint32_t*>(b + kOffTiles);
-    ushort4* rect = reinterpret_cast<ushort4*>(b + kOffRect);
-    uint32_t* offsets = reinterpret_cast<uint32_t*>(b + kOffOffsets);
-    uint32_t* gkeys[2] = {reinterpret_cast<uint32_t*>(b + kOffGKeys),
-                          reinterpret_cast<uint32_t*>(b + kOffGKeys) + kNaMaxGaussians};
-    uint32_t* gvals[2] = {reinterpret_cast<uint32_t*>(b + kOffGVals),
-                          reinterpret_cast<uint32_t*>(b + kOffGVals) + kNaMaxGaussians};
-    uint32_t* ptile[2] = {reinterpret_cast<uint32_t*>(b + kOffPTile),
-                          reinterpret_cast<uint32_t*>(b + kOffPTile) + kNaMaxPairs};
-    uint32_t* pgauss[2] = {reinterpret_cast<uint32_t*>(b + kOffPGauss),
-                           reinterpret_cast<uint32_t*>(b + kOffPGauss) + kNaMaxPairs};
-    uint2* ranges = reinterpret_cast<uint2*>(b + kOffRanges);
-    int32_t* last = reinterpret_cast<int32_t*>(b + kOffLast);
-    int32_t* trav = reinterpret_cast<int32_t*>(b + kOffTrav);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(b + kOffHist);
-    uint32_t* counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
-    uint32_t* status = reinterpret_cast<uint32_t*>(b + kOffStatus);
-    unsigned long long* lookback = reinterpret_cast<unsigned long long*>(b + kOffLookback);
-
+    const Workspace& ws = ds->ws;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
-    const int64_t num_tiles = (int64_t)cam.tiles_x * cam.tiles_y;
-    const int tile_bits = ceil_log2_tiles(num_tiles);
-    const int tile_passes = (tile_bits + kRadixBits - 1) / kRadixBits;
-
-    // Clear what must start at zero (the array keeps the previous call's contents).
-    if (cudaMemsetAsync(counters, 0, kCntSlots * 4, strm) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, 16, strm) != cudaSuccess ||
-        cudaMemsetAsync(hist, 0, (kMaxPasses + 2) * kRadix * 4, strm) != cudaSuccess ||
-        cudaMemsetAsync(ranges, 0, num_tiles * 8, strm) != cudaSuccess)
+    // The array keeps the previous call's contents: clear what must start at zero.
+    if (cudaMemsetAsync(ws.status, 0, 16, strm) != cudaSuccess)
         return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: cudaMemsetAsync failed");
-
-    launch_preprocess((int)n, means, scales, rots, opac, sh, cam, st, rec, aux, depth_key, tiles,
-                      rect, strm);
-    launch_digit_hist(depth_key, n, nullptr, 0, kMaxPasses, hist, ds->sm_count * 4, strm);
-    const uint32_t* kin = depth_key;
-    const uint32_t* vin = nullptr;
-    for (int p = 0; p < kMaxPasses; ++p) {
-        launch_onesweep(kin, vin, gkeys[p & 1], gvals[p & 1], n, nullptr, 8 * p, 8,
-                        hist + p * kRadix, lookback, next_epoch(*ds, lookback, strm),
-                        counters + kCntSortTicket0 + p, status, ds->sort_grid, strm);
-        kin = gkeys[p & 1];
-        vin = gvals[p & 1];
-    }
-    const uint32_t* order = vin;
-    launch_scan_tiles(order, tiles, n, offsets, lookback, next_epoch(*ds, lookback, strm), counters,
-                      status, ds->scan_grid, strm);
-    launch_emit(order, tiles, offsets, rect, n, cam, kNaMaxPairs, ptile[0], pgauss[0],
-                hist + kMaxPasses * kRadix, tile_passes, tile_bits, status, strm);
-    int cur = 0;
-    for (int p = 0; p < tile_passes; ++p) {
-        const int bits = (tile_bits - 8 * p) < 8 ? (tile_bits - 8 * p) : 8;
-        launch_onesweep(ptile[cur], pgauss[cur], ptile[cur ^ 1], pgauss[cur ^ 1], kNaMaxPairs,
-                        counters + kCntPairs, 8 * p, bits, hist + (kMaxPasses + p) * kRadix,
-                        lookback, next_epoch(*ds, lookback, strm),
-                        counters + kCntSortTicket0 + kMaxPasses + p, status, ds->sort_grid, strm);
-        cur ^= 1;
-    }
-    launch_ranges(ptile[cur], counters + kCntPairs, kNaMaxPairs, (uint32_t)num_tiles, ranges,
-                  ds->sm_count * 8, strm);
-    launch_render(ranges, pgauss[cur], rec, cam, st, img, t_final, load, last, trav, strm);
+    FrameState fs;
+    fill_frame_state(fs, n, cam, st);
+    enqueue_preprocess(ws, fs, ds->epoch, means, scales, rots, opac, sh, strm);
+    enqueue_sort(ws, fs, ds->epoch, strm);
+    enqueue_render(ws, fs, img, t_final, load, strm);
     if (cudaGetLastError() != cudaSuccess)
         return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: kernel launch failed");
 
     // Report pair overflow and bounded-wait expiry: read the status word and the
     // pair count back (into host stack memory) and wait for the frame.
     uint32_t words[2] = {0, 0};
-    if (cudaMemcpyAsync(&words[0], status, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
-        cudaMemcpyAsync(&words[1], counters + kCntPairs, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+    if (cudaMemcpyAsync(&words[0], ws.status, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+        cudaMemcpyAsync(&words[1], ws.counters + kCntPairs, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
         cudaStreamSynchronize(strm) != cudaSuccess)
         return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: status readback failed");
     if (words[0] & (kErrLookback | kErrRange))

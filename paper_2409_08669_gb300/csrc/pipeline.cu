@@ -1,0 +1,108 @@
+// Stage orchestration shared by every entry point: enqueues the kernels of
+// the six-stage rasterizer (Sec. 3.2.1) on one stream for a Workspace,
+// wherever its buffers come from.
+#include "adr_internal.cuh"
+
+namespace adr {
+
+uint32_t next_epoch(std::atomic<uint32_t>& epoch, const Workspace& ws, cudaStream_t stream) {
+    uint32_t e = epoch.fetch_add(1) + 1;
+    if (e == 0) {
+        // Every lookback word carries the epoch of the pass that wrote it; on
+        // wrap-around clear them all so no stale word can match a new pass.
+        cudaMemsetAsync(ws.lookback, 0, ws.lookback_words * sizeof(unsigned long long), stream);
+        e = epoch.fetch_add(1) + 1;
+    }
+    return e;
+}
+
+void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st) {
+    fs.n = n;
+    fs.cam = cam;
+    fs.st = st;
+    fs.num_tiles = cam.tiles_x * cam.tiles_y;
+    int b = 0;
+    while ((1 << b) < fs.num_tiles) ++b;
+    fs.tile_bits = b;
+    if (b <= kRadixBits) {            // one pass over all tile bits
+        fs.tile_passes = 1;
+        fs.bits1 = b;
+        fs.bits2 = 0;
+    } else {                          // two balanced passes (e.g. 7 + 6 bits at 1080p)
+        fs.tile_passes = 2;
+        fs.bits1 = (b + 1) / 2;
+        fs.bits2 = b - fs.bits1;
+    }
+    fs.order = nullptr;
+    fs.sorted_gauss = nullptr;
+}
+
+void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                        const float* means, const float* scales, const float* rots,
+                        const float* opac, const float* sh, cudaStream_t stream) {
+    const int64_t n = fs.n;
+    cudaMemsetAsync(ws.counters, 0, kCntSlots * sizeof(uint32_t), stream);
+    cudaMemsetAsync(ws.hist, 0, kHistWords * sizeof(uint32_t), stream);
+    // Stage 1: per-Gaussian projection, covariance, colour and early cull.
+    launch_preprocess((int)n, means, scales, rots, opac, sh, fs.cam, fs.st, ws.rec, ws.aux,
+                      ws.depth_key, ws.tiles, ws.rect, stream);
+    // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
+    // carry key 0xFFFFFFFF and end up behind the V that have tiles.
+    launch_digit_hist(ws.depth_key, n, 0, kMaxPasses, ws.hist, ws.sm_count * 4, stream);
+    const uint32_t* kin = ws.depth_key;
+    const uint32_t* vin = nullptr;
+    for (int p = 0; p < kMaxPasses; ++p) {
+        launch_onesweep(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, 8,
+                        ws.hist + p * kRadix, ws.lookback, next_epoch(epoch, ws, stream),
+                        ws.counters + kCntSortTicket0 + p, ws.status, ws.sort_grid, stream);
+        kin = ws.gkeys[p & 1];
+        vin = ws.gvals[p & 1];
+    }
+    fs.order = vin;
+    // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
+    launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
+                      ws.offsets, ws.chunk_first, ws.hist + kMaxPasses * kRadix, ws.lookback,
+                      next_epoch(epoch, ws, stream), ws.counters, ws.status, ws.scan_grid, stream);
+}
+
+void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                  cudaStream_t stream) {
+    const int t0 = kCntSortTicket0 + kMaxPasses;
+    cudaMemsetAsync(ws.counters + t0, 0, 2 * sizeof(uint32_t), stream);
+    launch_init_ranges(ws.ranges, fs.num_tiles, stream);
+    PairSource src;
+    src.order = fs.order;
+    src.offsets = ws.offsets;
+    src.rect = ws.rect;
+    src.chunk_first = ws.chunk_first;
+    src.counters = ws.counters;
+    src.capacity = ws.capacity;
+    src.tiles_x = fs.cam.tiles_x;
+    const uint32_t* hist_tiles = ws.hist + kMaxPasses * kRadix;
+    if (fs.n > 0 && fs.order) {
+        // Stages 3-5: emit + first tile digit, then (if needed) the second
+        // digit, which also yields the per-tile ranges.
+        const bool single = fs.tile_passes == 1;
+        launch_tile_pass_first(src, ws.ptile, ws.pgauss[0], fs.bits1, single, ws.ranges, hist_tiles,
+                               ws.lookback, next_epoch(epoch, ws, stream), ws.counters + t0,
+                               ws.status, ws.sort_grid, stream);
+        if (!single) {
+            launch_tile_pass_last(ws.ptile, ws.pgauss[0], ws.pgauss[1], ws.counters, ws.capacity,
+                                  fs.bits1, fs.bits2, ws.ranges, hist_tiles + kRadix, ws.lookback,
+                                  next_epoch(epoch, ws, stream), ws.counters + t0 + 1, ws.status,
+                                  ws.sort_grid, stream);
+        }
+        fs.sorted_gauss = single ? ws.pgauss[0] : ws.pgauss[1];
+    } else {
+        fs.sorted_gauss = ws.pgauss[0];
+    }
+}
+
+void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
+                    int32_t* load, cudaStream_t stream) {
+    // Stage 6.
+    launch_render(ws.ranges, fs.sorted_gauss, ws.rec, fs.cam, fs.st, img, t_final, load, ws.last,
+                  ws.trav, stream);
+}
+
+}  // namespace adr

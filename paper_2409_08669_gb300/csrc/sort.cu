@@ -1,27 +1,74 @@
-// Stage 4, SortPairs (Sec. 3.2.1): a stable least-significant-digit radix
-// sort of 32-bit keys with 32-bit values, one kernel per 8-bit digit
-// ("onesweep": each chunk ranks its keys locally, obtains the running digit
-// offsets of all earlier chunks by decoupled lookback, and scatters).
+// Stage 4, SortPairs (Sec. 3.2.1), as stable least-significant-digit radix
+// passes in the "onesweep" form: each chunk of 4096 items ranks its keys
+// locally (warp match_any), obtains the running per-digit offsets of all
+// earlier chunks by decoupled lookback, and scatters through shared memory so
+// that each digit's run is written contiguously.
 //
-// The same kernel sorts the Gaussians by view depth (4 digits) and the
-// depth-ordered pairs by tile (ceil(tile_bits / 8) digits).
+// Three uses:
+//   * the Gaussians by view depth (4 passes of 8 bits over N keys in memory);
+//   * the first tile pass: the (tile, Gaussian) pairs are generated on chip
+//     from the depth-ordered Gaussians (a load-balanced search over the
+//     scan offsets), so the unsorted pair list never exists in memory;
+//   * the last tile pass: writes only the Gaussian ids and derives every
+//     tile's [start, end) from its digit runs (atomicMin/atomicMax per run
+//     segment), replacing a separate IdentifyTileRanges pass.
 //
-// Persistent grid: every CTA takes chunk tickets in increasing order from an
-// atomic counter, so any chunk a CTA waits on is already held by a running
-// CTA.  Each wait is bounded; on expiry the kernel raises kErrLookback and
-// continues with a wrong (but in-bounds) placement rather than hanging.
+// Persistent grid: CTAs take chunk tickets in increasing order from an atomic
+// counter, so any chunk a CTA waits on is already held by a running CTA.
+// Every wait is bounded; on expiry the kernel raises kErrLookback and goes on
+// with a wrong but in-bounds placement instead of hanging.
 #include "adr_internal.cuh"
 
 namespace adr {
 namespace {
 
 // Lookback word: [63:32] epoch of the pass, [31:30] state (1 = aggregate of
-// this chunk only, 2 = inclusive prefix), [29:0] count.  A word whose epoch is
-// not the current pass's is "not ready yet".
+// this chunk only, 2 = inclusive prefix), [29:0] count.  A word from another
+// epoch reads as "not ready".
 constexpr unsigned long long kStateAgg = 1ull << 30;
 constexpr unsigned long long kStateInc = 2ull << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kMaxChunkGauss = kSortChunk + 1;   // every listed Gaussian has >= 1 pair
+
+struct SortShared {
+    union {
+        struct {
+            uint32_t keys[kSortChunk];
+            uint32_t vals[kSortChunk];
+        } kv;
+        struct {                      // Gaussians overlapping one pair chunk
+            uint32_t off[kMaxChunkGauss];
+            uint32_t gid[kMaxChunkGauss];
+            uint32_t box[kMaxChunkGauss];   // x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24
+        } stage;
+    } u;
+    uint32_t warp_cnt[kWarps][kRadix + 1];   // +1: out-of-range items of the tail chunk
+    uint32_t gbase[kRadix];                  // exclusive prefix of the global digit histogram
+    uint32_t local[kRadix + 1];              // exclusive prefix of this chunk's digit counts
+    uint32_t dst[kRadix];                    // global position of local slot 0, per digit
+    uint32_t wsum[kWarps];
+    uint32_t chunk;
+};
+constexpr size_t kSortSmem = sizeof(SortShared);
+
+struct SweepArgs {
+    const uint32_t* keys_in;
+    const uint32_t* vals_in;
+    uint32_t* keys_out;
+    uint32_t* vals_out;
+    int64_t n_host;              // item count, or the capacity bound when counters != null
+    const uint32_t* counters;    // tile passes: item count = min(counters[kCntPairs], n_host)
+    int shift, digit_bits;
+    const uint32_t* hist;        // 256 counts of this pass's digit
+    unsigned long long* lookback;
+    uint32_t epoch;
+    uint32_t* ticket;
+    uint32_t* status;
+    uint2* ranges;               // last tile pass
+    PairSource src;              // first tile pass
+};
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
     return *reinterpret_cast<const volatile unsigned long long*>(p);
@@ -29,7 +76,6 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 __device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
     *reinterpret_cast<volatile unsigned long long*>(p) = v;
 }
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -37,12 +83,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 __global__ void __launch_bounds__(256)
-k_digit_hist(const uint32_t* __restrict__ keys, int64_t n_host, const uint32_t* __restrict__ d_n,
-             int shift0, int passes, uint32_t* __restrict__ hist) {
+k_digit_hist(const uint32_t* __restrict__ keys, int64_t n, int shift0, int passes,
+             uint32_t* __restrict__ hist) {
     __shared__ uint32_t s_hist[kMaxPasses][kRadix];
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t n = d_n ? (int64_t)min((uint64_t)*d_n, (uint64_t)n_host) : n_host;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = keys[i];
@@ -55,88 +100,157 @@ k_digit_hist(const uint32_t* __restrict__ keys, int64_t n_host, const uint32_t* 
     }
 }
 
-struct SortSmem {
-    uint32_t keys[kSortChunk];
-    uint32_t vals[kSortChunk];
-    uint32_t warp_cnt[kSortThreads / 32][kRadix + 1];   // +1: out-of-range items
-    uint32_t gbase[kRadix];      // exclusive prefix of the global digit histogram
-    uint32_t local[kRadix + 1];  // exclusive prefix of this chunk's digit counts
-    uint32_t dst[kRadix];        // global position of local slot 0 of each digit
-    uint32_t chunk;
-};
-
-__global__ void __launch_bounds__(kSortThreads)
-k_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-           uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n_host,
-           const uint32_t* __restrict__ d_n, int shift, int digit_bits,
-           const uint32_t* __restrict__ hist, unsigned long long* __restrict__ lookback,
-           uint32_t epoch, uint32_t* __restrict__ ticket, uint32_t* __restrict__ status) {
-    __shared__ SortSmem sm;
+// Generate the pairs of chunk `chunk` (items base .. base+count-1 of the
+// depth-ordered emission) into key/val in warp-striped order.
+__device__ __forceinline__ void generate_pairs(const SweepArgs& a, SortShared& sm, uint32_t chunk,
+                                               int64_t base, int count, int64_t n,
+                                               uint32_t (&key)[kSortItems],
+                                               uint32_t (&val)[kSortItems]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t mask = (1u << digit_bits) - 1u;
-    const int64_t n = d_n ? (int64_t)min((uint64_t)*d_n, (uint64_t)n_host) : n_host;
-    const unsigned long long tag = (unsigned long long)epoch << 32;
+    const PairSource& src = a.src;
+    const uint32_t visible = src.counters[kCntVisible];
+    const uint32_t i0 = src.chunk_first[chunk];
+    // Gaussians [i0, i1] hold this chunk's pairs; the one holding the next
+    // chunk's first pair closes the range.
+    uint32_t i1 = (base + kSortChunk >= n) ? min(visible - 1u, i0 + (uint32_t)kMaxChunkGauss - 1u)
+                                           : src.chunk_first[chunk + 1];
+    if (visible == 0 || i1 < i0 || i1 >= visible || i1 - i0 + 1 > (uint32_t)kMaxChunkGauss) {
+        if (tid == 0) atomicOr(a.status, kErrRange);   // inconsistent scan output: stay in bounds
+        i1 = visible == 0 ? i0 : min(visible - 1u, i0 + (uint32_t)kMaxChunkGauss - 1u);
+        if (i1 < i0) i1 = i0;
+    }
+    const int G = (int)(i1 - i0 + 1);
+    for (int j = tid; j < G; j += kSortThreads) {
+        const uint32_t i = i0 + j;
+        const uint32_t g = src.order[i];
+        const ushort4 r = src.rect[g];
+        sm.u.stage.off[j] = src.offsets[i];
+        sm.u.stage.gid[j] = g;
+        sm.u.stage.box[j] = (uint32_t)r.x | ((uint32_t)r.y << 8) |
+                            ((uint32_t)(r.z - r.x - 1) << 16) | ((uint32_t)(r.w - r.y - 1) << 24);
+    }
+    __syncthreads();
+    // Each thread walks 16 consecutive items (blocked order) into key/val.
+    const int first = tid * kSortItems;
+    if (first < count) {
+        const uint32_t p0 = (uint32_t)(base + first);
+        int lo = 0, hi = G - 1;   // largest j with off[j] <= p0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.u.stage.off[mid] <= p0) lo = mid; else hi = mid - 1;
+        }
+        int j = lo;
+        uint32_t box = sm.u.stage.box[j], g = sm.u.stage.gid[j];
+        uint32_t w = ((box >> 16) & 0xFF) + 1, h = (box >> 24) + 1;
+        const uint32_t k = p0 - sm.u.stage.off[j];
+        uint32_t dy = k / w, dx = k - dy * w;
+#pragma unroll
+        for (int q = 0; q < kSortItems; ++q) {
+            key[q] = (((box >> 8) & 0xFF) + dy) * (uint32_t)src.tiles_x + (box & 0xFF) + dx;
+            val[q] = g;
+            if (++dx == w) {
+                dx = 0;
+                if (++dy == h && j + 1 < G) {
+                    ++j;
+                    dy = 0;
+                    box = sm.u.stage.box[j];
+                    g = sm.u.stage.gid[j];
+                    w = ((box >> 16) & 0xFF) + 1;
+                    h = (box >> 24) + 1;
+                }
+            }
+        }
+    }
+    __syncthreads();   // staging no longer needed: reuse it for the pairs
+    if (first < count) {
+#pragma unroll
+        for (int q = 0; q < kSortItems; ++q) {
+            if (first + q < count) {
+                sm.u.kv.keys[first + q] = key[q];
+                sm.u.kv.vals[first + q] = val[q];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSortItems; ++q) {
+        const int s = warp * (kSortItems * 32) + q * 32 + lane;
+        key[q] = s < count ? sm.u.kv.keys[s] : 0xFFFFFFFFu;
+        val[q] = s < count ? sm.u.kv.vals[s] : 0u;
+    }
+}
+
+template <bool kGen, bool kFinal>
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortShared& sm = *reinterpret_cast<SortShared*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t mask = (1u << a.digit_bits) - 1u;
+    const int64_t n = a.counters ? min((int64_t)a.counters[kCntPairs], a.n_host) : a.n_host;
+    const unsigned long long tag = (unsigned long long)a.epoch << 32;
 
     // Exclusive prefix of the global histogram of this digit (one digit per thread).
     {
-        const uint32_t h = hist[tid];
+        const uint32_t h = a.hist[tid];
         uint32_t x = h;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) sm.local[warp] = x;
+        if (lane == 31) sm.wsum[warp] = x;
         __syncthreads();
         uint32_t wbase = 0;
-        for (int w = 0; w < warp; ++w) wbase += sm.local[w];
+        for (int w = 0; w < warp; ++w) wbase += sm.wsum[w];
         sm.gbase[tid] = wbase + x - h;
-        __syncthreads();
     }
 
     for (;;) {
-        if (tid == 0) sm.chunk = atomicAdd(ticket, 1u);
+        if (tid == 0) sm.chunk = atomicAdd(a.ticket, 1u);
         for (int d = lane; d <= kRadix; d += 32) sm.warp_cnt[warp][d] = 0;
         __syncthreads();
         const uint32_t chunk = sm.chunk;
         const int64_t base = (int64_t)chunk * kSortChunk;
         if (base >= n) break;
+        const int count = (int)min((int64_t)kSortChunk, n - base);
 
-        // Warp-striped load: warp w owns 512 consecutive keys, item k of lane l
-        // is key w*512 + k*32 + l, so (k, lane) order is the input order.
-        uint32_t key[kSortItems], val[kSortItems], dig[kSortItems], rank[kSortItems];
+        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+        if constexpr (kGen) {
+            generate_pairs(a, sm, chunk, base, count, n, key, val);
+        } else {
+            // Warp-striped load: item q of lane l in warp w is base + w*512 + q*32 + l.
 #pragma unroll
-        for (int k = 0; k < kSortItems; ++k) {
-            const int64_t idx = base + warp * (kSortItems * 32) + k * 32 + lane;
-            const bool ok = idx < n;
-            key[k] = ok ? keys_in[idx] : 0xFFFFFFFFu;
-            val[k] = ok ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
-            dig[k] = ok ? ((key[k] >> shift) & mask) : (uint32_t)kRadix;
+            for (int q = 0; q < kSortItems; ++q) {
+                const int s = warp * (kSortItems * 32) + q * 32 + lane;
+                const bool ok = s < count;
+                key[q] = ok ? a.keys_in[base + s] : 0xFFFFFFFFu;
+                val[q] = ok ? (a.vals_in ? a.vals_in[base + s] : (uint32_t)(base + s)) : 0u;
+            }
         }
-        // Stable warp-level ranking with match_any.
+        // Stable warp-level ranking with match_any (digit kRadix = out of range).
 #pragma unroll
-        for (int k = 0; k < kSortItems; ++k) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
-            const uint32_t before = sm.warp_cnt[warp][dig[k]];
-            rank[k] = before + __popc(peers & lanemask_lt());
+        for (int q = 0; q < kSortItems; ++q) {
+            const int s = warp * (kSortItems * 32) + q * 32 + lane;
+            const uint32_t d = s < count ? ((key[q] >> a.shift) & mask) : (uint32_t)kRadix;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = sm.warp_cnt[warp][d];
+            rank[q] = before + __popc(peers & lanemask_lt());
             __syncwarp();
-            if (lane == 31 - __clz(peers)) sm.warp_cnt[warp][dig[k]] = before + __popc(peers);
+            if (lane == 31 - __clz(peers)) sm.warp_cnt[warp][d] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
 
-        // Per digit (thread tid = digit): prefix over warps and chunk count.
+        // Per digit (thread = digit): prefix over warps and this chunk's count.
         uint32_t cnt = 0;
-        {
 #pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t c = sm.warp_cnt[w][tid];
-                sm.warp_cnt[w][tid] = cnt;
-                cnt += c;
-            }
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = sm.warp_cnt[w][tid];
+            sm.warp_cnt[w][tid] = cnt;
+            cnt += c;
         }
-        // Publish this chunk's count, then look back for the earlier chunks'.
-        unsigned long long* my = lookback + (size_t)chunk * kRadix + tid;
+        // Publish, then look back over the earlier chunks.
+        unsigned long long* my = a.lookback + (size_t)chunk * kRadix + tid;
         uint32_t excl = 0;
         if (chunk == 0) {
             st_volatile(my, tag | kStateInc | cnt);
@@ -145,9 +259,9 @@ k_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ va
             int64_t j = (int64_t)chunk - 1;
             int spins = 0;
             while (j >= 0) {
-                const unsigned long long w = ld_volatile(lookback + (size_t)j * kRadix + tid);
-                if ((w >> 32) != epoch || (w & (3ull << 30)) == 0) {
-                    if (++spins > kSpinLimit) { atomicOr(status, kErrLookback); break; }
+                const unsigned long long w = ld_volatile(a.lookback + (size_t)j * kRadix + tid);
+                if ((uint32_t)(w >> 32) != a.epoch || (w & (3ull << 30)) == 0) {
+                    if (++spins > kSpinLimit) { atomicOr(a.status, kErrLookback); break; }
                     __nanosleep(32);
                     continue;
                 }
@@ -165,69 +279,136 @@ k_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ va
                 const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
-            __shared__ uint32_t s_wsum[kSortThreads / 32];
-            if (lane == 31) s_wsum[warp] = x;
+            if (lane == 31) sm.wsum[warp] = x;
             __syncthreads();
             uint32_t wbase = 0;
-            for (int w = 0; w < warp; ++w) wbase += s_wsum[w];
+            for (int w = 0; w < warp; ++w) wbase += sm.wsum[w];
             const uint32_t loc = wbase + x - cnt;
             sm.local[tid] = loc;
             if (tid == kSortThreads - 1) sm.local[kRadix] = loc + cnt;
             sm.dst[tid] = sm.gbase[tid] + excl - loc;
         }
         __syncthreads();
-        // Scatter into shared memory in digit order; out-of-range items (tail
-        // chunk only) are dropped.
+        // Scatter into shared memory in digit order.
 #pragma unroll
-        for (int k = 0; k < kSortItems; ++k) {
-            const uint32_t d = dig[k];
-            if (d < (uint32_t)kRadix) {
-                const uint32_t pos = sm.local[d] + sm.warp_cnt[warp][d] + rank[k];
-                sm.keys[pos] = key[k];
-                sm.vals[pos] = val[k];
+        for (int q = 0; q < kSortItems; ++q) {
+            const int s = warp * (kSortItems * 32) + q * 32 + lane;
+            if (s < count) {
+                const uint32_t d = (key[q] >> a.shift) & mask;
+                const uint32_t pos = sm.local[d] + sm.warp_cnt[warp][d] + rank[q];
+                sm.u.kv.keys[pos] = key[q];
+                sm.u.kv.vals[pos] = val[q];
             }
         }
         __syncthreads();
-        // Coalesced write-out: consecutive slots of one digit go to consecutive addresses.
-        const uint32_t valid = sm.local[kRadix];
-        for (uint32_t s = tid; s < valid; s += kSortThreads) {
-            const uint32_t k = sm.keys[s];
-            const uint32_t d = (k >> shift) & mask;
-            const uint32_t g = sm.dst[d] + s;   // exact modulo 2^32; true value < 2^30
-            if ((int64_t)g < n) {
-                keys_out[g] = k;
-                vals_out[g] = sm.vals[s];
+        // Coalesced write-out: each digit's run goes to consecutive addresses.
+        for (int s = tid; s < count; s += kSortThreads) {
+            const uint32_t k = sm.u.kv.keys[s];
+            const uint32_t d = (k >> a.shift) & mask;
+            const uint32_t g = sm.dst[d] + (uint32_t)s;   // exact modulo 2^32; true value < 2^30
+            if ((int64_t)g >= n) { atomicOr(a.status, kErrRange); continue; }
+            a.vals_out[g] = sm.u.kv.vals[s];
+            if constexpr (kFinal) {
+                // Within a digit's run the keys ascend, so each tile's pairs
+                // form one segment; record its first and last global slot.
+                const bool first = (s == (int)sm.local[d]) || sm.u.kv.keys[s - 1] != k;
+                const bool lastp = (s + 1 == (int)sm.local[d + 1]) || sm.u.kv.keys[s + 1] != k;
+                unsigned int* r = reinterpret_cast<unsigned int*>(a.ranges + k);
+                if (first) atomicMin(r, g);
+                if (lastp) atomicMax(r + 1, g + 1u);
             } else {
-                atomicOr(status, kErrRange);
+                a.keys_out[g] = k;
             }
         }
         __syncthreads();
     }
 }
 
+template <bool kGen, bool kFinal>
+void launch_sweep(const SweepArgs& a, int grid, cudaStream_t stream) {
+    k_onesweep<kGen, kFinal><<<grid, kSortThreads, kSortSmem, stream>>>(a);
+}
+
+SweepArgs base_args(const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
+                    uint32_t* ticket, uint32_t* status) {
+    SweepArgs a{};
+    a.hist = hist;
+    a.lookback = lookback;
+    a.epoch = epoch;
+    a.ticket = ticket;
+    a.status = status;
+    return a;
+}
+
 }  // namespace
 
 int onesweep_blocks_per_sm() {
+    // Opt the kernels into more than 48 KB of dynamic shared memory (per device).
+    cudaFuncSetAttribute(k_onesweep<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    cudaFuncSetAttribute(k_onesweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    cudaFuncSetAttribute(k_onesweep<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    cudaFuncSetAttribute(k_onesweep<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep, kSortThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep<true, false>, kSortThreads,
+                                                      kSortSmem) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
 }
 
-void launch_digit_hist(const uint32_t* keys, int64_t n, const uint32_t* d_n, int shift0, int passes,
-                       uint32_t* hist, int grid, cudaStream_t stream) {
+void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, uint32_t* hist,
+                       int grid, cudaStream_t stream) {
     if (n <= 0) return;
-    k_digit_hist<<<grid, 256, 0, stream>>>(keys, n, d_n, shift0, passes, hist);
+    k_digit_hist<<<grid, 256, 0, stream>>>(keys, n, shift0, passes, hist);
 }
 
 void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                     uint32_t* vals_out, int64_t n, const uint32_t* d_n, int shift, int digit_bits,
+                     uint32_t* vals_out, int64_t n, int shift, int digit_bits,
                      const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
                      uint32_t* ticket, uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
-    k_onesweep<<<grid, kSortThreads, 0, stream>>>(keys_in, vals_in, keys_out, vals_out, n, d_n,
-                                                   shift, digit_bits, hist, lookback, epoch,
-                                                   ticket, status);
+    SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
+    a.keys_in = keys_in;
+    a.vals_in = vals_in;
+    a.keys_out = keys_out;
+    a.vals_out = vals_out;
+    a.n_host = n;
+    a.shift = shift;
+    a.digit_bits = digit_bits;
+    launch_sweep<false, false>(a, grid, stream);
+}
+
+void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t* gauss_out,
+                            int digit_bits, bool final, uint2* ranges, const uint32_t* hist,
+                            unsigned long long* lookback, uint32_t epoch, uint32_t* ticket,
+                            uint32_t* status, int grid, cudaStream_t stream) {
+    SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
+    a.keys_out = tile_out;
+    a.vals_out = gauss_out;
+    a.n_host = src.capacity;
+    a.counters = src.counters;
+    a.shift = 0;
+    a.digit_bits = digit_bits;
+    a.ranges = ranges;
+    a.src = src;
+    if (final) launch_sweep<true, true>(a, grid, stream);
+    else launch_sweep<true, false>(a, grid, stream);
+}
+
+void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, uint32_t* gauss_out,
+                           const uint32_t* counters, int64_t capacity, int shift, int digit_bits,
+                           uint2* ranges, const uint32_t* hist, unsigned long long* lookback,
+                           uint32_t epoch, uint32_t* ticket, uint32_t* status, int grid,
+                           cudaStream_t stream) {
+    SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
+    a.keys_in = tile_in;
+    a.vals_in = gauss_in;
+    a.vals_out = gauss_out;
+    a.n_host = capacity;
+    a.counters = counters;
+    a.shift = shift;
+    a.digit_bits = digit_bits;
+    a.ranges = ranges;
+    launch_sweep<false, true>(a, grid, stream);
 }
 
 }  // namespace adr
