@@ -249,29 +249,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
             sm.warp_cnt[w][tid] = cnt;
             cnt += c;
         }
-        // Publish, then look back over the earlier chunks.
+        // Publish this chunk's per-digit count right away; the lookback waits
+        // until the local placement is done, giving predecessors time to post
+        // their inclusive prefixes.
         unsigned long long* my = a.lookback + (size_t)chunk * kRadix + tid;
-        uint32_t excl = 0;
-        if (chunk == 0) {
-            st_volatile(my, tag | kStateInc | cnt);
-        } else {
-            st_volatile(my, tag | kStateAgg | cnt);
-            int64_t j = (int64_t)chunk - 1;
-            int spins = 0;
-            while (j >= 0) {
-                const unsigned long long w = ld_volatile(a.lookback + (size_t)j * kRadix + tid);
-                if ((uint32_t)(w >> 32) != a.epoch || (w & (3ull << 30)) == 0) {
-                    if (++spins > kSpinLimit) { atomicOr(a.status, kErrLookback); break; }
-                    __nanosleep(32);
-                    continue;
-                }
-                excl += (uint32_t)w & kCountMask;
-                if (w & kStateInc) break;
-                --j;
-            }
-            st_volatile(my, tag | kStateInc | ((excl + cnt) & kCountMask));
-        }
+        st_volatile(my, tag | (chunk == 0 ? kStateInc : kStateAgg) | cnt);
         // Exclusive prefix of this chunk's digit counts (local placement).
+        uint32_t loc;
         {
             uint32_t x = cnt;
 #pragma unroll
@@ -283,10 +267,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
             __syncthreads();
             uint32_t wbase = 0;
             for (int w = 0; w < warp; ++w) wbase += sm.wsum[w];
-            const uint32_t loc = wbase + x - cnt;
+            loc = wbase + x - cnt;
             sm.local[tid] = loc;
             if (tid == kSortThreads - 1) sm.local[kRadix] = loc + cnt;
-            sm.dst[tid] = sm.gbase[tid] + excl - loc;
         }
         __syncthreads();
         // Scatter into shared memory in digit order.
@@ -300,6 +283,37 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
                 sm.u.kv.vals[pos] = val[q];
             }
         }
+        // Decoupled lookback: sum the earlier chunks' counts of this digit,
+        // reading 8 predecessors per round trip, until an inclusive prefix.
+        uint32_t excl = 0;
+        if (chunk > 0) {
+            int64_t j = (int64_t)chunk - 1;
+            int spins = 0;
+            bool done = false;
+            while (!done && j >= 0) {
+                unsigned long long wv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    wv[u] = j - u >= 0 ? ld_volatile(a.lookback + (size_t)(j - u) * kRadix + tid) : 0ull;
+                int used = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (done || used < u || j - u < 0) continue;
+                    const unsigned long long w = wv[u];
+                    if ((uint32_t)(w >> 32) != a.epoch || (w & (3ull << 30)) == 0) continue;
+                    excl += (uint32_t)w & kCountMask;
+                    used = u + 1;
+                    if (w & kStateInc) done = true;
+                }
+                j -= used;
+                if (!done && used < 8 && j >= 0) {   // the next word is not ready yet
+                    if (++spins > kSpinLimit) { atomicOr(a.status, kErrLookback); break; }
+                    __nanosleep(32);
+                }
+            }
+            st_volatile(my, tag | kStateInc | ((excl + cnt) & kCountMask));
+        }
+        sm.dst[tid] = sm.gbase[tid] + excl - loc;
         __syncthreads();
         // Coalesced write-out: each digit's run goes to consecutive addresses.
         for (int s = tid; s < count; s += kSortThreads) {
