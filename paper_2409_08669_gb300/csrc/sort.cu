@@ -130,53 +130,45 @@ __device__ __forceinline__ void generate_pairs(const SweepArgs& a, SortShared& s
                             ((uint32_t)(r.z - r.x - 1) << 16) | ((uint32_t)(r.w - r.y - 1) << 24);
     }
     __syncthreads();
-    // Each thread walks 16 consecutive items (blocked order) into key/val.
-    const int first = tid * kSortItems;
-    if (first < count) {
-        const uint32_t p0 = (uint32_t)(base + first);
+    // Warp w produces items w*512 + q*32 + lane (q = 0..15), i.e. directly in
+    // the warp-striped order the ranking needs.  A warp-uniform cursor j holds
+    // the Gaussian of the step's first item; 32 consecutive items lie within
+    // Gaussians j .. j+31, so each lane searches only that window.
+    const int wfirst = warp * (kSortItems * 32);
+    int j = 0;
+    if (wfirst < count) {
+        const uint32_t p0 = (uint32_t)(base + wfirst);
         int lo = 0, hi = G - 1;   // largest j with off[j] <= p0
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (sm.u.stage.off[mid] <= p0) lo = mid; else hi = mid - 1;
         }
-        int j = lo;
-        uint32_t box = sm.u.stage.box[j], g = sm.u.stage.gid[j];
-        uint32_t w = ((box >> 16) & 0xFF) + 1, h = (box >> 24) + 1;
-        const uint32_t k = p0 - sm.u.stage.off[j];
-        uint32_t dy = k / w, dx = k - dy * w;
-#pragma unroll
-        for (int q = 0; q < kSortItems; ++q) {
-            key[q] = (((box >> 8) & 0xFF) + dy) * (uint32_t)src.tiles_x + (box & 0xFF) + dx;
-            val[q] = g;
-            if (++dx == w) {
-                dx = 0;
-                if (++dy == h && j + 1 < G) {
-                    ++j;
-                    dy = 0;
-                    box = sm.u.stage.box[j];
-                    g = sm.u.stage.gid[j];
-                    w = ((box >> 16) & 0xFF) + 1;
-                    h = (box >> 24) + 1;
-                }
-            }
-        }
+        j = lo;
     }
-    __syncthreads();   // staging no longer needed: reuse it for the pairs
-    if (first < count) {
-#pragma unroll
-        for (int q = 0; q < kSortItems; ++q) {
-            if (first + q < count) {
-                sm.u.kv.keys[first + q] = key[q];
-                sm.u.kv.vals[first + q] = val[q];
-            }
-        }
-    }
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < kSortItems; ++q) {
-        const int s = warp * (kSortItems * 32) + q * 32 + lane;
-        key[q] = s < count ? sm.u.kv.keys[s] : 0xFFFFFFFFu;
-        val[q] = s < count ? sm.u.kv.vals[s] : 0u;
+        const int s = wfirst + q * 32 + lane;
+        int jj = j;
+        if (s < count) {
+            const uint32_t p = (uint32_t)(base + s);
+            int lo = j, hi = min(G - 1, j + 32);
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.u.stage.off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            jj = lo;
+            const uint32_t box = sm.u.stage.box[jj];
+            const uint32_t w = ((box >> 16) & 0xFF) + 1;
+            const uint32_t k = p - sm.u.stage.off[jj];
+            const uint32_t dy = k / w, dx = k - dy * w;
+            key[q] = (((box >> 8) & 0xFF) + dy) * (uint32_t)src.tiles_x + (box & 0xFF) + dx;
+            val[q] = sm.u.stage.gid[jj];
+        } else {
+            key[q] = 0xFFFFFFFFu;
+            val[q] = 0u;
+        }
+        // next step starts at or after the last lane's Gaussian (items ascend)
+        j = __reduce_max_sync(0xffffffffu, (unsigned)jj);
     }
 }
 
