@@ -48,8 +48,6 @@ struct SortShared {
     uint32_t gbase[kRadix];                  // exclusive prefix of the global digit histogram
     uint32_t local[kRadix + 1];              // exclusive prefix of this chunk's digit counts
     uint32_t dst[kRadix];                    // global position of local slot 0, per digit
-    uint32_t excl[kRadix];                   // lookback result: earlier chunks' count per digit
-    int32_t win[kRadix];                     // lookback: nearest predecessor not yet summed
     uint32_t wsum[kWarps];
     uint32_t chunk;
 };
@@ -277,64 +275,36 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
                 sm.u.kv.vals[pos] = val[q];
             }
         }
-        // Decoupled lookback, warp-wide: warp w resolves digits 32w .. 32w+31;
-        // for each digit its 32 lanes read 32 consecutive predecessors in one
-        // round trip, and ballots find the nearest inclusive prefix.
-        sm.excl[tid] = 0;
-        sm.win[tid] = (int32_t)chunk - 1;
-        __syncwarp();
+        // Decoupled lookback: sum the earlier chunks' counts of this digit,
+        // reading 8 predecessors per round trip, until an inclusive prefix.
+        uint32_t excl = 0;
         if (chunk > 0) {
-            const int d0 = warp * 32;
-            uint32_t pending = 0xffffffffu;
+            int64_t j = (int64_t)chunk - 1;
             int spins = 0;
-            while (pending) {
-                uint32_t progressed = 0;
+            bool done = false;
+            while (!done && j >= 0) {
+                unsigned long long wv[8];
 #pragma unroll
-                for (int g8 = 0; g8 < 32; g8 += 8) {
-                    if (!((pending >> g8) & 0xFFu)) continue;
-                    unsigned long long wv[8];
+                for (int u = 0; u < 8; ++u)
+                    wv[u] = j - u >= 0 ? ld_volatile(a.lookback + (size_t)(j - u) * kRadix + tid) : 0ull;
+                int used = 0;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int jj = sm.win[d0 + g8 + i] - lane;
-                        wv[i] = ((pending >> (g8 + i)) & 1u) && jj >= 0
-                                    ? ld_volatile(a.lookback + (size_t)jj * kRadix + d0 + g8 + i)
-                                    : 0ull;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int di = g8 + i;
-                        if (!((pending >> di) & 1u)) continue;   // warp-uniform
-                        const int jj = sm.win[d0 + di] - lane;
-                        const bool valid = jj >= 0;
-                        const bool ready = valid && (uint32_t)(wv[i] >> 32) == a.epoch &&
-                                           (wv[i] & (3ull << 30)) != 0;
-                        const uint32_t inc = __ballot_sync(0xffffffffu, ready && (wv[i] & kStateInc));
-                        const uint32_t rdy = __ballot_sync(0xffffffffu, ready);
-                        const uint32_t val_lanes = __ballot_sync(0xffffffffu, valid);
-                        // lanes up to the nearest inclusive prefix, else every valid lane
-                        const uint32_t upto = inc ? (((inc & (0u - inc)) << 1) - 1u) : val_lanes;
-                        if ((rdy & upto) == upto) {
-                            const uint32_t c = ((upto >> lane) & 1u) ? ((uint32_t)wv[i] & kCountMask) : 0u;
-                            const uint32_t sum = __reduce_add_sync(0xffffffffu, c);
-                            if (lane == 0) {
-                                sm.excl[d0 + di] += sum;
-                                sm.win[d0 + di] -= 32;
-                            }
-                            if (inc) pending &= ~(1u << di);
-                            progressed |= 1u << di;
-                        }
-                        __syncwarp();
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    if (done || used < u || j - u < 0) continue;
+                    const unsigned long long w = wv[u];
+                    if ((uint32_t)(w >> 32) != a.epoch || (w & (3ull << 30)) == 0) continue;
+                    excl += (uint32_t)w & kCountMask;
+                    used = u + 1;
+                    if (w & kStateInc) done = true;
                 }
-                if (pending && !progressed) {
-                    if (++spins > kSpinLimit) { if (lane == 0) atomicOr(a.status, kErrLookback); break; }
+                j -= used;
+                if (!done && used < 8 && j >= 0) {   // the next word is not ready yet
+                    if (++spins > kSpinLimit) { atomicOr(a.status, kErrLookback); break; }
                     __nanosleep(32);
                 }
             }
+            st_volatile(my, tag | kStateInc | ((excl + cnt) & kCountMask));
         }
-        __syncwarp();
-        const uint32_t excl = sm.excl[tid];
-        if (chunk > 0) st_volatile(my, tag | kStateInc | ((excl + cnt) & kCountMask));
         sm.dst[tid] = sm.gbase[tid] + excl - loc;
         __syncthreads();
         // Coalesced write-out: each digit's run goes to consecutive addresses.
