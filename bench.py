@@ -56,8 +56,10 @@ def select_workload(name):
     kind, n, w, h, cap = WORKLOADS[name]
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
-LAUNCHES_PER_FRAME = 12   # preprocess, digit hist, 4 depth passes, scan, emit, 2 tile passes, ranges, render
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
+# DRAM bytes (read + write) per launch from an ncu capture of the kernel,
+# scaled to the full workload (see profiles/); None until one is taken.
+TRAFFIC_BYTES = {}
 
 
 def peaks():
@@ -166,12 +168,19 @@ def build_workload(rank=0):
 # Our arm: the CUDA path through the C ABI
 # ---------------------------------------------------------------------------
 
-def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stages=True):
-    """Returns (seconds for `steps` frames, per-stage ms lists, per-frame render ms)."""
+def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stages=True,
+              kernel_times=False):
+    """Returns (seconds for `steps` frames, per-stage ms lists, per-kernel times).
+
+    With kernel_times the library records CUDA events around each of its kernel
+    launches on `stream` during the timed frames (adr_profile_enable)."""
     import torch
     for k in range(warmup):
         rast.forward(params, cams[k % len(cams)], st, stream=stream, want_aux=False)
     barrier(pg)
+    if kernel_times:
+        rast.profile(True)
+        rast.profile_read()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device="cuda")
@@ -197,18 +206,52 @@ def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stage
         stages = {"preprocess_scan_emit": [e[0].elapsed_time(e[1]) for e in ev],
                   "sort_ranges": [e[1].elapsed_time(e[2]) for e in ev],
                   "render": [e[2].elapsed_time(e[3]) for e in ev]}
-    return total, stages
+    kernels = None
+    if kernel_times:
+        kernels = rast.profile_read()
+        rast.profile(False)
+    return total, stages, kernels
 
 
 def frame_units(rast, params, cams, st, stream, count):
-    """Untimed: pairs P and sum over pixels of Gaussians evaluated, per frame."""
+    """Untimed, per frame: pairs P, Gaussians with tiles V, the sum over pixels
+    of Gaussians evaluated, and the sum over tiles of the list prefix Render
+    had to load (the longest pixel traversal in the tile, in whole batches of
+    256, capped at the list length)."""
     out = []
     for k in range(count):
         rast.forward(params, cams[k], st, stream=stream, want_aux=False)
         p = rast.num_pairs()
+        geom, rect, tiles = rast.read_gaussians(stream=stream)
+        v = int(np.count_nonzero(tiles))
         _, trav = rast.read_pixel_stats(stream=stream)
-        out.append((p, int(trav.astype(np.int64).sum())))
+        ranges = rast.read_ranges(stream=stream).astype(np.int64)
+        h, w = trav.shape
+        ty, tx = (h + 15) // 16, (w + 15) // 16
+        pad = np.zeros((ty * 16, tx * 16), np.int64)
+        pad[:h, :w] = trav
+        tmax = pad.reshape(ty, 16, tx, 16).max(axis=(1, 3)).reshape(-1)
+        length = ranges[:, 1] - ranges[:, 0]
+        loaded = np.minimum(length, ((tmax + 255) // 256) * 256)
+        out.append(dict(pairs=p, visible=v, evals=int(trav.astype(np.int64).sum()),
+                        loaded=int(loaded.sum())))
     return out
+
+
+def kernel_bytes(name, n, u, hw):
+    """Algorithmic DRAM bytes of one launch of each kernel (the data the
+    stage has to move; see the design notes for the derivation)."""
+    P, V = u["pairs"], u["visible"]
+    return {
+        "preprocess": 44 * n + 192 * V + 96 * n,   # params (+SH of kept) in, records out
+        "depth_hist": 4 * n,
+        "depth_pass": 16 * n,                      # key + value in and out
+        "scan_tiles": 12 * n + 8 * V,
+        "init_ranges": 8 * (hw // 256),
+        "tile_pass_first": 8 * P + 16 * V,         # generated pairs out (tile, Gaussian)
+        "tile_pass_last": 12 * P,                  # pairs in, Gaussian ids out
+        "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
+    }[name]
 
 
 def e2e_host(rast_ctx, scene, cams, st, steps, warmup):
@@ -261,7 +304,8 @@ def run_ours(args):
     rast.num_pairs()
 
     with ClockSampler(local) as clk:
-        t_adr, stages = time_mode(rast, params, cams, st_adr, args.steps, args.warmup, stream, pg)
+        t_adr, stages, kernels = time_mode(rast, params, cams, st_adr, args.steps, args.warmup,
+                                           stream, pg, kernel_times=True)
     clocks = clk.summary()
     status = rast.sync_status()
     if status != 0:
@@ -272,10 +316,10 @@ def run_ours(args):
             print(json.dumps({"workload": WORKLOAD, "fps": args.steps * world / t_adr,
                               "stages_ms": {k: statistics.mean(v) for k, v in stages.items()}}))
         return
-    t_plain, stages_plain = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
-                                      stream, pg)
-    t_circle, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
-                            with_stages=False)
+    t_plain, stages_plain, _ = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
+                                         stream, pg)
+    t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
+                               with_stages=False)
     t_adr = max_over_ranks(pg, t_adr)
     t_plain = max_over_ranks(pg, t_plain)
     t_circle = max_over_ranks(pg, t_circle)
@@ -287,16 +331,37 @@ def run_ours(args):
     ucams = [cams[(args.warmup + k) % len(cams)] for k in range(nu)]
     units_adr = frame_units(rast, params, ucams, st_adr, stream, nu)
     units_plain = frame_units(rast, params, ucams, st_plain, stream, nu)
-    render_ms = stages["render"][:nu]
-    evals = [u[1] for u in units_adr]
-    pairs = [u[0] for u in units_adr]
+    u_mean = {k: statistics.mean(u[k] for u in units_adr) for k in units_adr[0]}
     hbm_gbs, sm_max_mhz, peak_src = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = clocks.get("sm_mhz") or sm_max_mhz
-    alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12          # FP32 lane-ops per s, in T/s
-    alu_achieved = statistics.mean(e * EVAL_FP32_OPS / (ms / 1e3) for e, ms in zip(evals, render_ms)) / 1e12
-    render_bytes = [p * 52 + WIDTH * HEIGHT * 12 for p in pairs]
-    render_gbs = statistics.mean(b / (ms / 1e3) for b, ms in zip(render_bytes, render_ms)) / 1e9
+    hw = WIDTH * HEIGHT
+    # Per-kernel live timing from the library's events on the launch stream.
+    ktable = {}
+    for name, (ms, launches) in kernels.items():
+        per = ms / launches
+        b = kernel_bytes(name, N_GAUSS, u_mean, hw)
+        ktable[name] = {"launches": launches, "ms_per_launch": per,
+                        "share": ms / sum(v[0] for v in kernels.values()),
+                        "algorithmic_bytes": b, "gbs": b / (per / 1e3) / 1e9}
+    dominant = max(ktable, key=lambda k: ktable[k]["ms_per_launch"] * ktable[k]["launches"])
+    dk = ktable[dominant]
+    traffic = TRAFFIC_BYTES.get((WORKLOAD, dominant))
+    if dominant == "render":
+        alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
+        achieved = u_mean["evals"] * EVAL_FP32_OPS / (dk["ms_per_launch"] / 1e3) / 1e12
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                    "unit": "T FP32 lane-ops/s", "frac": achieved / alu_peak, "traffic": traffic,
+                    "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz"}
+    else:
+        roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["gbs"], "peak": hbm_gbs,
+                    "unit": "GB/s", "frac": dk["gbs"] / hbm_gbs, "traffic": traffic,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
+    render = ktable.get("render")
+    render_ms = render["ms_per_launch"] if render else float("nan")
+    alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
+    render_alu = u_mean["evals"] * EVAL_FP32_OPS / (render_ms / 1e3) / 1e12
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
     stage_ms_plain = {k: statistics.mean(v) for k, v in stages_plain.items()}
 
@@ -324,21 +389,21 @@ def run_ours(args):
         "speedup_vs_plain": t_plain / t_adr,
         "stages_ms": stage_ms,
         "stages_ms_plain": stage_ms_plain,
-        "pairs_per_frame": {"adr_aabb": statistics.mean(pairs),
-                            "plain": statistics.mean(u[0] for u in units_plain)},
-        "evals_per_frame": {"adr_aabb": statistics.mean(evals),
-                            "plain": statistics.mean(u[1] for u in units_plain)},
-        "roofline": {"kernel": "k_render", "bound": "alu", "achieved": alu_achieved,
-                     "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                     "frac": alu_achieved / alu_peak, "traffic": None,
-                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock under load)",
-                     "work": f"{EVAL_FP32_OPS} FP32 ops per Gaussian-pixel evaluation"},
-        "render_hbm": {"achieved_gbs": render_gbs, "peak_gbs": hbm_gbs,
-                       "frac": render_gbs / hbm_gbs, "peak_source": peak_src,
-                       "bytes": "52 B per tile-pair (record + index) + 12 B per pixel written"},
+        "pairs_per_frame": {"adr_aabb": u_mean["pairs"],
+                            "plain": statistics.mean(u["pairs"] for u in units_plain)},
+        "evals_per_frame": {"adr_aabb": u_mean["evals"],
+                            "plain": statistics.mean(u["evals"] for u in units_plain)},
+        "roofline": roofline,
+        "kernels": ktable,
+        "render_roofline": {"alu": {"achieved": render_alu, "peak": alu_peak,
+                                    "unit": "T FP32 lane-ops/s", "frac": render_alu / alu_peak,
+                                    "work": f"{EVAL_FP32_OPS} FP32 ops per Gaussian-pixel evaluation"},
+                            "hbm": {"achieved_gbs": render["gbs"] if render else None,
+                                    "peak_gbs": hbm_gbs,
+                                    "frac": (render["gbs"] / hbm_gbs) if render else None}},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
+        "gpu_launches": sum(v["launches"] for v in ktable.values()),
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

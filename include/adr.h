@@ -157,6 +157,19 @@ adr_status adr_read_ranges(adr_ctx *ctx, uint32_t *ranges, void *stream);
  * the pixel thread's serial load (Sec. 4.4). */
 adr_status adr_read_pixel_stats(adr_ctx *ctx, int32_t *last, int32_t *traversed, void *stream);
 
+/* Per-kernel timing (tracing).  While enabled, every kernel launch of the
+ * context is bracketed by CUDA events recorded on the launching stream (a
+ * few microseconds of host overhead per launch; the kernels themselves are
+ * unchanged).  adr_profile_read waits for the recorded launches, reports for
+ * each kernel that ran its id, summed device milliseconds and launch count
+ * (at most max_kernels entries; *num_kernels = entries written), and resets
+ * the record.  Names come from adr_profile_kernel_name.  Up to 8192 launches
+ * are kept between reads; later ones are not timed. */
+adr_status adr_profile_enable(adr_ctx *ctx, int32_t enable);
+adr_status adr_profile_read(adr_ctx *ctx, int32_t max_kernels, int32_t *kernel_ids,
+                            double *total_ms, int32_t *launches, int32_t *num_kernels);
+const char *adr_profile_kernel_name(int32_t kernel_id);
+
 /* Waits for the context's work and reports device-side flags as a status
  * (ADR_ERR_CAPACITY, ADR_ERR_TIMEOUT or ADR_OK); clears them.  SYNCHRONISES. */
 adr_status adr_sync_status(adr_ctx *ctx);

@@ -70,6 +70,9 @@ _SIGNATURES = {
                                ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
     "adr_render_frame_noalloc": (_I32, [_P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
                                         ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
+    "adr_profile_enable": (_I32, [_P, _I32]),
+    "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
     "adr_last_error": (ctypes.c_char_p, []),
     "adr_version": (ctypes.c_char_p, []),
 }
@@ -193,6 +196,24 @@ def adr_render_host(ctx, means, scales, rots, opac, sh, n, camera, settings, img
     return check(load().adr_render_host(ctx, means, scales, rots, opac, sh, n,
                                         ctypes.byref(camera), ctypes.byref(settings), img,
                                         t_final, load_, stream), "adr_render_host")
+
+
+def adr_profile_enable(ctx, enable):
+    return check(load().adr_profile_enable(ctx, 1 if enable else 0), "adr_profile_enable")
+
+
+def adr_profile_read(ctx, max_kernels=16):
+    """{kernel name: (total ms, launches)} since the last read."""
+    import numpy as np
+    ids = np.zeros(max_kernels, np.int32)
+    ms = np.zeros(max_kernels, np.float64)
+    cnt = np.zeros(max_kernels, np.int32)
+    k = _I32(0)
+    check(load().adr_profile_read(ctx, max_kernels, ids.ctypes.data, ms.ctypes.data,
+                                  cnt.ctypes.data, ctypes.byref(k)), "adr_profile_read")
+    lib = load()
+    return {lib.adr_profile_kernel_name(int(ids[i])).decode(): (float(ms[i]), int(cnt[i]))
+            for i in range(k.value)}
 
 
 def adr_version():

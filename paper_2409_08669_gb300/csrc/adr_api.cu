@@ -133,6 +133,11 @@ namespace {
 
 void free_ctx(adr_ctx* c) {
     Workspace& w = c->ws;
+    if (w.prof) {
+        for (int i = 0; i < w.prof->created; ++i) cudaEventDestroy(w.prof->ev[i]);
+        delete w.prof;
+        w.prof = nullptr;
+    }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
                     w.chunk_first, w.ranges, w.last, w.trav, w.hist, w.counters, w.status,
@@ -355,6 +360,51 @@ adr_status adr_read_pixel_stats(adr_ctx* c, int32_t* last, int32_t* traversed, v
         ADR_CUDA(cudaMemcpyAsync(traversed, c->ws.trav, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return ok();
 }
+
+adr_status adr_profile_enable(adr_ctx* c, int32_t enable) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    if (enable && !c->ws.prof) c->ws.prof = new Profiler();
+    if (!enable && c->ws.prof) {
+        ADR_CUDA(cudaDeviceSynchronize());
+        for (int i = 0; i < c->ws.prof->created; ++i) cudaEventDestroy(c->ws.prof->ev[i]);
+        delete c->ws.prof;
+        c->ws.prof = nullptr;
+    }
+    return ok();
+}
+
+adr_status adr_profile_read(adr_ctx* c, int32_t max_kernels, int32_t* kernel_ids, double* total_ms,
+                            int32_t* launches, int32_t* num_kernels) {
+    if (!c || !kernel_ids || !total_ms || !launches || !num_kernels)
+        return fail(ADR_ERR_INVALID, "NULL argument");
+    Profiler* p = c->ws.prof;
+    *num_kernels = 0;
+    if (!p) return fail(ADR_ERR_INVALID, "profiling is not enabled");
+    DeviceGuard guard(c->device);
+    double ms[kKernelCount] = {0};
+    int cnt[kKernelCount] = {0};
+    for (int i = 0; i < p->used; ++i) {
+        float t = 0.f;
+        ADR_CUDA(cudaEventSynchronize(p->ev[2 * i + 1]));
+        ADR_CUDA(cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]));
+        ms[p->id[i]] += t;
+        cnt[p->id[i]] += 1;
+    }
+    p->used = 0;
+    int k = 0;
+    for (int id = 0; id < kKernelCount && k < max_kernels; ++id) {
+        if (!cnt[id]) continue;
+        kernel_ids[k] = id;
+        total_ms[k] = ms[id];
+        launches[k] = cnt[id];
+        ++k;
+    }
+    *num_kernels = k;
+    return ok();
+}
+
+const char* adr_profile_kernel_name(int32_t kernel_id) { return kernel_name(kernel_id); }
 
 adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, const float* rots,
                            const float* opac, const float* sh, int64_t n, const adr_camera* camera,

@@ -66,6 +66,22 @@ enum Counter : int {
     kCntSlots = 16
 };
 
+// Optional per-launch timing with CUDA events recorded on the launching
+// stream (adr_profile_enable / adr_profile_read).
+enum KernelId : int {
+    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKInitRanges, kKTilePassFirst,
+    kKTilePassLast, kKRender, kKernelCount
+};
+const char* kernel_name(int id);
+struct Profiler {
+    static constexpr int kMaxEntries = 8192;
+    cudaEvent_t ev[2 * kMaxEntries];
+    int id[kMaxEntries];
+    int used = 0, created = 0;
+    void begin(int kernel, cudaStream_t s);
+    void end(cudaStream_t s);
+};
+
 // Device buffers one frame needs.  The context path allocates them with
 // cudaMalloc; the allocation-free path carves them out of a static array.
 struct Workspace {
@@ -91,6 +107,7 @@ struct Workspace {
     uint32_t* status = nullptr;            // [4]
     unsigned long long* lookback = nullptr;
     size_t lookback_words = 0;             // (max(max_n, capacity) / kSortChunk + 2) * kRadix
+    Profiler* prof = nullptr;              // non-null: time every launch
 };
 
 // hist layout: 4 x 256 depth digits, then 2 x 256 tile digits.

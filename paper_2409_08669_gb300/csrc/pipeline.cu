@@ -5,6 +5,37 @@
 
 namespace adr {
 
+const char* kernel_name(int id) {
+    static const char* names[kKernelCount] = {"preprocess", "depth_hist", "depth_pass",
+                                              "scan_tiles", "init_ranges", "tile_pass_first",
+                                              "tile_pass_last", "render"};
+    return (id >= 0 && id < kKernelCount) ? names[id] : "?";
+}
+
+void Profiler::begin(int kernel, cudaStream_t s) {
+    if (used >= kMaxEntries) return;
+    while (created < 2 * (used + 1)) {
+        if (cudaEventCreate(&ev[created]) != cudaSuccess) return;
+        ++created;
+    }
+    id[used] = kernel;
+    cudaEventRecord(ev[2 * used], s);
+}
+
+void Profiler::end(cudaStream_t s) {
+    if (used >= kMaxEntries || created < 2 * (used + 1)) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+}
+
+// Times one launch when the workspace has a profiler.
+#define TIMED(ws, kid, stream, launch)                      \
+    do {                                                    \
+        if ((ws).prof) (ws).prof->begin((kid), (stream));   \
+        launch;                                             \
+        if ((ws).prof) (ws).prof->end(stream);              \
+    } while (0)
+
 uint32_t next_epoch(std::atomic<uint32_t>& epoch, const Workspace& ws, cudaStream_t stream) {
     uint32_t e = epoch.fetch_add(1) + 1;
     if (e == 0) {
@@ -44,32 +75,38 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     cudaMemsetAsync(ws.counters, 0, kCntSlots * sizeof(uint32_t), stream);
     cudaMemsetAsync(ws.hist, 0, kHistWords * sizeof(uint32_t), stream);
     // Stage 1: per-Gaussian projection, covariance, colour and early cull.
-    launch_preprocess((int)n, means, scales, rots, opac, sh, fs.cam, fs.st, ws.rec, ws.aux,
-                      ws.depth_key, ws.tiles, ws.rect, stream);
+    TIMED(ws, kKPreprocess, stream,
+          launch_preprocess((int)n, means, scales, rots, opac, sh, fs.cam, fs.st, ws.rec, ws.aux,
+                            ws.depth_key, ws.tiles, ws.rect, stream));
     // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
     // carry key 0xFFFFFFFF and end up behind the V that have tiles.
-    launch_digit_hist(ws.depth_key, n, 0, kMaxPasses, ws.hist, ws.sm_count * 4, stream);
+    TIMED(ws, kKDepthHist, stream,
+          launch_digit_hist(ws.depth_key, n, 0, kMaxPasses, ws.hist, ws.sm_count * 4, stream));
     const uint32_t* kin = ws.depth_key;
     const uint32_t* vin = nullptr;
     for (int p = 0; p < kMaxPasses; ++p) {
-        launch_onesweep(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, 8,
-                        ws.hist + p * kRadix, ws.lookback, next_epoch(epoch, ws, stream),
-                        ws.counters + kCntSortTicket0 + p, ws.status, ws.sort_grid, stream);
+        const uint32_t ep = next_epoch(epoch, ws, stream);
+        TIMED(ws, kKDepthPass, stream,
+              launch_onesweep(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, 8,
+                              ws.hist + p * kRadix, ws.lookback, ep,
+                              ws.counters + kCntSortTicket0 + p, ws.status, ws.sort_grid, stream));
         kin = ws.gkeys[p & 1];
         vin = ws.gvals[p & 1];
     }
     fs.order = vin;
     // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
-    launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
-                      ws.offsets, ws.chunk_first, ws.hist + kMaxPasses * kRadix, ws.lookback,
-                      next_epoch(epoch, ws, stream), ws.counters, ws.status, ws.scan_grid, stream);
+    const uint32_t ep = next_epoch(epoch, ws, stream);
+    TIMED(ws, kKScanTiles, stream,
+          launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
+                            ws.offsets, ws.chunk_first, ws.hist + kMaxPasses * kRadix, ws.lookback,
+                            ep, ws.counters, ws.status, ws.scan_grid, stream));
 }
 
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream) {
     const int t0 = kCntSortTicket0 + kMaxPasses;
     cudaMemsetAsync(ws.counters + t0, 0, 2 * sizeof(uint32_t), stream);
-    launch_init_ranges(ws.ranges, fs.num_tiles, stream);
+    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, stream));
     PairSource src;
     src.order = fs.order;
     src.offsets = ws.offsets;
@@ -83,14 +120,18 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
         // Stages 3-5: emit + first tile digit, then (if needed) the second
         // digit, which also yields the per-tile ranges.
         const bool single = fs.tile_passes == 1;
-        launch_tile_pass_first(src, ws.ptile, ws.pgauss[0], fs.bits1, single, ws.ranges, hist_tiles,
-                               ws.lookback, next_epoch(epoch, ws, stream), ws.counters + t0,
-                               ws.status, ws.sort_grid, stream);
+        const uint32_t ep1 = next_epoch(epoch, ws, stream);
+        TIMED(ws, kKTilePassFirst, stream,
+              launch_tile_pass_first(src, ws.ptile, ws.pgauss[0], fs.bits1, single, ws.ranges,
+                                     hist_tiles, ws.lookback, ep1, ws.counters + t0, ws.status,
+                                     ws.sort_grid, stream));
         if (!single) {
-            launch_tile_pass_last(ws.ptile, ws.pgauss[0], ws.pgauss[1], ws.counters, ws.capacity,
-                                  fs.bits1, fs.bits2, ws.ranges, hist_tiles + kRadix, ws.lookback,
-                                  next_epoch(epoch, ws, stream), ws.counters + t0 + 1, ws.status,
-                                  ws.sort_grid, stream);
+            const uint32_t ep2 = next_epoch(epoch, ws, stream);
+            TIMED(ws, kKTilePassLast, stream,
+                  launch_tile_pass_last(ws.ptile, ws.pgauss[0], ws.pgauss[1], ws.counters,
+                                        ws.capacity, fs.bits1, fs.bits2, ws.ranges,
+                                        hist_tiles + kRadix, ws.lookback, ep2, ws.counters + t0 + 1,
+                                        ws.status, ws.sort_grid, stream));
         }
         fs.sorted_gauss = single ? ws.pgauss[0] : ws.pgauss[1];
     } else {
@@ -101,8 +142,9 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream) {
     // Stage 6.
-    launch_render(ws.ranges, fs.sorted_gauss, ws.rec, fs.cam, fs.st, img, t_final, load, ws.last,
-                  ws.trav, stream);
+    TIMED(ws, kKRender, stream,
+          launch_render(ws.ranges, fs.sorted_gauss, ws.rec, fs.cam, fs.st, img, t_final, load,
+                        ws.last, ws.trav, stream));
 }
 
 }  // namespace adr

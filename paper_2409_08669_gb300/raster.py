@@ -125,5 +125,11 @@ class Rasterizer:
         torch.cuda.synchronize(self.device)
         return last.cpu().numpy(), trav.cpu().numpy()
 
+    def profile(self, enable: bool):
+        _lib.adr_profile_enable(self.ctx, enable)
+
+    def profile_read(self):
+        return _lib.adr_profile_read(self.ctx)
+
     def sync_status(self):
         return _lib.adr_sync_status(self.ctx)
