@@ -138,7 +138,7 @@ void free_ctx(adr_ctx* c) {
         delete w.prof;
         w.prof = nullptr;
     }
-    void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.gkeys[0],
+    void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
                     w.chunk_first, w.ranges, w.last, w.trav, w.hist, w.counters, w.status,
                     w.lookback, c->stage, c->stage_img, c->stage_load};
@@ -207,6 +207,7 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     ALLOC(w.tiles, N * sizeof(uint32_t));
     ALLOC(w.rect, N * sizeof(ushort4));
     ALLOC(w.offsets, N * sizeof(uint32_t));
+    ALLOC(w.sorted_box, N * sizeof(uint32_t));
     for (int b = 0; b < 2; ++b) {
         ALLOC(w.gkeys[b], N * sizeof(uint32_t));
         ALLOC(w.gvals[b], N * sizeof(uint32_t));

@@ -94,6 +94,7 @@ struct Workspace {
     uint32_t* tiles = nullptr;             // [max_n]
     ushort4* rect = nullptr;               // [max_n]
     uint32_t* offsets = nullptr;           // [max_n]
+    uint32_t* sorted_box = nullptr;        // [max_n] packed tile rectangle per depth-order position
     uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* ptile = nullptr;             // [capacity]  pair tiles after the first tile pass
@@ -157,7 +158,7 @@ void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t*
 struct PairSource {
     const uint32_t* order = nullptr;       // Gaussians by depth
     const uint32_t* offsets = nullptr;     // exclusive scan of their tile counts
-    const ushort4* rect = nullptr;         // tile rectangle per Gaussian index
+    const uint32_t* sorted_box = nullptr;  // packed rectangle per depth-order position
     const uint32_t* chunk_first = nullptr; // sorted position holding each chunk's first pair
     const uint32_t* counters = nullptr;    // kCntPairs, kCntVisible
     int64_t capacity = 0;
@@ -179,16 +180,20 @@ void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, ui
                            uint32_t epoch, uint32_t* ticket, uint32_t* status, int grid,
                            cudaStream_t stream);
 
+// Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
+// coordinates and extents fit 8 bits because images are at most 4096 pixels
+// per side).
 // Exclusive scan of tiles[order[i]] with decoupled lookback.  Also writes the
+// packed rectangle of each depth-order position with tiles (sorted_box), the
 // pair total and visible count to counters, the tile-digit histograms of the
 // two tile passes (hist_tiles[0..255] low digit of bits1 bits, [256..511]
 // high digit) and chunk_first[c] = position of the Gaussian holding pair
 // c * kSortChunk.
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
                        int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
-                       uint32_t* chunk_first, uint32_t* hist_tiles, unsigned long long* lookback,
-                       uint32_t epoch, uint32_t* counters, uint32_t* status, int grid,
-                       cudaStream_t stream);
+                       uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
+                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
+                       uint32_t* status, int grid, cudaStream_t stream);
 
 void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
 

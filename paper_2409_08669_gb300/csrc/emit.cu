@@ -28,7 +28,8 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
              const ushort4* __restrict__ rect, int64_t n, int tiles_x, int bits1,
-             int64_t capacity, uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
+             int64_t capacity, uint32_t* __restrict__ offsets, uint32_t* __restrict__ sorted_box,
+             uint32_t* __restrict__ chunk_first,
              uint32_t* __restrict__ hist_tiles, unsigned long long* __restrict__ lookback,
              uint32_t epoch, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -126,6 +127,8 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
                 // digit histograms of this Gaussian's pairs, row by row
                 const ushort4 r = rect[order[i]];
                 const uint32_t w = (uint32_t)(r.z - r.x);
+                sorted_box[i] = (uint32_t)r.x | ((uint32_t)r.y << 8) | ((w - 1u) << 16) |
+                                ((uint32_t)(r.w - r.y - 1) << 24);
                 for (uint32_t ty = r.y; ty < r.w; ++ty) {
                     const uint32_t a0 = ty * (uint32_t)tiles_x + r.x;   // tile ids a0 .. a0+w-1
                     my_full += w >> bits1;
@@ -229,13 +232,13 @@ int scan_blocks_per_sm() {
 
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
                        int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
-                       uint32_t* chunk_first, uint32_t* hist_tiles, unsigned long long* lookback,
-                       uint32_t epoch, uint32_t* counters, uint32_t* status, int grid,
-                       cudaStream_t stream) {
+                       uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
+                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
+                       uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
     k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, tiles_x, bits1, capacity,
-                                                    offsets, chunk_first, hist_tiles, lookback,
-                                                    epoch, counters, status);
+                                                    offsets, sorted_box, chunk_first, hist_tiles,
+                                                    lookback, epoch, counters, status);
 }
 
 void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream) {

@@ -39,7 +39,8 @@ constexpr size_t kOffDepth = align256(kOffAux + kNaMaxGaussians * kAuxFloat4 * 1
 constexpr size_t kOffTiles = align256(kOffDepth + kNaMaxGaussians * 4);
 constexpr size_t kOffRect = align256(kOffTiles + kNaMaxGaussians * 4);
 constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
-constexpr size_t kOffGKeys = align256(kOffOffsets + kNaMaxGaussians * 4);     // 2 buffers
+constexpr size_t kOffSortedBox = align256(kOffOffsets + kNaMaxGaussians * 4);
+constexpr size_t kOffGKeys = align256(kOffSortedBox + kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffPTile = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
 constexpr size_t kOffPGauss = align256(kOffPTile + kNaMaxPairs * 4);          // 2 buffers
@@ -95,6 +96,7 @@ adr_status setup(int dev, DeviceState*& out) {
         w.tiles = reinterpret_cast<uint32_t*>(b + kOffTiles);
         w.rect = reinterpret_cast<ushort4*>(b + kOffRect);
         w.offsets = reinterpret_cast<uint32_t*>(b + kOffOffsets);
+        w.sorted_box = reinterpret_cast<uint32_t*>(b + kOffSortedBox);
         for (int k = 0; k < 2; ++k) {
             w.gkeys[k] = reinterpret_cast<uint32_t*>(b + kOffGKeys) + k * kNaMaxGaussians;
             w.gvals[k] = reinterpret_cast<uint32_t*>(b + kOffGVals) + k * kNaMaxGaussians;

@@ -98,8 +98,9 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     const uint32_t ep = next_epoch(epoch, ws, stream);
     TIMED(ws, kKScanTiles, stream,
           launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
-                            ws.offsets, ws.chunk_first, ws.hist + kMaxPasses * kRadix, ws.lookback,
-                            ep, ws.counters, ws.status, ws.scan_grid, stream));
+                            ws.offsets, ws.sorted_box, ws.chunk_first,
+                            ws.hist + kMaxPasses * kRadix, ws.lookback, ep, ws.counters,
+                            ws.status, ws.scan_grid, stream));
 }
 
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
@@ -110,7 +111,7 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
     PairSource src;
     src.order = fs.order;
     src.offsets = ws.offsets;
-    src.rect = ws.rect;
+    src.sorted_box = ws.sorted_box;
     src.chunk_first = ws.chunk_first;
     src.counters = ws.counters;
     src.capacity = ws.capacity;

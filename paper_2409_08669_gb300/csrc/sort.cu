@@ -17,6 +17,8 @@
 // counter, so any chunk a CTA waits on is already held by a running CTA.
 // Every wait is bounded; on expiry the kernel raises kErrLookback and goes on
 // with a wrong but in-bounds placement instead of hanging.
+#include <cstddef>
+
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -31,17 +33,19 @@ constexpr uint32_t kCountMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxChunkGauss = kSortChunk + 1;   // every listed Gaussian has >= 1 pair
+constexpr int kStageLen = (kMaxChunkGauss + 3) & ~3;   // keeps the arrays after it 16-byte aligned
 
-struct SortShared {
+struct alignas(16) SortShared {
     union {
         struct {
             uint32_t keys[kSortChunk];
             uint32_t vals[kSortChunk];
         } kv;
         struct {                      // Gaussians overlapping one pair chunk
-            uint32_t off[kMaxChunkGauss];
-            uint32_t gid[kMaxChunkGauss];
-            uint32_t box[kMaxChunkGauss];   // x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24
+            uint32_t off[kStageLen];
+            uint32_t gid[kStageLen];
+            uint32_t box[kStageLen];        // x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24
+            alignas(16) uint16_t map[kSortChunk];   // chunk slot -> staged Gaussian holding it
         } stage;
     } u;
     uint32_t warp_cnt[kWarps][kRadix + 1];   // +1: out-of-range items of the tail chunk
@@ -52,6 +56,8 @@ struct SortShared {
     uint32_t chunk;
 };
 constexpr size_t kSortSmem = sizeof(SortShared);
+static_assert(offsetof(SortShared, u) % 16 == 0, "staging must be 16-byte aligned");
+static_assert((3 * kStageLen * sizeof(uint32_t)) % 16 == 0, "map must be 16-byte aligned");
 
 struct SweepArgs {
     const uint32_t* keys_in;
@@ -120,55 +126,74 @@ __device__ __forceinline__ void generate_pairs(const SweepArgs& a, SortShared& s
         if (i1 < i0) i1 = i0;
     }
     const int G = (int)(i1 - i0 + 1);
-    for (int j = tid; j < G; j += kSortThreads) {
+    uint32_t* map32 = reinterpret_cast<uint32_t*>(sm.u.stage.map);
+    for (int x = tid; x < kSortChunk / 2; x += kSortThreads) map32[x] = 0u;
+    for (int j = tid; j < G; j += kSortThreads) {   // coalesced staging
         const uint32_t i = i0 + j;
-        const uint32_t g = src.order[i];
-        const ushort4 r = src.rect[g];
         sm.u.stage.off[j] = src.offsets[i];
-        sm.u.stage.gid[j] = g;
-        sm.u.stage.box[j] = (uint32_t)r.x | ((uint32_t)r.y << 8) |
-                            ((uint32_t)(r.z - r.x - 1) << 16) | ((uint32_t)(r.w - r.y - 1) << 24);
+        sm.u.stage.gid[j] = src.order[i];
+        sm.u.stage.box[j] = src.sorted_box[i];
     }
     __syncthreads();
-    // Warp w produces items w*512 + q*32 + lane (q = 0..15), i.e. directly in
-    // the warp-striped order the ranking needs.  A warp-uniform cursor j holds
-    // the Gaussian of the step's first item; 32 consecutive items lie within
-    // Gaussians j .. j+31, so each lane searches only that window.
-    const int wfirst = warp * (kSortItems * 32);
-    int j = 0;
-    if (wfirst < count) {
-        const uint32_t p0 = (uint32_t)(base + wfirst);
-        int lo = 0, hi = G - 1;   // largest j with off[j] <= p0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sm.u.stage.off[mid] <= p0) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
+    // Mark the slot where each staged Gaussian's first pair falls (slot 0
+    // belongs to staged Gaussian 0, the holder of the chunk's first pair).
+    for (int j = tid; j < G; j += kSortThreads) {
+        const int64_t slot = (int64_t)sm.u.stage.off[j] - base;
+        if (slot > 0 && slot < count) sm.u.stage.map[slot] = (uint16_t)j;
     }
+    __syncthreads();
+    // Running maximum over the slots: thread t owns slots 16t .. 16t+15, then
+    // a block-wide exclusive max-scan of the thread maxima.
+    {
+        uint4* m4 = reinterpret_cast<uint4*>(sm.u.stage.map) + 2 * tid;
+        const uint4 a = m4[0], b = m4[1];
+        const uint32_t w32[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t tmax = 0;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) tmax = max(tmax, max(w32[x] & 0xFFFFu, w32[x] >> 16));
+        uint32_t incl = tmax;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = 0;
+        if (lane == 31) sm.wsum[warp] = incl;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) excl = max(excl, sm.wsum[w]);
+        uint32_t run = excl, out[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const uint32_t lo = run = max(run, w32[x] & 0xFFFFu);
+            const uint32_t hi = run = max(run, w32[x] >> 16);
+            out[x] = lo | (hi << 16);
+        }
+        m4[0] = make_uint4(out[0], out[1], out[2], out[3]);
+        m4[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    }
+    __syncthreads();
+    // Warp w produces items w*512 + q*32 + lane, the warp-striped order the
+    // ranking needs.  k / w is exact through a reciprocal biased up by 2^-20:
+    // k < 2^16 and w <= 256 keep the product within (q, q + 1).
+    const int wfirst = warp * (kSortItems * 32);
 #pragma unroll
     for (int q = 0; q < kSortItems; ++q) {
         const int s = wfirst + q * 32 + lane;
-        int jj = j;
         if (s < count) {
-            const uint32_t p = (uint32_t)(base + s);
-            int lo = j, hi = min(G - 1, j + 32);
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sm.u.stage.off[mid] <= p) lo = mid; else hi = mid - 1;
-            }
-            jj = lo;
+            const int jj = sm.u.stage.map[s];
             const uint32_t box = sm.u.stage.box[jj];
-            const uint32_t w = ((box >> 16) & 0xFF) + 1;
-            const uint32_t k = p - sm.u.stage.off[jj];
-            const uint32_t dy = k / w, dx = k - dy * w;
-            key[q] = (((box >> 8) & 0xFF) + dy) * (uint32_t)src.tiles_x + (box & 0xFF) + dx;
+            const uint32_t w = ((box >> 16) & 0xFFu) + 1u;
+            const uint32_t k = (uint32_t)(base + s) - sm.u.stage.off[jj];
+            const float r = __frcp_rn((float)w) * 1.00000095367431640625f;   // (1 + 2^-20) / w
+            const uint32_t dy = (uint32_t)((float)k * r);
+            const uint32_t dx = k - dy * w;
+            key[q] = (((box >> 8) & 0xFFu) + dy) * (uint32_t)src.tiles_x + (box & 0xFFu) + dx;
             val[q] = sm.u.stage.gid[jj];
         } else {
             key[q] = 0xFFFFFFFFu;
             val[q] = 0u;
         }
-        // next step starts at or after the last lane's Gaussian (items ascend)
-        j = __reduce_max_sync(0xffffffffu, (unsigned)jj);
     }
 }
 
