@@ -57,9 +57,10 @@ def select_workload(name):
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
-# DRAM bytes (read + write) per launch from an ncu capture of the kernel,
-# scaled to the full workload (see profiles/); None until one is taken.
-TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per Gaussian-tile pair from an ncu capture of the
+# tile passes on the heavy-load 600k workload (P = 25.8M; profiles/
+# tile_passes_heavy-600k-1080p.md), scaled to a launch by the measured P.
+TRAFFIC_BYTES_PER_PAIR = {"tile_pass_first": 215.57e6 / 25.81e6, "tile_pass_last": 354.68e6 / 25.81e6}
 
 
 def peaks():
@@ -346,7 +347,8 @@ def run_ours(args):
                         "algorithmic_bytes": b, "gbs": b / (per / 1e3) / 1e9}
     dominant = max(ktable, key=lambda k: ktable[k]["ms_per_launch"] * ktable[k]["launches"])
     dk = ktable[dominant]
-    traffic = TRAFFIC_BYTES.get((WORKLOAD, dominant))
+    tpp = TRAFFIC_BYTES_PER_PAIR.get(dominant)
+    traffic = tpp * u_mean["pairs"] if tpp else None
     if dominant == "render":
         alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
         achieved = u_mean["evals"] * EVAL_FP32_OPS / (dk["ms_per_launch"] / 1e3) / 1e12
