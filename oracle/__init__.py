@@ -91,7 +91,8 @@ def preprocess(scene, camera, settings, tol_rel: float = 1e-6):
     early cull selected by `settings.mode`.  Returns a dict of per-Gaussian arrays."""
     lib = _load()
     n = scene.n
-    means, scales, rots, opac, sh = (_c(a, np.float32) for a in scene.arrays())
+    # float32 inputs promote exactly; float64 inputs (finite differences) pass through
+    means, scales, rots, opac, sh = (_c(a, np.float64) for a in scene.arrays())
     cam = _c(camera.record(), np.float32)
     geom = np.zeros((n, GEOM), np.float64)
     depth = np.zeros(n, np.float32)

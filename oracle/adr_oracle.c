@@ -145,7 +145,7 @@ double orc_real_sh(int l, int m, const double d[3])
 }
 
 /* rgb = max(0, sum_k sh_k Y_k(d) + 0.5), d = normalise(X0 - cam_pos). */
-static void sh_colour(const float *sh /*[16][3]*/, int degree, const double X0[3],
+static void sh_colour(const double *sh /*[16][3]*/, int degree, const double X0[3],
                       const double cam[3], double rgb[3])
 {
     double d[3] = {X0[0] - cam[0], X0[1] - cam[1], X0[2] - cam[2]};
@@ -156,7 +156,7 @@ static void sh_colour(const float *sh /*[16][3]*/, int degree, const double X0[3
         for (int m = -l; m <= l; ++m) {
             double y = orc_real_sh(l, m, d);
             int k = l * l + l + m;
-            for (int c = 0; c < 3; ++c) acc[c] += (double)sh[k * 3 + c] * y;
+            for (int c = 0; c < 3; ++c) acc[c] += sh[k * 3 + c] * y;
         }
     for (int c = 0; c < 3; ++c) rgb[c] = fmax(0.0, acc[c] + 0.5);
 }
@@ -226,8 +226,8 @@ static int interval_fragile(double c, double r, int size, double tol_rel)
  *   flags[i]                F_VISIBLE | F_NEAR
  * Returns the number of pairs sum(tiles).
  */
-int64_t orc_preprocess(int64_t n, const float *means, const float *scales, const float *rots,
-                       const float *opac, const float *sh, int sh_degree,
+int64_t orc_preprocess(int64_t n, const double *means, const double *scales, const double *rots,
+                       const double *opac, const double *sh, int sh_degree,
                        const float *cam, int width, int height,
                        int mode, double alpha_low, double lowpass, double jac_clamp,
                        double tol_rel,
@@ -255,8 +255,9 @@ int64_t orc_preprocess(int64_t n, const float *means, const float *scales, const
         rgb[i * 3 + 0] = rgb[i * 3 + 1] = rgb[i * 3 + 2] = 0.0;
         flags[i] = 0;
 
-        /* Sort depth: float32, fixed order, no contraction. */
-        float xf = means[i * 3 + 0], yf = means[i * 3 + 1], zf = means[i * 3 + 2];
+        /* Sort depth: float32, fixed order, no contraction (the inputs are
+         * float32 values carried in doubles; the conversion is exact). */
+        float xf = (float)means[i * 3 + 0], yf = (float)means[i * 3 + 1], zf = (float)means[i * 3 + 2];
         float d32 = cam[8] * xf;
         d32 = d32 + cam[9] * yf;
         d32 = d32 + cam[10] * zf;
