@@ -126,6 +126,30 @@ adr_status adr_sort(adr_ctx *ctx, void *stream);
  *   load [H,W] int32 Gaussians blended per pixel, l_i of Eq. 12 (may be NULL). */
 adr_status adr_render(adr_ctx *ctx, float *img, float *t_final, int32_t *load, void *stream);
 
+/* Backward of the last adr_render (the differentiable path the paper trains
+ * through, Sec. 4.4 total loss): given dL/dimg [3,H,W] and optionally
+ * dL/dload [H,W] (the straight-through reading of Eq. 12: d l_i / d alpha_ik = 1
+ * for every blended pair; may be NULL), writes dL/d means [n,3], scales [n,3],
+ * rots [n,4] (w,x,y,z; 16-byte aligned), opac [n] and sh [n,16,3] (coefficients
+ * above sh_degree get 0).  The parameter arrays must be the ones passed to
+ * adr_preprocess for this frame, unchanged.  Gradient buffers are overwritten.
+ * Per tile, each pixel walks its blended Gaussians back to front recovering
+ * T_k = T_{k+1}/(1-alpha_k); contributions are warp-reduced and then added to
+ * per-Gaussian accumulators with atomics (summation order varies run to run). */
+adr_status adr_render_backward(adr_ctx *ctx, const float *means, const float *scales,
+                               const float *rots, const float *opac, const float *sh,
+                               const float *dl_dimg, const float *dl_dload, float *g_means,
+                               float *g_scales, float *g_rots, float *g_opac, float *g_sh,
+                               void *stream);
+
+/* Load-balancing loss (Sec. 4.4, Eq. 13): L_load = std over the hw pixels of
+ * load (int32, population standard deviation).  Writes stats[0] = mean,
+ * stats[1] = std (device doubles) and, if dl_dload is non-NULL, the gradient
+ * weight * dL_load/dl_i = weight * (l_i - mean) / (hw * std) (0 if std = 0),
+ * ready to pass to adr_render_backward. */
+adr_status adr_load_loss(adr_ctx *ctx, const int32_t *load, int64_t hw, float weight,
+                         double *stats, float *dl_dload, void *stream);
+
 /* Waits for the context's last stream and returns the pair count P (the sum
  * of tiles over Gaussians, which may exceed pair_capacity).  Returns
  * ADR_ERR_CAPACITY if P > pair_capacity, ADR_ERR_TIMEOUT if a bounded device

@@ -70,6 +70,8 @@ _SIGNATURES = {
                                ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
     "adr_render_frame_noalloc": (_I32, [_P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
                                         ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
+    "adr_render_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "adr_load_loss": (_I32, [_P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "adr_profile_enable": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -196,6 +198,18 @@ def adr_render_host(ctx, means, scales, rots, opac, sh, n, camera, settings, img
     return check(load().adr_render_host(ctx, means, scales, rots, opac, sh, n,
                                         ctypes.byref(camera), ctypes.byref(settings), img,
                                         t_final, load_, stream), "adr_render_host")
+
+
+def adr_render_backward(ctx, means, scales, rots, opac, sh, dl_dimg, dl_dload, g_means, g_scales,
+                        g_rots, g_opac, g_sh, stream):
+    return check(load().adr_render_backward(ctx, means, scales, rots, opac, sh, dl_dimg, dl_dload,
+                                            g_means, g_scales, g_rots, g_opac, g_sh, stream),
+                 "adr_render_backward")
+
+
+def adr_load_loss(ctx, load_, hw, weight, stats, dl_dload, stream):
+    return check(load().adr_load_loss(ctx, load_, hw, weight, stats, dl_dload, stream),
+                 "adr_load_loss")
 
 
 def adr_profile_enable(ctx, enable):

@@ -140,7 +140,8 @@ void free_ctx(adr_ctx* c) {
     }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
-                    w.chunk_first, w.ranges, w.last, w.trav, w.hist, w.counters, w.status,
+                    w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
+                    w.hist, w.counters, w.status,
                     w.lookback, c->stage, c->stage_img, c->stage_load};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -218,6 +219,9 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     ALLOC(w.ranges, (size_t)w.max_tiles * sizeof(uint2));
     ALLOC(w.last, pixels * sizeof(int32_t));
     ALLOC(w.trav, pixels * sizeof(int32_t));
+    ALLOC(w.tfin, pixels * sizeof(float));
+    ALLOC(w.g2d, N * 9 * sizeof(float));
+    ALLOC(w.load_sums, 4 * sizeof(double));
     ALLOC(w.hist, kHistWords * sizeof(uint32_t));
     ALLOC(w.counters, kCntSlots * sizeof(uint32_t));
     ALLOC(w.status, sizeof(uint32_t) * 4);
@@ -360,6 +364,41 @@ adr_status adr_read_pixel_stats(adr_ctx* c, int32_t* last, int32_t* traversed, v
     if (traversed)
         ADR_CUDA(cudaMemcpyAsync(traversed, c->ws.trav, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return ok();
+}
+
+adr_status adr_render_backward(adr_ctx* c, const float* means, const float* scales,
+                               const float* rots, const float* opac, const float* sh,
+                               const float* dl_dimg, const float* dl_dload, float* g_means,
+                               float* g_scales, float* g_rots, float* g_opac, float* g_sh,
+                               void* stream) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (!c->have_render) return fail(ADR_ERR_INVALID, "adr_render_backward before adr_render");
+    adr_status s;
+    if ((s = check_params(means, scales, rots, opac, sh, c->fs.n, c->ws.max_n)) != ADR_OK) return s;
+    if (!dl_dimg) return fail(ADR_ERR_INVALID, "dl_dimg is NULL");
+    if (c->fs.n > 0 && (!g_means || !g_scales || !g_rots || !g_opac || !g_sh))
+        return fail(ADR_ERR_INVALID, "a gradient output pointer is NULL");
+    if (c->fs.n > 0 && !aligned(g_rots, 16))
+        return fail(ADR_ERR_INVALID, "g_rots must be 16-byte aligned");
+    DeviceGuard guard(c->device);
+    cudaStream_t strm = (cudaStream_t)stream;
+    c->last_stream = strm;
+    enqueue_backward(c->ws, c->fs, means, scales, rots, opac, sh, dl_dimg, dl_dload, g_means,
+                     g_scales, g_rots, g_opac, g_sh, strm);
+    return check_launch("adr_render_backward") == ADR_OK ? ok() : ADR_ERR_CUDA;
+}
+
+adr_status adr_load_loss(adr_ctx* c, const int32_t* load, int64_t hw, float weight,
+                         double* stats, float* dl_dload, void* stream) {
+    if (!c || !load || !stats) return fail(ADR_ERR_INVALID, "NULL argument");
+    if (hw <= 0) return fail(ADR_ERR_INVALID, "hw must be positive");
+    DeviceGuard guard(c->device);
+    cudaStream_t strm = (cudaStream_t)stream;
+    c->last_stream = strm;
+    launch_load_loss(load, hw, c->ws.load_sums, weight, dl_dload, c->ws.sm_count, strm);
+    ADR_CUDA(cudaMemcpyAsync(stats, c->ws.load_sums + 2, 2 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, strm));
+    return check_launch("adr_load_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
 }
 
 adr_status adr_profile_enable(adr_ctx* c, int32_t enable) {

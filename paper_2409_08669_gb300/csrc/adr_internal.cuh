@@ -70,7 +70,7 @@ enum Counter : int {
 // stream (adr_profile_enable / adr_profile_read).
 enum KernelId : int {
     kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKInitRanges, kKTilePassFirst,
-    kKTilePassLast, kKRender, kKernelCount
+    kKTilePassLast, kKRender, kKRenderBackward, kKPreprocessBackward, kKernelCount
 };
 const char* kernel_name(int id);
 struct Profiler {
@@ -103,6 +103,9 @@ struct Workspace {
     uint2* ranges = nullptr;               // [max_tiles]
     int32_t* last = nullptr;               // [max pixels]
     int32_t* trav = nullptr;               // [max pixels]
+    float* tfin = nullptr;                 // [max pixels] final transmittance of the last render
+    float* g2d = nullptr;                  // [max_n * 9] backward: dL/d(px, py, conic, sigma, rgb)
+    double* load_sums = nullptr;           // [4] load-balancing loss moments
     uint32_t* hist = nullptr;              // [kHistWords]
     uint32_t* counters = nullptr;          // [kCntSlots]
     uint32_t* status = nullptr;            // [4]
@@ -199,7 +202,24 @@ void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, int32_t* trav, cudaStream_t stream);
+                   int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream);
+
+// Backward (backward.cu).
+void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
+                            const float4* aux, const CamDev& cam, const SetDev& st,
+                            const int32_t* last, const float* t_final, const float* dl_dimg,
+                            const float* dl_dload, float* g2d, cudaStream_t stream);
+void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
+                                const float* opac, const float* sh, const CamDev& cam,
+                                const SetDev& st, const uint32_t* tiles, const float4* aux,
+                                const float* g2d, float* g_means, float* g_scales, float* g_rots,
+                                float* g_opac, float* g_sh, cudaStream_t stream);
+void launch_load_loss(const int32_t* load, int64_t hw, double* sums, float weight, float* dl_dload,
+                      int sm_count, cudaStream_t stream);
+void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,
+                      const float* scales, const float* rots, const float* opac, const float* sh,
+                      const float* dl_dimg, const float* dl_dload, float* g_means, float* g_scales,
+                      float* g_rots, float* g_opac, float* g_sh, cudaStream_t stream);
 
 // Inspection: sorted pairs as (tile << 32 | depth bits, Gaussian) from the ranges.
 void launch_pair_keys(const uint2* ranges, int num_tiles, const uint32_t* sorted_gauss,

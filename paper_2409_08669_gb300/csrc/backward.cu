@@ -1,0 +1,413 @@
+// Backward pass of the rasterization path (the differentiable form the
+// paper trains through, Sec. 4.4 total loss): gradients of a loss on the
+// rendered image (and, through the straight-through reading of Eq. 12, on
+// the per-pixel load) with respect to every Gaussian parameter.
+//
+//   k_render_backward     per tile, walks each pixel's blended Gaussians from
+//                         back to front, recovering T_k = T_{k+1} / (1 - alpha_k),
+//                         and accumulates dL/d(px, py, conic, sigma, rgb);
+//                         warp-reduced, then atomicAdd into 9 floats per Gaussian.
+//   k_preprocess_backward chain rule from those 2D quantities to means, scales,
+//                         rotations, opacities and SH coefficients.
+//   k_load_moments / k_load_grad
+//                         L_load = std over pixels of l_i (Eq. 13, population
+//                         form) and dL_load/dl_i = (l_i - mean) / (HW std).
+#include "adr_internal.cuh"
+
+namespace adr {
+namespace {
+
+constexpr int kBwdThreads = kTilePixels;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kBwdThreads)
+k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
+                  const float4* __restrict__ rec, const float4* __restrict__ aux, CamDev cam,
+                  SetDev st, const int32_t* __restrict__ last_pos, const float* __restrict__ t_final,
+                  const float* __restrict__ dl_dimg, const float* __restrict__ dl_dload,
+                  float* __restrict__ g2d) {
+    __shared__ float2 s_xy[kBwdThreads];
+    __shared__ float4 s_w[kBwdThreads];
+    __shared__ float4 s_c[kBwdThreads];
+    __shared__ float4 s_conic[kBwdThreads];   // conic a, b, c, sigma
+    __shared__ uint32_t s_g[kBwdThreads];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int x = tx * kTile + lx, y = ty * kTile + ly;
+    const bool inside = x < cam.width && y < cam.height;
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const float fx = (float)lx, fy = (float)ly;
+    const size_t hw = (size_t)cam.width * cam.height;
+    const size_t pix = inside ? (size_t)y * cam.width + x : 0;
+
+    const uint2 range = ranges[tile];
+    int32_t last = inside ? last_pos[pix] : 0;          // 1-based position of the last blend
+    float T = inside ? t_final[pix] : 1.f;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, gl = 0.f;
+    if (inside) {
+        g0 = dl_dimg[pix];
+        g1 = dl_dimg[hw + pix];
+        g2 = dl_dimg[2 * hw + pix];
+        if (dl_dload) gl = dl_dload[pix];
+    }
+    float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];   // colour behind the current Gaussian
+    const float alpha_low = st.alpha_low;
+
+    if (range.x < range.y) {
+        // The longest prefix any pixel of the tile needs.
+        int max_last = last;
+        max_last = __reduce_max_sync(0xffffffffu, max_last);
+        __shared__ int s_max[kBwdThreads / 32];
+        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = max_last;
+        __syncthreads();
+        int tile_last = 0;
+        for (int w = 0; w < kBwdThreads / 32; ++w) tile_last = max(tile_last, s_max[w]);
+        // Batches of 256 list positions, from the back.
+        for (int bend = tile_last; bend > 0; bend -= kBwdThreads) {
+            const int bstart = max(0, bend - kBwdThreads);
+            __syncthreads();
+            const int pos = bstart + threadIdx.x;
+            if (pos < bend) {
+                const uint32_t g = sorted_gauss[range.x + pos];
+                const float4 r0 = rec[3 * (size_t)g + 0];
+                s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
+                                                __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
+                s_w[threadIdx.x] = rec[3 * (size_t)g + 1];
+                s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
+                s_conic[threadIdx.x] = aux[2 * (size_t)g + 0];
+                s_g[threadIdx.x] = g;
+            }
+            __syncthreads();
+            for (int p = bend - 1; p >= bstart; --p) {
+                const int j = p - bstart;
+                bool contrib = false;
+                float d_px = 0.f, d_py = 0.f, d_ca = 0.f, d_cb = 0.f, d_cc = 0.f, d_sig = 0.f;
+                float d_r = 0.f, d_g = 0.f, d_b = 0.f;
+                if (p < last) {
+                    // Same evaluation as the forward pass, so the same skip decision.
+                    const float2 c = s_xy[j];
+                    const float4 w = s_w[j];
+                    const float4 col = s_c[j];
+                    const float dx = c.x - fx, dy = c.y - fy;
+                    const float u1 = fmaf(w.x, dx, w.y * dy);
+                    const float u2 = fmaf(w.z, dx, w.w * dy);
+                    const float raw = exp2f(fmaf(-u1, u1, fmaf(-u2, u2, col.w)));
+                    const float alpha = fminf(0.99f, raw);
+                    if (alpha >= alpha_low) {
+                        contrib = true;
+                        const float one_m = 1.f - alpha;
+                        T = T / one_m;                                    // T before this blend
+                        const float wgt = alpha * T;
+                        d_r = wgt * g0;
+                        d_g = wgt * g1;
+                        d_b = wgt * g2;
+                        float dalpha = T * ((col.x - acc0) * g0 + (col.y - acc1) * g1 + (col.z - acc2) * g2);
+                        dalpha += gl;                                     // straight-through load term
+                        acc0 = fmaf(col.x, alpha, one_m * acc0);
+                        acc1 = fmaf(col.y, alpha, one_m * acc1);
+                        acc2 = fmaf(col.z, alpha, one_m * acc2);
+                        if (raw < 0.99f) {                                // not clamped
+                            const float4 cn = s_conic[j];
+                            d_sig = dalpha * raw / cn.w;                  // alpha = sigma * G
+                            const float dq = -0.5f * raw * dalpha;        // G = exp(-q/2)
+                            d_px = dq * 2.f * fmaf(cn.x, dx, cn.y * dy);
+                            d_py = dq * 2.f * fmaf(cn.y, dx, cn.z * dy);
+                            d_ca = dq * dx * dx;
+                            d_cb = dq * 2.f * dx * dy;
+                            d_cc = dq * dy * dy;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    d_px = warp_sum(d_px); d_py = warp_sum(d_py);
+                    d_ca = warp_sum(d_ca); d_cb = warp_sum(d_cb); d_cc = warp_sum(d_cc);
+                    d_sig = warp_sum(d_sig);
+                    d_r = warp_sum(d_r); d_g = warp_sum(d_g); d_b = warp_sum(d_b);
+                    if ((threadIdx.x & 31) == 0) {
+                        float* o = g2d + (size_t)s_g[j] * 9;
+                        atomicAdd(o + 0, d_px); atomicAdd(o + 1, d_py);
+                        atomicAdd(o + 2, d_ca); atomicAdd(o + 3, d_cb); atomicAdd(o + 4, d_cc);
+                        atomicAdd(o + 5, d_sig);
+                        atomicAdd(o + 6, d_r); atomicAdd(o + 7, d_g); atomicAdd(o + 8, d_b);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// SH basis gradient: dY_k/d(x, y, z) of the degree-3 real polynomials used in
+// the forward pass (Condon-Shortley phase).
+constexpr float kY1 = 0.48860251190291992f, kY2a = 1.0925484305920792f,
+                kY2b = 0.31539156525252005f, kY2c = 0.54627421529603959f,
+                kY3a = 0.59004358992664352f, kY3b = 2.8906114426405538f,
+                kY3c = 0.45704579946446572f, kY3d = 0.37317633259011540f,
+                kY3e = 1.4453057213202769f, kY00 = 0.28209479177387814f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16], float dY[16][3]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = kY00;                dY[0][0] = 0.f; dY[0][1] = 0.f; dY[0][2] = 0.f;
+    Y[1] = -kY1 * y;            dY[1][0] = 0.f; dY[1][1] = -kY1; dY[1][2] = 0.f;
+    Y[2] = kY1 * z;             dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = kY1;
+    Y[3] = -kY1 * x;            dY[3][0] = -kY1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    Y[4] = kY2a * x * y;        dY[4][0] = kY2a * y; dY[4][1] = kY2a * x; dY[4][2] = 0.f;
+    Y[5] = -kY2a * y * z;       dY[5][0] = 0.f; dY[5][1] = -kY2a * z; dY[5][2] = -kY2a * y;
+    Y[6] = kY2b * (2.f * zz - xx - yy);
+    dY[6][0] = -2.f * kY2b * x; dY[6][1] = -2.f * kY2b * y; dY[6][2] = 4.f * kY2b * z;
+    Y[7] = -kY2a * x * z;       dY[7][0] = -kY2a * z; dY[7][1] = 0.f; dY[7][2] = -kY2a * x;
+    Y[8] = kY2c * (xx - yy);    dY[8][0] = 2.f * kY2c * x; dY[8][1] = -2.f * kY2c * y; dY[8][2] = 0.f;
+    Y[9] = -kY3a * y * (3.f * xx - yy);
+    dY[9][0] = -6.f * kY3a * x * y; dY[9][1] = -kY3a * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+    Y[10] = kY3b * x * y * z;
+    dY[10][0] = kY3b * y * z; dY[10][1] = kY3b * x * z; dY[10][2] = kY3b * x * y;
+    Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+    dY[11][0] = 2.f * kY3c * x * y; dY[11][1] = -kY3c * (4.f * zz - xx - 3.f * yy);
+    dY[11][2] = -8.f * kY3c * y * z;
+    Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    dY[12][0] = -6.f * kY3d * x * z; dY[12][1] = -6.f * kY3d * y * z;
+    dY[12][2] = kY3d * (6.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+    dY[13][0] = -kY3c * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * kY3c * x * y;
+    dY[13][2] = -8.f * kY3c * x * z;
+    Y[14] = kY3e * z * (xx - yy);
+    dY[14][0] = 2.f * kY3e * x * z; dY[14][1] = -2.f * kY3e * y * z; dY[14][2] = kY3e * (xx - yy);
+    Y[15] = -kY3a * x * (xx - 3.f * yy);
+    dY[15][0] = -kY3a * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * kY3a * x * y; dY[15][2] = 0.f;
+}
+
+__global__ void __launch_bounds__(128)
+k_preprocess_backward(int n, const float* __restrict__ means, const float* __restrict__ scales,
+                      const float* __restrict__ rots, const float* __restrict__ opac,
+                      const float* __restrict__ sh, CamDev cam, SetDev st,
+                      const uint32_t* __restrict__ tiles, const float4* __restrict__ aux,
+                      const float* __restrict__ g2d, float* __restrict__ g_means,
+                      float* __restrict__ g_scales, float* __restrict__ g_rots,
+                      float* __restrict__ g_opac, float* __restrict__ g_sh) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    float go = 0.f;
+    float* gsh = g_sh + (size_t)i * 48;
+    if (tiles[i] == 0) {
+        for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+    } else {
+        const float* G = g2d + (size_t)i * 9;
+        const float gpx = G[0], gpy = G[1], gca = G[2], gcb = G[3], gcc = G[4];
+        go = G[5];
+        const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        // --- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5), d = (X0 - cam) / |X0 - cam|
+        float vx = mx - cam.cam_pos[0], vy = my - cam.cam_pos[1], vz = mz - cam.cam_pos[2];
+        const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx / vn, dy = vy / vn, dz = vz / vn;
+        float Y[16], dY[16][3];
+        sh_basis(dx, dy, dz, Y, dY);
+        const int nb = (st.sh_degree + 1) * (st.sh_degree + 1);
+        const float* s = sh + (size_t)i * 48;
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < nb; ++k)
+            for (int c = 0; c < 3; ++c) raw[c] = fmaf(s[3 * k + c], Y[k], raw[c]);
+        float grgb[3];
+        for (int c = 0; c < 3; ++c) grgb[c] = raw[c] > 0.f ? G[6 + c] : 0.f;
+        float gdir[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < 16; ++k) {
+            float sk = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const float v = k < nb ? Y[k] * grgb[c] : 0.f;
+                gsh[3 * k + c] = v;
+                if (k < nb) sk = fmaf(s[3 * k + c], grgb[c], sk);
+            }
+            if (k < nb) {
+                gdir[0] = fmaf(sk, dY[k][0], gdir[0]);
+                gdir[1] = fmaf(sk, dY[k][1], gdir[1]);
+                gdir[2] = fmaf(sk, dY[k][2], gdir[2]);
+            }
+        }
+        // through the normalisation: d(d)/dv = (I - d d^T) / |v|
+        const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+        gm[0] += (gdir[0] - dd * dx) / vn;
+        gm[1] += (gdir[1] - dd * dy) / vn;
+        gm[2] += (gdir[2] - dd * dz) / vn;
+
+        // --- recompute the projection (FP32; gradients are tolerant to ~1e-6 error)
+        const float* V = cam.v;
+        const float px_v = V[0] * mx + V[1] * my + V[2] * mz + V[3];
+        const float py_v = V[4] * mx + V[5] * my + V[6] * mz + V[7];
+        const float pz_v = V[8] * mx + V[9] * my + V[10] * mz + V[11];
+        const float4 q4 = reinterpret_cast<const float4*>(rots)[i];
+        const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+        const float w = q4.x / qn, x = q4.y / qn, y = q4.z / qn, z = q4.w / qn;
+        float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                         {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                         {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+        const float sc[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+        float M[3][3], Sig[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * sc[b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Sig[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
+        const float iz = 1.f / pz_v;
+        const float limx = st.jac_clamp * cam.tan_fovx, limy = st.jac_clamp * cam.tan_fovy;
+        const float rx = px_v * iz, ry = py_v * iz;
+        const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+        const float tx = fminf(limx, fmaxf(-limx, rx)), ty = fminf(limy, fmaxf(-limy, ry));
+        const float J[2][3] = {{cam.fx * iz, 0.f, -cam.fx * tx * iz}, {0.f, cam.fy * iz, -cam.fy * ty * iz}};
+        float T[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) T[r][c] = J[r][0] * V[c] + J[r][1] * V[4 + c] + J[r][2] * V[8 + c];
+        // dL/dSigma' = -C G_C C with the conic C (from the forward pass) and the
+        // symmetric gradient G_C = [[gca, gcb/2], [gcb/2, gcc]].
+        const float4 cn = aux[2 * (size_t)i];
+        const float Ca = cn.x, Cb = cn.y, Cc = cn.z;
+        const float Ga = gca, Gb = 0.5f * gcb, Gc = gcc;
+        // X = G_C C
+        const float X00 = Ga * Ca + Gb * Cb, X01 = Ga * Cb + Gb * Cc;
+        const float X10 = Gb * Ca + Gc * Cb, X11 = Gb * Cb + Gc * Cc;
+        const float D00 = -(Ca * X00 + Cb * X10), D01 = -(Ca * X01 + Cb * X11);
+        const float D11 = -(Cb * X01 + Cc * X11);
+        const float D[2][2] = {{D00, D01}, {D01, D11}};
+        // dL/dSigma = T^T D T ; dL/dT = 2 D T Sigma
+        float gSig[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                float acc = 0.f;
+                for (int r = 0; r < 2; ++r)
+                    for (int c = 0; c < 2; ++c) acc += T[r][a] * D[r][c] * T[c][b];
+                gSig[a][b] = acc;
+            }
+        float DT[2][3], gT[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) DT[r][c] = D[r][0] * T[0][c] + D[r][1] * T[1][c];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c)
+                gT[r][c] = 2.f * (DT[r][0] * Sig[0][c] + DT[r][1] * Sig[1][c] + DT[r][2] * Sig[2][c]);
+        // T = J W  ->  dL/dJ = dL/dT W^T
+        float gJ[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) gJ[r][c] = gT[r][0] * V[4 * c + 0] + gT[r][1] * V[4 * c + 1] + gT[r][2] * V[4 * c + 2];
+        // J -> view-space position
+        float gp[3] = {0.f, 0.f, 0.f};
+        gp[2] += gJ[0][0] * (-cam.fx * iz * iz) + gJ[1][1] * (-cam.fy * iz * iz);
+        if (clx) {
+            gp[2] += gJ[0][2] * (cam.fx * tx * iz * iz);
+        } else {
+            gp[0] += gJ[0][2] * (-cam.fx * iz * iz);
+            gp[2] += gJ[0][2] * (2.f * cam.fx * px_v * iz * iz * iz);
+        }
+        if (cly) {
+            gp[2] += gJ[1][2] * (cam.fy * ty * iz * iz);
+        } else {
+            gp[1] += gJ[1][2] * (-cam.fy * iz * iz);
+            gp[2] += gJ[1][2] * (2.f * cam.fy * py_v * iz * iz * iz);
+        }
+        // pixel centre px = fx x / z + cx, py = fy y / z + cy
+        gp[0] += gpx * cam.fx * iz;
+        gp[1] += gpy * cam.fy * iz;
+        gp[2] += -gpx * cam.fx * px_v * iz * iz - gpy * cam.fy * py_v * iz * iz;
+        // p = W X + t  ->  dL/dX = W^T dL/dp
+        for (int c = 0; c < 3; ++c) gm[c] += gp[0] * V[c] + gp[1] * V[4 + c] + gp[2] * V[8 + c];
+        // Sigma = M M^T, M = R S
+        float gM[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                gM[a][b] = 2.f * (gSig[a][0] * M[0][b] + gSig[a][1] * M[1][b] + gSig[a][2] * M[2][b]);
+        float gR[3][3];
+        for (int b = 0; b < 3; ++b) {
+            gs[b] = gM[0][b] * R[0][b] + gM[1][b] * R[1][b] + gM[2][b] * R[2][b];
+            for (int a = 0; a < 3; ++a) gR[a][b] = gM[a][b] * sc[b];
+        }
+        // rotation matrix of the unit quaternion (w, x, y, z)
+        const float gw = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+        const float gx = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.f * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] + w * gR[2][1] - 2.f * x * gR[2][2]);
+        const float gy = 2.f * (-2.f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] - w * gR[2][0] + z * gR[2][1] - 2.f * y * gR[2][2]);
+        const float gz = 2.f * (-2.f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.f * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+        // through q / |q|
+        const float dot = gw * w + gx * x + gy * y + gz * z;
+        gq[0] = (gw - dot * w) / qn;
+        gq[1] = (gx - dot * x) / qn;
+        gq[2] = (gy - dot * y) / qn;
+        gq[3] = (gz - dot * z) / qn;
+        (void)opac;
+    }
+    for (int c = 0; c < 3; ++c) {
+        g_means[3 * i + c] = gm[c];
+        g_scales[3 * i + c] = gs[c];
+    }
+    for (int c = 0; c < 4; ++c) g_rots[4 * i + c] = gq[c];
+    g_opac[i] = go;
+}
+
+__global__ void __launch_bounds__(256)
+k_load_moments(const int32_t* __restrict__ load, int64_t hw, double* __restrict__ sums) {
+    double s = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hw;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)load[i];
+        s += v;
+        s2 += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sums + 0, s);
+        atomicAdd(sums + 1, s2);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_load_grad(const int32_t* __restrict__ load, int64_t hw, double* __restrict__ sums,
+            float weight, float* __restrict__ dl_dload, int write_stats) {
+    const double mean = sums[0] / (double)hw;
+    const double var = fmax(sums[1] / (double)hw - mean * mean, 0.0);
+    const double sd = sqrt(var);
+    if (write_stats && blockIdx.x == 0 && threadIdx.x == 0) {
+        sums[2] = mean;
+        sums[3] = sd;
+    }
+    if (!dl_dload) return;
+    const double scale = sd > 0.0 ? (double)weight / ((double)hw * sd) : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hw;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dl_dload[i] = (float)(((double)load[i] - mean) * scale);
+}
+
+}  // namespace
+
+void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
+                            const float4* aux, const CamDev& cam, const SetDev& st,
+                            const int32_t* last, const float* t_final, const float* dl_dimg,
+                            const float* dl_dload, float* g2d, cudaStream_t stream) {
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    if (tiles <= 0) return;
+    k_render_backward<<<tiles, kBwdThreads, 0, stream>>>(ranges, sorted_gauss, rec, aux, cam, st,
+                                                         last, t_final, dl_dimg, dl_dload, g2d);
+}
+
+void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
+                                const float* opac, const float* sh, const CamDev& cam,
+                                const SetDev& st, const uint32_t* tiles, const float4* aux,
+                                const float* g2d, float* g_means, float* g_scales, float* g_rots,
+                                float* g_opac, float* g_sh, cudaStream_t stream) {
+    if (n <= 0) return;
+    k_preprocess_backward<<<(n + 127) / 128, 128, 0, stream>>>(n, means, scales, rots, opac, sh, cam,
+                                                               st, tiles, aux, g2d, g_means,
+                                                               g_scales, g_rots, g_opac, g_sh);
+}
+
+void launch_load_loss(const int32_t* load, int64_t hw, double* sums, float weight, float* dl_dload,
+                      int sm_count, cudaStream_t stream) {
+    if (hw <= 0) return;
+    cudaMemsetAsync(sums, 0, 4 * sizeof(double), stream);
+    k_load_moments<<<sm_count * 4, 256, 0, stream>>>(load, hw, sums);
+    k_load_grad<<<sm_count * 4, 256, 0, stream>>>(load, hw, sums, weight, dl_dload, 1);
+}
+
+}  // namespace adr

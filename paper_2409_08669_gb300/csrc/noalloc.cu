@@ -48,7 +48,8 @@ constexpr size_t kOffChunkFirst = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
 constexpr size_t kOffRanges = align256(kOffChunkFirst + (kNaMaxPairs / kSortChunk + 2) * 4);
 constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
 constexpr size_t kOffTrav = align256(kOffLast + kPixels * 4);
-constexpr size_t kOffHist = align256(kOffTrav + kPixels * 4);
+constexpr size_t kOffTfin = align256(kOffTrav + kPixels * 4);
+constexpr size_t kOffHist = align256(kOffTfin + kPixels * 4);
 constexpr size_t kOffCounters = align256(kOffHist + kHistWords * 4);
 constexpr size_t kOffStatus = align256(kOffCounters + kCntSlots * 4);
 constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 2) * kRadix;
@@ -107,6 +108,7 @@ adr_status setup(int dev, DeviceState*& out) {
         w.ranges = reinterpret_cast<uint2*>(b + kOffRanges);
         w.last = reinterpret_cast<int32_t*>(b + kOffLast);
         w.trav = reinterpret_cast<int32_t*>(b + kOffTrav);
+        w.tfin = reinterpret_cast<float*>(b + kOffTfin);
         w.hist = reinterpret_cast<uint32_t*>(b + kOffHist);
         w.counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
         w.status = reinterpret_cast<uint32_t*>(b + kOffStatus);

@@ -8,7 +8,8 @@ namespace adr {
 const char* kernel_name(int id) {
     static const char* names[kKernelCount] = {"preprocess", "depth_hist", "depth_pass",
                                               "scan_tiles", "init_ranges", "tile_pass_first",
-                                              "tile_pass_last", "render"};
+                                              "tile_pass_last", "render", "render_backward",
+                                              "preprocess_backward"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
 }
 
@@ -145,7 +146,22 @@ void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float
     // Stage 6.
     TIMED(ws, kKRender, stream,
           launch_render(ws.ranges, fs.sorted_gauss, ws.rec, fs.cam, fs.st, img, t_final, load,
-                        ws.last, ws.trav, stream));
+                        ws.last, ws.trav, ws.tfin, stream));
+}
+
+void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,
+                      const float* scales, const float* rots, const float* opac, const float* sh,
+                      const float* dl_dimg, const float* dl_dload, float* g_means, float* g_scales,
+                      float* g_rots, float* g_opac, float* g_sh, cudaStream_t stream) {
+    if (fs.n <= 0) return;
+    cudaMemsetAsync(ws.g2d, 0, (size_t)fs.n * 9 * sizeof(float), stream);
+    TIMED(ws, kKRenderBackward, stream,
+          launch_render_backward(ws.ranges, fs.sorted_gauss, ws.rec, ws.aux, fs.cam, fs.st, ws.last,
+                                 ws.tfin, dl_dimg, dl_dload, ws.g2d, stream));
+    TIMED(ws, kKPreprocessBackward, stream,
+          launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, fs.cam, fs.st,
+                                     ws.tiles, ws.aux, ws.g2d, g_means, g_scales, g_rots, g_opac,
+                                     g_sh, stream));
 }
 
 }  // namespace adr

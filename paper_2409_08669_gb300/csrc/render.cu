@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kRenderThreads)
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const float4* __restrict__ rec, CamDev cam, SetDev st, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
-         int32_t* __restrict__ trav_out) {
+         int32_t* __restrict__ trav_out, float* __restrict__ tfin) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
@@ -87,6 +87,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         if (load) load[pix] = count;
         if (last_out) last_out[pix] = last;
         if (trav_out) trav_out[pix] = trav;
+        if (tfin) tfin[pix] = T;
     }
 }
 
@@ -94,11 +95,11 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, int32_t* trav, cudaStream_t stream) {
+                   int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream) {
     const int tiles = cam.tiles_x * cam.tiles_y;
     if (tiles <= 0) return;
     k_render<<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, rec, cam, st, img,
-                                                   t_final, load, last, trav);
+                                                   t_final, load, last, trav, tfin);
 }
 
 }  // namespace adr

@@ -39,6 +39,7 @@ class Rasterizer:
                                    int(max_height), int(device))
         self.n = 0
         self.camera = None
+        self.frame = 0          # increments per adr_preprocess; backward needs the last frame
 
     def close(self):
         if self.ctx:
@@ -59,6 +60,7 @@ class Rasterizer:
             assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
         self.n = n
         self.camera = camera
+        self.frame += 1
         _lib.adr_preprocess(self.ctx, _ptr(means), _ptr(scales), _ptr(rots), _ptr(opac), _ptr(sh),
                             n, _lib.make_camera(camera), _lib.make_settings(settings),
                             _stream(stream))
@@ -82,6 +84,26 @@ class Rasterizer:
         self.preprocess(params, camera, settings, stream)
         self.sort(stream)
         return self.render(stream=stream, **kw)
+
+    def backward(self, params, dl_dimg, dl_dload=None, stream=None):
+        """Gradients of the last rendered frame: (g_means, g_scales, g_rots, g_opac, g_sh)."""
+        grads = tuple(torch.empty_like(p) for p in params)
+        dl_dimg = dl_dimg.contiguous().float()
+        if dl_dload is not None:
+            dl_dload = dl_dload.contiguous().float()
+        _lib.adr_render_backward(self.ctx, *(_ptr(p) for p in params), _ptr(dl_dimg),
+                                 _ptr(dl_dload), *(_ptr(g) for g in grads), _stream(stream))
+        return grads
+
+    def load_loss(self, load, weight=1.0, want_grad=True, stream=None):
+        """(mean, std) of the per-pixel load and weight * dL_load/dl (Eq. 13)."""
+        load = load.contiguous()
+        assert load.dtype == torch.int32
+        stats = torch.empty(2, dtype=torch.float64, device=load.device)
+        grad = torch.empty(load.shape, dtype=torch.float32, device=load.device) if want_grad else None
+        _lib.adr_load_loss(self.ctx, _ptr(load), load.numel(), float(weight), _ptr(stats), _ptr(grad),
+                           _stream(stream))
+        return stats, grad
 
     # -- inspection -------------------------------------------------------------
     def num_pairs(self, raise_on_error=True):
