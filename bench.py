@@ -255,6 +255,56 @@ def kernel_bytes(name, n, u, hw):
     }[name]
 
 
+def train_step_rate(local, steps=20, warmup=5):
+    """Differentiable training step on 1M clustered Gaussians at 1280x720:
+    forward, L1 loss against the render of a perturbed copy, backward through
+    adr_render_backward, and an Adam update of the raw parameters."""
+    import torch
+    from paper_2409_08669_gb300.autograd import rasterize
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
+    base = S.cluster_scene(n=1_000_000, seed=1)
+    target = S.perturbed_scene(base, seed=4)
+    cams = S.orbit_cameras(50, width=1280, height=720)
+    st = S.Settings(mode=S.MODE_AABB)
+    rast = Rasterizer(max_gaussians=base.n, pair_capacity=1 << 27, max_width=1280,
+                      max_height=720, device=local)
+    tparams = upload(target)
+    targets = []
+    for cam in cams[:8]:
+        img, _, _ = rast.forward(tparams, cam, st, want_aux=False)
+        targets.append(img.clone())
+    means, scales, rots, opac, sh = upload(base)
+    raw = [means.clone().requires_grad_(True), torch.log(scales).requires_grad_(True),
+           rots.clone().requires_grad_(True),
+           torch.logit(opac.clamp(1e-4, 1 - 1e-4)).requires_grad_(True), sh.clone().requires_grad_(True)]
+    opt = torch.optim.Adam(raw, lr=1e-3)
+
+    def step(k):
+        opt.zero_grad(set_to_none=True)
+        params = (raw[0], torch.exp(raw[1]), raw[2], torch.sigmoid(raw[3]), raw[4])
+        img, _, _ = rasterize(params, rast, cams[k % 8], st)
+        loss = torch.abs(img - targets[k % 8]).mean()
+        loss.backward()
+        opt.step()
+        return loss
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(steps):
+        loss = step(warmup + k)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    rast.close()
+    return {"workload": "cluster-1M-720p", "steps_per_s": 1e3 / ms, "ms_per_step": ms,
+            "final_l1": float(loss.item()),
+            "step": "forward + L1 + adr_render_backward + Adam on 1M Gaussians, 1280x720"}
+
+
 def e2e_host(rast_ctx, scene, cams, st, steps, warmup):
     """FPS through adr_render_host with pinned host buffers (scene uploaded
     and the image read back inside every step)."""
@@ -408,9 +458,12 @@ def run_ours(args):
         "gpu_launches": sum(v["launches"] for v in ktable.values()),
         "clocks": clocks,
     }
+    rast.close()
+    del params
+    if not args.no_train:
+        result["train_step"] = train_step_rate(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(scene, cams, st_adr, budget_s=args.cpu_budget)
-    rast.close()
     if rank == 0:
         print(json.dumps(result))
 
@@ -522,6 +575,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heavy-3M-1080p")
     ap.add_argument("--quick", action="store_true",
