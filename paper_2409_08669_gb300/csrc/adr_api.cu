@@ -142,7 +142,7 @@ void free_ctx(adr_ctx* c) {
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status,
-                    w.lookback, c->stage, c->stage_img, c->stage_load};
+                    w.lookback, w.d_fp, w.d_stage, c->stage, c->stage_img, c->stage_load};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_words) cudaFreeHost(c->host_words);
@@ -226,12 +226,15 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     ALLOC(w.counters, kCntSlots * sizeof(uint32_t));
     ALLOC(w.status, sizeof(uint32_t) * 4);
     ALLOC(w.lookback, w.lookback_words * sizeof(unsigned long long));
+    ALLOC(w.d_fp, sizeof(FrameParams));
+    ALLOC(w.d_stage, sizeof(uint32_t));
 #undef ALLOC
     e = cudaHostAlloc((void**)&c->host_words, 64 * sizeof(uint32_t), cudaHostAllocDefault);
     if (e != cudaSuccess) { free_ctx(c); return fail(ADR_ERR_CUDA, "cudaHostAlloc: %s", cudaGetErrorString(e)); }
     if (cudaMemset(w.lookback, 0, w.lookback_words * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(w.status, 0, sizeof(uint32_t) * 4) != cudaSuccess ||
         cudaMemset(w.counters, 0, kCntSlots * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(w.d_stage, 0, sizeof(uint32_t)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return fail(ADR_ERR_CUDA, "workspace initialisation failed");

@@ -37,6 +37,21 @@ struct SetDev {
     int sh_degree;
 };
 
+// Camera and settings of a frame, read by the kernels from device memory so a
+// captured CUDA graph can be replayed for another camera by updating them.
+struct FrameParams {
+    CamDev cam;
+    SetDev st;
+};
+
+// Decoupled-lookback pass tag: epoch = (*stage) * 8 + pass, where *stage is a
+// device counter bumped by the first kernel of every preprocess / sort call,
+// so every pass (also in a replayed graph) gets a tag no stale word carries.
+struct EpochRef {
+    const uint32_t* stage;
+    uint32_t pass;
+};
+
 // Per-Gaussian render record, three float4 per Gaussian:
 //   rec[3g+0] = (px_hi, py_hi, px_lo, py_lo)   pixel centre as a float-float pair
 //   rec[3g+1] = (w1x, w1y, w2x, w2y)           q(d) = d^T Sigma'^-1 d = 2/log2(e) *
@@ -112,6 +127,8 @@ struct Workspace {
     unsigned long long* lookback = nullptr;
     size_t lookback_words = 0;             // (max(max_n, capacity) / kSortChunk + 2) * kRadix
     Profiler* prof = nullptr;              // non-null: time every launch
+    FrameParams* d_fp = nullptr;           // [1] camera + settings of the current frame
+    uint32_t* d_stage = nullptr;           // [1] stage counter (see EpochRef)
 };
 
 // hist layout: 4 x 256 depth digits, then 2 x 256 tile digits.
@@ -127,8 +144,14 @@ struct FrameState {
     const uint32_t* sorted_gauss = nullptr;  // pairs' Gaussians by (tile, depth)
 };
 
-// Monotone pass tag for the lookback words; on wrap-around clears them.
-uint32_t next_epoch(std::atomic<uint32_t>& epoch, const Workspace& ws, cudaStream_t stream);
+// Counts stage calls on the host; every 2^28 calls (before the device tag
+// wraps) clears the lookback words.
+void count_stage(std::atomic<uint32_t>& calls, const Workspace& ws, cudaStream_t stream);
+// One-thread kernel that stores a frame's camera and settings in device
+// memory; in a captured graph its by-value argument is the one node a replay
+// for another camera updates (cudaGraphExecKernelNodeSetParams).
+void launch_set_frame_params(const FrameParams& p, FrameParams* d_fp, cudaStream_t stream);
+const void* set_frame_params_kernel();
 
 // Stage orchestration shared by every entry point (pipeline.cu).
 void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
@@ -142,9 +165,9 @@ void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev
 
 // Kernel launchers (each enqueues on `stream`; all pointers are device memory).
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
-                       const float* opac, const float* sh, const CamDev& cam, const SetDev& st,
-                       float4* rec, float4* aux, uint32_t* depth_key, uint32_t* tiles,
-                       ushort4* rect, cudaStream_t stream);
+                       const float* opac, const float* sh, const FrameParams* fp,
+                       uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
+                       uint32_t* tiles, ushort4* rect, cudaStream_t stream);
 
 // Histogram of `passes` 8-bit digits of u32 keys.  hist must hold passes*256 zeroed u32.
 void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, uint32_t* hist,
@@ -154,7 +177,7 @@ void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, 
 // (2^digit_bits - 1).  vals_in == nullptr means the values are 0..n-1.
 void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                      uint32_t* vals_out, int64_t n, int shift, int digit_bits,
-                     const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
+                     const uint32_t* hist, unsigned long long* lookback, EpochRef epoch,
                      uint32_t* ticket, uint32_t* status, int grid, cudaStream_t stream);
 
 // Inputs of the tile passes.
@@ -173,14 +196,14 @@ struct PairSource {
 // With final = true (single pass) it writes only Gaussian ids and the ranges.
 void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t* gauss_out,
                             int digit_bits, bool final, uint2* ranges, const uint32_t* hist,
-                            unsigned long long* lookback, uint32_t epoch, uint32_t* ticket,
+                            unsigned long long* lookback, EpochRef epoch, uint32_t* ticket,
                             uint32_t* status, int grid, cudaStream_t stream);
 // Second tile pass: scatter by the high digit, write only Gaussian ids, and
 // derive each tile's [start, end) from the digit runs.
 void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, uint32_t* gauss_out,
                            const uint32_t* counters, int64_t capacity, int shift, int digit_bits,
                            uint2* ranges, const uint32_t* hist, unsigned long long* lookback,
-                           uint32_t epoch, uint32_t* ticket, uint32_t* status, int grid,
+                           EpochRef epoch, uint32_t* ticket, uint32_t* status, int grid,
                            cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
@@ -195,23 +218,23 @@ void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, ui
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
                        int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
                        uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
-                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
+                       unsigned long long* lookback, EpochRef epoch, uint32_t* counters,
                        uint32_t* status, int grid, cudaStream_t stream);
 
-void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
+void launch_init_ranges(uint2* ranges, int num_tiles, uint32_t* stage, cudaStream_t stream);
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                   const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream);
+                   const FrameParams* fp, int num_tiles, float* img, float* t_final,
+                   int32_t* load, int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream);
 
 // Backward (backward.cu).
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                            const float4* aux, const CamDev& cam, const SetDev& st,
+                            const float4* aux, const FrameParams* fp, int num_tiles,
                             const int32_t* last, const float* t_final, const float* dl_dimg,
                             const float* dl_dload, float* g2d, cudaStream_t stream);
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
-                                const float* opac, const float* sh, const CamDev& cam,
-                                const SetDev& st, const uint32_t* tiles, const float4* aux,
+                                const float* opac, const float* sh, const FrameParams* fp,
+                                const uint32_t* tiles, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream);
 void launch_load_loss(const int32_t* load, int64_t hw, double* sums, float weight, float* dl_dload,

@@ -27,8 +27,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 __global__ void __launch_bounds__(kBwdThreads)
 k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
-                  const float4* __restrict__ rec, const float4* __restrict__ aux, CamDev cam,
-                  SetDev st, const int32_t* __restrict__ last_pos, const float* __restrict__ t_final,
+                  const float4* __restrict__ rec, const float4* __restrict__ aux,
+                  const FrameParams* __restrict__ fp, const int32_t* __restrict__ last_pos,
+                  const float* __restrict__ t_final,
                   const float* __restrict__ dl_dimg, const float* __restrict__ dl_dload,
                   float* __restrict__ g2d) {
     __shared__ float2 s_xy[kBwdThreads];
@@ -37,6 +38,8 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
     __shared__ float4 s_conic[kBwdThreads];   // conic a, b, c, sigma
     __shared__ uint32_t s_g[kBwdThreads];
 
+    const CamDev cam = fp->cam;
+    const SetDev st = fp->st;
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
@@ -185,13 +188,15 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16],
 __global__ void __launch_bounds__(128)
 k_preprocess_backward(int n, const float* __restrict__ means, const float* __restrict__ scales,
                       const float* __restrict__ rots, const float* __restrict__ opac,
-                      const float* __restrict__ sh, CamDev cam, SetDev st,
+                      const float* __restrict__ sh, const FrameParams* __restrict__ fp,
                       const uint32_t* __restrict__ tiles, const float4* __restrict__ aux,
                       const float* __restrict__ g2d, float* __restrict__ g_means,
                       float* __restrict__ g_scales, float* __restrict__ g_rots,
                       float* __restrict__ g_opac, float* __restrict__ g_sh) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const CamDev cam = fp->cam;
+    const SetDev st = fp->st;
     float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float go = 0.f;
     float* gsh = g_sh + (size_t)i * 48;
@@ -382,23 +387,23 @@ k_load_grad(const int32_t* __restrict__ load, int64_t hw, double* __restrict__ s
 }  // namespace
 
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                            const float4* aux, const CamDev& cam, const SetDev& st,
+                            const float4* aux, const FrameParams* fp, int num_tiles,
                             const int32_t* last, const float* t_final, const float* dl_dimg,
                             const float* dl_dload, float* g2d, cudaStream_t stream) {
-    const int tiles = cam.tiles_x * cam.tiles_y;
+    const int tiles = num_tiles;
     if (tiles <= 0) return;
-    k_render_backward<<<tiles, kBwdThreads, 0, stream>>>(ranges, sorted_gauss, rec, aux, cam, st,
+    k_render_backward<<<tiles, kBwdThreads, 0, stream>>>(ranges, sorted_gauss, rec, aux, fp,
                                                          last, t_final, dl_dimg, dl_dload, g2d);
 }
 
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
-                                const float* opac, const float* sh, const CamDev& cam,
-                                const SetDev& st, const uint32_t* tiles, const float4* aux,
+                                const float* opac, const float* sh, const FrameParams* fp,
+                                const uint32_t* tiles, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream) {
     if (n <= 0) return;
-    k_preprocess_backward<<<(n + 127) / 128, 128, 0, stream>>>(n, means, scales, rots, opac, sh, cam,
-                                                               st, tiles, aux, g2d, g_means,
+    k_preprocess_backward<<<(n + 127) / 128, 128, 0, stream>>>(n, means, scales, rots, opac, sh, fp,
+                                                               tiles, aux, g2d, g_means,
                                                                g_scales, g_rots, g_opac, g_sh);
 }
 

@@ -31,7 +31,8 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
              int64_t capacity, uint32_t* __restrict__ offsets, uint32_t* __restrict__ sorted_box,
              uint32_t* __restrict__ chunk_first,
              uint32_t* __restrict__ hist_tiles, unsigned long long* __restrict__ lookback,
-             uint32_t epoch, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
+             EpochRef eref, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
+    const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
     __shared__ uint32_t s_lo_diff[kRadix + 1];   // circular difference array of the low digit
@@ -172,7 +173,8 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
         if (s_hi[d]) atomicAdd(hist_tiles + kRadix + d, s_hi[d]);
 }
 
-__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles) {
+__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles, uint32_t* __restrict__ stage) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(stage, 1u);   // new tag for the sort passes
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x)
         ranges[t] = make_uint2(0xFFFFFFFFu, 0u);
 }
@@ -233,7 +235,7 @@ int scan_blocks_per_sm() {
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
                        int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
                        uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
-                       unsigned long long* lookback, uint32_t epoch, uint32_t* counters,
+                       unsigned long long* lookback, EpochRef epoch, uint32_t* counters,
                        uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
     k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, tiles_x, bits1, capacity,
@@ -241,9 +243,9 @@ void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushor
                                                     lookback, epoch, counters, status);
 }
 
-void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream) {
+void launch_init_ranges(uint2* ranges, int num_tiles, uint32_t* stage, cudaStream_t stream) {
     if (num_tiles <= 0) return;
-    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles);
+    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles, stage);
 }
 
 void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream) {

@@ -53,7 +53,9 @@ constexpr size_t kOffHist = align256(kOffTfin + kPixels * 4);
 constexpr size_t kOffCounters = align256(kOffHist + kHistWords * 4);
 constexpr size_t kOffStatus = align256(kOffCounters + kCntSlots * 4);
 constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 2) * kRadix;
-constexpr size_t kOffLookback = align256(kOffStatus + 16);
+constexpr size_t kOffFrameParams = align256(kOffStatus + 16);
+constexpr size_t kOffStage = align256(kOffFrameParams + sizeof(FrameParams));
+constexpr size_t kOffLookback = align256(kOffStage + 16);
 constexpr size_t kNaBytes = align256(kOffLookback + kLookbackWords * 8);
 
 // The scratch.  Zero-initialised when the module loads (the lookback words
@@ -113,6 +115,8 @@ adr_status setup(int dev, DeviceState*& out) {
         w.counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
         w.status = reinterpret_cast<uint32_t*>(b + kOffStatus);
         w.lookback = reinterpret_cast<unsigned long long*>(b + kOffLookback);
+        w.d_fp = reinterpret_cast<FrameParams*>(b + kOffFrameParams);
+        w.d_stage = reinterpret_cast<uint32_t*>(b + kOffStage);
         w.lookback_words = kLookbackWords;
         s.base = b;
     }

@@ -37,15 +37,22 @@ void Profiler::end(cudaStream_t s) {
         if ((ws).prof) (ws).prof->end(stream);              \
     } while (0)
 
-uint32_t next_epoch(std::atomic<uint32_t>& epoch, const Workspace& ws, cudaStream_t stream) {
-    uint32_t e = epoch.fetch_add(1) + 1;
-    if (e == 0) {
-        // Every lookback word carries the epoch of the pass that wrote it; on
-        // wrap-around clear them all so no stale word can match a new pass.
+namespace {
+__global__ void k_set_frame_params(FrameParams p, FrameParams* __restrict__ out) { *out = p; }
+}  // namespace
+
+void launch_set_frame_params(const FrameParams& p, FrameParams* d_fp, cudaStream_t stream) {
+    k_set_frame_params<<<1, 1, 0, stream>>>(p, d_fp);
+}
+
+const void* set_frame_params_kernel() { return reinterpret_cast<const void*>(&k_set_frame_params); }
+
+void count_stage(std::atomic<uint32_t>& calls, const Workspace& ws, cudaStream_t stream) {
+    // The device tag is (stage count) * 8 + pass in 32 bits; clear the lookback
+    // words well before it wraps so no stale word can match a new pass.
+    const uint32_t c = calls.fetch_add(1) + 1;
+    if ((c & ((1u << 28) - 1u)) == 0)
         cudaMemsetAsync(ws.lookback, 0, ws.lookback_words * sizeof(unsigned long long), stream);
-        e = epoch.fetch_add(1) + 1;
-    }
-    return e;
 }
 
 void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st) {
@@ -73,12 +80,14 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                         const float* means, const float* scales, const float* rots,
                         const float* opac, const float* sh, cudaStream_t stream) {
     const int64_t n = fs.n;
+    count_stage(epoch, ws, stream);
+    launch_set_frame_params(FrameParams{fs.cam, fs.st}, ws.d_fp, stream);
     cudaMemsetAsync(ws.counters, 0, kCntSlots * sizeof(uint32_t), stream);
     cudaMemsetAsync(ws.hist, 0, kHistWords * sizeof(uint32_t), stream);
     // Stage 1: per-Gaussian projection, covariance, colour and early cull.
     TIMED(ws, kKPreprocess, stream,
-          launch_preprocess((int)n, means, scales, rots, opac, sh, fs.cam, fs.st, ws.rec, ws.aux,
-                            ws.depth_key, ws.tiles, ws.rect, stream));
+          launch_preprocess((int)n, means, scales, rots, opac, sh, ws.d_fp, ws.d_stage, ws.rec,
+                            ws.aux, ws.depth_key, ws.tiles, ws.rect, stream));
     // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
     // carry key 0xFFFFFFFF and end up behind the V that have tiles.
     TIMED(ws, kKDepthHist, stream,
@@ -86,7 +95,7 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     const uint32_t* kin = ws.depth_key;
     const uint32_t* vin = nullptr;
     for (int p = 0; p < kMaxPasses; ++p) {
-        const uint32_t ep = next_epoch(epoch, ws, stream);
+        const EpochRef ep{ws.d_stage, (uint32_t)p};
         TIMED(ws, kKDepthPass, stream,
               launch_onesweep(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, 8,
                               ws.hist + p * kRadix, ws.lookback, ep,
@@ -96,7 +105,7 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     }
     fs.order = vin;
     // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
-    const uint32_t ep = next_epoch(epoch, ws, stream);
+    const EpochRef ep{ws.d_stage, (uint32_t)kMaxPasses};
     TIMED(ws, kKScanTiles, stream,
           launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
                             ws.offsets, ws.sorted_box, ws.chunk_first,
@@ -107,8 +116,9 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream) {
     const int t0 = kCntSortTicket0 + kMaxPasses;
+    count_stage(epoch, ws, stream);
     cudaMemsetAsync(ws.counters + t0, 0, 2 * sizeof(uint32_t), stream);
-    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, stream));
+    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, ws.d_stage, stream));
     PairSource src;
     src.order = fs.order;
     src.offsets = ws.offsets;
@@ -122,13 +132,13 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
         // Stages 3-5: emit + first tile digit, then (if needed) the second
         // digit, which also yields the per-tile ranges.
         const bool single = fs.tile_passes == 1;
-        const uint32_t ep1 = next_epoch(epoch, ws, stream);
+        const EpochRef ep1{ws.d_stage, 0u};
         TIMED(ws, kKTilePassFirst, stream,
               launch_tile_pass_first(src, ws.ptile, ws.pgauss[0], fs.bits1, single, ws.ranges,
                                      hist_tiles, ws.lookback, ep1, ws.counters + t0, ws.status,
                                      ws.sort_grid, stream));
         if (!single) {
-            const uint32_t ep2 = next_epoch(epoch, ws, stream);
+            const EpochRef ep2{ws.d_stage, 1u};
             TIMED(ws, kKTilePassLast, stream,
                   launch_tile_pass_last(ws.ptile, ws.pgauss[0], ws.pgauss[1], ws.counters,
                                         ws.capacity, fs.bits1, fs.bits2, ws.ranges,
@@ -145,8 +155,8 @@ void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float
                     int32_t* load, cudaStream_t stream) {
     // Stage 6.
     TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, fs.sorted_gauss, ws.rec, fs.cam, fs.st, img, t_final, load,
-                        ws.last, ws.trav, ws.tfin, stream));
+          launch_render(ws.ranges, fs.sorted_gauss, ws.rec, ws.d_fp, fs.num_tiles, img, t_final,
+                        load, ws.last, ws.trav, ws.tfin, stream));
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,
@@ -156,12 +166,12 @@ void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* me
     if (fs.n <= 0) return;
     cudaMemsetAsync(ws.g2d, 0, (size_t)fs.n * 9 * sizeof(float), stream);
     TIMED(ws, kKRenderBackward, stream,
-          launch_render_backward(ws.ranges, fs.sorted_gauss, ws.rec, ws.aux, fs.cam, fs.st, ws.last,
-                                 ws.tfin, dl_dimg, dl_dload, ws.g2d, stream));
+          launch_render_backward(ws.ranges, fs.sorted_gauss, ws.rec, ws.aux, ws.d_fp, fs.num_tiles,
+                                 ws.last, ws.tfin, dl_dimg, dl_dload, ws.g2d, stream));
     TIMED(ws, kKPreprocessBackward, stream,
-          launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, fs.cam, fs.st,
-                                     ws.tiles, ws.aux, ws.g2d, g_means, g_scales, g_rots, g_opac,
-                                     g_sh, stream));
+          launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, ws.d_fp, ws.tiles,
+                                     ws.aux, ws.g2d, g_means, g_scales, g_rots, g_opac, g_sh,
+                                     stream));
 }
 
 }  // namespace adr

@@ -141,11 +141,15 @@ constexpr float kHalfLog2e = 0.84932180028801907f;
 __global__ void __launch_bounds__(256)
 k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ scales,
              const float* __restrict__ rots, const float* __restrict__ opac,
-             const float* __restrict__ sh, CamDev cam, SetDev st, float4* __restrict__ rec,
+             const float* __restrict__ sh, const FrameParams* __restrict__ fp,
+             uint32_t* __restrict__ stage, float4* __restrict__ rec,
              float4* __restrict__ aux, uint32_t* __restrict__ depth_key,
              uint32_t* __restrict__ tiles, ushort4* __restrict__ rect) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) atomicAdd(stage, 1u);   // new lookback tag for this call's passes
     if (i >= n) return;
+    const CamDev cam = fp->cam;
+    const SetDev st = fp->st;
 
     const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
     // Sort depth: fixed evaluation order, each operation rounded separately.
@@ -275,13 +279,13 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
 }  // namespace
 
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
-                       const float* opac, const float* sh, const CamDev& cam, const SetDev& st,
-                       float4* rec, float4* aux, uint32_t* depth_key, uint32_t* tiles,
-                       ushort4* rect, cudaStream_t stream) {
+                       const float* opac, const float* sh, const FrameParams* fp,
+                       uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
+                       uint32_t* tiles, ushort4* rect, cudaStream_t stream) {
     if (n <= 0) return;
     const int threads = 256;
     k_preprocess<<<(n + threads - 1) / threads, threads, 0, stream>>>(
-        n, means, scales, rots, opac, sh, cam, st, rec, aux, depth_key, tiles, rect);
+        n, means, scales, rots, opac, sh, fp, stage, rec, aux, depth_key, tiles, rect);
 }
 
 }  // namespace adr

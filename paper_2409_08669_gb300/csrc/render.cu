@@ -17,13 +17,15 @@ constexpr int kRenderThreads = kTilePixels;
 
 __global__ void __launch_bounds__(kRenderThreads)
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
-         const float4* __restrict__ rec, CamDev cam, SetDev st, float* __restrict__ img,
+         const float4* __restrict__ rec, const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
          int32_t* __restrict__ trav_out, float* __restrict__ tfin) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
 
+    const CamDev cam = fp->cam;
+    const SetDev st = fp->st;
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
@@ -94,11 +96,11 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 }  // namespace
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                   const CamDev& cam, const SetDev& st, float* img, float* t_final, int32_t* load,
-                   int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream) {
-    const int tiles = cam.tiles_x * cam.tiles_y;
+                   const FrameParams* fp, int num_tiles, float* img, float* t_final,
+                   int32_t* load, int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream) {
+    const int tiles = num_tiles;
     if (tiles <= 0) return;
-    k_render<<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, rec, cam, st, img,
+    k_render<<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, rec, fp, img,
                                                    t_final, load, last, trav, tfin);
 }
 

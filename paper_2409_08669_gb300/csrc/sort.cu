@@ -69,7 +69,7 @@ struct SweepArgs {
     int shift, digit_bits;
     const uint32_t* hist;        // 256 counts of this pass's digit
     unsigned long long* lookback;
-    uint32_t epoch;
+    EpochRef epoch;
     uint32_t* ticket;
     uint32_t* status;
     uint2* ranges;               // last tile pass
@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t mask = (1u << a.digit_bits) - 1u;
     const int64_t n = a.counters ? min((int64_t)a.counters[kCntPairs], a.n_host) : a.n_host;
-    const unsigned long long tag = (unsigned long long)a.epoch << 32;
+    const uint32_t epoch = (*a.epoch.stage) * 8u + a.epoch.pass;
+    const unsigned long long tag = (unsigned long long)epoch << 32;
 
     // Exclusive prefix of the global histogram of this digit (one digit per thread).
     {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(SweepArgs a) {
                 for (int u = 0; u < 8; ++u) {
                     if (done || used < u || j - u < 0) continue;
                     const unsigned long long w = wv[u];
-                    if ((uint32_t)(w >> 32) != a.epoch || (w & (3ull << 30)) == 0) continue;
+                    if ((uint32_t)(w >> 32) != epoch || (w & (3ull << 30)) == 0) continue;
                     excl += (uint32_t)w & kCountMask;
                     used = u + 1;
                     if (w & kStateInc) done = true;
@@ -360,7 +361,7 @@ void launch_sweep(const SweepArgs& a, int grid, cudaStream_t stream) {
     k_onesweep<kGen, kFinal><<<grid, kSortThreads, kSortSmem, stream>>>(a);
 }
 
-SweepArgs base_args(const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
+SweepArgs base_args(const uint32_t* hist, unsigned long long* lookback, EpochRef epoch,
                     uint32_t* ticket, uint32_t* status) {
     SweepArgs a{};
     a.hist = hist;
@@ -394,7 +395,7 @@ void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, 
 
 void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                      uint32_t* vals_out, int64_t n, int shift, int digit_bits,
-                     const uint32_t* hist, unsigned long long* lookback, uint32_t epoch,
+                     const uint32_t* hist, unsigned long long* lookback, EpochRef epoch,
                      uint32_t* ticket, uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
     SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
@@ -410,7 +411,7 @@ void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t*
 
 void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t* gauss_out,
                             int digit_bits, bool final, uint2* ranges, const uint32_t* hist,
-                            unsigned long long* lookback, uint32_t epoch, uint32_t* ticket,
+                            unsigned long long* lookback, EpochRef epoch, uint32_t* ticket,
                             uint32_t* status, int grid, cudaStream_t stream) {
     SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
     a.keys_out = tile_out;
@@ -428,7 +429,7 @@ void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t*
 void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, uint32_t* gauss_out,
                            const uint32_t* counters, int64_t capacity, int shift, int digit_bits,
                            uint2* ranges, const uint32_t* hist, unsigned long long* lookback,
-                           uint32_t epoch, uint32_t* ticket, uint32_t* status, int grid,
+                           EpochRef epoch, uint32_t* ticket, uint32_t* status, int grid,
                            cudaStream_t stream) {
     SweepArgs a = base_args(hist, lookback, epoch, ticket, status);
     a.keys_in = tile_in;
