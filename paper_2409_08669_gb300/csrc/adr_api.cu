@@ -127,12 +127,8 @@ adr_status camera_to_dev(const adr_camera* cam, int max_w, int max_h, CamDev& d)
     return make_cam(max_w, max_h, cam, d);
 }
 adr_status settings_to_dev(const adr_settings* s, SetDev& d) { return make_settings(s, d); }
-}  // namespace adr
 
-namespace {
-
-void free_ctx(adr_ctx* c) {
-    Workspace& w = c->ws;
+void free_workspace(Workspace& w) {
     if (w.prof) {
         for (int i = 0; i < w.prof->created; ++i) cudaEventDestroy(w.prof->ev[i]);
         delete w.prof;
@@ -141,8 +137,91 @@ void free_ctx(adr_ctx* c) {
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
-                    w.hist, w.counters, w.status,
-                    w.lookback, w.d_fp, w.d_stage, c->stage, c->stage_img, c->stage_load};
+                    w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    w = Workspace{};
+}
+
+size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max_width,
+                       int32_t max_height) {
+    const size_t N = (size_t)max_gaussians, P = (size_t)pair_capacity;
+    const size_t pixels = (size_t)max_width * max_height;
+    const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+    const size_t lb = (((N > P ? N : P) + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 12 +
+           (P / kSortChunk + 2) * 4 + tiles * 8 + pixels * 12 + lb + 4096;
+}
+
+adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_capacity,
+                           int32_t max_width, int32_t max_height, int device) {
+    w = Workspace{};
+    w.max_n = max_gaussians;
+    w.capacity = pair_capacity;
+    w.max_tiles = ((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess || sms <= 0)
+        return fail(ADR_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    w.sm_count = sms;
+    w.sort_grid = sms * onesweep_blocks_per_sm();
+    w.scan_grid = sms * scan_blocks_per_sm();
+    const size_t N = (size_t)max_gaussians, P = (size_t)pair_capacity;
+    const size_t pixels = (size_t)max_width * max_height;
+    w.lookback_words = (((N > P ? N : P) + kSortChunk - 1) / kSortChunk + 2) * kRadix;
+#define ALLOC(ptr, bytes)                                                                   \
+    do {                                                                                    \
+        e = cudaMalloc((void**)&(ptr), (bytes));                                           \
+        if (e != cudaSuccess) {                                                             \
+            free_workspace(w);                                                              \
+            return fail(ADR_ERR_CUDA, "cudaMalloc(%zu) for %s: %s", (size_t)(bytes), #ptr,  \
+                        cudaGetErrorString(e));                                             \
+        }                                                                                   \
+    } while (0)
+    ALLOC(w.rec, N * kRecFloat4 * sizeof(float4));
+    ALLOC(w.aux, N * kAuxFloat4 * sizeof(float4));
+    ALLOC(w.depth_key, N * sizeof(uint32_t));
+    ALLOC(w.tiles, N * sizeof(uint32_t));
+    ALLOC(w.rect, N * sizeof(ushort4));
+    ALLOC(w.offsets, N * sizeof(uint32_t));
+    ALLOC(w.sorted_box, N * sizeof(uint32_t));
+    for (int b = 0; b < 2; ++b) {
+        ALLOC(w.gkeys[b], N * sizeof(uint32_t));
+        ALLOC(w.gvals[b], N * sizeof(uint32_t));
+        ALLOC(w.pgauss[b], P * sizeof(uint32_t));
+    }
+    ALLOC(w.ptile, P * sizeof(uint32_t));
+    ALLOC(w.chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
+    ALLOC(w.ranges, (size_t)w.max_tiles * sizeof(uint2));
+    ALLOC(w.last, pixels * sizeof(int32_t));
+    ALLOC(w.trav, pixels * sizeof(int32_t));
+    ALLOC(w.tfin, pixels * sizeof(float));
+    ALLOC(w.g2d, N * 9 * sizeof(float));
+    ALLOC(w.load_sums, 4 * sizeof(double));
+    ALLOC(w.hist, kHistWords * sizeof(uint32_t));
+    ALLOC(w.counters, kCntSlots * sizeof(uint32_t));
+    ALLOC(w.status, sizeof(uint32_t) * 4);
+    ALLOC(w.lookback, w.lookback_words * sizeof(unsigned long long));
+    ALLOC(w.d_fp, sizeof(FrameParams));
+    ALLOC(w.d_stage, sizeof(uint32_t));
+#undef ALLOC
+    if (cudaMemset(w.lookback, 0, w.lookback_words * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(w.status, 0, sizeof(uint32_t) * 4) != cudaSuccess ||
+        cudaMemset(w.counters, 0, kCntSlots * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(w.d_stage, 0, sizeof(uint32_t)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        free_workspace(w);
+        return fail(ADR_ERR_CUDA, "workspace initialisation failed");
+    }
+    return ADR_OK;
+}
+}  // namespace adr
+
+namespace {
+
+void free_ctx(adr_ctx* c) {
+    free_workspace(c->ws);
+    void* ptrs[] = {c->stage, c->stage_img, c->stage_load};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_words) cudaFreeHost(c->host_words);
@@ -176,69 +255,13 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     c->device = device;
     c->max_w = max_width;
     c->max_h = max_height;
-    Workspace& w = c->ws;
-    w.max_n = max_gaussians;
-    w.capacity = pair_capacity;
-    w.max_tiles = ((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
-    int sms = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess || sms <= 0) {
-        free_ctx(c);
-        return fail(ADR_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    adr_status st = alloc_workspace(c->ws, max_gaussians, pair_capacity, max_width, max_height, device);
+    if (st != ADR_OK) {
+        delete c;
+        return st;
     }
-    w.sm_count = sms;
-    w.sort_grid = sms * onesweep_blocks_per_sm();
-    w.scan_grid = sms * scan_blocks_per_sm();
-
-    const size_t N = (size_t)max_gaussians, P = (size_t)pair_capacity;
-    const size_t pixels = (size_t)max_width * max_height;
-    w.lookback_words = (((N > P ? N : P) + kSortChunk - 1) / kSortChunk + 2) * kRadix;
-#define ALLOC(ptr, bytes)                                                                   \
-    do {                                                                                    \
-        e = cudaMalloc((void**)&(ptr), (bytes));                                           \
-        if (e != cudaSuccess) {                                                             \
-            free_ctx(c);                                                                    \
-            return fail(ADR_ERR_CUDA, "cudaMalloc(%zu) for %s: %s", (size_t)(bytes), #ptr,  \
-                        cudaGetErrorString(e));                                             \
-        }                                                                                   \
-    } while (0)
-    ALLOC(w.rec, N * kRecFloat4 * sizeof(float4));
-    ALLOC(w.aux, N * kAuxFloat4 * sizeof(float4));
-    ALLOC(w.depth_key, N * sizeof(uint32_t));
-    ALLOC(w.tiles, N * sizeof(uint32_t));
-    ALLOC(w.rect, N * sizeof(ushort4));
-    ALLOC(w.offsets, N * sizeof(uint32_t));
-    ALLOC(w.sorted_box, N * sizeof(uint32_t));
-    for (int b = 0; b < 2; ++b) {
-        ALLOC(w.gkeys[b], N * sizeof(uint32_t));
-        ALLOC(w.gvals[b], N * sizeof(uint32_t));
-        ALLOC(w.pgauss[b], P * sizeof(uint32_t));
-    }
-    ALLOC(w.ptile, P * sizeof(uint32_t));
-    ALLOC(w.chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
-    ALLOC(w.ranges, (size_t)w.max_tiles * sizeof(uint2));
-    ALLOC(w.last, pixels * sizeof(int32_t));
-    ALLOC(w.trav, pixels * sizeof(int32_t));
-    ALLOC(w.tfin, pixels * sizeof(float));
-    ALLOC(w.g2d, N * 9 * sizeof(float));
-    ALLOC(w.load_sums, 4 * sizeof(double));
-    ALLOC(w.hist, kHistWords * sizeof(uint32_t));
-    ALLOC(w.counters, kCntSlots * sizeof(uint32_t));
-    ALLOC(w.status, sizeof(uint32_t) * 4);
-    ALLOC(w.lookback, w.lookback_words * sizeof(unsigned long long));
-    ALLOC(w.d_fp, sizeof(FrameParams));
-    ALLOC(w.d_stage, sizeof(uint32_t));
-#undef ALLOC
-    e = cudaHostAlloc((void**)&c->host_words, 64 * sizeof(uint32_t), cudaHostAllocDefault);
+    cudaError_t e = cudaHostAlloc((void**)&c->host_words, 64 * sizeof(uint32_t), cudaHostAllocDefault);
     if (e != cudaSuccess) { free_ctx(c); return fail(ADR_ERR_CUDA, "cudaHostAlloc: %s", cudaGetErrorString(e)); }
-    if (cudaMemset(w.lookback, 0, w.lookback_words * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(w.status, 0, sizeof(uint32_t) * 4) != cudaSuccess ||
-        cudaMemset(w.counters, 0, kCntSlots * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMemset(w.d_stage, 0, sizeof(uint32_t)) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
-        free_ctx(c);
-        return fail(ADR_ERR_CUDA, "workspace initialisation failed");
-    }
     *out = c;
     return ok();
 }

@@ -259,6 +259,13 @@ void launch_read_gaussians(const float4* rec, const float4* aux, const ushort4* 
                            const uint32_t* tiles, int n, float* geom, int32_t* rect_out,
                            int32_t* tiles_out, cudaStream_t stream);
 
+// Workspace allocation with cudaMalloc (context and serving paths).
+adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_capacity,
+                           int32_t max_width, int32_t max_height, int device);
+void free_workspace(Workspace& w);
+size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max_width,
+                       int32_t max_height);
+
 // Error reporting and argument conversion shared by the entry points.
 adr_status report_error(adr_status st, const char* msg);
 adr_status report_ok();
