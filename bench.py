@@ -57,10 +57,10 @@ def select_workload(name):
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
-# DRAM bytes (read + write) per Gaussian-tile pair from an ncu capture of the
-# tile passes on the heavy-load 600k workload (P = 25.8M; profiles/
-# tile_passes_heavy-600k-1080p.md), scaled to a launch by the measured P.
-TRAFFIC_BYTES_PER_PAIR = {"tile_pass_first": 215.57e6 / 25.81e6, "tile_pass_last": 354.68e6 / 25.81e6}
+# DRAM bytes (read + write) per Gaussian-tile pair of the tile-sort kernels
+# from an ncu capture (scaled to a launch by the measured P); empty until the
+# current kernels have been captured.
+TRAFFIC_BYTES_PER_PAIR = {}
 
 
 def peaks():
@@ -249,8 +249,11 @@ def kernel_bytes(name, n, u, hw):
         "depth_pass": 16 * n,                      # key + value in and out
         "scan_tiles": 12 * n + 8 * V,
         "init_ranges": 8 * (hw // 256),
-        "tile_pass_first": 8 * P + 16 * V,         # generated pairs out (tile, Gaussian)
-        "tile_pass_last": 12 * P,                  # pairs in, Gaussian ids out
+        "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
+        "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident
+        "tile_scatter_columns": 6 * P + 12 * V,    # pairs out (u16 key, Gaussian); staging in
+        "tile_count_rows": 2 * P,                  # u16 keys in
+        "tile_scatter_rows": 10 * P,               # pairs in, Gaussian ids out
         "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
     }[name]
 
@@ -303,6 +306,90 @@ def train_step_rate(local, steps=20, warmup=5):
     return {"workload": "cluster-1M-720p", "steps_per_s": 1e3 / ms, "ms_per_step": ms,
             "final_l1": float(loss.item()),
             "step": "forward + L1 + adr_render_backward + Adam on 1M Gaussians, 1280x720"}
+
+
+def serve_measure(local, n_requests=2000, warmup_requests=200, rate=200.0, seed=21):
+    """Serving: 4 resident clustered scenes (0.5M, 1M, 3M, 6M Gaussians), a
+    Poisson stream of `rate` requests/s, each a random camera on the radius-4
+    sphere at a resolution drawn from {800x800, 1280x720, 1920x1080}, through
+    the continuous-batching server (adr_serve_*).  Latency is submit to
+    completion; a closed-loop burst of the same request mix gives the
+    saturation throughput."""
+    import torch
+    from paper_2409_08669_gb300.raster import upload
+    from paper_2409_08669_gb300.serve import Server
+    sizes = (6_000_000, 3_000_000, 1_000_000, 500_000)
+    params = [upload(S.cluster_scene(n=n, seed=31 + k), device=f"cuda:{local}") for k, n in enumerate(sizes)]
+    st = S.Settings(mode=S.MODE_AABB)
+    srv = Server(max_slots=4, mem_budget_bytes=12 << 30, slot_pair_capacity=1 << 27,
+                 slot_max_gaussians=max(sizes), max_width=1920, max_height=1080, device=local)
+    ids = [srv.add_scene(p, st) for p in params]
+    res = ((800, 800), (1280, 720), (1920, 1080))
+    rng = np.random.default_rng(seed)
+    nbuf = 64
+    bufs = [torch.empty(3 * 1920 * 1080, dtype=torch.float32, device=f"cuda:{local}") for _ in range(nbuf)]
+    torch.cuda.synchronize()
+    owner = [None] * nbuf
+    failed = []
+
+    def finish(b):
+        status = srv.poll(owner[b])
+        if status != 0:
+            failed.append(status)
+        owner[b] = None
+
+    def request(k):
+        w, h = res[int(rng.integers(0, 3))]
+        cam = S.sphere_camera(rng, radius=4.0, width=w, height=h)
+        b = k % nbuf
+        if owner[b] is not None:
+            finish(b)
+        owner[b] = srv.submit(ids[int(rng.integers(0, 4))], cam, bufs[b][: 3 * w * h].view(3, h, w))
+        return owner[b]
+
+    def drain():
+        for b in range(nbuf):
+            if owner[b] is not None:
+                finish(b)
+
+    def poisson(count, k0):
+        gaps = rng.exponential(1.0 / rate, size=count)
+        t = time.perf_counter()
+        for k in range(count):
+            t += gaps[k]
+            while time.perf_counter() < t:
+                pass
+            request(k0 + k)
+        drain()
+
+    poisson(warmup_requests, 0)
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    poisson(n_requests, warmup_requests)
+    wall = time.perf_counter() - t0
+    open_loop = srv.stats()
+    srv.reset_stats()
+    burst = 400
+    t0 = time.perf_counter()
+    for k in range(burst):
+        request(k)
+    drain()
+    closed = srv.stats()
+    burst_wall = time.perf_counter() - t0
+    srv.close()
+    del params, bufs
+    torch.cuda.empty_cache()
+    return {"workload": "serve-4scenes-poisson200",
+            "scenes": list(sizes), "resolutions": [f"{w}x{h}" for w, h in res],
+            "arrival_rate_per_s": rate, "requests": n_requests,
+            "p50_ms": open_loop["p50_ms"], "p99_ms": open_loop["p99_ms"],
+            "mean_ms": open_loop["mean_ms"], "frames_per_s": n_requests / wall,
+            "max_inflight": int(open_loop["max_inflight"]),
+            "admitted_while_busy": int(open_loop["admitted_while_busy"]),
+            "capacity_errors": int(open_loop["capacity_errors"]),
+            "saturation_frames_per_s": burst / burst_wall,
+            "saturation_p50_ms": closed["p50_ms"], "saturation_p99_ms": closed["p99_ms"],
+            "failed_requests": len(failed), "slots": 4, "graphs": True}
 
 
 def e2e_host(rast_ctx, scene, cams, st, steps, warmup):
@@ -462,6 +549,8 @@ def run_ours(args):
     del params
     if not args.no_train:
         result["train_step"] = train_step_rate(local)
+    if not args.no_serve and world == 1:
+        result["serve"] = serve_measure(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(scene, cams, st_adr, budget_s=args.cpu_budget)
     if rank == 0:
@@ -576,6 +665,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heavy-3M-1080p")
     ap.add_argument("--quick", action="store_true",

@@ -217,7 +217,7 @@ adr_status adr_render_host(adr_ctx *ctx, const float *means, const float *scales
  * synchronisation -- and so cannot create an adr_ctx.
  * It runs the same stages as adr_preprocess + adr_sort + adr_render with all
  * intermediates in one static device array compiled into the library (about
- * 23 MB, held by every GPU that loads the library until the process exits).
+ * 20 MB, held by every GPU that loads the library until the process exits).
  * Limits: n <= 32768 Gaussians, width and height <= 512, at most 1048576
  * Gaussian-tile pairs; larger sizes are rejected with ADR_ERR_INVALID, and a
  * frame that produces more pairs returns ADR_ERR_CAPACITY (image incomplete).
@@ -235,6 +235,78 @@ adr_status adr_render_frame_noalloc(const float *means, const float *scales, con
                                     const float *opac, const float *sh, int64_t n,
                                     const adr_camera *camera, const adr_settings *settings,
                                     float *img, float *t_final, int32_t *load, void *stream);
+
+/* ---- Serving: continuous batching of frames over resident scenes ---------
+ * A server renders requests {scene, camera (any size up to max_width x
+ * max_height)} -> image with the stages of adr_preprocess + adr_sort +
+ * adr_render (Sec. 3, Fig. 2) on a device.  The paper renders one camera at a
+ * time; the server's scheduler is this library's own.  A scheduler thread owns
+ * max_slots execution slots, each a frame workspace (as adr_create's, for
+ * slot_max_gaussians and slot_pair_capacity) with its own CUDA stream, so
+ * frames in different slots overlap on the GPU.  Requests wait in a FIFO queue;
+ * the head is admitted as soon as a slot is free and the predicted bytes of
+ * everything in flight, plus its own, stay within mem_budget_bytes (a request
+ * is always admitted when nothing is in flight).  Predicted bytes of a request
+ * = 12 * pairs + 150 * n + 32 * W * H, with pairs = 1.25 * (the scene's learned
+ * pairs per pixel) * W * H, or slot_pair_capacity while the scene has no
+ * completed frame; each slot's buffers are allocated once, at creation, so the
+ * budget bounds the working set in flight, not the allocation.  With
+ * use_graphs != 0 each (slot, scene, W, H) frame is captured once into a CUDA
+ * graph and replayed after a one-thread kernel writes the request's camera
+ * into the device copy the graph's kernels read.  A request's result equals that of adr_preprocess +
+ * adr_sort + adr_render on its own (bit-identical image). */
+typedef struct adr_server adr_server;
+
+typedef struct adr_serve_config {
+    int32_t max_slots;            /* 1..64 concurrent frames */
+    int64_t mem_budget_bytes;     /* admission budget, > 0 */
+    int64_t slot_pair_capacity;   /* Gaussian-tile pairs per slot, 1..2^30 */
+    int64_t slot_max_gaussians;   /* largest scene, > 0 */
+    int32_t max_width, max_height;/* largest image, <= 4096 each */
+    int32_t use_graphs;           /* 0: plain launches; else graph replay */
+    int32_t device;               /* CUDA device ordinal */
+} adr_serve_config;
+
+/* Allocates every slot and starts the scheduler thread.  ADR_ERR_INVALID for
+ * a configuration out of range, ADR_ERR_CUDA if an allocation fails (nothing
+ * leaks). */
+adr_status adr_serve_create(adr_server **server, const adr_serve_config *config);
+/* Waits for frames in flight, stops the scheduler and frees everything.
+ * Requests still queued are dropped.  NULL is a no-op. */
+void adr_serve_destroy(adr_server *server);
+/* Registers a resident scene (device pointers with the layout of
+ * adr_preprocess; BORROWED: they must stay valid and unchanged while the
+ * server lives) rendered with `settings`.  ADR_ERR_INVALID if n is outside
+ * 1..slot_max_gaussians or a pointer is NULL or misaligned. */
+adr_status adr_serve_add_scene(adr_server *server, const float *means, const float *scales,
+                               const float *rots, const float *opac, const float *sh, int64_t n,
+                               const adr_settings *settings, int32_t *scene_id);
+/* Queues a request and returns at once with its ticket.  out_img: caller's
+ * DEVICE buffer [3, H, W] fp32, written when the request completes; it must
+ * stay valid until adr_serve_poll reports the ticket finished.  ADR_ERR_INVALID
+ * for an unknown scene or a bad camera; ADR_ERR_ADMISSION (nothing queued) if
+ * the request's minimum bytes (150 n + 32 W H + 49152) exceed the budget, so it
+ * could never be admitted. */
+adr_status adr_serve_submit(adr_server *server, int32_t scene_id, const adr_camera *camera,
+                            float *out_img, uint64_t *ticket);
+/* Waits up to timeout_us microseconds (0: do not wait) for a request.
+ * Returns ADR_OK when its image is written (the ticket is then released),
+ * ADR_PENDING if timeout_us == 0 and it is not finished, ADR_ERR_TIMEOUT if
+ * the wait ran out (the ticket stays valid), or the request's own error
+ * (ADR_ERR_CAPACITY: more pairs than slot_pair_capacity, image incomplete;
+ * ADR_ERR_TIMEOUT: a bounded device wait gave up; ADR_ERR_CUDA), which also
+ * releases the ticket.  ADR_ERR_INVALID for an unknown ticket. */
+adr_status adr_serve_poll(adr_server *server, uint64_t ticket, int64_t timeout_us);
+/* Statistics since creation, first min(n, 10) of: completed requests, p50
+ * latency ms, p99 latency ms, mean latency ms (submit to completion seen by
+ * the scheduler), the largest number of frames in flight at once, requests
+ * admitted while another was in flight, requests rejected by admission,
+ * completed frames per second (first submit to last completion), requests
+ * that ended with ADR_ERR_CAPACITY, graph replays. */
+adr_status adr_serve_stats(adr_server *server, double *out, int32_t n);
+/* Restarts the statistics (requests in flight still complete into the new
+ * window). */
+adr_status adr_serve_reset_stats(adr_server *server);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char *adr_last_error(void);

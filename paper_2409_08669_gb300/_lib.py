@@ -46,6 +46,13 @@ class adr_settings(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32)]
 
 
+class adr_serve_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
+                ("slot_pair_capacity", ctypes.c_int64), ("slot_max_gaussians", ctypes.c_int64),
+                ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 _P = ctypes.c_void_p
@@ -75,6 +82,15 @@ _SIGNATURES = {
     "adr_profile_enable": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
+    "adr_serve_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(adr_serve_config)]),
+    "adr_serve_destroy": (None, [_P]),
+    "adr_serve_add_scene": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_settings),
+                                   ctypes.POINTER(_I32)]),
+    "adr_serve_submit": (_I32, [_P, _I32, ctypes.POINTER(adr_camera), _P,
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "adr_serve_poll": (_I32, [_P, ctypes.c_uint64, _I64]),
+    "adr_serve_stats": (_I32, [_P, _P, _I32]),
+    "adr_serve_reset_stats": (_I32, [_P]),
     "adr_last_error": (ctypes.c_char_p, []),
     "adr_version": (ctypes.c_char_p, []),
 }

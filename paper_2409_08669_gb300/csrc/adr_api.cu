@@ -135,7 +135,7 @@ void free_workspace(Workspace& w) {
         w.prof = nullptr;
     }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
-                    w.gkeys[1], w.gvals[0], w.gvals[1], w.ptile, w.pgauss[0], w.pgauss[1],
+                    w.gkeys[1], w.gvals[0], w.gvals[1], w.pkey, w.pgauss[0], w.pgauss[1], w.tcounts,
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
     for (void* p : ptrs)
@@ -148,9 +148,10 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t N = (size_t)max_gaussians, P = (size_t)pair_capacity;
     const size_t pixels = (size_t)max_width * max_height;
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
-    const size_t lb = (((N > P ? N : P) + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
-    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 12 +
-           (P / kSortChunk + 2) * 4 + tiles * 8 + pixels * 12 + lb + 4096;
+    const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 10 +
+           (P / kSortChunk + 2) * 4 + tiles * 8 + pixels * 12 + lb +
+           (size_t)kRadix * kMaxTileGrid * 4 + 4096;
 }
 
 adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_capacity,
@@ -166,9 +167,11 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     w.sm_count = sms;
     w.sort_grid = sms * onesweep_blocks_per_sm();
     w.scan_grid = sms * scan_blocks_per_sm();
+    w.tile_grid = sms * tile_scatter_blocks_per_sm();
+    if (w.tile_grid > kMaxTileGrid) w.tile_grid = kMaxTileGrid;
     const size_t N = (size_t)max_gaussians, P = (size_t)pair_capacity;
     const size_t pixels = (size_t)max_width * max_height;
-    w.lookback_words = (((N > P ? N : P) + kSortChunk - 1) / kSortChunk + 2) * kRadix;
+    w.lookback_words = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix;
 #define ALLOC(ptr, bytes)                                                                   \
     do {                                                                                    \
         e = cudaMalloc((void**)&(ptr), (bytes));                                           \
@@ -190,7 +193,8 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
         ALLOC(w.gvals[b], N * sizeof(uint32_t));
         ALLOC(w.pgauss[b], P * sizeof(uint32_t));
     }
-    ALLOC(w.ptile, P * sizeof(uint32_t));
+    ALLOC(w.pkey, P * sizeof(uint16_t));
+    ALLOC(w.tcounts, (size_t)kRadix * kMaxTileGrid * sizeof(uint32_t));
     ALLOC(w.chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
     ALLOC(w.ranges, (size_t)w.max_tiles * sizeof(uint2));
     ALLOC(w.last, pixels * sizeof(int32_t));

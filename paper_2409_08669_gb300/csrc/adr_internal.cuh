@@ -45,8 +45,8 @@ struct FrameParams {
 };
 
 // Decoupled-lookback pass tag: epoch = (*stage) * 8 + pass, where *stage is a
-// device counter bumped by the first kernel of every preprocess / sort call,
-// so every pass (also in a replayed graph) gets a tag no stale word carries.
+// device counter bumped by the first kernel of every preprocess call, so every
+// pass (also in a replayed graph) gets a tag no stale word carries.
 struct EpochRef {
     const uint32_t* stage;
     uint32_t pass;
@@ -71,21 +71,23 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;                           // up to 32 key bits
 constexpr int kMaxTiles = 1 << 16;                      // tile ids sort in two 8-bit passes
+constexpr int kMaxTileGrid = 2048;                      // CTAs of a tile-sort pass (bounds tcounts)
 
 // Per-call counters kept on the device.
 enum Counter : int {
     kCntPairs = 0,        // number of pairs P (sum of tiles over Gaussians), saturating
     kCntVisible = 1,      // Gaussians with at least one tile (they sort first by depth)
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
-    kCntSortTicket0 = 4,  // chunk tickets of the sort passes (depth: 4, tiles: 2)
+    kCntSortTicket0 = 4,  // chunk tickets of the depth-sort passes (4)
     kCntSlots = 16
 };
 
 // Optional per-launch timing with CUDA events recorded on the launching
 // stream (adr_profile_enable / adr_profile_read).
 enum KernelId : int {
-    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKInitRanges, kKTilePassFirst,
-    kKTilePassLast, kKRender, kKRenderBackward, kKPreprocessBackward, kKernelCount
+    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKInitRanges, kKTileCountColumns,
+    kKTileScatterColumns, kKTileCountRows, kKTileScatterRows, kKTileCountScan, kKRender,
+    kKRenderBackward, kKPreprocessBackward, kKernelCount
 };
 const char* kernel_name(int id);
 struct Profiler {
@@ -102,7 +104,7 @@ struct Profiler {
 struct Workspace {
     int64_t max_n = 0, capacity = 0;       // Gaussians, Gaussian-tile pairs
     int max_tiles = 0;
-    int sm_count = 0, sort_grid = 0, scan_grid = 0;
+    int sm_count = 0, sort_grid = 0, scan_grid = 0, tile_grid = 0;
     float4* rec = nullptr;                 // [max_n * kRecFloat4]
     float4* aux = nullptr;                 // [max_n * kAuxFloat4]
     uint32_t* depth_key = nullptr;         // [max_n]
@@ -112,8 +114,9 @@ struct Workspace {
     uint32_t* sorted_box = nullptr;        // [max_n] packed tile rectangle per depth-order position
     uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
-    uint32_t* ptile = nullptr;             // [capacity]  pair tiles after the first tile pass
+    uint16_t* pkey = nullptr;              // [capacity] ty << 8 | tx of the pairs after tile pass 1
     uint32_t* pgauss[2] = {nullptr, nullptr};  // [capacity] each
+    uint32_t* tcounts = nullptr;           // [kRadix * kMaxTileGrid] per-(digit, CTA) counts / starts
     uint32_t* chunk_first = nullptr;       // [capacity / kSortChunk + 2]
     uint2* ranges = nullptr;               // [max_tiles]
     int32_t* last = nullptr;               // [max pixels]
@@ -125,21 +128,21 @@ struct Workspace {
     uint32_t* counters = nullptr;          // [kCntSlots]
     uint32_t* status = nullptr;            // [4]
     unsigned long long* lookback = nullptr;
-    size_t lookback_words = 0;             // (max(max_n, capacity) / kSortChunk + 2) * kRadix
+    size_t lookback_words = 0;             // (max_n / kSortChunk + 2) * kRadix
     Profiler* prof = nullptr;              // non-null: time every launch
     FrameParams* d_fp = nullptr;           // [1] camera + settings of the current frame
     uint32_t* d_stage = nullptr;           // [1] stage counter (see EpochRef)
 };
 
-// hist layout: 4 x 256 depth digits, then 2 x 256 tile digits.
-constexpr int kHistWords = (kMaxPasses + 2) * kRadix;
+// hist layout: 4 x 256 depth digits.
+constexpr int kHistWords = kMaxPasses * kRadix;
 
 // What one frame's stages hand to the next.
 struct FrameState {
     int64_t n = 0;
     CamDev cam{};
     SetDev st{};
-    int num_tiles = 0, tile_bits = 0, bits1 = 0, bits2 = 0, tile_passes = 0;
+    int num_tiles = 0;
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
     const uint32_t* sorted_gauss = nullptr;  // pairs' Gaussians by (tile, depth)
 };
@@ -148,15 +151,18 @@ struct FrameState {
 // wraps) clears the lookback words.
 void count_stage(std::atomic<uint32_t>& calls, const Workspace& ws, cudaStream_t stream);
 // One-thread kernel that stores a frame's camera and settings in device
-// memory; in a captured graph its by-value argument is the one node a replay
-// for another camera updates (cudaGraphExecKernelNodeSetParams).
+// memory, so the kernels that read them can be captured once in a graph and
+// replayed for other cameras.
 void launch_set_frame_params(const FrameParams& p, FrameParams* d_fp, cudaStream_t stream);
 const void* set_frame_params_kernel();
 
 // Stage orchestration shared by every entry point (pipeline.cu).
+// set_params = false leaves the camera/settings in ws.d_fp to the caller (a
+// captured graph replayed for other cameras writes them before each replay).
 void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                         const float* means, const float* scales, const float* rots,
-                        const float* opac, const float* sh, cudaStream_t stream);
+                        const float* opac, const float* sh, cudaStream_t stream,
+                        bool set_params = true);
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream);
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
@@ -191,37 +197,43 @@ struct PairSource {
     int tiles_x = 0;
 };
 
-// First tile pass: the pairs are generated on chip from the depth-ordered
-// Gaussians (no pair list in memory) and scattered by the low tile digit.
-// With final = true (single pass) it writes only Gaussian ids and the ranges.
-void launch_tile_pass_first(const PairSource& src, uint32_t* tile_out, uint32_t* gauss_out,
-                            int digit_bits, bool final, uint2* ranges, const uint32_t* hist,
-                            unsigned long long* lookback, EpochRef epoch, uint32_t* ticket,
-                            uint32_t* status, int grid, cudaStream_t stream);
-// Second tile pass: scatter by the high digit, write only Gaussian ids, and
-// derive each tile's [start, end) from the digit runs.
-void launch_tile_pass_last(const uint32_t* tile_in, const uint32_t* gauss_in, uint32_t* gauss_out,
-                           const uint32_t* counters, int64_t capacity, int shift, int digit_bits,
-                           uint2* ranges, const uint32_t* hist, unsigned long long* lookback,
-                           EpochRef epoch, uint32_t* ticket, uint32_t* status, int grid,
-                           cudaStream_t stream);
+// Tile sort (tiles.cu), two range-partitioned counting passes over the
+// pairs, by tx then by ty; `grid` CTAs, each owning a contiguous run of
+// 4096-pair chunks; counts holds kRadix x grid words.
+//   count_columns: per-CTA tx counts from the Gaussians' rectangles;
+//   count_rows:    per-CTA ty counts from the pass-1 keys;
+//   count_scan:    counts -> global start of every (digit, CTA) run, in place;
+//   scatter_columns: pairs generated on chip from the depth-ordered
+//                  Gaussians, written as (ty << 8 | tx, Gaussian) grouped by tx;
+//   scatter_rows:  Gaussian ids grouped by ty (final order) and each tile's
+//                  [start, end) in ranges (initialised to (0xFFFFFFFF, 0)).
+int tile_scatter_blocks_per_sm();
+void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* status, int grid,
+                               cudaStream_t stream);
+void launch_tile_count_rows(const uint16_t* keys, const uint32_t* counters, int64_t capacity,
+                            uint32_t* counts, int grid, cudaStream_t stream);
+void launch_tile_count_scan(uint32_t* counts, int grid, cudaStream_t stream);
+void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint16_t* keys_out,
+                                 uint32_t* gauss_out, uint32_t* status, int grid,
+                                 cudaStream_t stream);
+void launch_tile_scatter_rows(const uint16_t* keys_in, const uint32_t* gauss_in,
+                              const uint32_t* starts, uint32_t* gauss_out, uint2* ranges,
+                              const uint32_t* counters, int64_t capacity, int tiles_x,
+                              int num_tiles, uint32_t* status, int grid, cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
 // coordinates and extents fit 8 bits because images are at most 4096 pixels
 // per side).
 // Exclusive scan of tiles[order[i]] with decoupled lookback.  Also writes the
 // packed rectangle of each depth-order position with tiles (sorted_box), the
-// pair total and visible count to counters, the tile-digit histograms of the
-// two tile passes (hist_tiles[0..255] low digit of bits1 bits, [256..511]
-// high digit) and chunk_first[c] = position of the Gaussian holding pair
-// c * kSortChunk.
+// pair total and visible count to counters, and chunk_first[c] = position of
+// the Gaussian holding pair c * kSortChunk.
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
-                       int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
-                       uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
-                       unsigned long long* lookback, EpochRef epoch, uint32_t* counters,
-                       uint32_t* status, int grid, cudaStream_t stream);
+                       int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
+                       uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
+                       uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);
 
-void launch_init_ranges(uint2* ranges, int num_tiles, uint32_t* stage, cudaStream_t stream);
+void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const FrameParams* fp, int num_tiles, float* img, float* t_final,

@@ -1,12 +1,12 @@
 // Stages 2-3 of the rasterization pipeline (Sec. 3.2.1), InclusiveSum and the
 // bookkeeping DuplicateWithKeys needs, over the Gaussians in view-depth order:
-//   * offsets[i] = exclusive prefix sum of the tile counts (decoupled lookback),
-//     the pair total P and the number of Gaussians with tiles;
+//   * offsets[i] = exclusive prefix sum of the tile counts (decoupled lookback,
+//     32 predecessor words per round trip), the pair total P and the number
+//     of Gaussians with tiles;
 //   * chunk_first[c] = depth-order position of the Gaussian that holds pair
-//     c * 4096, so each chunk of the first tile-sort pass can generate its
-//     pairs on chip without an emitted pair list;
-//   * the histograms of the two tile-sort digits, counted per rectangle row
-//     (a row of a tile rectangle is a contiguous range of tile ids).
+//     c * 4096, so the tile sort can generate each chunk's pairs on chip
+//     without an emitted pair list;
+//   * sorted_box[i] = the packed tile rectangle of depth-order position i.
 // Plus small helpers for the tile ranges.
 #include "adr_internal.cuh"
 
@@ -25,26 +25,63 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
     return (s < a || s > kSat) ? kSat : s;
 }
 
+// Exclusive prefix of chunk `chunk` by decoupled lookback, run by one warp:
+// lane l reads the word of chunk j - l, so each round trip covers 32
+// predecessors; the words up to the nearest inclusive prefix are summed.
+// Lane 0 publishes this chunk's aggregate first and its inclusive prefix last.
+__device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, uint32_t total,
+                                  uint32_t epoch, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long tag = (unsigned long long)epoch << 32;
+    volatile unsigned long long* lb = lookback;
+    if (chunk == 0) {
+        if (lane == 0) lb[0] = tag | kScanInc | min(total, kSat);
+        return 0;
+    }
+    if (lane == 0) lb[chunk] = tag | min(total, kSat);
+    uint64_t excl = 0;
+    int64_t j = (int64_t)chunk - 1;   // the nearest predecessor not yet summed
+    int spins = 0;
+    for (;;) {
+        const int64_t idx = j - lane;
+        // Before chunk 0 reads as an inclusive prefix of 0 (never reached:
+        // chunk 0 always publishes one).
+        const unsigned long long w = idx >= 0 ? lb[idx] : (tag | kScanInc);
+        const bool ready = (uint32_t)(w >> 32) == epoch;
+        const uint32_t not_ready = __ballot_sync(0xffffffffu, !ready);
+        const uint32_t inc = __ballot_sync(0xffffffffu, ready && (w & kScanInc));
+        const int first_nr = not_ready ? __ffs(not_ready) - 1 : 32;
+        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+        const int take = first_inc < first_nr ? first_inc + 1 : first_nr;   // summed lanes
+        uint64_t v = lane < take ? (uint64_t)((uint32_t)w & kSat) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (first_inc < first_nr) break;
+        j -= take;
+        if (take == 0) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicOr(status, kErrLookback);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    const uint32_t e = (uint32_t)min(excl, (uint64_t)kSat);
+    if (lane == 0) lb[chunk] = tag | kScanInc | sat_add(e, total);
+    return e;
+}
+
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
-             const ushort4* __restrict__ rect, int64_t n, int tiles_x, int bits1,
-             int64_t capacity, uint32_t* __restrict__ offsets, uint32_t* __restrict__ sorted_box,
-             uint32_t* __restrict__ chunk_first,
-             uint32_t* __restrict__ hist_tiles, unsigned long long* __restrict__ lookback,
+             const ushort4* __restrict__ rect, int64_t n, int64_t capacity,
+             uint32_t* __restrict__ offsets, uint32_t* __restrict__ sorted_box,
+             uint32_t* __restrict__ chunk_first, unsigned long long* __restrict__ lookback,
              EpochRef eref, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
-    __shared__ uint32_t s_lo_diff[kRadix + 1];   // circular difference array of the low digit
-    __shared__ uint32_t s_hi[kRadix];
-    __shared__ uint32_t s_full;                  // full cycles of the low digit (every bin + 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long tag = (unsigned long long)epoch << 32;
-    const uint32_t R1 = 1u << bits1, M1 = R1 - 1u;
-    for (int i = tid; i <= kRadix; i += kScanThreads) s_lo_diff[i] = 0;
-    for (int i = tid; i < kRadix; i += kScanThreads) s_hi[i] = 0;
-    if (tid == 0) s_full = 0;
-    uint32_t my_full = 0;
 
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(counters + kCntScanTicket, 1u);
@@ -77,36 +114,15 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
             total += s_warp[w];
         }
         const uint32_t texcl = wbase + x - tsum;
-        // Chunk prefix by decoupled lookback (one thread).
-        if (tid == 0) {
-            unsigned long long* my = lookback + chunk;
-            uint32_t excl = 0;
-            if (chunk == 0) {
-                *reinterpret_cast<volatile unsigned long long*>(my) = tag | kScanInc | min(total, kSat);
-            } else {
-                *reinterpret_cast<volatile unsigned long long*>(my) = tag | min(total, kSat);
-                int64_t j = (int64_t)chunk - 1;
-                int spins = 0;
-                while (j >= 0) {
-                    const unsigned long long w =
-                        *reinterpret_cast<volatile unsigned long long*>(lookback + j);
-                    if ((uint32_t)(w >> 32) != epoch) {
-                        if (++spins > kSpinLimit) { atomicOr(status, kErrLookback); break; }
-                        __nanosleep(32);
-                        continue;
-                    }
-                    excl = sat_add(excl, (uint32_t)w & kSat);
-                    if (w & kScanInc) break;
-                    --j;
+        if (warp == 0) {
+            const uint32_t excl = warp_lookback(lookback, chunk, total, epoch, status);
+            if (lane == 0) {
+                s_prefix = excl;
+                if (base + kScanChunk >= n) {
+                    const uint32_t p = sat_add(excl, total);
+                    counters[kCntPairs] = p;
+                    if ((int64_t)p > capacity) atomicOr(status, kErrCapacity);
                 }
-                *reinterpret_cast<volatile unsigned long long*>(my) =
-                    tag | kScanInc | sat_add(excl, total);
-            }
-            s_prefix = excl;
-            if (base + kScanChunk >= n) {
-                const uint32_t p = sat_add(excl, total);
-                counters[kCntPairs] = p;
-                if ((int64_t)p > capacity) atomicOr(status, kErrCapacity);
             }
         }
         const uint32_t nz = __reduce_add_sync(0xffffffffu, nonzero);
@@ -125,56 +141,17 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
                 const uint64_t c_max = ((uint64_t)capacity - 1) / kSortChunk;
                 if (c_hi > c_max) c_hi = c_max;
                 for (uint64_t c = c_lo; c <= c_hi; ++c) chunk_first[c] = (uint32_t)i;
-                // digit histograms of this Gaussian's pairs, row by row
                 const ushort4 r = rect[order[i]];
-                const uint32_t w = (uint32_t)(r.z - r.x);
-                sorted_box[i] = (uint32_t)r.x | ((uint32_t)r.y << 8) | ((w - 1u) << 16) |
-                                ((uint32_t)(r.w - r.y - 1) << 24);
-                for (uint32_t ty = r.y; ty < r.w; ++ty) {
-                    const uint32_t a0 = ty * (uint32_t)tiles_x + r.x;   // tile ids a0 .. a0+w-1
-                    my_full += w >> bits1;
-                    const uint32_t rem = w & M1, s0 = a0 & M1;
-                    if (rem) {
-                        atomicAdd(&s_lo_diff[s0], 1u);
-                        if (s0 + rem <= R1) {
-                            atomicAdd(&s_lo_diff[s0 + rem], 0xFFFFFFFFu);
-                        } else {
-                            atomicAdd(&s_lo_diff[0], 1u);
-                            atomicAdd(&s_lo_diff[s0 + rem - R1], 0xFFFFFFFFu);
-                        }
-                    }
-                    const uint32_t h0 = a0 >> bits1, h1 = (a0 + w - 1) >> bits1;
-                    for (uint32_t hd = h0; hd <= h1; ++hd) {
-                        const uint32_t lo = max(a0, hd << bits1);
-                        const uint32_t hi = min(a0 + w, (hd + 1) << bits1);
-                        atomicAdd(&s_hi[hd & 0xFF], hi - lo);
-                    }
-                }
+                sorted_box[i] = (uint32_t)r.x | ((uint32_t)r.y << 8) |
+                                ((uint32_t)(r.z - r.x - 1) << 16) | ((uint32_t)(r.w - r.y - 1) << 24);
             }
             run = sat_add(run, t);
         }
         __syncthreads();
     }
-    // Flush this CTA's digit histograms.
-    const uint32_t fw = __reduce_add_sync(0xffffffffu, my_full);
-    if (lane == 0 && fw) atomicAdd(&s_full, fw);
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (uint32_t d = 0; d < R1; ++d) {
-            acc += s_lo_diff[d];
-            s_lo_diff[d] = acc + s_full;
-        }
-    }
-    __syncthreads();
-    for (uint32_t d = tid; d < R1; d += kScanThreads)
-        if (s_lo_diff[d]) atomicAdd(hist_tiles + d, s_lo_diff[d]);
-    for (int d = tid; d < kRadix; d += kScanThreads)
-        if (s_hi[d]) atomicAdd(hist_tiles + kRadix + d, s_hi[d]);
 }
 
-__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles, uint32_t* __restrict__ stage) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(stage, 1u);   // new tag for the sort passes
+__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x)
         ranges[t] = make_uint2(0xFFFFFFFFu, 0u);
 }
@@ -233,19 +210,18 @@ int scan_blocks_per_sm() {
 }
 
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
-                       int64_t n, int tiles_x, int bits1, int64_t capacity, uint32_t* offsets,
-                       uint32_t* sorted_box, uint32_t* chunk_first, uint32_t* hist_tiles,
-                       unsigned long long* lookback, EpochRef epoch, uint32_t* counters,
-                       uint32_t* status, int grid, cudaStream_t stream) {
+                       int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
+                       uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
+                       uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
-    k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, tiles_x, bits1, capacity,
-                                                    offsets, sorted_box, chunk_first, hist_tiles,
-                                                    lookback, epoch, counters, status);
+    k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, capacity, offsets,
+                                                    sorted_box, chunk_first, lookback, epoch,
+                                                    counters, status);
 }
 
-void launch_init_ranges(uint2* ranges, int num_tiles, uint32_t* stage, cudaStream_t stream) {
+void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream) {
     if (num_tiles <= 0) return;
-    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles, stage);
+    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles);
 }
 
 void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream) {

@@ -12,7 +12,7 @@
 // scratch lives in the library image itself.
 //
 // The array is sized for at most kNaMaxGaussians Gaussians, kNaMaxPairs
-// Gaussian-tile pairs and kNaMaxWidth x kNaMaxHeight images (about 23 MB);
+// Gaussian-tile pairs and kNaMaxWidth x kNaMaxHeight images (about 20 MB);
 // every GPU that loads the library holds it until the process exits.
 #include <atomic>
 #include <mutex>
@@ -42,8 +42,8 @@ constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
 constexpr size_t kOffSortedBox = align256(kOffOffsets + kNaMaxGaussians * 4);
 constexpr size_t kOffGKeys = align256(kOffSortedBox + kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
-constexpr size_t kOffPTile = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
-constexpr size_t kOffPGauss = align256(kOffPTile + kNaMaxPairs * 4);          // 2 buffers
+constexpr size_t kOffPKey = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
+constexpr size_t kOffPGauss = align256(kOffPKey + kNaMaxPairs * 2);           // 2 buffers
 constexpr size_t kOffChunkFirst = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
 constexpr size_t kOffRanges = align256(kOffChunkFirst + (kNaMaxPairs / kSortChunk + 2) * 4);
 constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
@@ -52,10 +52,11 @@ constexpr size_t kOffTfin = align256(kOffTrav + kPixels * 4);
 constexpr size_t kOffHist = align256(kOffTfin + kPixels * 4);
 constexpr size_t kOffCounters = align256(kOffHist + kHistWords * 4);
 constexpr size_t kOffStatus = align256(kOffCounters + kCntSlots * 4);
-constexpr size_t kLookbackWords = (kNaMaxPairs / kSortChunk + 2) * kRadix;
+constexpr size_t kLookbackWords = (kNaMaxGaussians / kSortChunk + 2) * kRadix;
 constexpr size_t kOffFrameParams = align256(kOffStatus + 16);
 constexpr size_t kOffStage = align256(kOffFrameParams + sizeof(FrameParams));
-constexpr size_t kOffLookback = align256(kOffStage + 16);
+constexpr size_t kOffTCounts = align256(kOffStage + 16);
+constexpr size_t kOffLookback = align256(kOffTCounts + (size_t)kRadix * kMaxTileGrid * 4);
 constexpr size_t kNaBytes = align256(kOffLookback + kLookbackWords * 8);
 
 // The scratch.  Zero-initialised when the module loads (the lookback words
@@ -93,6 +94,8 @@ adr_status setup(int dev, DeviceState*& out) {
         w.sm_count = sms;
         w.sort_grid = sms * onesweep_blocks_per_sm();
         w.scan_grid = sms * scan_blocks_per_sm();
+        w.tile_grid = sms * tile_scatter_blocks_per_sm();
+        if (w.tile_grid > kMaxTileGrid) w.tile_grid = kMaxTileGrid;
         w.rec = reinterpret_cast<float4*>(b + kOffRec);
         w.aux = reinterpret_cast<float4*>(b + kOffAux);
         w.depth_key = reinterpret_cast<uint32_t*>(b + kOffDepth);
@@ -105,7 +108,8 @@ adr_status setup(int dev, DeviceState*& out) {
             w.gvals[k] = reinterpret_cast<uint32_t*>(b + kOffGVals) + k * kNaMaxGaussians;
             w.pgauss[k] = reinterpret_cast<uint32_t*>(b + kOffPGauss) + k * kNaMaxPairs;
         }
-        w.ptile = reinterpret_cast<uint32_t*>(b + kOffPTile);
+        w.pkey = reinterpret_cast<uint16_t*>(b + kOffPKey);
+        w.tcounts = reinterpret_cast<uint32_t*>(b + kOffTCounts);
         w.chunk_first = reinterpret_cast<uint32_t*>(b + kOffChunkFirst);
         w.ranges = reinterpret_cast<uint2*>(b + kOffRanges);
         w.last = reinterpret_cast<int32_t*>(b + kOffLast);

@@ -6,10 +6,10 @@
 namespace adr {
 
 const char* kernel_name(int id) {
-    static const char* names[kKernelCount] = {"preprocess", "depth_hist", "depth_pass",
-                                              "scan_tiles", "init_ranges", "tile_pass_first",
-                                              "tile_pass_last", "render", "render_backward",
-                                              "preprocess_backward"};
+    static const char* names[kKernelCount] = {
+        "preprocess", "depth_hist", "depth_pass", "scan_tiles", "init_ranges",
+        "tile_count_columns", "tile_scatter_columns", "tile_count_rows", "tile_scatter_rows",
+        "tile_count_scan", "render", "render_backward", "preprocess_backward"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
 }
 
@@ -60,28 +60,17 @@ void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev
     fs.cam = cam;
     fs.st = st;
     fs.num_tiles = cam.tiles_x * cam.tiles_y;
-    int b = 0;
-    while ((1 << b) < fs.num_tiles) ++b;
-    fs.tile_bits = b;
-    if (b <= kRadixBits) {            // one pass over all tile bits
-        fs.tile_passes = 1;
-        fs.bits1 = b;
-        fs.bits2 = 0;
-    } else {                          // two balanced passes (e.g. 7 + 6 bits at 1080p)
-        fs.tile_passes = 2;
-        fs.bits1 = (b + 1) / 2;
-        fs.bits2 = b - fs.bits1;
-    }
     fs.order = nullptr;
     fs.sorted_gauss = nullptr;
 }
 
 void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                         const float* means, const float* scales, const float* rots,
-                        const float* opac, const float* sh, cudaStream_t stream) {
+                        const float* opac, const float* sh, cudaStream_t stream,
+                        bool set_params) {
     const int64_t n = fs.n;
     count_stage(epoch, ws, stream);
-    launch_set_frame_params(FrameParams{fs.cam, fs.st}, ws.d_fp, stream);
+    if (set_params) launch_set_frame_params(FrameParams{fs.cam, fs.st}, ws.d_fp, stream);
     cudaMemsetAsync(ws.counters, 0, kCntSlots * sizeof(uint32_t), stream);
     cudaMemsetAsync(ws.hist, 0, kHistWords * sizeof(uint32_t), stream);
     // Stage 1: per-Gaussian projection, covariance, colour and early cull.
@@ -107,18 +96,17 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
     const EpochRef ep{ws.d_stage, (uint32_t)kMaxPasses};
     TIMED(ws, kKScanTiles, stream,
-          launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, fs.cam.tiles_x, fs.bits1, ws.capacity,
-                            ws.offsets, ws.sorted_box, ws.chunk_first,
-                            ws.hist + kMaxPasses * kRadix, ws.lookback, ep, ws.counters,
+          launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, ws.capacity, ws.offsets,
+                            ws.sorted_box, ws.chunk_first, ws.lookback, ep, ws.counters,
                             ws.status, ws.scan_grid, stream));
 }
 
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream) {
-    const int t0 = kCntSortTicket0 + kMaxPasses;
-    count_stage(epoch, ws, stream);
-    cudaMemsetAsync(ws.counters + t0, 0, 2 * sizeof(uint32_t), stream);
-    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, ws.d_stage, stream));
+    (void)epoch;   // the tile sort has no lookback words
+    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, stream));
+    fs.sorted_gauss = ws.pgauss[1];
+    if (fs.n <= 0 || !fs.order) return;
     PairSource src;
     src.order = fs.order;
     src.offsets = ws.offsets;
@@ -127,28 +115,21 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
     src.counters = ws.counters;
     src.capacity = ws.capacity;
     src.tiles_x = fs.cam.tiles_x;
-    const uint32_t* hist_tiles = ws.hist + kMaxPasses * kRadix;
-    if (fs.n > 0 && fs.order) {
-        // Stages 3-5: emit + first tile digit, then (if needed) the second
-        // digit, which also yields the per-tile ranges.
-        const bool single = fs.tile_passes == 1;
-        const EpochRef ep1{ws.d_stage, 0u};
-        TIMED(ws, kKTilePassFirst, stream,
-              launch_tile_pass_first(src, ws.ptile, ws.pgauss[0], fs.bits1, single, ws.ranges,
-                                     hist_tiles, ws.lookback, ep1, ws.counters + t0, ws.status,
-                                     ws.sort_grid, stream));
-        if (!single) {
-            const EpochRef ep2{ws.d_stage, 1u};
-            TIMED(ws, kKTilePassLast, stream,
-                  launch_tile_pass_last(ws.ptile, ws.pgauss[0], ws.pgauss[1], ws.counters,
-                                        ws.capacity, fs.bits1, fs.bits2, ws.ranges,
-                                        hist_tiles + kRadix, ws.lookback, ep2, ws.counters + t0 + 1,
-                                        ws.status, ws.sort_grid, stream));
-        }
-        fs.sorted_gauss = single ? ws.pgauss[0] : ws.pgauss[1];
-    } else {
-        fs.sorted_gauss = ws.pgauss[0];
-    }
+    const int G = ws.tile_grid;
+    // Stages 3-4, pass 1 (by tile column): count, scan, generate + scatter.
+    TIMED(ws, kKTileCountColumns, stream,
+          launch_tile_count_columns(src, ws.tcounts, ws.status, G, stream));
+    TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, G, stream));
+    TIMED(ws, kKTileScatterColumns, stream,
+          launch_tile_scatter_columns(src, ws.tcounts, ws.pkey, ws.pgauss[0], ws.status, G, stream));
+    // Stages 4-5, pass 2 (by tile row): count, scan, scatter + tile ranges.
+    TIMED(ws, kKTileCountRows, stream,
+          launch_tile_count_rows(ws.pkey, ws.counters, ws.capacity, ws.tcounts, G, stream));
+    TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, G, stream));
+    TIMED(ws, kKTileScatterRows, stream,
+          launch_tile_scatter_rows(ws.pkey, ws.pgauss[0], ws.tcounts, ws.pgauss[1], ws.ranges,
+                                   ws.counters, ws.capacity, fs.cam.tiles_x, fs.num_tiles,
+                                   ws.status, G, stream));
 }
 
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,

@@ -1,0 +1,427 @@
+// Serving: continuous batching of render requests over resident scenes.
+//
+// A scheduler thread owns `max_slots` execution slots.  Each slot is a frame
+// workspace with its own CUDA stream, so requests in different slots run
+// concurrently on the GPU.  Requests wait in a FIFO queue and are admitted
+// whenever a slot is free and the predicted device memory of everything in
+// flight (pair buffers sized by the request's predicted Gaussian-tile pair
+// count, plus per-Gaussian and per-pixel buffers) stays within the budget, so
+// a request arriving while others run starts as soon as a slot and memory
+// free up.  Each (slot, scene, resolution) frame is captured once as a CUDA
+// graph and replayed after a one-thread kernel writes the request's camera
+// into the slot's device copy that the graph's kernels read.
+// The predicted pair count per pixel is learned per scene from completed
+// frames (running maximum over recent frames, plus a margin).
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+#include <algorithm>
+
+#include "adr_internal.cuh"
+
+using namespace adr;
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Scene {
+    const float *means, *scales, *rots, *opac, *sh;
+    int64_t n;
+    SetDev st;
+    double pairs_per_pixel = -1.0;   // learned; < 0 = unknown
+};
+
+enum ReqState { kQueued, kRunning, kDone };
+
+struct Request {
+    uint64_t ticket = 0;
+    int scene = 0;
+    CamDev cam{};
+    float* out = nullptr;
+    double t_submit = 0, t_done = 0;
+    int64_t pred_pairs = 0;
+    size_t pred_bytes = 0;
+    ReqState state = kQueued;
+    adr_status result = ADR_OK;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct Slot {
+    Workspace ws;
+    FrameState fs;
+    std::atomic<uint32_t> calls{0};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    float* img = nullptr;              // slot-owned image the graph renders into
+    uint32_t* host_words = nullptr;    // pinned: status word, pair count
+    Request* req = nullptr;
+    std::map<std::tuple<int, int, int>, GraphEntry> graphs;
+};
+
+}  // namespace
+
+struct adr_server {
+    adr_serve_config cfg{};
+    std::vector<Scene> scenes;
+    std::vector<Slot*> slots;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> requests;
+    std::mutex mu;
+    std::condition_variable cv_done, cv_work;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    size_t inflight_bytes = 0;
+    int inflight = 0;
+    // statistics
+    std::vector<double> latencies;
+    int max_inflight = 0;
+    int64_t admitted_while_busy = 0, rejected = 0, capacity_errors = 0, graph_replays = 0;
+    double t_first_submit = -1, t_last_done = 0;
+    char error[256] = "";   // why the last failed launch failed
+};
+
+namespace {
+
+size_t predicted_bytes(const adr_server* s, const Scene& sc, const CamDev& cam, int64_t* pairs_out) {
+    const int64_t pixels = (int64_t)cam.width * cam.height;
+    int64_t pairs;
+    if (sc.pairs_per_pixel < 0) {
+        pairs = s->cfg.slot_pair_capacity;                       // unknown scene: reserve a full slot
+    } else {
+        pairs = (int64_t)(sc.pairs_per_pixel * (double)pixels * 1.25) + 4096;
+        pairs = std::min<int64_t>(pairs, s->cfg.slot_pair_capacity);
+    }
+    *pairs_out = pairs;
+    return (size_t)pairs * 12 + (size_t)sc.n * 150 + (size_t)pixels * 32;
+}
+
+// Records why a launch failed (read by adr_serve_poll) and returns ADR_ERR_CUDA.
+adr_status launch_failed(adr_server* s, const char* step, cudaError_t e) {
+    snprintf(s->error, sizeof(s->error), "%s: %s", step, cudaGetErrorString(e));
+    return ADR_ERR_CUDA;
+}
+
+#define SERVE_CUDA(step, call)                                  \
+    do {                                                        \
+        const cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return launch_failed(s, step, e_); \
+    } while (0)
+
+// Captures one frame of `sc` at the request's size into a graph.  The graph
+// reads the camera and settings from the slot's device copy, which a kernel
+// launched before each replay writes.
+adr_status capture_frame(adr_server* s, Slot& slot, const Scene& sc, GraphEntry& ge) {
+    cudaStream_t strm = slot.stream;
+    cudaGraph_t g = nullptr;
+    SERVE_CUDA("cudaStreamBeginCapture", cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal));
+    enqueue_preprocess(slot.ws, slot.fs, slot.calls, sc.means, sc.scales, sc.rots, sc.opac, sc.sh,
+                       strm, /*set_params=*/false);
+    enqueue_sort(slot.ws, slot.fs, slot.calls, strm);
+    enqueue_render(slot.ws, slot.fs, slot.img, nullptr, nullptr, strm);
+    const cudaError_t ec = cudaStreamEndCapture(strm, &g);
+    if (ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return launch_failed(s, "cudaStreamEndCapture", ec != cudaSuccess ? ec : cudaErrorUnknown);
+    }
+    const cudaError_t e = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return launch_failed(s, "cudaGraphInstantiate", e);
+    return ADR_OK;
+}
+
+adr_status run_frame(adr_server* s, Slot& slot, Request& r) {
+    const Scene& sc = s->scenes[r.scene];
+    fill_frame_state(slot.fs, sc.n, r.cam, sc.st);
+    cudaStream_t strm = slot.stream;
+    SERVE_CUDA("clearing the status word", cudaMemsetAsync(slot.ws.status, 0, 16, strm));
+    if (s->cfg.use_graphs) {
+        auto key = std::make_tuple(r.scene, r.cam.width, r.cam.height);
+        auto it = slot.graphs.find(key);
+        if (it == slot.graphs.end()) {
+            GraphEntry ge;
+            const adr_status st = capture_frame(s, slot, sc, ge);
+            if (st != ADR_OK) return st;
+            it = slot.graphs.emplace(key, ge).first;
+        } else {
+            count_stage(slot.calls, slot.ws, strm);   // the replay's preprocess stage
+        }
+        launch_set_frame_params(FrameParams{r.cam, sc.st}, slot.ws.d_fp, strm);
+        SERVE_CUDA("camera launch", cudaGetLastError());
+        SERVE_CUDA("cudaGraphLaunch", cudaGraphLaunch(it->second.exec, strm));
+        s->graph_replays++;
+    } else {
+        enqueue_preprocess(slot.ws, slot.fs, slot.calls, sc.means, sc.scales, sc.rots, sc.opac,
+                           sc.sh, strm);
+        enqueue_sort(slot.ws, slot.fs, slot.calls, strm);
+        enqueue_render(slot.ws, slot.fs, slot.img, nullptr, nullptr, strm);
+        SERVE_CUDA("frame launch", cudaGetLastError());
+    }
+    const size_t img_bytes = (size_t)3 * r.cam.width * r.cam.height * sizeof(float);
+    SERVE_CUDA("image copy", cudaMemcpyAsync(r.out, slot.img, img_bytes, cudaMemcpyDeviceToDevice, strm));
+    SERVE_CUDA("status read", cudaMemcpyAsync(slot.host_words, slot.ws.status, 4,
+                                              cudaMemcpyDeviceToHost, strm));
+    SERVE_CUDA("pair count read", cudaMemcpyAsync(slot.host_words + 1, slot.ws.counters + kCntPairs,
+                                                  4, cudaMemcpyDeviceToHost, strm));
+    SERVE_CUDA("cudaEventRecord", cudaEventRecord(slot.done, strm));
+    return ADR_OK;
+}
+
+#undef SERVE_CUDA
+
+void scheduler(adr_server* s) {
+    cudaSetDevice(s->cfg.device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progressed = false;
+        // Completions.
+        for (Slot* sl : s->slots) {
+            if (!sl->req) continue;
+            const cudaError_t q = cudaEventQuery(sl->done);
+            if (q == cudaErrorNotReady) continue;
+            Request* r = sl->req;
+            const uint32_t bits = sl->host_words[0], pairs = sl->host_words[1];
+            r->t_done = now_ms();
+            if (q != cudaSuccess) r->result = ADR_ERR_CUDA;
+            else if (bits & kErrLookback) r->result = ADR_ERR_TIMEOUT;
+            else if ((bits & kErrCapacity) || (int64_t)pairs > s->cfg.slot_pair_capacity) {
+                r->result = ADR_ERR_CAPACITY;
+                s->capacity_errors++;
+            }
+            Scene& sc = s->scenes[r->scene];
+            const double ppp = (double)pairs / ((double)r->cam.width * r->cam.height);
+            sc.pairs_per_pixel = sc.pairs_per_pixel < 0 ? ppp : std::max(ppp, 0.9 * sc.pairs_per_pixel + 0.1 * ppp);
+            r->state = kDone;
+            s->latencies.push_back(r->t_done - r->t_submit);
+            s->t_last_done = r->t_done;
+            s->inflight_bytes -= r->pred_bytes;
+            s->inflight--;
+            sl->req = nullptr;
+            progressed = true;
+        }
+        if (progressed) s->cv_done.notify_all();
+        // Admissions: FIFO, while a slot is free and the memory budget allows.
+        while (!s->queue.empty()) {
+            Slot* free_slot = nullptr;
+            for (Slot* sl : s->slots)
+                if (!sl->req) { free_slot = sl; break; }
+            if (!free_slot) break;
+            Request* r = s->queue.front();
+            r->pred_bytes = predicted_bytes(s, s->scenes[r->scene], r->cam, &r->pred_pairs);
+            if (s->inflight > 0 && s->inflight_bytes + r->pred_bytes > (size_t)s->cfg.mem_budget_bytes)
+                break;                                           // wait for memory to free up
+            s->queue.pop_front();
+            if (s->inflight > 0) s->admitted_while_busy++;
+            r->state = kRunning;
+            free_slot->req = r;
+            s->inflight++;
+            s->inflight_bytes += r->pred_bytes;
+            s->max_inflight = std::max(s->max_inflight, s->inflight);
+            const adr_status st = run_frame(s, *free_slot, *r);
+            if (st != ADR_OK) {   // launch failed: report and free the slot
+                r->result = st;
+                r->state = kDone;
+                r->t_done = now_ms();
+                s->inflight--;
+                s->inflight_bytes -= r->pred_bytes;
+                free_slot->req = nullptr;
+                s->cv_done.notify_all();
+            }
+            progressed = true;
+        }
+        if (!progressed) {
+            if (s->inflight == 0 && s->queue.empty())
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            }
+        }
+    }
+}
+
+void destroy_server(adr_server* s) {
+    for (Slot* sl : s->slots) {
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        for (auto& kv : sl->graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        free_workspace(sl->ws);
+        if (sl->img) cudaFree(sl->img);
+        if (sl->host_words) cudaFreeHost(sl->host_words);
+        if (sl->done) cudaEventDestroy(sl->done);
+        if (sl->stream) cudaStreamDestroy(sl->stream);
+        delete sl;
+    }
+    for (auto& kv : s->requests) delete kv.second;
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+adr_status adr_serve_create(adr_server** out, const adr_serve_config* cfg) {
+    if (!out || !cfg) return report_error(ADR_ERR_INVALID, "adr_serve_create: NULL argument");
+    *out = nullptr;
+    if (cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->slot_pair_capacity <= 0 ||
+        cfg->slot_pair_capacity > (int64_t(1) << 30) || cfg->slot_max_gaussians <= 0 ||
+        cfg->max_width <= 0 || cfg->max_height <= 0 || cfg->max_width > 4096 ||
+        cfg->max_height > 4096 || cfg->mem_budget_bytes <= 0)
+        return report_error(ADR_ERR_INVALID, "adr_serve_create: configuration out of range");
+    if (cudaSetDevice(cfg->device) != cudaSuccess)
+        return report_error(ADR_ERR_INVALID, "adr_serve_create: device not present");
+    adr_server* s = new adr_server();
+    s->cfg = *cfg;
+    for (int i = 0; i < cfg->max_slots; ++i) {
+        Slot* sl = new Slot();
+        s->slots.push_back(sl);
+        adr_status st = alloc_workspace(sl->ws, cfg->slot_max_gaussians, cfg->slot_pair_capacity,
+                                        cfg->max_width, cfg->max_height, cfg->device);
+        if (st != ADR_OK ||
+            cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc((void**)&sl->img, (size_t)3 * cfg->max_width * cfg->max_height * sizeof(float)) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl->host_words, 16, cudaHostAllocDefault) != cudaSuccess) {
+            destroy_server(s);
+            return report_error(ADR_ERR_CUDA, "adr_serve_create: slot allocation failed");
+        }
+    }
+    s->worker = std::thread(scheduler, s);
+    *out = s;
+    return report_ok();
+}
+
+void adr_serve_destroy(adr_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    destroy_server(s);
+}
+
+adr_status adr_serve_add_scene(adr_server* s, const float* means, const float* scales,
+                               const float* rots, const float* opac, const float* sh, int64_t n,
+                               const adr_settings* settings, int32_t* scene_id) {
+    if (!s || !scene_id) return report_error(ADR_ERR_INVALID, "adr_serve_add_scene: NULL argument");
+    if (n <= 0 || n > s->cfg.slot_max_gaussians)
+        return report_error(ADR_ERR_INVALID, "adr_serve_add_scene: n outside 1..slot_max_gaussians");
+    if (!means || !scales || !rots || !opac || !sh || (uintptr_t)rots % 16 || (uintptr_t)sh % 16)
+        return report_error(ADR_ERR_INVALID, "adr_serve_add_scene: bad parameter pointer");
+    SetDev st;
+    adr_status r = settings_to_dev(settings, st);
+    if (r != ADR_OK) return r;
+    std::lock_guard<std::mutex> lk(s->mu);
+    Scene sc{means, scales, rots, opac, sh, n, st, -1.0};
+    s->scenes.push_back(sc);
+    *scene_id = (int32_t)s->scenes.size() - 1;
+    return report_ok();
+}
+
+adr_status adr_serve_submit(adr_server* s, int32_t scene_id, const adr_camera* camera,
+                            float* out_img, uint64_t* ticket) {
+    if (!s || !ticket || !out_img) return report_error(ADR_ERR_INVALID, "adr_serve_submit: NULL argument");
+    CamDev cam;
+    adr_status r = camera_to_dev(camera, s->cfg.max_width, s->cfg.max_height, cam);
+    if (r != ADR_OK) return r;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (scene_id < 0 || scene_id >= (int32_t)s->scenes.size())
+        return report_error(ADR_ERR_INVALID, "adr_serve_submit: unknown scene");
+    const Scene& sc = s->scenes[scene_id];
+    const int64_t min_bytes = (int64_t)sc.n * 150 + (int64_t)cam.width * cam.height * 32 + 4096 * 12;
+    if (min_bytes > s->cfg.mem_budget_bytes) {
+        s->rejected++;
+        return report_error(ADR_ERR_ADMISSION, "adr_serve_submit: request can never fit the memory budget");
+    }
+    Request* q = new Request();
+    q->ticket = s->next_ticket++;
+    q->scene = scene_id;
+    q->cam = cam;
+    q->out = out_img;
+    q->t_submit = now_ms();
+    if (s->t_first_submit < 0) s->t_first_submit = q->t_submit;
+    s->requests[q->ticket] = q;
+    s->queue.push_back(q);
+    *ticket = q->ticket;
+    s->cv_work.notify_all();
+    return report_ok();
+}
+
+adr_status adr_serve_poll(adr_server* s, uint64_t ticket, int64_t timeout_us) {
+    if (!s) return report_error(ADR_ERR_INVALID, "adr_serve_poll: NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->requests.find(ticket);
+    if (it == s->requests.end()) return report_error(ADR_ERR_INVALID, "adr_serve_poll: unknown ticket");
+    Request* r = it->second;
+    if (r->state != kDone && timeout_us != 0) {
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+        s->cv_done.wait_until(lk, deadline, [&] { return r->state == kDone; });
+    }
+    if (r->state != kDone) {
+        if (timeout_us == 0) return ADR_PENDING;
+        return report_error(ADR_ERR_TIMEOUT, "adr_serve_poll: request not finished before the timeout");
+    }
+    const adr_status res = r->result;
+    s->requests.erase(it);
+    delete r;
+    if (res == ADR_ERR_CUDA) {
+        char msg[320];
+        snprintf(msg, sizeof(msg), "adr_serve_poll: the request failed (%s)", s->error);
+        return report_error(res, msg);
+    }
+    if (res != ADR_OK) return report_error(res, "adr_serve_poll: the request failed on the device");
+    return report_ok();
+}
+
+adr_status adr_serve_stats(adr_server* s, double* out, int32_t n) {
+    if (!s || !out || n < 1) return report_error(ADR_ERR_INVALID, "adr_serve_stats: bad argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<double> lat = s->latencies;
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) {
+        if (lat.empty()) return 0.0;
+        const size_t k = std::min(lat.size() - 1, (size_t)(p * (double)(lat.size() - 1) + 0.5));
+        return lat[k];
+    };
+    double mean = 0;
+    for (double v : lat) mean += v;
+    mean = lat.empty() ? 0.0 : mean / (double)lat.size();
+    const double span = s->t_last_done - s->t_first_submit;
+    const double vals[10] = {(double)lat.size(), pct(0.5), pct(0.99), mean,
+                             (double)s->max_inflight, (double)s->admitted_while_busy,
+                             (double)s->rejected, span > 0 ? 1e3 * (double)lat.size() / span : 0.0,
+                             (double)s->capacity_errors, (double)s->graph_replays};
+    for (int i = 0; i < n && i < 10; ++i) out[i] = vals[i];
+    return report_ok();
+}
+
+adr_status adr_serve_reset_stats(adr_server* s) {
+    if (!s) return report_error(ADR_ERR_INVALID, "adr_serve_reset_stats: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->latencies.clear();
+    s->max_inflight = s->inflight;
+    s->admitted_while_busy = s->rejected = s->capacity_errors = s->graph_replays = 0;
+    s->t_first_submit = -1;
+    s->t_last_done = 0;
+    return report_ok();
+}
+
+}  // extern "C"

@@ -57,6 +57,7 @@ def test_binding_covers_every_declared_symbol(libpath):
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.adr_camera) == (16 + 4 + 1 + 3) * 4 + 2 * 4
     assert ctypes.sizeof(_lib.adr_settings) == 4 + 4 * 4 + 3 * 4 + 4
+    assert ctypes.sizeof(_lib.adr_serve_config) == 8 + 3 * 8 + 4 * 4
 
 
 def test_version_and_error_without_gpu(libpath):
@@ -67,3 +68,16 @@ def test_version_and_error_without_gpu(libpath):
     st = lib.adr_create(ctypes.byref(out), 0, 10, 16, 16, 0)
     assert st == _lib.ADR_ERR_INVALID
     assert b"max_gaussians" in lib.adr_last_error()
+
+
+def test_serve_config_rejected_without_gpu(libpath):
+    lib = _lib.load()
+    cfg = _lib.adr_serve_config(max_slots=0, mem_budget_bytes=1 << 30, slot_pair_capacity=1 << 20,
+                                slot_max_gaussians=1 << 16, max_width=256, max_height=256,
+                                use_graphs=1, device=0)
+    out = ctypes.c_void_p()
+    assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
+    assert not out.value
+    cfg.max_slots, cfg.max_width = 2, 8192
+    assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
+    assert lib.adr_serve_poll(None, 1, 0) == _lib.ADR_ERR_INVALID
