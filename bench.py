@@ -234,7 +234,8 @@ def frame_units(rast, params, cams, st, stream, count):
         tmax = pad.reshape(ty, 16, tx, 16).max(axis=(1, 3)).reshape(-1)
         length = ranges[:, 1] - ranges[:, 0]
         loaded = np.minimum(length, ((tmax + 255) // 256) * 256)
-        out.append(dict(pairs=p, visible=v, evals=int(trav.astype(np.int64).sum()),
+        runs = int((rect[:, 2].astype(np.int64) - rect[:, 0])[tiles > 0].sum())
+        out.append(dict(pairs=p, visible=v, runs=runs, evals=int(trav.astype(np.int64).sum()),
                         loaded=int(loaded.sum())))
     return out
 
@@ -242,18 +243,18 @@ def frame_units(rast, params, cams, st, stream, count):
 def kernel_bytes(name, n, u, hw):
     """Algorithmic DRAM bytes of one launch of each kernel (the data the
     stage has to move; see the design notes for the derivation)."""
-    P, V = u["pairs"], u["visible"]
+    P, V, C = u["pairs"], u["visible"], u["runs"]
     return {
         "preprocess": 44 * n + 192 * V + 96 * n,   # params (+SH of kept) in, records out
         "depth_hist": 4 * n,
         "depth_pass": 16 * n,                      # key + value in and out
-        "scan_tiles": 12 * n + 8 * V,
-        "init_ranges": 8 * (hw // 256),
+        "scan_tiles": 12 * n + 16 * V,
         "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
         "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident
-        "tile_scatter_columns": 6 * P + 12 * V,    # pairs out (u16 key, Gaussian); staging in
-        "tile_count_rows": 2 * P,                  # u16 keys in
-        "tile_scatter_rows": 10 * P,               # pairs in, Gaussian ids out
+        "tile_scatter_columns": 8 * C + 12 * V,    # column runs out; Gaussian staging in
+        "tile_count_rows": 8 * C,                  # column runs in
+        "tile_scatter_rows": 8 * C + 4 * P,        # column runs in, Gaussian ids of the pairs out
+        "tile_ranges": 12 * (hw // 256),           # tile counts in, ranges out
         "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
     }[name]
 

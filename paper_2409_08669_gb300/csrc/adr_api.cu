@@ -135,7 +135,7 @@ void free_workspace(Workspace& w) {
         w.prof = nullptr;
     }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
-                    w.gkeys[1], w.gvals[0], w.gvals[1], w.pkey, w.pgauss[0], w.pgauss[1], w.tcounts,
+                    w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
     for (void* p : ptrs)
@@ -149,9 +149,9 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t pixels = (size_t)max_width * max_height;
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
     const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
-    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 10 +
-           (P / kSortChunk + 2) * 4 + tiles * 8 + pixels * 12 + lb +
-           (size_t)kRadix * kMaxTileGrid * 4 + 4096;
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 12 +
+           (P / kSortChunk + 2) * 4 + tiles * 12 + pixels * 12 + lb +
+           (size_t)kRadix * (kMaxTileGrid + 2) * 4 + 4096;
 }
 
 adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_capacity,
@@ -191,10 +191,12 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     for (int b = 0; b < 2; ++b) {
         ALLOC(w.gkeys[b], N * sizeof(uint32_t));
         ALLOC(w.gvals[b], N * sizeof(uint32_t));
-        ALLOC(w.pgauss[b], P * sizeof(uint32_t));
     }
-    ALLOC(w.pkey, P * sizeof(uint16_t));
+    ALLOC(w.pruns, P * sizeof(uint2));
+    ALLOC(w.pgauss, P * sizeof(uint32_t));
+    ALLOC(w.tile_counts, (size_t)w.max_tiles * sizeof(uint32_t));
     ALLOC(w.tcounts, (size_t)kRadix * kMaxTileGrid * sizeof(uint32_t));
+    ALLOC(w.ttotals, 2 * kRadix * sizeof(uint32_t));
     ALLOC(w.chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
     ALLOC(w.ranges, (size_t)w.max_tiles * sizeof(uint2));
     ALLOC(w.last, pixels * sizeof(int32_t));

@@ -78,14 +78,16 @@ enum Counter : int {
     kCntPairs = 0,        // number of pairs P (sum of tiles over Gaussians), saturating
     kCntVisible = 1,      // Gaussians with at least one tile (they sort first by depth)
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
+    kCntRuns = 3,         // number of column runs C (sum of rectangle widths), saturating
     kCntSortTicket0 = 4,  // chunk tickets of the depth-sort passes (4)
+    kCntPairs64 = 8,      // words 8-9: P as a 64-bit sum
     kCntSlots = 16
 };
 
 // Optional per-launch timing with CUDA events recorded on the launching
 // stream (adr_profile_enable / adr_profile_read).
 enum KernelId : int {
-    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKInitRanges, kKTileCountColumns,
+    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKTileRanges, kKTileCountColumns,
     kKTileScatterColumns, kKTileCountRows, kKTileScatterRows, kKTileCountScan, kKRender,
     kKRenderBackward, kKPreprocessBackward, kKernelCount
 };
@@ -114,9 +116,11 @@ struct Workspace {
     uint32_t* sorted_box = nullptr;        // [max_n] packed tile rectangle per depth-order position
     uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
-    uint16_t* pkey = nullptr;              // [capacity] ty << 8 | tx of the pairs after tile pass 1
-    uint32_t* pgauss[2] = {nullptr, nullptr};  // [capacity] each
+    uint2* pruns = nullptr;                // [capacity] column runs grouped by tile column
+    uint32_t* pgauss = nullptr;            // [capacity] Gaussian ids of the pairs by (tile, depth)
     uint32_t* tcounts = nullptr;           // [kRadix * kMaxTileGrid] per-(digit, CTA) counts / starts
+    uint32_t* ttotals = nullptr;           // [2 * kRadix] per-digit totals of the two tile passes
+    uint32_t* tile_counts = nullptr;       // [max_tiles] pairs per tile
     uint32_t* chunk_first = nullptr;       // [capacity / kSortChunk + 2]
     uint2* ranges = nullptr;               // [max_tiles]
     int32_t* last = nullptr;               // [max pixels]
@@ -189,51 +193,53 @@ void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t*
 // Inputs of the tile passes.
 struct PairSource {
     const uint32_t* order = nullptr;       // Gaussians by depth
-    const uint32_t* offsets = nullptr;     // exclusive scan of their tile counts
+    const uint32_t* offsets = nullptr;     // exclusive scan of their column-run counts
     const uint32_t* sorted_box = nullptr;  // packed rectangle per depth-order position
-    const uint32_t* chunk_first = nullptr; // sorted position holding each chunk's first pair
-    const uint32_t* counters = nullptr;    // kCntPairs, kCntVisible
+    const uint32_t* chunk_first = nullptr; // sorted position holding each chunk's first run
+    const uint32_t* counters = nullptr;    // kCntPairs, kCntRuns, kCntVisible
     int64_t capacity = 0;
     int tiles_x = 0;
 };
 
-// Tile sort (tiles.cu), two range-partitioned counting passes over the
-// pairs, by tx then by ty; `grid` CTAs, each owning a contiguous run of
-// 4096-pair chunks; counts holds kRadix x grid words.
-//   count_columns: per-CTA tx counts from the Gaussians' rectangles;
-//   count_rows:    per-CTA ty counts from the pass-1 keys;
-//   count_scan:    counts -> global start of every (digit, CTA) run, in place;
-//   scatter_columns: pairs generated on chip from the depth-ordered
-//                  Gaussians, written as (ty << 8 | tx, Gaussian) grouped by tx;
-//   scatter_rows:  Gaussian ids grouped by ty (final order) and each tile's
-//                  [start, end) in ranges (initialised to (0xFFFFFFFF, 0)).
+// Tile sort (tiles.cu): two range-partitioned counting passes, over the
+// column runs by tx, then over the pairs by ty; `grid` CTAs, each owning a
+// contiguous run of 4096-item chunks; counts holds kRadix x grid words, totals
+// kRadix words (zeroed before the count kernel that sums into them).
+//   count_columns:   per-CTA tx counts of the runs, from the Gaussians' rectangles;
+//   scatter_columns: runs generated on chip from the depth-ordered Gaussians,
+//                    written grouped by tx (x = Gaussian, y = y0 | (h-1) << 8 | tx << 16);
+//   count_rows:      per-CTA ty counts of the pairs and the pairs of every
+//                    tile (tile_counts, zeroed before);
+//   tile_ranges:     each tile's [start, end) from tile_counts;
+//   scatter_rows:    runs expanded into pairs, Gaussian ids grouped by ty;
+//   count_scan:      counts -> global start of every (digit, CTA) run, in place.
 int tile_scatter_blocks_per_sm();
-void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* status, int grid,
-                               cudaStream_t stream);
-void launch_tile_count_rows(const uint16_t* keys, const uint32_t* counters, int64_t capacity,
-                            uint32_t* counts, int grid, cudaStream_t stream);
-void launch_tile_count_scan(uint32_t* counts, int grid, cudaStream_t stream);
-void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint16_t* keys_out,
-                                 uint32_t* gauss_out, uint32_t* status, int grid,
-                                 cudaStream_t stream);
-void launch_tile_scatter_rows(const uint16_t* keys_in, const uint32_t* gauss_in,
-                              const uint32_t* starts, uint32_t* gauss_out, uint2* ranges,
-                              const uint32_t* counters, int64_t capacity, int tiles_x,
-                              int num_tiles, uint32_t* status, int grid, cudaStream_t stream);
+void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* totals,
+                               uint32_t* status, int grid, cudaStream_t stream);
+void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
+                                 uint32_t* status, int grid, cudaStream_t stream);
+void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
+                            int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
+                            uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream);
+void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
+                        int64_t capacity, uint2* ranges, cudaStream_t stream);
+void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
+                              const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
+                              int grid, cudaStream_t stream);
+void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
 // coordinates and extents fit 8 bits because images are at most 4096 pixels
 // per side).
-// Exclusive scan of tiles[order[i]] with decoupled lookback.  Also writes the
-// packed rectangle of each depth-order position with tiles (sorted_box), the
-// pair total and visible count to counters, and chunk_first[c] = position of
-// the Gaussian holding pair c * kSortChunk.
+// Exclusive scan of the column-run counts (rectangle widths) of the
+// Gaussians in depth order, with decoupled lookback.  Also writes the packed
+// rectangle of each depth-order position with tiles (sorted_box), the run
+// total, visible count and pair total to counters (with the capacity flag),
+// and chunk_first[c] = position of the Gaussian holding run c * kSortChunk.
 void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
                        int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);
-
-void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream);
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                    const FrameParams* fp, int num_tiles, float* img, float* t_final,

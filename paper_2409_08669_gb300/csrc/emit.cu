@@ -1,11 +1,14 @@
 // Stages 2-3 of the rasterization pipeline (Sec. 3.2.1), InclusiveSum and the
-// bookkeeping DuplicateWithKeys needs, over the Gaussians in view-depth order:
-//   * offsets[i] = exclusive prefix sum of the tile counts (decoupled lookback,
-//     32 predecessor words per round trip), the pair total P and the number
+// bookkeeping DuplicateWithKeys needs, over the Gaussians in view-depth order.
+// A Gaussian's pairs form w x h tiles, i.e. w column runs (one per tile
+// column); the tile sort works on the runs, so the scan is over w:
+//   * offsets[i] = exclusive prefix sum of the run counts (decoupled lookback,
+//     32 predecessor words per round trip), the run total C and the number
 //     of Gaussians with tiles;
-//   * chunk_first[c] = depth-order position of the Gaussian that holds pair
-//     c * 4096, so the tile sort can generate each chunk's pairs on chip
-//     without an emitted pair list;
+//   * the pair total P = sum of w h (64-bit atomics, published by a one-thread
+//     kernel after the scan) and the capacity check;
+//   * chunk_first[c] = depth-order position of the Gaussian that holds run
+//     c * 4096, so the tile sort can generate each chunk's runs on chip;
 //   * sorted_box[i] = the packed tile rectangle of depth-order position i.
 // Plus small helpers for the tile ranges.
 #include "adr_internal.cuh"
@@ -68,6 +71,7 @@ __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, 
         }
     }
     const uint32_t e = (uint32_t)min(excl, (uint64_t)kSat);
+    __threadfence();
     if (lane == 0) lb[chunk] = tag | kScanInc | sat_add(e, total);
     return e;
 }
@@ -79,9 +83,10 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
              uint32_t* __restrict__ chunk_first, unsigned long long* __restrict__ lookback,
              EpochRef eref, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
-    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_warp[kScanThreads / 32], s_pairs[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long* pairs64 = reinterpret_cast<unsigned long long*>(counters + kCntPairs64);
 
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(counters + kCntScanTicket, 1u);
@@ -90,39 +95,52 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
         const int64_t base = (int64_t)chunk * kScanChunk;
         if (base >= n) break;
         // Blocked arrangement: thread t owns items base + t*16 .. +15.
-        uint32_t v[kScanItems];
-        uint32_t tsum = 0, nonzero = 0;
+        uint32_t w[kScanItems], box[kScanItems];
+        uint32_t tsum = 0, psum = 0, nonzero = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + tid * kScanItems + k;
-            v[k] = i < n ? tiles[order[i]] : 0u;
-            tsum += v[k];   // <= 16 * 2^16 per thread, no overflow
-            nonzero += v[k] != 0;
+            uint32_t t = 0;
+            w[k] = 0;
+            box[k] = 0;
+            if (i < n) {
+                const uint32_t g = order[i];
+                t = tiles[g];
+                if (t) {
+                    const ushort4 r = rect[g];
+                    w[k] = (uint32_t)(r.z - r.x);
+                    box[k] = (uint32_t)r.x | ((uint32_t)r.y << 8) | ((w[k] - 1u) << 16) |
+                             ((uint32_t)(r.w - r.y - 1) << 24);
+                }
+            }
+            tsum += w[k];   // <= 16 * 256 per thread
+            psum += t;      // <= 16 * 2^16 per thread
+            nonzero += t != 0;
         }
-        // Block exclusive scan of the thread sums (chunk total < 2^31).
+        // Block exclusive scan of the thread run sums, block sum of the pairs.
         uint32_t x = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
+        const uint32_t wp = __reduce_add_sync(0xffffffffu, psum);
         if (lane == 31) s_warp[warp] = x;
+        if (lane == 0) s_pairs[warp] = wp;
         __syncthreads();
-        uint32_t wbase = 0, total = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) {
-            if (w < warp) wbase += s_warp[w];
-            total += s_warp[w];
+        uint32_t wbase = 0, total = 0, pairs = 0;
+        for (int q = 0; q < kScanThreads / 32; ++q) {
+            if (q < warp) wbase += s_warp[q];
+            total += s_warp[q];
+            pairs += s_pairs[q];   // <= 4096 * 2^16
         }
         const uint32_t texcl = wbase + x - tsum;
         if (warp == 0) {
+            if (lane == 0 && pairs) atomicAdd(pairs64, (unsigned long long)pairs);
             const uint32_t excl = warp_lookback(lookback, chunk, total, epoch, status);
             if (lane == 0) {
                 s_prefix = excl;
-                if (base + kScanChunk >= n) {
-                    const uint32_t p = sat_add(excl, total);
-                    counters[kCntPairs] = p;
-                    if ((int64_t)p > capacity) atomicOr(status, kErrCapacity);
-                }
+                if (base + kScanChunk >= n) counters[kCntRuns] = sat_add(excl, total);
             }
         }
         const uint32_t nz = __reduce_add_sync(0xffffffffu, nonzero);
@@ -132,18 +150,16 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + tid * kScanItems + k;
-            const uint32_t t = v[k];
+            const uint32_t t = w[k];
             if (i < n) offsets[i] = run;
             if (t != 0 && (int64_t)run < capacity) {
-                // chunk starts inside [run, run + t)
+                // run chunks start inside [run, run + t)
                 const uint64_t c_lo = ((uint64_t)run + kSortChunk - 1) / kSortChunk;
                 uint64_t c_hi = ((uint64_t)run + t - 1) / kSortChunk;
                 const uint64_t c_max = ((uint64_t)capacity - 1) / kSortChunk;
                 if (c_hi > c_max) c_hi = c_max;
                 for (uint64_t c = c_lo; c <= c_hi; ++c) chunk_first[c] = (uint32_t)i;
-                const ushort4 r = rect[order[i]];
-                sorted_box[i] = (uint32_t)r.x | ((uint32_t)r.y << 8) |
-                                ((uint32_t)(r.z - r.x - 1) << 16) | ((uint32_t)(r.w - r.y - 1) << 24);
+                sorted_box[i] = box[k];
             }
             run = sat_add(run, t);
         }
@@ -151,9 +167,12 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
     }
 }
 
-__global__ void k_init_ranges(uint2* __restrict__ ranges, int num_tiles) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x)
-        ranges[t] = make_uint2(0xFFFFFFFFu, 0u);
+// After the scan: the pair total P (saturated to 31 bits) and the capacity flag.
+__global__ void k_finish_pairs(uint32_t* __restrict__ counters, int64_t capacity,
+                               uint32_t* __restrict__ status) {
+    const unsigned long long p = *reinterpret_cast<const unsigned long long*>(counters + kCntPairs64);
+    counters[kCntPairs] = (uint32_t)min(p, (unsigned long long)kSat);
+    if (p > (unsigned long long)capacity) atomicOr(status, kErrCapacity);
 }
 
 __global__ void k_copy_ranges(const uint2* __restrict__ ranges, int num_tiles, uint2* __restrict__ out) {
@@ -213,15 +232,11 @@ void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushor
                        int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream) {
-    if (n <= 0) return;
-    k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, capacity, offsets,
-                                                    sorted_box, chunk_first, lookback, epoch,
-                                                    counters, status);
-}
-
-void launch_init_ranges(uint2* ranges, int num_tiles, cudaStream_t stream) {
-    if (num_tiles <= 0) return;
-    k_init_ranges<<<(num_tiles + 255) / 256, 256, 0, stream>>>(ranges, num_tiles);
+    if (n > 0)
+        k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, capacity, offsets,
+                                                        sorted_box, chunk_first, lookback, epoch,
+                                                        counters, status);
+    k_finish_pairs<<<1, 1, 0, stream>>>(counters, capacity, status);
 }
 
 void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream) {

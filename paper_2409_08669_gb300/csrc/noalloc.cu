@@ -42,9 +42,9 @@ constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
 constexpr size_t kOffSortedBox = align256(kOffOffsets + kNaMaxGaussians * 4);
 constexpr size_t kOffGKeys = align256(kOffSortedBox + kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
-constexpr size_t kOffPKey = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
-constexpr size_t kOffPGauss = align256(kOffPKey + kNaMaxPairs * 2);           // 2 buffers
-constexpr size_t kOffChunkFirst = align256(kOffPGauss + 2 * kNaMaxPairs * 4);
+constexpr size_t kOffPRuns = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
+constexpr size_t kOffPGauss = align256(kOffPRuns + kNaMaxPairs * 8);
+constexpr size_t kOffChunkFirst = align256(kOffPGauss + kNaMaxPairs * 4);
 constexpr size_t kOffRanges = align256(kOffChunkFirst + (kNaMaxPairs / kSortChunk + 2) * 4);
 constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
 constexpr size_t kOffTrav = align256(kOffLast + kPixels * 4);
@@ -56,7 +56,9 @@ constexpr size_t kLookbackWords = (kNaMaxGaussians / kSortChunk + 2) * kRadix;
 constexpr size_t kOffFrameParams = align256(kOffStatus + 16);
 constexpr size_t kOffStage = align256(kOffFrameParams + sizeof(FrameParams));
 constexpr size_t kOffTCounts = align256(kOffStage + 16);
-constexpr size_t kOffLookback = align256(kOffTCounts + (size_t)kRadix * kMaxTileGrid * 4);
+constexpr size_t kOffTTotals = align256(kOffTCounts + (size_t)kRadix * kMaxTileGrid * 4);
+constexpr size_t kOffTileCounts = align256(kOffTTotals + 2 * kRadix * 4);
+constexpr size_t kOffLookback = align256(kOffTileCounts + kNaMaxTiles * 4);
 constexpr size_t kNaBytes = align256(kOffLookback + kLookbackWords * 8);
 
 // The scratch.  Zero-initialised when the module loads (the lookback words
@@ -106,10 +108,12 @@ adr_status setup(int dev, DeviceState*& out) {
         for (int k = 0; k < 2; ++k) {
             w.gkeys[k] = reinterpret_cast<uint32_t*>(b + kOffGKeys) + k * kNaMaxGaussians;
             w.gvals[k] = reinterpret_cast<uint32_t*>(b + kOffGVals) + k * kNaMaxGaussians;
-            w.pgauss[k] = reinterpret_cast<uint32_t*>(b + kOffPGauss) + k * kNaMaxPairs;
         }
-        w.pkey = reinterpret_cast<uint16_t*>(b + kOffPKey);
+        w.pruns = reinterpret_cast<uint2*>(b + kOffPRuns);
+        w.pgauss = reinterpret_cast<uint32_t*>(b + kOffPGauss);
+        w.tile_counts = reinterpret_cast<uint32_t*>(b + kOffTileCounts);
         w.tcounts = reinterpret_cast<uint32_t*>(b + kOffTCounts);
+        w.ttotals = reinterpret_cast<uint32_t*>(b + kOffTTotals);
         w.chunk_first = reinterpret_cast<uint32_t*>(b + kOffChunkFirst);
         w.ranges = reinterpret_cast<uint2*>(b + kOffRanges);
         w.last = reinterpret_cast<int32_t*>(b + kOffLast);

@@ -7,7 +7,7 @@ namespace adr {
 
 const char* kernel_name(int id) {
     static const char* names[kKernelCount] = {
-        "preprocess", "depth_hist", "depth_pass", "scan_tiles", "init_ranges",
+        "preprocess", "depth_hist", "depth_pass", "scan_tiles", "tile_ranges",
         "tile_count_columns", "tile_scatter_columns", "tile_count_rows", "tile_scatter_rows",
         "tile_count_scan", "render", "render_backward", "preprocess_backward"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
@@ -104,32 +104,40 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream) {
     (void)epoch;   // the tile sort has no lookback words
-    TIMED(ws, kKInitRanges, stream, launch_init_ranges(ws.ranges, fs.num_tiles, stream));
-    fs.sorted_gauss = ws.pgauss[1];
-    if (fs.n <= 0 || !fs.order) return;
-    PairSource src;
-    src.order = fs.order;
-    src.offsets = ws.offsets;
-    src.sorted_box = ws.sorted_box;
-    src.chunk_first = ws.chunk_first;
-    src.counters = ws.counters;
-    src.capacity = ws.capacity;
-    src.tiles_x = fs.cam.tiles_x;
+    fs.sorted_gauss = ws.pgauss;
+    cudaMemsetAsync(ws.ttotals, 0, 2 * kRadix * sizeof(uint32_t), stream);
+    cudaMemsetAsync(ws.tile_counts, 0, (size_t)fs.num_tiles * sizeof(uint32_t), stream);
     const int G = ws.tile_grid;
-    // Stages 3-4, pass 1 (by tile column): count, scan, generate + scatter.
-    TIMED(ws, kKTileCountColumns, stream,
-          launch_tile_count_columns(src, ws.tcounts, ws.status, G, stream));
-    TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, G, stream));
-    TIMED(ws, kKTileScatterColumns, stream,
-          launch_tile_scatter_columns(src, ws.tcounts, ws.pkey, ws.pgauss[0], ws.status, G, stream));
-    // Stages 4-5, pass 2 (by tile row): count, scan, scatter + tile ranges.
-    TIMED(ws, kKTileCountRows, stream,
-          launch_tile_count_rows(ws.pkey, ws.counters, ws.capacity, ws.tcounts, G, stream));
-    TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, G, stream));
-    TIMED(ws, kKTileScatterRows, stream,
-          launch_tile_scatter_rows(ws.pkey, ws.pgauss[0], ws.tcounts, ws.pgauss[1], ws.ranges,
-                                   ws.counters, ws.capacity, fs.cam.tiles_x, fs.num_tiles,
-                                   ws.status, G, stream));
+    if (fs.n > 0 && fs.order) {
+        PairSource src;
+        src.order = fs.order;
+        src.offsets = ws.offsets;
+        src.sorted_box = ws.sorted_box;
+        src.chunk_first = ws.chunk_first;
+        src.counters = ws.counters;
+        src.capacity = ws.capacity;
+        src.tiles_x = fs.cam.tiles_x;
+        // Stage 3-4, pass 1: column runs generated from the Gaussians, grouped by tx.
+        TIMED(ws, kKTileCountColumns, stream,
+              launch_tile_count_columns(src, ws.tcounts, ws.ttotals, ws.status, G, stream));
+        TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
+        TIMED(ws, kKTileScatterColumns, stream,
+              launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
+        // Stage 4, pass 2: pairs expanded from the runs, grouped by ty.
+        TIMED(ws, kKTileCountRows, stream,
+              launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x,
+                                     fs.num_tiles, ws.tcounts, ws.ttotals + kRadix, ws.tile_counts,
+                                     ws.status, G, stream));
+        TIMED(ws, kKTileCountScan, stream,
+              launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G, stream));
+        TIMED(ws, kKTileScatterRows, stream,
+              launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
+                                       ws.status, G, stream));
+    }
+    // Stage 5: every tile's [start, end) from its pair count.
+    TIMED(ws, kKTileRanges, stream,
+          launch_tile_ranges(ws.tile_counts, fs.num_tiles, ws.counters, ws.capacity, ws.ranges,
+                             stream));
 }
 
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,

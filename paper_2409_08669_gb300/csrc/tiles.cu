@@ -1,25 +1,34 @@
 // Stages 3-5 of the rasterization pipeline (Sec. 3.2.1): DuplicateWithKeys,
-// SortPairs by tile and IdentifyTileRanges, as two stable counting-sort
-// passes over the Gaussian-tile pairs, first by the tile column tx, then by
-// the tile row ty.  The pairs of each Gaussian are listed in depth order
-// (the Gaussians were sorted by view depth before), so the result is ordered
-// by (tile, depth), as the paper's 64-bit (tile | depth) key orders them.
+// SortPairs by tile and IdentifyTileRanges.  The result is the paper's: for
+// every tile, the Gaussians overlapping it in view-depth order (the order of
+// the 64-bit (tile | depth) keys), and each tile's [start, end).
 //
-// Each pass is range-partitioned (reduce, scan, scatter): CTA b of a grid of
-// G owns a contiguous run of 4096-pair chunks,
-//   1. counts its pairs per digit (pass 1 straight from the Gaussians'
-//      tile rectangles, without generating the pairs; pass 2 from the keys),
-//   2. one CTA turns the G x 256 counts into the global start of every
-//      (digit, CTA) run,
-//   3. CTA b walks its chunks in order, ranks each chunk's keys stably
-//      (warp match_any), groups them by digit in shared memory and writes
-//      every digit's run contiguously from its running offset.
-// No CTA ever waits for another one, so the passes need no co-residency and
-// no spin-waits.  Pass 1 generates the pairs on chip from the depth-ordered
-// Gaussians (the unsorted pair list never exists in memory) and writes a
-// 16-bit key (ty << 8 | tx) and the Gaussian id; pass 2 writes only the
-// Gaussian ids and each tile's [start, end) (atomicMin / atomicMax per run of
-// equal keys).
+// Every Gaussian overlaps a rectangle of tiles, so its pairs are w column runs
+// (one per tile column tx, covering rows y0 .. y0+h-1).  The sort works on
+// that structure in two stable counting passes:
+//   pass 1 (columns): the column runs, generated on chip from the
+//          depth-ordered Gaussians, are grouped by tx -- C = sum of w items,
+//          a few times fewer than the P = sum of w*h pairs;
+//   pass 2 (rows):    every run is expanded into its h pairs on chip and the
+//          pairs are grouped by ty; only the Gaussian ids are written.
+// Grouping by tx and then stably by ty orders the pairs by (ty, tx) = tile id,
+// and by depth within a tile, since both passes keep the input order.  Each
+// tile's range comes from its pair count (the runs of column tx that cover
+// row ty) by one scan, with no boundary search.
+//
+// Each pass is range-partitioned (count, scan, scatter): CTA b of a grid of G
+// owns a contiguous run of 4096-item chunks,
+//   1. counts its items per digit (pass 1 straight from the Gaussians'
+//      rectangles, pass 2 from the runs' row intervals, as difference arrays),
+//   2. the G x 256 counts become the global start of every (digit, CTA) run
+//      (per-digit totals are summed with atomics while counting),
+//   3. CTA b walks its chunks in order, ranks each chunk's items stably,
+//      groups them by digit in shared memory and writes every digit's run
+//      contiguously from its running offset.  Pass 1 ranks with warp
+//      match_any; pass 2 with per-warp row counts and lanes that each own
+//      a set of rows (see k_scatter_rows).
+// No CTA ever waits for another one: the passes need no co-residency and no
+// spin-waits.
 #include <cstddef>
 
 #include "adr_internal.cuh"
@@ -28,19 +37,27 @@ namespace adr {
 namespace {
 
 constexpr int kWarps = kSortThreads / 32;
-constexpr int kMaxChunkGauss = kSortChunk + 1;          // every listed Gaussian has >= 1 pair
+constexpr int kMaxChunkGauss = kSortChunk + 1;          // every listed Gaussian has >= 1 run
 constexpr int kStageLen = (kMaxChunkGauss + 3) & ~3;    // keeps the arrays after it 16-byte aligned
+constexpr int kRunStage = 2048;                         // runs staged per pass-2 chunk
+constexpr int kRunsPerThread = kRunStage / kSortThreads;
+constexpr int kColSlots = 8;                            // tile-count columns a CTA keeps on chip
 
-struct alignas(16) TileShared {
+// Column run record: x = Gaussian id, y = y0 | (h - 1) << 8 | tx << 16.
+__device__ __forceinline__ uint32_t run_y0(uint32_t y) { return y & 0xFFu; }
+__device__ __forceinline__ uint32_t run_h(uint32_t y) { return ((y >> 8) & 0xFFu) + 1u; }
+__device__ __forceinline__ uint32_t run_tx(uint32_t y) { return y >> 16; }
+
+struct alignas(16) ColumnShared {
     union {
         struct {
-            uint32_t keys[kSortChunk];
-            uint32_t vals[kSortChunk];
+            uint32_t keys[kSortChunk];   // run record y (digit tx = key >> 16)
+            uint32_t vals[kSortChunk];   // Gaussian id
         } kv;
-        struct {                      // Gaussians overlapping one pair chunk
+        struct {                         // Gaussians overlapping one run chunk
             uint32_t off[kStageLen];
             uint32_t gid[kStageLen];
-            uint32_t box[kStageLen];        // x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24
+            uint32_t box[kStageLen];     // x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24
             alignas(16) uint16_t map[kSortChunk];   // chunk slot -> staged Gaussian holding it
         } stage;
     } u;
@@ -50,9 +67,27 @@ struct alignas(16) TileShared {
     uint32_t dst[kRadix];                    // global position of local slot 0, per digit
     uint32_t wsum[kWarps];
 };
-constexpr size_t kTileSmem = sizeof(TileShared);
-static_assert(offsetof(TileShared, u) % 16 == 0, "staging must be 16-byte aligned");
+
+constexpr int kMaxWindows = kRunStage * 256 / kSortChunk + 2;   // 4096-pair windows per staging
+constexpr int kSlices = kRadix / 32;                            // rows owned per lane: ty = 32 k + lane
+
+struct alignas(16) RowShared {
+    uint2 runs[kRunStage];                   // staged column runs
+    uint32_t pre[kRunStage + 4];             // exclusive prefix of their pair counts
+    uint32_t win_first[kMaxWindows];         // staged run holding each window's first pair
+    uint32_t gid[kSortChunk];                // the window's pairs grouped by ty
+    alignas(16) uint16_t map[kSortChunk];    // window slot -> staged run holding it
+    uint8_t ty[kSortChunk];
+    int hist[kWarps][kRadix + 1];            // per-warp row counts (difference array, then prefix)
+    uint32_t run[kRadix];                    // next global position of each row
+    uint32_t local[kRadix];                  // exclusive prefix of the window's row counts
+    uint32_t dst[kRadix];                    // global position of window slot 0, per row
+    uint32_t wsum[kWarps];
+};
+static_assert(offsetof(ColumnShared, u) % 16 == 0, "staging must be 16-byte aligned");
 static_assert((3 * kStageLen * sizeof(uint32_t)) % 16 == 0, "map must be 16-byte aligned");
+constexpr size_t kColumnSmem = sizeof(ColumnShared);
+constexpr size_t kRowSmem = sizeof(RowShared);
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -60,22 +95,128 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// The chunks [c0, c1) of CTA b and the pair count n of the frame.
+// The item count of a pass and the chunks [c0, c1) of CTA blockIdx.x.
 struct Span {
     int64_t n;
     uint32_t nchunks, c0, c1;
 };
-__device__ __forceinline__ Span cta_span(const uint32_t* counters, int64_t capacity, int grid) {
+__device__ __forceinline__ Span cta_span(int64_t n, int grid) {
     Span s;
-    s.n = min((int64_t)counters[kCntPairs], capacity);
-    s.nchunks = (uint32_t)((s.n + kSortChunk - 1) / kSortChunk);
+    s.n = n;
+    s.nchunks = (uint32_t)((n + kSortChunk - 1) / kSortChunk);
     const uint32_t per = (s.nchunks + (uint32_t)grid - 1u) / (uint32_t)grid;
     s.c0 = min(s.nchunks, per * blockIdx.x);
     s.c1 = min(s.nchunks, s.c0 + per);
     return s;
 }
 
-// Depth-order positions [i0, i1] of the Gaussians holding pairs of chunks
+// Items of the two passes: the column runs C, or none when the pairs
+// overflowed the capacity (the frame then reports ADR_ERR_CAPACITY).
+__device__ __forceinline__ int64_t run_count(const uint32_t* counters, int64_t capacity) {
+    if ((int64_t)counters[kCntPairs] > capacity) return 0;
+    return min((int64_t)counters[kCntRuns], capacity);
+}
+
+// Exclusive block scan over the 256 threads (one value each); returns the
+// thread's exclusive prefix, `total` the sum.  Uses wsum; ends synchronised.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* wsum, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t s = wsum[w];
+        base += w < warp ? s : 0u;
+        total += s;
+    }
+    __syncthreads();
+    return base + x - v;
+}
+
+// In-place running maximum over map[0 .. kSortChunk) (u16 entries, 16 per
+// thread), so that every slot names the staged item holding it.
+__device__ __forceinline__ void map_running_max(uint16_t* map, uint32_t* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint4* m4 = reinterpret_cast<uint4*>(map) + 2 * tid;
+    const uint4 a = m4[0], b = m4[1];
+    const uint32_t w32[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t tmax = 0;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) tmax = max(tmax, max(w32[x] & 0xFFFFu, w32[x] >> 16));
+    uint32_t incl = tmax;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, y);
+    }
+    uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) excl = max(excl, wsum[w]);
+    uint32_t run = excl, out[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const uint32_t lo = run = max(run, w32[x] & 0xFFFFu);
+        const uint32_t hi = run = max(run, w32[x] >> 16);
+        out[x] = lo | (hi << 16);
+    }
+    m4[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    m4[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    __syncthreads();
+}
+
+// Stable ranking of one chunk by digit (kRadix = out of range) and the
+// per-digit bookkeeping shared by both scatters.  On return: rank[q] = the
+// item's position among the items of its digit in its warp; sm.local,
+// sm.warp_cnt (exclusive prefix over warps) and sm.dst are set and sm.run
+// advanced past the chunk.
+template <class Shared>
+__device__ __forceinline__ void rank_chunk(Shared& sm, const uint32_t (&dig)[kSortItems],
+                                           uint32_t (&rank)[kSortItems]) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < kSortItems; ++q) {
+        const uint32_t d = dig[q];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = sm.warp_cnt[warp][d];
+        rank[q] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (lane == 31 - __clz(peers)) sm.warp_cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // Per digit (thread = digit): prefix over warps and this chunk's count.
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = sm.warp_cnt[w][tid];
+        sm.warp_cnt[w][tid] = cnt;
+        cnt += c;
+    }
+    uint32_t total;
+    const uint32_t loc = block_exclusive_scan(cnt, sm.wsum, total);
+    sm.local[tid] = loc;
+    if (tid == kSortThreads - 1) sm.local[kRadix] = loc + cnt;
+    const uint32_t r = sm.run[tid];
+    sm.dst[tid] = r - loc;
+    sm.run[tid] = r + cnt;
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: column runs grouped by tx.
+// ---------------------------------------------------------------------------
+
+// Depth-order positions [i0, i1] of the Gaussians holding runs of chunks
 // [c0, c1); false (and kErrRange) if the scan output is inconsistent.
 __device__ __forceinline__ bool gauss_span(const PairSource& src, const Span& sp, uint32_t c0,
                                            uint32_t c1, uint32_t* status, uint32_t& i0,
@@ -90,23 +231,18 @@ __device__ __forceinline__ bool gauss_span(const PairSource& src, const Span& sp
     return true;
 }
 
-// ---------------------------------------------------------------------------
-// 1. Per-CTA digit counts.
-// ---------------------------------------------------------------------------
-
-// Pass 1: counts of tx over the pairs of this CTA's chunks, from the packed
-// rectangles.  A Gaussian's pairs k = 0 .. w*h-1 run over its rectangle row
-// by row (ty = y0 + k / w, tx = x0 + k % w); the part of them inside the
-// CTA's pair range is a partial row, whole rows and a partial row, each a
-// contiguous tx interval, added to a difference array.
+// Counts of tx over the column runs of this CTA's chunks.  Gaussian i owns
+// runs offsets[i] .. offsets[i] + w - 1 for columns x0 .. x0 + w - 1; the part
+// inside the CTA's range is one tx interval, added to a difference array.
 __global__ void __launch_bounds__(kSortThreads)
-k_count_columns(PairSource src, int grid, uint32_t* __restrict__ counts, uint32_t* __restrict__ status) {
+k_count_columns(PairSource src, int grid, uint32_t* __restrict__ counts, uint32_t* __restrict__ totals,
+                uint32_t* __restrict__ status) {
     __shared__ int s_diff[kRadix + 1];
     __shared__ uint32_t s_wsum[kWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     for (int d = tid; d <= kRadix; d += kSortThreads) s_diff[d] = 0;
     __syncthreads();
-    const Span sp = cta_span(src.counters, src.capacity, grid);
+    const Span sp = cta_span(run_count(src.counters, src.capacity), grid);
     uint32_t i0, i1;
     if (sp.c0 < sp.c1 && gauss_span(src, sp, sp.c0, sp.c1, status, i0, i1)) {
         const int64_t A = (int64_t)sp.c0 * kSortChunk;
@@ -114,135 +250,37 @@ k_count_columns(PairSource src, int grid, uint32_t* __restrict__ counts, uint32_
         for (uint32_t i = i0 + tid; i <= i1; i += kSortThreads) {
             const int64_t off = src.offsets[i];
             const uint32_t box = src.sorted_box[i];
-            const int w = (int)((box >> 16) & 0xFFu) + 1, h = (int)(box >> 24) + 1;
+            const int w = (int)((box >> 16) & 0xFFu) + 1;
             const int x0 = (int)(box & 0xFFu);
-            const int64_t k0 = max(A - off, (int64_t)0), k1 = min(B - off, (int64_t)w * h);
+            const int64_t k0 = max(A - off, (int64_t)0), k1 = min(B - off, (int64_t)w);
             if (k0 >= k1) continue;
             if (x0 + w > kRadix) { atomicOr(status, kErrRange); continue; }   // not a scan box
-            const int r0 = (int)(k0 / w), q0 = (int)(k0 - (int64_t)r0 * w);
-            const int r1 = (int)((k1 - 1) / w), q1 = (int)(k1 - 1 - (int64_t)r1 * w);
-            auto add = [&](int lo, int hi, int v) {
-                atomicAdd(&s_diff[lo], v);
-                atomicAdd(&s_diff[hi + 1], -v);
-            };
-            if (r0 == r1) {
-                add(x0 + q0, x0 + q1, 1);
-            } else {
-                add(x0 + q0, x0 + w - 1, 1);
-                if (r1 - r0 > 1) add(x0, x0 + w - 1, r1 - r0 - 1);
-                add(x0, x0 + q1, 1);
-            }
+            atomicAdd(&s_diff[x0 + k0], 1);
+            atomicAdd(&s_diff[x0 + k1], -1);
         }
     }
     __syncthreads();
     // Inclusive prefix of the difference array = the count of each tx.
+    uint32_t total;
     const int v = s_diff[tid];
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = (uint32_t)x;
-    __syncthreads();
-    int wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += (int)s_wsum[w];
-    counts[(size_t)tid * grid + blockIdx.x] = (uint32_t)(wbase + x);
+    const uint32_t c = block_exclusive_scan((uint32_t)v, s_wsum, total) + (uint32_t)v;
+    counts[(size_t)tid * grid + blockIdx.x] = c;
+    if (c) atomicAdd(totals + tid, c);
 }
 
-// Pass 2: counts of ty (key >> 8) over this CTA's chunks of pass-1 keys.
-__global__ void __launch_bounds__(kSortThreads)
-k_count_rows(const uint16_t* __restrict__ keys, const uint32_t* __restrict__ counters,
-             int64_t capacity, int grid, uint32_t* __restrict__ counts) {
-    __shared__ uint32_t s_cnt[kRadix];
-    const int tid = threadIdx.x;
-    s_cnt[tid] = 0;
-    __syncthreads();
-    const Span sp = cta_span(counters, capacity, grid);
-    if (sp.c0 < sp.c1) {
-        const int64_t A = (int64_t)sp.c0 * kSortChunk;
-        const int64_t B = min((int64_t)sp.c1 * kSortChunk, sp.n);   // > A
-        // A is a multiple of 4096 keys; read 8 keys per 16-byte load up to the
-        // last whole group, then the tail one by one.
-        const int64_t Bv = A + ((B - A) & ~(int64_t)7);
-        const uint4* k4 = reinterpret_cast<const uint4*>(keys + A);
-        for (int64_t j = tid; A + 8 * j < Bv; j += kSortThreads) {
-            const uint4 q = k4[j];
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                atomicAdd(&s_cnt[(w[u] >> 8) & 0xFFu], 1u);
-                atomicAdd(&s_cnt[w[u] >> 24], 1u);
-            }
-        }
-        for (int64_t i = Bv + tid; i < B; i += kSortThreads) atomicAdd(&s_cnt[keys[i] >> 8], 1u);
-    }
-    __syncthreads();
-    counts[(size_t)tid * grid + blockIdx.x] = s_cnt[tid];
-}
-
-// ---------------------------------------------------------------------------
-// 2. Global start of every (digit, CTA) run: counts [256][grid] in place.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_count_scan(uint32_t* __restrict__ counts, int grid) {
-    __shared__ uint32_t s_tot[kRadix], s_base[kRadix];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int d = warp; d < kRadix; d += 32) {
-        uint32_t s = 0;
-        for (int b = lane; b < grid; b += 32) s += counts[(size_t)d * grid + b];
-        s = __reduce_add_sync(0xffffffffu, s);
-        if (lane == 0) s_tot[d] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {   // exclusive prefix over the 256 digits, 8 per lane
-        uint32_t v[8], t = 0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) { v[u] = s_tot[lane * 8 + u]; t += v[u]; }
-        uint32_t x = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        uint32_t run = x - t;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) { s_base[lane * 8 + u] = run; run += v[u]; }
-    }
-    __syncthreads();
-    for (int d = warp; d < kRadix; d += 32) {
-        uint32_t run = s_base[d];
-        for (int b0 = 0; b0 < grid; b0 += 32) {
-            const int b = b0 + lane;
-            const uint32_t v = b < grid ? counts[(size_t)d * grid + b] : 0u;
-            uint32_t x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (b < grid) counts[(size_t)d * grid + b] = run + x - v;
-            run += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// 3. Scatter.
-// ---------------------------------------------------------------------------
-
-// Generate the pairs of chunk `chunk` (items base .. base+count-1 of the
-// depth-ordered emission) into key/val in warp-striped order:
-// key = ty << 8 | tx, val = Gaussian id.
-__device__ __forceinline__ void generate_pairs(const PairSource& src, const Span& sp,
-                                               TileShared& sm, uint32_t chunk, int64_t base,
-                                               int count, uint32_t* status,
-                                               uint32_t (&key)[kSortItems],
-                                               uint32_t (&val)[kSortItems]) {
+// Generate the column runs of chunk `chunk` (items base .. base+count-1 of
+// the depth-ordered emission) into key (run record y) / val (Gaussian id) in
+// warp-striped order.
+__device__ __forceinline__ void generate_runs(const PairSource& src, const Span& sp,
+                                              ColumnShared& sm, uint32_t chunk, int64_t base,
+                                              int count, uint32_t* status,
+                                              uint32_t (&key)[kSortItems],
+                                              uint32_t (&val)[kSortItems]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t visible = src.counters[kCntVisible];
     uint32_t i0 = src.chunk_first[chunk];
-    // Gaussians [i0, i1] hold this chunk's pairs; the one holding the next
-    // chunk's first pair closes the range (the last chunk: at most 4097 on).
+    // Gaussians [i0, i1] hold this chunk's runs; the one holding the next
+    // chunk's first run closes the range (the last chunk: at most 4097 on).
     uint32_t i1 = chunk + 1 < sp.nchunks ? src.chunk_first[chunk + 1]
                                          : min(visible - 1u, i0 + (uint32_t)kMaxChunkGauss - 1u);
     if (visible == 0 || i0 >= visible || i1 < i0 || i1 >= visible ||
@@ -261,47 +299,14 @@ __device__ __forceinline__ void generate_pairs(const PairSource& src, const Span
         sm.u.stage.box[j] = src.sorted_box[i];
     }
     __syncthreads();
-    // Mark the slot where each staged Gaussian's first pair falls (slot 0
-    // belongs to staged Gaussian 0, the holder of the chunk's first pair).
+    // Mark the slot where each staged Gaussian's first run falls (slot 0
+    // belongs to staged Gaussian 0, the holder of the chunk's first run).
     for (int j = tid; j < G; j += kSortThreads) {
         const int64_t slot = (int64_t)sm.u.stage.off[j] - base;
         if (slot > 0 && slot < count) sm.u.stage.map[slot] = (uint16_t)j;
     }
     __syncthreads();
-    // Running maximum over the slots: thread t owns slots 16t .. 16t+15, then
-    // a block-wide exclusive max-scan of the thread maxima.
-    {
-        uint4* m4 = reinterpret_cast<uint4*>(sm.u.stage.map) + 2 * tid;
-        const uint4 a = m4[0], b = m4[1];
-        const uint32_t w32[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        uint32_t tmax = 0;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) tmax = max(tmax, max(w32[x] & 0xFFFFu, w32[x] >> 16));
-        uint32_t incl = tmax;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl = max(incl, y);
-        }
-        uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) excl = 0;
-        if (lane == 31) sm.wsum[warp] = incl;
-        __syncthreads();
-        for (int w = 0; w < warp; ++w) excl = max(excl, sm.wsum[w]);
-        uint32_t run = excl, out[8];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const uint32_t lo = run = max(run, w32[x] & 0xFFFFu);
-            const uint32_t hi = run = max(run, w32[x] >> 16);
-            out[x] = lo | (hi << 16);
-        }
-        m4[0] = make_uint4(out[0], out[1], out[2], out[3]);
-        m4[1] = make_uint4(out[4], out[5], out[6], out[7]);
-    }
-    __syncthreads();
-    // Warp w produces items w*512 + q*32 + lane, the warp-striped order the
-    // ranking needs.  k / w is exact through a reciprocal biased up by 2^-20:
-    // k < 2^16 and w <= 256 keep the product within (q, q + 1).
+    map_running_max(sm.u.stage.map, sm.wsum);
     const int wfirst = warp * (kSortItems * 32);
 #pragma unroll
     for (int q = 0; q < kSortItems; ++q) {
@@ -309,111 +314,44 @@ __device__ __forceinline__ void generate_pairs(const PairSource& src, const Span
         if (s < count) {
             const int jj = sm.u.stage.map[s];
             const uint32_t box = sm.u.stage.box[jj];
-            const uint32_t w = ((box >> 16) & 0xFFu) + 1u;
-            const uint32_t k = (uint32_t)(base + s) - sm.u.stage.off[jj];
-            const float r = __frcp_rn((float)w) * 1.00000095367431640625f;   // (1 + 2^-20) / w
-            const uint32_t dy = (uint32_t)((float)k * r);
-            const uint32_t dx = k - dy * w;
-            key[q] = ((((box >> 8) & 0xFFu) + dy) << 8) | ((box & 0xFFu) + dx);
+            const uint32_t k = (uint32_t)(base + s) - sm.u.stage.off[jj];   // column offset
+            const uint32_t tx = (box & 0xFFu) + k;
+            key[q] = ((box >> 8) & 0xFFu) | ((box >> 24) << 8) | (tx << 16);
             val[q] = sm.u.stage.gid[jj];
         } else {
-            key[q] = 0xFFFFu;
+            key[q] = 0u;
             val[q] = 0u;
         }
     }
 }
 
-struct ScatterArgs {
-    PairSource src;                  // pass 1: pairs generated from the Gaussians
-    const uint16_t* keys_in;         // pass 2
-    const uint32_t* vals_in;         // pass 2
-    uint16_t* keys_out;              // pass 1
-    uint32_t* vals_out;
-    const uint32_t* starts;          // [256][grid] global start of each (digit, CTA) run
-    uint2* ranges;                   // pass 2
-    const uint32_t* counters;
-    int64_t capacity;
-    int grid;
-    int tiles_x, num_tiles;
-    uint32_t* status;
-};
-
-template <bool kFirst>
-__global__ void __launch_bounds__(kSortThreads, 3) k_tile_scatter(ScatterArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 3)
+k_scatter_columns(PairSource src, const uint32_t* __restrict__ starts, uint2* __restrict__ runs_out,
+                  int grid, uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileShared& sm = *reinterpret_cast<TileShared*>(smem_raw);
+    ColumnShared& sm = *reinterpret_cast<ColumnShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const Span sp = cta_span(a.counters, a.capacity, a.grid);
+    const Span sp = cta_span(run_count(src.counters, src.capacity), grid);
     if (sp.c0 >= sp.c1) return;
     const int64_t n = sp.n;
-    sm.run[tid] = a.starts[(size_t)tid * a.grid + blockIdx.x];
-    // digit of a key: tx in pass 1, ty in pass 2
-    auto digit = [](uint32_t k) { return kFirst ? (k & 0xFFu) : (k >> 8); };
-
+    sm.run[tid] = starts[(size_t)tid * grid + blockIdx.x];
     for (uint32_t chunk = sp.c0; chunk < sp.c1; ++chunk) {
         for (int d = lane; d <= kRadix; d += 32) sm.warp_cnt[warp][d] = 0;
         const int64_t base = (int64_t)chunk * kSortChunk;
         const int count = (int)min((int64_t)kSortChunk, n - base);
-        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-        if constexpr (kFirst) {
-            generate_pairs(a.src, sp, sm, chunk, base, count, a.status, key, val);
-        } else {
-#pragma unroll
-            for (int q = 0; q < kSortItems; ++q) {
-                const int s = warp * (kSortItems * 32) + q * 32 + lane;
-                const bool ok = s < count;
-                key[q] = ok ? (uint32_t)a.keys_in[base + s] : 0xFFFFu;
-                val[q] = ok ? a.vals_in[base + s] : 0u;
-            }
-        }
-        __syncthreads();   // warp_cnt cleared; staging (pass 1) no longer read
-        // Stable warp-level ranking with match_any (digit kRadix = out of range).
+        uint32_t key[kSortItems], val[kSortItems], dig[kSortItems], rank[kSortItems];
+        generate_runs(src, sp, sm, chunk, base, count, status, key, val);
 #pragma unroll
         for (int q = 0; q < kSortItems; ++q) {
             const int s = warp * (kSortItems * 32) + q * 32 + lane;
-            const uint32_t d = s < count ? digit(key[q]) : (uint32_t)kRadix;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = sm.warp_cnt[warp][d];
-            rank[q] = before + __popc(peers & lanemask_lt());
-            __syncwarp();
-            if (lane == 31 - __clz(peers)) sm.warp_cnt[warp][d] = before + __popc(peers);
-            __syncwarp();
+            dig[q] = s < count ? min(run_tx(key[q]), (uint32_t)kRadix - 1u) : (uint32_t)kRadix;
         }
-        __syncthreads();
-        // Per digit (thread = digit): prefix over warps and this chunk's count.
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = sm.warp_cnt[w][tid];
-            sm.warp_cnt[w][tid] = cnt;
-            cnt += c;
-        }
-        uint32_t loc;
-        {
-            uint32_t x = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) sm.wsum[warp] = x;
-            __syncthreads();
-            uint32_t wbase = 0;
-            for (int w = 0; w < warp; ++w) wbase += sm.wsum[w];
-            loc = wbase + x - cnt;
-            sm.local[tid] = loc;
-            if (tid == kSortThreads - 1) sm.local[kRadix] = loc + cnt;
-        }
-        const uint32_t r = sm.run[tid];
-        sm.dst[tid] = r - loc;
-        sm.run[tid] = r + cnt;
-        __syncthreads();
-        // Group by digit in shared memory.
+        __syncthreads();   // staging no longer read
+        rank_chunk(sm, dig, rank);
 #pragma unroll
         for (int q = 0; q < kSortItems; ++q) {
-            const int s = warp * (kSortItems * 32) + q * 32 + lane;
-            if (s < count) {
-                const uint32_t d = digit(key[q]);
+            if (dig[q] < (uint32_t)kRadix) {
+                const uint32_t d = dig[q];
                 const uint32_t pos = sm.local[d] + sm.warp_cnt[warp][d] + rank[q];
                 sm.u.kv.keys[pos] = key[q];
                 sm.u.kv.vals[pos] = val[q];
@@ -423,90 +361,358 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_scatter(ScatterArgs a)
         // Coalesced write-out: each digit's run goes to consecutive addresses.
         for (int s = tid; s < count; s += kSortThreads) {
             const uint32_t k = sm.u.kv.keys[s];
-            const uint32_t d = digit(k);
-            const uint32_t g = sm.dst[d] + (uint32_t)s;   // exact modulo 2^32; true value < 2^30
-            if ((int64_t)g >= n) { atomicOr(a.status, kErrRange); continue; }
-            a.vals_out[g] = sm.u.kv.vals[s];
-            if constexpr (kFirst) {
-                a.keys_out[g] = (uint16_t)k;
-            } else {
-                // Within a digit's run the keys ascend, so each tile's pairs
-                // form one segment; record its first and last global slot.
-                const bool first = (s == (int)sm.local[d]) || sm.u.kv.keys[s - 1] != k;
-                const bool lastp = (s + 1 == (int)sm.local[d + 1]) || sm.u.kv.keys[s + 1] != k;
-                const uint32_t tile = (k >> 8) * (uint32_t)a.tiles_x + (k & 0xFFu);
-                if ((k & 0xFFu) >= (uint32_t)a.tiles_x || tile >= (uint32_t)a.num_tiles) {
-                    atomicOr(a.status, kErrRange);   // not a pass-1 key: skip
-                    continue;
-                }
-                unsigned int* rr = reinterpret_cast<unsigned int*>(a.ranges + tile);
-                if (first) atomicMin(rr, g);
-                if (lastp) atomicMax(rr + 1, g + 1u);
-            }
+            const uint32_t g = sm.dst[min(run_tx(k), (uint32_t)kRadix - 1u)] + (uint32_t)s;
+            if ((int64_t)g < n) runs_out[g] = make_uint2(sm.u.kv.vals[s], k);
+            else atomicOr(status, kErrRange);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: pairs grouped by ty.
+// ---------------------------------------------------------------------------
+
+// Counts of ty over the pairs of this CTA's runs (each run adds its row
+// interval to a difference array), and the pairs of every tile: runs of
+// column tx covering row ty.  Runs arrive grouped by tx, so the CTA's first
+// kColSlots columns are counted on chip; runs beyond them (only in columns
+// with few runs) add to tile_counts directly.
+__global__ void __launch_bounds__(kSortThreads)
+k_count_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters, int64_t capacity,
+             int grid, int tiles_x, int num_tiles, uint32_t* __restrict__ counts,
+             uint32_t* __restrict__ totals, uint32_t* __restrict__ tile_counts,
+             uint32_t* __restrict__ status) {
+    __shared__ int s_diff[kRadix + 1];
+    __shared__ int s_col[kColSlots][kRadix + 1];
+    __shared__ uint32_t s_wsum[kWarps];
+    const int tid = threadIdx.x;
+    for (int d = tid; d <= kRadix; d += kSortThreads) s_diff[d] = 0;
+    for (int d = tid; d < kColSlots * (kRadix + 1); d += kSortThreads) (&s_col[0][0])[d] = 0;
+    __syncthreads();
+    const Span sp = cta_span(run_count(counters, capacity), grid);
+    uint32_t tx0 = 0;
+    if (sp.c0 < sp.c1) {
+        const int64_t A = (int64_t)sp.c0 * kSortChunk;
+        const int64_t B = min((int64_t)sp.c1 * kSortChunk, sp.n);
+        tx0 = run_tx(runs[A].y);
+        for (int64_t i = A + tid; i < B; i += kSortThreads) {
+            const uint32_t y = runs[i].y;
+            const uint32_t y0 = run_y0(y), h = run_h(y), tx = run_tx(y);
+            if (y0 + h > (uint32_t)kRadix || tx >= (uint32_t)tiles_x) {   // not a pass-1 record
+                atomicOr(status, kErrRange);
+                continue;
+            }
+            atomicAdd(&s_diff[y0], 1);
+            atomicAdd(&s_diff[y0 + h], -1);
+            const uint32_t c = tx - tx0;
+            if (c < (uint32_t)kColSlots) {
+                atomicAdd(&s_col[c][y0], 1);
+                atomicAdd(&s_col[c][y0 + h], -1);
+            } else {
+                for (uint32_t ty = y0; ty < y0 + h; ++ty) {
+                    const uint32_t t = ty * (uint32_t)tiles_x + tx;
+                    if (t < (uint32_t)num_tiles) atomicAdd(tile_counts + t, 1u);
+                    else atomicOr(status, kErrRange);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t total;
+    const int v = s_diff[tid];
+    const uint32_t c = block_exclusive_scan((uint32_t)v, s_wsum, total) + (uint32_t)v;
+    counts[(size_t)tid * grid + blockIdx.x] = c;
+    if (c) atomicAdd(totals + tid, c);
+    // Tile counts of the on-chip columns: prefix over rows, one warp per column.
+    if (sp.c0 < sp.c1) {
+        const int lane = tid & 31, warp = tid >> 5;
+        const uint32_t tx = tx0 + (uint32_t)warp;
+        if (warp < kColSlots && tx < (uint32_t)tiles_x) {
+            int run = 0;
+            for (int ty0 = 0; ty0 < kRadix; ty0 += 32) {
+                int x = s_col[warp][ty0 + lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const int cnt = run + x;
+                const uint32_t t = (uint32_t)(ty0 + lane) * (uint32_t)tiles_x + tx;
+                if (cnt > 0 && t < (uint32_t)num_tiles) atomicAdd(tile_counts + t, (uint32_t)cnt);
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+    }
+}
+
+// Tile ranges: exclusive scan of the tile pair counts in tile order.  One CTA.
+constexpr int kRangeThreads = 1024;
+__global__ void __launch_bounds__(kRangeThreads)
+k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
+              const uint32_t* __restrict__ counters, int64_t capacity, uint2* __restrict__ ranges) {
+    __shared__ uint32_t s_w[kRangeThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool overflow = (int64_t)counters[kCntPairs] > capacity;
+    const int per = (num_tiles + kRangeThreads - 1) / kRangeThreads;
+    const int t0 = tid * per, t1 = min(t0 + per, num_tiles);
+    uint32_t sum = 0;
+    for (int t = t0; t < t1; ++t) sum += overflow ? 0u : tile_counts[t];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t run = x - sum;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = overflow ? 0u : tile_counts[t];
+        ranges[t] = make_uint2(run, run + c);
+        run += c;
+    }
+}
+
+// Expand the runs of this CTA's chunks into pairs and scatter their Gaussian
+// ids by ty.  Up to kRunStage runs are staged at a time; their pairs are cut
+// into windows of 4096.  In a window, warp w takes slots 512w .. 512w+511;
+// it counts its pairs per row (each run adds its row interval to a
+// difference array), the counts of the warps before it give its first slot
+// of every row, and it then walks its runs in order with lane l owning rows
+// l, l + 32, ...: the lanes whose row a run covers put the run's Gaussian at
+// their next slot.  The window's pairs leave grouped by row, one contiguous
+// piece per row.
+__global__ void __launch_bounds__(kSortThreads, 3)
+k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
+               int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
+               int grid, uint32_t* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowShared& sm = *reinterpret_cast<RowShared*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Span sp = cta_span(run_count(counters, capacity), grid);
+    if (sp.c0 >= sp.c1) return;
+    const int64_t n_pairs = min((int64_t)counters[kCntPairs], capacity);
+    sm.run[tid] = starts[(size_t)tid * grid + blockIdx.x];
+    const int64_t B = min((int64_t)sp.c1 * kSortChunk, sp.n);
+    for (int64_t r = (int64_t)sp.c0 * kSortChunk; r < B; r += kRunStage) {
+        // Stage the runs and the exclusive prefix of their pair counts.
+        const int avail = (int)min((int64_t)kRunStage, B - r);
+        uint32_t h[kRunsPerThread], hsum = 0;
+#pragma unroll
+        for (int u = 0; u < kRunsPerThread; ++u) {
+            const int j = tid * kRunsPerThread + u;
+            uint2 rec = make_uint2(0u, 0u);
+            if (j < avail) rec = runs[r + j];
+            sm.runs[j] = rec;
+            h[u] = j < avail ? run_h(rec.y) : 0u;
+            hsum += h[u];
+        }
+        uint32_t T;
+        uint32_t pre = block_exclusive_scan(hsum, sm.wsum, T);
+#pragma unroll
+        for (int u = 0; u < kRunsPerThread; ++u) {
+            const int j = tid * kRunsPerThread + u;
+            sm.pre[j] = pre;
+            // the window starting inside this run (a run has at most 256 pairs)
+            const uint32_t w0 = (pre + kSortChunk - 1) / kSortChunk;
+            if (h[u] && w0 * kSortChunk < pre + h[u]) sm.win_first[w0] = (uint32_t)j;
+            pre += h[u];
+        }
+        if (tid == kSortThreads - 1) sm.pre[kRunStage] = pre;
+        __syncthreads();
+        const int nwin = (int)((T + kSortChunk - 1) / kSortChunk);
+        for (int k = 0; k < nwin; ++k) {
+            const uint32_t P0 = (uint32_t)k * kSortChunk;
+            const int count = (int)min((uint32_t)kSortChunk, T - P0);
+            const uint32_t jfirst = sm.win_first[k];
+            const uint32_t jlast = k + 1 < nwin ? sm.win_first[k + 1] : (uint32_t)avail - 1u;
+            // Slot -> run map: mark where each run after the first starts.
+            uint32_t* map32 = reinterpret_cast<uint32_t*>(sm.map);
+            for (int x = tid; x < kSortChunk / 2; x += kSortThreads) map32[x] = 0u;
+            for (int d = lane; d <= kRadix; d += 32) sm.hist[warp][d] = 0;
+            __syncthreads();
+            if (tid == 0) sm.map[0] = (uint16_t)jfirst;
+            for (uint32_t j = jfirst + 1 + tid; j <= jlast; j += kSortThreads) {
+                const uint32_t slot = sm.pre[j] - P0;
+                if (slot < (uint32_t)count) sm.map[slot] = (uint16_t)j;
+            }
+            __syncthreads();
+            map_running_max(sm.map, sm.wsum);
+            // This warp's slots [S0, S1) (window coordinates) and runs [jA, jB].
+            const int S0 = warp * (kSortChunk / kWarps), S1 = min(S0 + kSortChunk / kWarps, count);
+            const bool any = S0 < S1;
+            const uint32_t jA = any ? sm.map[S0] : 1u, jB = any ? sm.map[S1 - 1] : 0u;
+            // Per-warp row counts.
+            for (uint32_t j = jA + lane; j <= jB; j += 32) {
+                const uint32_t y = sm.runs[j].y, p = sm.pre[j];
+                const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(y)) - p;
+                if (lo < hi) {
+                    atomicAdd(&sm.hist[warp][run_y0(y) + lo], 1);
+                    atomicAdd(&sm.hist[warp][run_y0(y) + hi], -1);
+                }
+            }
+            __syncwarp();
+            {   // inclusive prefix of the warp's difference array, 8 rows per lane
+                int v[kRadix / 32], t = 0;
+#pragma unroll
+                for (int u = 0; u < kRadix / 32; ++u) { v[u] = sm.hist[warp][lane * 8 + u]; t += v[u]; }
+                int x = t;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                int acc = x - t;
+#pragma unroll
+                for (int u = 0; u < kRadix / 32; ++u) { acc += v[u]; sm.hist[warp][lane * 8 + u] = acc; }
+            }
+            __syncthreads();
+            // Per row (thread = row): exclusive prefix over warps, window count.
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = (uint32_t)sm.hist[w][tid];
+                sm.hist[w][tid] = (int)cnt;
+                cnt += c;
+            }
+            uint32_t total;
+            const uint32_t loc = block_exclusive_scan(cnt, sm.wsum, total);
+            sm.local[tid] = loc;
+            const uint32_t rr = sm.run[tid];
+            sm.dst[tid] = rr - loc;
+            sm.run[tid] = rr + cnt;
+            __syncthreads();
+            // Walk the warp's runs in order; lane l fills rows l + 32 s.
+            uint32_t slot[kSlices];
+#pragma unroll
+            for (int u = 0; u < kSlices; ++u)
+                slot[u] = sm.local[u * 32 + lane] + (uint32_t)sm.hist[warp][u * 32 + lane];
+            for (uint32_t j = jA; j <= jB; ++j) {
+                const uint2 rec = sm.runs[j];
+                const uint32_t p = sm.pre[j];
+                const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(rec.y)) - p;
+                const uint32_t t0 = run_y0(rec.y) + lo, t1 = run_y0(rec.y) + hi;   // rows [t0, t1)
+#pragma unroll
+                for (int u = 0; u < kSlices; ++u) {   // the branches are uniform over the warp
+                    if (u * 32 >= (int)t1) break;
+                    if (u * 32 + 32 <= (int)t0) continue;
+                    const uint32_t ty = (uint32_t)(u * 32 + lane);
+                    if (ty >= t0 && ty < t1) {
+                        const uint32_t q = min(slot[u], (uint32_t)kSortChunk - 1u);
+                        sm.gid[q] = rec.x;
+                        sm.ty[q] = (uint8_t)ty;
+                        ++slot[u];
+                    }
+                }
+            }
+            __syncthreads();
+            // Coalesced write-out: each row's piece goes to consecutive addresses.
+            for (int s = tid; s < count; s += kSortThreads) {
+                const uint32_t g = sm.dst[sm.ty[s]] + (uint32_t)s;   // exact modulo 2^32
+                if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[s];
+                else atomicOr(status, kErrRange);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Global start of every (digit, CTA) run: counts [256][grid] in place.
+// CTA d: start of digit d = sum of the totals of the digits below it, then an
+// exclusive scan of its grid counts.
+// ---------------------------------------------------------------------------
+constexpr int kScanCtaThreads = 512;
+constexpr int kScanPerThread = kMaxTileGrid / kScanCtaThreads;
+static_assert(kScanPerThread * kScanCtaThreads == kMaxTileGrid, "scan covers the largest grid");
+
+__global__ void __launch_bounds__(kScanCtaThreads)
+k_count_scan(uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals, int grid) {
+    __shared__ uint32_t s_w[kScanCtaThreads / 32];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int d = blockIdx.x;
+    if (warp == 0) {
+        uint32_t b = 0;
+        for (int e = lane; e < d; e += 32) b += totals[e];
+        b = __reduce_add_sync(0xffffffffu, b);
+        if (lane == 0) s_base = b;
+    }
+    uint32_t* row = counts + (size_t)d * grid;
+    uint32_t v[kScanPerThread], t = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) {
+        const int b = tid * kScanPerThread + u;
+        v[u] = b < grid ? row[b] : 0u;
+        t += v[u];
+    }
+    uint32_t x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t run = s_base + x - t;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+#pragma unroll
+    for (int u = 0; u < kScanPerThread; ++u) {
+        const int b = tid * kScanPerThread + u;
+        if (b < grid) row[b] = run;
+        run += v[u];
     }
 }
 
 }  // namespace
 
 int tile_scatter_blocks_per_sm() {
-    cudaFuncSetAttribute(k_tile_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    cudaFuncSetAttribute(k_tile_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile_scatter<true>, kSortThreads,
-                                                      kTileSmem) != cudaSuccess)
+    cudaFuncSetAttribute(k_scatter_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColumnSmem);
+    cudaFuncSetAttribute(k_scatter_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+    int b1 = 0, b2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_scatter_columns, kSortThreads,
+                                                      kColumnSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_scatter_rows, kSortThreads,
+                                                      kRowSmem) != cudaSuccess)
         return 1;
+    const int b = b1 < b2 ? b1 : b2;
     return b > 0 ? b : 1;
 }
 
-void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* status, int grid,
-                               cudaStream_t stream) {
-    k_count_columns<<<grid, kSortThreads, 0, stream>>>(src, grid, counts, status);
+void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* totals,
+                               uint32_t* status, int grid, cudaStream_t stream) {
+    k_count_columns<<<grid, kSortThreads, 0, stream>>>(src, grid, counts, totals, status);
 }
 
-void launch_tile_count_rows(const uint16_t* keys, const uint32_t* counters, int64_t capacity,
-                            uint32_t* counts, int grid, cudaStream_t stream) {
-    k_count_rows<<<grid, kSortThreads, 0, stream>>>(keys, counters, capacity, grid, counts);
+void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
+                                 uint32_t* status, int grid, cudaStream_t stream) {
+    k_scatter_columns<<<grid, kSortThreads, kColumnSmem, stream>>>(src, starts, runs_out, grid, status);
 }
 
-void launch_tile_count_scan(uint32_t* counts, int grid, cudaStream_t stream) {
-    k_count_scan<<<1, 1024, 0, stream>>>(counts, grid);
+void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
+                            int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
+                            uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream) {
+    k_count_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, grid, tiles_x, num_tiles,
+                                                    counts, totals, tile_counts, status);
 }
 
-void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint16_t* keys_out,
-                                 uint32_t* gauss_out, uint32_t* status, int grid,
-                                 cudaStream_t stream) {
-    ScatterArgs a{};
-    a.src = src;
-    a.keys_out = keys_out;
-    a.vals_out = gauss_out;
-    a.starts = starts;
-    a.counters = src.counters;
-    a.capacity = src.capacity;
-    a.grid = grid;
-    a.tiles_x = src.tiles_x;
-    a.status = status;
-    k_tile_scatter<true><<<grid, kSortThreads, kTileSmem, stream>>>(a);
+void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
+                        int64_t capacity, uint2* ranges, cudaStream_t stream) {
+    if (num_tiles <= 0) return;
+    k_tile_ranges<<<1, kRangeThreads, 0, stream>>>(tile_counts, num_tiles, counters, capacity, ranges);
 }
 
-void launch_tile_scatter_rows(const uint16_t* keys_in, const uint32_t* gauss_in,
-                              const uint32_t* starts, uint32_t* gauss_out, uint2* ranges,
-                              const uint32_t* counters, int64_t capacity, int tiles_x,
-                              int num_tiles, uint32_t* status, int grid, cudaStream_t stream) {
-    ScatterArgs a{};
-    a.keys_in = keys_in;
-    a.vals_in = gauss_in;
-    a.vals_out = gauss_out;
-    a.starts = starts;
-    a.ranges = ranges;
-    a.counters = counters;
-    a.capacity = capacity;
-    a.grid = grid;
-    a.tiles_x = tiles_x;
-    a.num_tiles = num_tiles;
-    a.status = status;
-    k_tile_scatter<false><<<grid, kSortThreads, kTileSmem, stream>>>(a);
+void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
+                              const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
+                              int grid, cudaStream_t stream) {
+    k_scatter_rows<<<grid, kSortThreads, kRowSmem, stream>>>(runs, counters, capacity, starts,
+                                                             gauss_out, grid, status);
+}
+
+void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream) {
+    k_count_scan<<<kRadix, kScanCtaThreads, 0, stream>>>(counts, totals, grid);
 }
 
 }  // namespace adr
