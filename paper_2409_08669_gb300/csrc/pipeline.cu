@@ -123,16 +123,19 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
         TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
         TIMED(ws, kKTileScatterColumns, stream,
               launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
-        // Stage 4, pass 2: pairs expanded from the runs, grouped by ty.
+        // Stage 4, pass 2: pairs expanded from the runs, grouped by ty.  The
+        // runs' pair counts vary, so the pass uses many small run ranges
+        // (kMaxTileGrid CTAs) that the hardware schedules as CTAs finish.
+        const int G2 = kMaxTileGrid;
         TIMED(ws, kKTileCountRows, stream,
               launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x,
                                      fs.num_tiles, ws.tcounts, ws.ttotals + kRadix, ws.tile_counts,
-                                     ws.status, G, stream));
+                                     ws.status, G2, stream));
         TIMED(ws, kKTileCountScan, stream,
-              launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G, stream));
+              launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G2, stream));
         TIMED(ws, kKTileScatterRows, stream,
               launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
-                                       ws.status, G, stream));
+                                       ws.status, G2, stream));
     }
     // Stage 5: every tile's [start, end) from its pair count.
     TIMED(ws, kKTileRanges, stream,

@@ -25,8 +25,8 @@
 //   3. CTA b walks its chunks in order, ranks each chunk's items stably,
 //      groups them by digit in shared memory and writes every digit's run
 //      contiguously from its running offset.  Pass 1 ranks with warp
-//      match_any; pass 2 with per-warp row counts and lanes that each own
-//      a set of rows (see k_scatter_rows).
+//      match_any; pass 2 from per-warp row counts and a walk over the runs
+//      (see k_scatter_rows).
 // No CTA ever waits for another one: the passes need no co-residency and no
 // spin-waits.
 #include <cstddef>
@@ -69,7 +69,6 @@ struct alignas(16) ColumnShared {
 };
 
 constexpr int kMaxWindows = kRunStage * 256 / kSortChunk + 2;   // 4096-pair windows per staging
-constexpr int kSlices = kRadix / 32;                            // rows owned per lane: ty = 32 k + lane
 
 struct alignas(16) RowShared {
     uint2 runs[kRunStage];                   // staged column runs
@@ -77,10 +76,9 @@ struct alignas(16) RowShared {
     uint32_t win_first[kMaxWindows];         // staged run holding each window's first pair
     uint32_t gid[kSortChunk];                // the window's pairs grouped by ty
     alignas(16) uint16_t map[kSortChunk];    // window slot -> staged run holding it
-    uint8_t ty[kSortChunk];
-    int hist[kWarps][kRadix + 1];            // per-warp row counts (difference array, then prefix)
+    uint8_t ty[kSortChunk];                  // row of each slot of gid
+    int hist[kWarps][kRadix + 1];            // per-warp row counts, then the warp's row cursors
     uint32_t run[kRadix];                    // next global position of each row
-    uint32_t local[kRadix];                  // exclusive prefix of the window's row counts
     uint32_t dst[kRadix];                    // global position of window slot 0, per row
     uint32_t wsum[kWarps];
 };
@@ -480,10 +478,10 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 // into windows of 4096.  In a window, warp w takes slots 512w .. 512w+511;
 // it counts its pairs per row (each run adds its row interval to a
 // difference array), the counts of the warps before it give its first slot
-// of every row, and it then walks its runs in order with lane l owning rows
-// l, l + 32, ...: the lanes whose row a run covers put the run's Gaussian at
-// their next slot.  The window's pairs leave grouped by row, one contiguous
-// piece per row.
+// of every row, and it then walks its runs in order, lane l serving the rows
+// ty = l mod 32, putting each run's Gaussian at its next slot of each row the
+// run covers.  The window's pairs leave grouped by row, one contiguous piece
+// per row.
 __global__ void __launch_bounds__(kSortThreads, 3)
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
@@ -569,49 +567,64 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
                 for (int u = 0; u < kRadix / 32; ++u) { acc += v[u]; sm.hist[warp][lane * 8 + u] = acc; }
             }
             __syncthreads();
-            // Per row (thread = row): exclusive prefix over warps, window count.
+            // Per row (thread = row): the window's count, its first slot, and
+            // each warp's first slot of the row (the cursors of the walk).
             uint32_t cnt = 0;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = (uint32_t)sm.hist[w][tid];
-                sm.hist[w][tid] = (int)cnt;
-                cnt += c;
-            }
+            for (int w = 0; w < kWarps; ++w) cnt += (uint32_t)sm.hist[w][tid];
             uint32_t total;
             const uint32_t loc = block_exclusive_scan(cnt, sm.wsum, total);
-            sm.local[tid] = loc;
+            {
+                uint32_t c = loc;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t v = (uint32_t)sm.hist[w][tid];
+                    sm.hist[w][tid] = (int)c;
+                    c += v;
+                }
+            }
             const uint32_t rr = sm.run[tid];
             sm.dst[tid] = rr - loc;
             sm.run[tid] = rr + cnt;
             __syncthreads();
-            // Walk the warp's runs in order; lane l fills rows l + 32 s.
-            uint32_t slot[kSlices];
-#pragma unroll
-            for (int u = 0; u < kSlices; ++u)
-                slot[u] = sm.local[u * 32 + lane] + (uint32_t)sm.hist[warp][u * 32 + lane];
-            for (uint32_t j = jA; j <= jB; ++j) {
-                const uint2 rec = sm.runs[j];
-                const uint32_t p = sm.pre[j];
-                const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(rec.y)) - p;
-                const uint32_t t0 = run_y0(rec.y) + lo, t1 = run_y0(rec.y) + hi;   // rows [t0, t1)
-#pragma unroll
-                for (int u = 0; u < kSlices; ++u) {   // the branches are uniform over the warp
-                    if (u * 32 >= (int)t1) break;
-                    if (u * 32 + 32 <= (int)t0) continue;
-                    const uint32_t ty = (uint32_t)(u * 32 + lane);
-                    if (ty >= t0 && ty < t1) {
-                        const uint32_t q = min(slot[u], (uint32_t)kSortChunk - 1u);
-                        sm.gid[q] = rec.x;
-                        sm.ty[q] = (uint8_t)ty;
-                        ++slot[u];
+            // Walk the warp's runs in order.  Lane l owns the rows ty = l mod
+            // 32 (their cursors are touched by no other lane): for each run,
+            // the lane on each of its rows puts the run's Gaussian at the
+            // warp's next slot of that row.  Runs are fetched 32 at a time,
+            // one per lane, and broadcast by shuffles.
+            int* cursor = sm.hist[warp];
+            for (uint32_t jb = jA; jb <= jB; jb += 32) {
+                const uint32_t j = jb + (uint32_t)lane;
+                uint32_t t0 = 0, t1 = 0, gid = 0;
+                if (j <= jB) {
+                    const uint2 rec = sm.runs[j];
+                    const uint32_t p = sm.pre[j];
+                    const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(rec.y)) - p;
+                    t0 = run_y0(rec.y) + lo;   // rows [t0, t1)
+                    t1 = run_y0(rec.y) + hi;
+                    gid = rec.x;
+                }
+                const int nb = (int)min(32u, jB - jb + 1u);
+                for (int i = 0; i < nb; ++i) {
+                    const uint32_t r0 = __shfl_sync(0xffffffffu, t0, i);
+                    const uint32_t r1 = __shfl_sync(0xffffffffu, t1, i);
+                    const uint32_t g = __shfl_sync(0xffffffffu, gid, i);
+                    for (uint32_t base = r0; base < r1; base += 32) {   // once for runs of <= 32 rows
+                        const uint32_t ty = base + (((uint32_t)lane - base) & 31u);   // = lane mod 32
+                        if (ty < r1) {
+                            const uint32_t q = min((uint32_t)cursor[ty], (uint32_t)kSortChunk - 1u);
+                            sm.gid[q] = g;
+                            sm.ty[q] = (uint8_t)ty;
+                            cursor[ty] = (int)(q + 1u);
+                        }
                     }
                 }
             }
             __syncthreads();
             // Coalesced write-out: each row's piece goes to consecutive addresses.
-            for (int s = tid; s < count; s += kSortThreads) {
-                const uint32_t g = sm.dst[sm.ty[s]] + (uint32_t)s;   // exact modulo 2^32
-                if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[s];
+            for (int q = tid; q < count; q += kSortThreads) {
+                const uint32_t g = sm.dst[sm.ty[q]] + (uint32_t)q;   // exact modulo 2^32
+                if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[q];
                 else atomicOr(status, kErrRange);
             }
             __syncthreads();
