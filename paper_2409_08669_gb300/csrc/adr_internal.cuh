@@ -225,7 +225,7 @@ void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32
                         int64_t capacity, uint2* ranges, cudaStream_t stream);
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
-                              int grid, cudaStream_t stream);
+                              int grid, int tiles_y, cudaStream_t stream);
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile

@@ -135,7 +135,7 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
               launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G2, stream));
         TIMED(ws, kKTileScatterRows, stream,
               launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
-                                       ws.status, G2, stream));
+                                       ws.status, G2, fs.cam.tiles_y, stream));
     }
     // Stage 5: every tile's [start, end) from its pair count.
     TIMED(ws, kKTileRanges, stream,

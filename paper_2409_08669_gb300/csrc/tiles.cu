@@ -39,8 +39,7 @@ namespace {
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxChunkGauss = kSortChunk + 1;          // every listed Gaussian has >= 1 run
 constexpr int kStageLen = (kMaxChunkGauss + 3) & ~3;    // keeps the arrays after it 16-byte aligned
-constexpr int kRunStage = 2048;                         // runs staged per pass-2 chunk
-constexpr int kRunsPerThread = kRunStage / kSortThreads;
+constexpr int kRunStage = 2048;                         // runs staged at a time in pass 2
 constexpr int kColSlots = 8;                            // tile-count columns a CTA keeps on chip
 
 // Column run record: x = Gaussian id, y = y0 | (h - 1) << 8 | tx << 16.
@@ -68,24 +67,14 @@ struct alignas(16) ColumnShared {
     uint32_t wsum[kWarps];
 };
 
-constexpr int kMaxWindows = kRunStage * 256 / kSortChunk + 2;   // 4096-pair windows per staging
-
 struct alignas(16) RowShared {
-    uint2 runs[kRunStage];                   // staged column runs
-    uint32_t pre[kRunStage + 4];             // exclusive prefix of their pair counts
-    uint32_t win_first[kMaxWindows];         // staged run holding each window's first pair
-    uint32_t gid[kSortChunk];                // the window's pairs grouped by ty
-    alignas(16) uint16_t map[kSortChunk];    // window slot -> staged run holding it
-    uint8_t ty[kSortChunk];                  // row of each slot of gid
-    int hist[kWarps][kRadix + 1];            // per-warp row counts, then the warp's row cursors
-    uint32_t run[kRadix];                    // next global position of each row
-    uint32_t dst[kRadix];                    // global position of window slot 0, per row
-    uint32_t wsum[kWarps];
+    uint32_t rows[kRunStage];                // staged runs: y0 | y1 << 16 (rows [y0, y1))
+    uint32_t gid[kRunStage];                 // their Gaussians
+    uint32_t pos[kRadix];                    // next global position of each tile row
 };
 static_assert(offsetof(ColumnShared, u) % 16 == 0, "staging must be 16-byte aligned");
 static_assert((3 * kStageLen * sizeof(uint32_t)) % 16 == 0, "map must be 16-byte aligned");
 constexpr size_t kColumnSmem = sizeof(ColumnShared);
-constexpr size_t kRowSmem = sizeof(RowShared);
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -474,160 +463,54 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 }
 
 // Expand the runs of this CTA's chunks into pairs and scatter their Gaussian
-// ids by ty.  Up to kRunStage runs are staged at a time; their pairs are cut
-// into windows of 4096.  In a window, warp w takes slots 512w .. 512w+511;
-// it counts its pairs per row (each run adds its row interval to a
-// difference array), the counts of the warps before it give its first slot
-// of every row, and it then walks its runs in order, lane l serving the rows
-// ty = l mod 32, putting each run's Gaussian at its next slot of each row the
-// run covers.  The window's pairs leave grouped by row, one contiguous piece
-// per row.
-__global__ void __launch_bounds__(kSortThreads, 3)
+// ids by tile row.  The runs are staged kRunStage at a time; then warp w takes
+// the rows ty = w, w + 8, ... below tiles_y, and for each row sweeps the staged
+// runs 32 at a time: the lanes whose run covers ty (ballot) write their
+// Gaussians to consecutive positions of the row, in run order.  Each row's
+// output is thus written front to back with coalesced stores, and no pair is
+// staged on chip.
+__global__ void __launch_bounds__(kSortThreads)
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
-               int grid, uint32_t* __restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    RowShared& sm = *reinterpret_cast<RowShared*>(smem_raw);
+               int grid, int tiles_y, uint32_t* __restrict__ status) {
+    __shared__ RowShared sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Span sp = cta_span(run_count(counters, capacity), grid);
     if (sp.c0 >= sp.c1) return;
     const int64_t n_pairs = min((int64_t)counters[kCntPairs], capacity);
-    sm.run[tid] = starts[(size_t)tid * grid + blockIdx.x];
+    sm.pos[tid] = starts[(size_t)tid * grid + blockIdx.x];
     const int64_t B = min((int64_t)sp.c1 * kSortChunk, sp.n);
+    const uint32_t lt = lanemask_lt();
     for (int64_t r = (int64_t)sp.c0 * kSortChunk; r < B; r += kRunStage) {
-        // Stage the runs and the exclusive prefix of their pair counts.
         const int avail = (int)min((int64_t)kRunStage, B - r);
-        uint32_t h[kRunsPerThread], hsum = 0;
-#pragma unroll
-        for (int u = 0; u < kRunsPerThread; ++u) {
-            const int j = tid * kRunsPerThread + u;
-            uint2 rec = make_uint2(0u, 0u);
-            if (j < avail) rec = runs[r + j];
-            sm.runs[j] = rec;
-            h[u] = j < avail ? run_h(rec.y) : 0u;
-            hsum += h[u];
+        __syncthreads();   // the previous staging is no longer read
+        for (int j = tid; j < kRunStage; j += kSortThreads) {
+            uint32_t rows = 0u, gid = 0u;   // rows [0, 0): covers nothing
+            if (j < avail) {
+                const uint2 rec = runs[r + j];
+                rows = run_y0(rec.y) | ((run_y0(rec.y) + run_h(rec.y)) << 16);
+                gid = rec.x;
+            }
+            sm.rows[j] = rows;
+            sm.gid[j] = gid;
         }
-        uint32_t T;
-        uint32_t pre = block_exclusive_scan(hsum, sm.wsum, T);
-#pragma unroll
-        for (int u = 0; u < kRunsPerThread; ++u) {
-            const int j = tid * kRunsPerThread + u;
-            sm.pre[j] = pre;
-            // the window starting inside this run (a run has at most 256 pairs)
-            const uint32_t w0 = (pre + kSortChunk - 1) / kSortChunk;
-            if (h[u] && w0 * kSortChunk < pre + h[u]) sm.win_first[w0] = (uint32_t)j;
-            pre += h[u];
-        }
-        if (tid == kSortThreads - 1) sm.pre[kRunStage] = pre;
         __syncthreads();
-        const int nwin = (int)((T + kSortChunk - 1) / kSortChunk);
-        for (int k = 0; k < nwin; ++k) {
-            const uint32_t P0 = (uint32_t)k * kSortChunk;
-            const int count = (int)min((uint32_t)kSortChunk, T - P0);
-            const uint32_t jfirst = sm.win_first[k];
-            const uint32_t jlast = k + 1 < nwin ? sm.win_first[k + 1] : (uint32_t)avail - 1u;
-            // Slot -> run map: mark where each run after the first starts.
-            uint32_t* map32 = reinterpret_cast<uint32_t*>(sm.map);
-            for (int x = tid; x < kSortChunk / 2; x += kSortThreads) map32[x] = 0u;
-            for (int d = lane; d <= kRadix; d += 32) sm.hist[warp][d] = 0;
-            __syncthreads();
-            if (tid == 0) sm.map[0] = (uint16_t)jfirst;
-            for (uint32_t j = jfirst + 1 + tid; j <= jlast; j += kSortThreads) {
-                const uint32_t slot = sm.pre[j] - P0;
-                if (slot < (uint32_t)count) sm.map[slot] = (uint16_t)j;
-            }
-            __syncthreads();
-            map_running_max(sm.map, sm.wsum);
-            // This warp's slots [S0, S1) (window coordinates) and runs [jA, jB].
-            const int S0 = warp * (kSortChunk / kWarps), S1 = min(S0 + kSortChunk / kWarps, count);
-            const bool any = S0 < S1;
-            const uint32_t jA = any ? sm.map[S0] : 1u, jB = any ? sm.map[S1 - 1] : 0u;
-            // Per-warp row counts.
-            for (uint32_t j = jA + lane; j <= jB; j += 32) {
-                const uint32_t y = sm.runs[j].y, p = sm.pre[j];
-                const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(y)) - p;
-                if (lo < hi) {
-                    atomicAdd(&sm.hist[warp][run_y0(y) + lo], 1);
-                    atomicAdd(&sm.hist[warp][run_y0(y) + hi], -1);
+        const int nblk = (avail + 31) >> 5;
+        for (int ty = warp; ty < tiles_y; ty += kWarps) {
+            uint32_t p = sm.pos[ty];
+            for (int blk = 0; blk < nblk; ++blk) {
+                const int j = blk * 32 + lane;
+                const uint32_t rows = sm.rows[j];
+                const bool cover = (rows & 0xFFFFu) <= (uint32_t)ty && (uint32_t)ty < (rows >> 16);
+                const uint32_t m = __ballot_sync(0xffffffffu, cover);
+                if (cover) {
+                    const uint32_t g = p + __popc(m & lt);
+                    if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[j];
+                    else atomicOr(status, kErrRange);
                 }
+                p += __popc(m);
             }
-            __syncwarp();
-            {   // inclusive prefix of the warp's difference array, 8 rows per lane
-                int v[kRadix / 32], t = 0;
-#pragma unroll
-                for (int u = 0; u < kRadix / 32; ++u) { v[u] = sm.hist[warp][lane * 8 + u]; t += v[u]; }
-                int x = t;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                int acc = x - t;
-#pragma unroll
-                for (int u = 0; u < kRadix / 32; ++u) { acc += v[u]; sm.hist[warp][lane * 8 + u] = acc; }
-            }
-            __syncthreads();
-            // Per row (thread = row): the window's count, its first slot, and
-            // each warp's first slot of the row (the cursors of the walk).
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) cnt += (uint32_t)sm.hist[w][tid];
-            uint32_t total;
-            const uint32_t loc = block_exclusive_scan(cnt, sm.wsum, total);
-            {
-                uint32_t c = loc;
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    const uint32_t v = (uint32_t)sm.hist[w][tid];
-                    sm.hist[w][tid] = (int)c;
-                    c += v;
-                }
-            }
-            const uint32_t rr = sm.run[tid];
-            sm.dst[tid] = rr - loc;
-            sm.run[tid] = rr + cnt;
-            __syncthreads();
-            // Walk the warp's runs in order.  Lane l owns the rows ty = l mod
-            // 32 (their cursors are touched by no other lane): for each run,
-            // the lane on each of its rows puts the run's Gaussian at the
-            // warp's next slot of that row.  Runs are fetched 32 at a time,
-            // one per lane, and broadcast by shuffles.
-            int* cursor = sm.hist[warp];
-            for (uint32_t jb = jA; jb <= jB; jb += 32) {
-                const uint32_t j = jb + (uint32_t)lane;
-                uint32_t t0 = 0, t1 = 0, gid = 0;
-                if (j <= jB) {
-                    const uint2 rec = sm.runs[j];
-                    const uint32_t p = sm.pre[j];
-                    const uint32_t lo = max(P0 + S0, p) - p, hi = min(P0 + S1, p + run_h(rec.y)) - p;
-                    t0 = run_y0(rec.y) + lo;   // rows [t0, t1)
-                    t1 = run_y0(rec.y) + hi;
-                    gid = rec.x;
-                }
-                const int nb = (int)min(32u, jB - jb + 1u);
-                for (int i = 0; i < nb; ++i) {
-                    const uint32_t r0 = __shfl_sync(0xffffffffu, t0, i);
-                    const uint32_t r1 = __shfl_sync(0xffffffffu, t1, i);
-                    const uint32_t g = __shfl_sync(0xffffffffu, gid, i);
-                    for (uint32_t base = r0; base < r1; base += 32) {   // once for runs of <= 32 rows
-                        const uint32_t ty = base + (((uint32_t)lane - base) & 31u);   // = lane mod 32
-                        if (ty < r1) {
-                            const uint32_t q = min((uint32_t)cursor[ty], (uint32_t)kSortChunk - 1u);
-                            sm.gid[q] = g;
-                            sm.ty[q] = (uint8_t)ty;
-                            cursor[ty] = (int)(q + 1u);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            // Coalesced write-out: each row's piece goes to consecutive addresses.
-            for (int q = tid; q < count; q += kSortThreads) {
-                const uint32_t g = sm.dst[sm.ty[q]] + (uint32_t)q;   // exact modulo 2^32
-                if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[q];
-                else atomicOr(status, kErrRange);
-            }
-            __syncthreads();
+            if (lane == 0) sm.pos[ty] = p;
         }
     }
 }
@@ -683,14 +566,10 @@ k_count_scan(uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals,
 
 int tile_scatter_blocks_per_sm() {
     cudaFuncSetAttribute(k_scatter_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColumnSmem);
-    cudaFuncSetAttribute(k_scatter_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
-    int b1 = 0, b2 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_scatter_columns, kSortThreads,
-                                                      kColumnSmem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_scatter_rows, kSortThreads,
-                                                      kRowSmem) != cudaSuccess)
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter_columns, kSortThreads,
+                                                      kColumnSmem) != cudaSuccess)
         return 1;
-    const int b = b1 < b2 ? b1 : b2;
     return b > 0 ? b : 1;
 }
 
@@ -719,9 +598,9 @@ void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32
 
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
-                              int grid, cudaStream_t stream) {
-    k_scatter_rows<<<grid, kSortThreads, kRowSmem, stream>>>(runs, counters, capacity, starts,
-                                                             gauss_out, grid, status);
+                              int grid, int tiles_y, cudaStream_t stream) {
+    k_scatter_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, starts, gauss_out,
+                                                      grid, tiles_y, status);
 }
 
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream) {
