@@ -67,9 +67,13 @@ struct alignas(16) ColumnShared {
     uint32_t wsum[kWarps];
 };
 
+constexpr int kBands = kWarps;               // horizontal bands of tile rows in pass 2
+
 struct alignas(16) RowShared {
     uint32_t rows[kRunStage];                // staged runs: y0 | y1 << 16 (rows [y0, y1))
     uint32_t gid[kRunStage];                 // their Gaussians
+    uint16_t band[kBands][kRunStage];        // staged runs meeting each band, in run order
+    uint32_t band_len[kBands];
     uint32_t pos[kRadix];                    // next global position of each tile row
 };
 static_assert(offsetof(ColumnShared, u) % 16 == 0, "staging must be 16-byte aligned");
@@ -463,12 +467,14 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 }
 
 // Expand the runs of this CTA's chunks into pairs and scatter their Gaussian
-// ids by tile row.  The runs are staged kRunStage at a time; then warp w takes
-// the rows ty = w, w + 8, ... below tiles_y, and for each row sweeps the staged
-// runs 32 at a time: the lanes whose run covers ty (ballot) write their
-// Gaussians to consecutive positions of the row, in run order.  Each row's
-// output is thus written front to back with coalesced stores, and no pair is
-// staged on chip.
+// ids by tile row.  The runs are staged kRunStage at a time and listed per
+// band of rows (the tile rows split into kBands bands; a run is listed in
+// every band it meets, in run order).  Warp w then takes the rows
+// ty = w, w + 8, ... below tiles_y, and for each row sweeps its band's list 32
+// runs at a time: the lanes whose run covers ty (ballot) write their Gaussians
+// to consecutive positions of the row, in run order.  Each row's output is
+// thus written front to back with coalesced stores, and no pair is staged on
+// chip.
 __global__ void __launch_bounds__(kSortThreads)
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
@@ -481,6 +487,7 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
     sm.pos[tid] = starts[(size_t)tid * grid + blockIdx.x];
     const int64_t B = min((int64_t)sp.c1 * kSortChunk, sp.n);
     const uint32_t lt = lanemask_lt();
+    const int band_h = (tiles_y + kBands - 1) / kBands;   // rows per band
     for (int64_t r = (int64_t)sp.c0 * kSortChunk; r < B; r += kRunStage) {
         const int avail = (int)min((int64_t)kRunStage, B - r);
         __syncthreads();   // the previous staging is no longer read
@@ -495,12 +502,31 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
             sm.gid[j] = gid;
         }
         __syncthreads();
+        // Warp w lists, in run order, the staged runs meeting band w of the rows.
         const int nblk = (avail + 31) >> 5;
-        for (int ty = warp; ty < tiles_y; ty += kWarps) {
-            uint32_t p = sm.pos[ty];
+        {
+            const uint32_t b0 = (uint32_t)(warp * band_h), b1 = min(b0 + (uint32_t)band_h, (uint32_t)tiles_y);
+            uint32_t n = 0;
             for (int blk = 0; blk < nblk; ++blk) {
                 const int j = blk * 32 + lane;
                 const uint32_t rows = sm.rows[j];
+                const bool meets = (rows & 0xFFFFu) < b1 && (rows >> 16) > b0;
+                const uint32_t m = __ballot_sync(0xffffffffu, meets);
+                if (meets) sm.band[warp][n + __popc(m & lt)] = (uint16_t)j;
+                n += __popc(m);
+            }
+            if (lane == 0) sm.band_len[warp] = n;
+        }
+        __syncthreads();
+        for (int ty = warp; ty < tiles_y; ty += kWarps) {
+            const int k = ty / band_h;
+            const uint32_t len = sm.band_len[k];
+            const uint16_t* list = sm.band[k];
+            uint32_t p = sm.pos[ty];
+            for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+                const uint32_t i = i0 + (uint32_t)lane;
+                const uint32_t j = i < len ? list[i] : 0u;
+                const uint32_t rows = i < len ? sm.rows[j] : 0u;
                 const bool cover = (rows & 0xFFFFu) <= (uint32_t)ty && (uint32_t)ty < (rows >> 16);
                 const uint32_t m = __ballot_sync(0xffffffffu, cover);
                 if (cover) {
