@@ -39,7 +39,7 @@ namespace {
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxChunkGauss = kSortChunk + 1;          // every listed Gaussian has >= 1 run
 constexpr int kStageLen = (kMaxChunkGauss + 3) & ~3;    // keeps the arrays after it 16-byte aligned
-constexpr int kRunStage = 2048;                         // runs staged at a time in pass 2
+constexpr int kRunStage = 1024;                         // runs staged at a time in pass 2
 constexpr int kColSlots = 8;                            // tile-count columns a CTA keeps on chip
 
 // Column run record: x = Gaussian id, y = y0 | (h - 1) << 8 | tx << 16.
@@ -67,7 +67,8 @@ struct alignas(16) ColumnShared {
     uint32_t wsum[kWarps];
 };
 
-constexpr int kBands = kWarps;               // horizontal bands of tile rows in pass 2
+constexpr int kBands = 16;                   // horizontal bands of tile rows in pass 2
+constexpr int kMaxBandRows = kRadix / kBands;   // rows per band at most (256 tile rows)
 
 struct alignas(16) RowShared {
     uint32_t rows[kRunStage];                // staged runs: y0 | y1 << 16 (rows [y0, y1))
@@ -469,12 +470,11 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 // Expand the runs of this CTA's chunks into pairs and scatter their Gaussian
 // ids by tile row.  The runs are staged kRunStage at a time and listed per
 // band of rows (the tile rows split into kBands bands; a run is listed in
-// every band it meets, in run order).  Warp w then takes the rows
-// ty = w, w + 8, ... below tiles_y, and for each row sweeps its band's list 32
-// runs at a time: the lanes whose run covers ty (ballot) write their Gaussians
-// to consecutive positions of the row, in run order.  Each row's output is
-// thus written front to back with coalesced stores, and no pair is staged on
-// chip.
+// every band it meets, in run order).  Warp w then takes bands w and w + 8
+// and sweeps each band's list 32 runs at a time: for every row ty of the band,
+// the lanes whose run covers ty (ballot) write their Gaussians to consecutive
+// positions of the row, in run order.  Each row's output is thus written front
+// to back with coalesced stores, and no pair is staged on chip.
 __global__ void __launch_bounds__(kSortThreads)
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
@@ -504,39 +504,54 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
         __syncthreads();
         // Warp w lists, in run order, the staged runs meeting band w of the rows.
         const int nblk = (avail + 31) >> 5;
-        {
-            const uint32_t b0 = (uint32_t)(warp * band_h), b1 = min(b0 + (uint32_t)band_h, (uint32_t)tiles_y);
+        for (int k = warp; k < kBands; k += kWarps) {
+            const uint32_t b0 = (uint32_t)(k * band_h), b1 = min(b0 + (uint32_t)band_h, (uint32_t)tiles_y);
             uint32_t n = 0;
             for (int blk = 0; blk < nblk; ++blk) {
                 const int j = blk * 32 + lane;
                 const uint32_t rows = sm.rows[j];
                 const bool meets = (rows & 0xFFFFu) < b1 && (rows >> 16) > b0;
                 const uint32_t m = __ballot_sync(0xffffffffu, meets);
-                if (meets) sm.band[warp][n + __popc(m & lt)] = (uint16_t)j;
+                if (meets) sm.band[k][n + __popc(m & lt)] = (uint16_t)j;
                 n += __popc(m);
             }
-            if (lane == 0) sm.band_len[warp] = n;
+            if (lane == 0) sm.band_len[k] = n;
         }
         __syncthreads();
-        for (int ty = warp; ty < tiles_y; ty += kWarps) {
-            const int k = ty / band_h;
+        // Warp w sweeps bands w, w + 8: each batch of 32 listed runs is tested
+        // against every row of the band.
+        for (int k = warp; k < kBands; k += kWarps) {
+            const int y0b = k * band_h, nr = min(band_h, tiles_y - y0b);
+            if (nr <= 0) continue;
             const uint32_t len = sm.band_len[k];
             const uint16_t* list = sm.band[k];
-            uint32_t p = sm.pos[ty];
+            uint32_t p[kMaxBandRows];
+#pragma unroll
+            for (int q = 0; q < kMaxBandRows; ++q) p[q] = q < nr ? sm.pos[y0b + q] : 0u;
             for (uint32_t i0 = 0; i0 < len; i0 += 32) {
                 const uint32_t i = i0 + (uint32_t)lane;
                 const uint32_t j = i < len ? list[i] : 0u;
-                const uint32_t rows = i < len ? sm.rows[j] : 0u;
-                const bool cover = (rows & 0xFFFFu) <= (uint32_t)ty && (uint32_t)ty < (rows >> 16);
-                const uint32_t m = __ballot_sync(0xffffffffu, cover);
-                if (cover) {
-                    const uint32_t g = p + __popc(m & lt);
-                    if ((int64_t)g < n_pairs) gauss_out[g] = sm.gid[j];
-                    else atomicOr(status, kErrRange);
+                const uint32_t rows = i < len ? sm.rows[j] : 0u;   // rows [0, 0): covers nothing
+                const uint32_t gid = sm.gid[j];
+#pragma unroll
+                for (int q = 0; q < kMaxBandRows; ++q) {
+                    if (q >= nr) break;
+                    const uint32_t ty = (uint32_t)(y0b + q);
+                    const bool cover = (rows & 0xFFFFu) <= ty && ty < (rows >> 16);
+                    const uint32_t m = __ballot_sync(0xffffffffu, cover);
+                    if (cover) {
+                        const uint32_t g = p[q] + __popc(m & lt);
+                        if ((int64_t)g < n_pairs) gauss_out[g] = gid;
+                        else atomicOr(status, kErrRange);
+                    }
+                    p[q] += __popc(m);
                 }
-                p += __popc(m);
             }
-            if (lane == 0) sm.pos[ty] = p;
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < kMaxBandRows; ++q)
+                    if (q < nr) sm.pos[y0b + q] = p[q];
+            }
         }
     }
 }
