@@ -75,6 +75,7 @@ struct alignas(16) RowShared {
     uint32_t gid[kRunStage];                 // their Gaussians
     uint16_t band[kBands][kRunStage];        // staged runs meeting each band, in run order
     uint32_t band_len[kBands];
+    uint32_t next_band;                      // next band to sweep
     uint32_t pos[kRadix];                    // next global position of each tile row
 };
 static_assert(offsetof(ColumnShared, u) % 16 == 0, "staging must be 16-byte aligned");
@@ -470,8 +471,8 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 // Expand the runs of this CTA's chunks into pairs and scatter their Gaussian
 // ids by tile row.  The runs are staged kRunStage at a time and listed per
 // band of rows (the tile rows split into kBands bands; a run is listed in
-// every band it meets, in run order).  Warp w then takes bands w and w + 8
-// and sweeps each band's list 32 runs at a time: for every row ty of the band,
+// every band it meets, in run order).  The warps then take the bands one by
+// one and sweep each band's list 32 runs at a time: for every row ty of the band,
 // the lanes whose run covers ty (ballot) write their Gaussians to consecutive
 // positions of the row, in run order.  Each row's output is thus written front
 // to back with coalesced stores, and no pair is staged on chip.
@@ -517,10 +518,14 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
             }
             if (lane == 0) sm.band_len[k] = n;
         }
+        if (tid == 0) sm.next_band = 0u;
         __syncthreads();
-        // Warp w sweeps bands w, w + 8: each batch of 32 listed runs is tested
-        // against every row of the band.
-        for (int k = warp; k < kBands; k += kWarps) {
+        // The warps take bands dynamically (their lists differ in length):
+        // each batch of 32 listed runs is tested against every row of the band.
+        for (int k = 0;;) {
+            if (lane == 0) k = (int)atomicAdd(&sm.next_band, 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= kBands) break;
             const int y0b = k * band_h, nr = min(band_h, tiles_y - y0b);
             if (nr <= 0) continue;
             const uint32_t len = sm.band_len[k];
