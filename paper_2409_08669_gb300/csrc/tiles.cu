@@ -39,7 +39,7 @@ namespace {
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kMaxChunkGauss = kSortChunk + 1;          // every listed Gaussian has >= 1 run
 constexpr int kStageLen = (kMaxChunkGauss + 3) & ~3;    // keeps the arrays after it 16-byte aligned
-constexpr int kRunStage = 1024;                         // runs staged at a time in pass 2
+constexpr int kRunStage = 512;                          // runs staged at a time in pass 2
 constexpr int kColSlots = 8;                            // tile-count columns a CTA keeps on chip
 
 // Column run record: x = Gaussian id, y = y0 | (h - 1) << 8 | tx << 16.
@@ -476,7 +476,7 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 // the lanes whose run covers ty (ballot) write their Gaussians to consecutive
 // positions of the row, in run order.  Each row's output is thus written front
 // to back with coalesced stores, and no pair is staged on chip.
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 8)   // 8 CTAs per SM: 32 registers, 22 KB shared
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
                int grid, int tiles_y, uint32_t* __restrict__ status) {
