@@ -246,8 +246,7 @@ def kernel_bytes(name, n, u, hw):
     P, V, C = u["pairs"], u["visible"], u["runs"]
     return {
         "preprocess": 44 * n + 192 * V + 96 * n,   # params (+SH of kept) in, records out
-        "depth_hist": 4 * n,
-        "depth_pass": 16 * n,                      # key + value in and out
+        "depth_pass": 20 * n,                      # count: key in; scatter: key + value in and out
         "scan_tiles": 12 * n + 16 * V,
         "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
         "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident

@@ -79,7 +79,7 @@ enum Counter : int {
     kCntVisible = 1,      // Gaussians with at least one tile (they sort first by depth)
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
     kCntRuns = 3,         // number of column runs C (sum of rectangle widths), saturating
-    kCntSortTicket0 = 4,  // chunk tickets of the depth-sort passes (4)
+    kCntSortTicket0 = 4,  // words 4-7: unused
     kCntPairs64 = 8,      // words 8-9: P as a 64-bit sum
     kCntSlots = 16
 };
@@ -87,7 +87,7 @@ enum Counter : int {
 // Optional per-launch timing with CUDA events recorded on the launching
 // stream (adr_profile_enable / adr_profile_read).
 enum KernelId : int {
-    kKPreprocess = 0, kKDepthHist, kKDepthPass, kKScanTiles, kKTileRanges, kKTileCountColumns,
+    kKPreprocess = 0, kKDepthPass, kKScanTiles, kKTileRanges, kKTileCountColumns,
     kKTileScatterColumns, kKTileCountRows, kKTileScatterRows, kKTileCountScan, kKRender,
     kKRenderBackward, kKPreprocessBackward, kKernelCount
 };
@@ -138,7 +138,7 @@ struct Workspace {
     uint32_t* d_stage = nullptr;           // [1] stage counter (see EpochRef)
 };
 
-// hist layout: 4 x 256 depth digits.
+// hist layout: 4 x 256 per-digit totals of the depth passes.
 constexpr int kHistWords = kMaxPasses * kRadix;
 
 // What one frame's stages hand to the next.
@@ -179,16 +179,12 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
                        uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
                        uint32_t* tiles, ushort4* rect, cudaStream_t stream);
 
-// Histogram of `passes` 8-bit digits of u32 keys.  hist must hold passes*256 zeroed u32.
-void launch_digit_hist(const uint32_t* keys, int64_t n, int shift0, int passes, uint32_t* hist,
-                       int grid, cudaStream_t stream);
-
-// Stable onesweep pass over u32 keys in memory: digit (key >> shift) &
-// (2^digit_bits - 1).  vals_in == nullptr means the values are 0..n-1.
-void launch_onesweep(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                     uint32_t* vals_out, int64_t n, int shift, int digit_bits,
-                     const uint32_t* hist, unsigned long long* lookback, EpochRef epoch,
-                     uint32_t* ticket, uint32_t* status, int grid, cudaStream_t stream);
+// One stable 8-bit pass of the depth sort (sort.cu): keys (>> shift) & 255;
+// vals_in == nullptr means the values are 0..n-1.  counts: kRadix x grid
+// words; totals: kRadix words, zeroed before.
+void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                       uint32_t* vals_out, int64_t n, int shift, uint32_t* counts, uint32_t* totals,
+                       uint32_t* status, int grid, cudaStream_t stream);
 
 // Inputs of the tile passes.
 struct PairSource {

@@ -7,7 +7,7 @@ namespace adr {
 
 const char* kernel_name(int id) {
     static const char* names[kKernelCount] = {
-        "preprocess", "depth_hist", "depth_pass", "scan_tiles", "tile_ranges",
+        "preprocess", "depth_pass", "scan_tiles", "tile_ranges",
         "tile_count_columns", "tile_scatter_columns", "tile_count_rows", "tile_scatter_rows",
         "tile_count_scan", "render", "render_backward", "preprocess_backward"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
@@ -79,16 +79,12 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                             ws.aux, ws.depth_key, ws.tiles, ws.rect, stream));
     // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
     // carry key 0xFFFFFFFF and end up behind the V that have tiles.
-    TIMED(ws, kKDepthHist, stream,
-          launch_digit_hist(ws.depth_key, n, 0, kMaxPasses, ws.hist, ws.sm_count * 4, stream));
     const uint32_t* kin = ws.depth_key;
     const uint32_t* vin = nullptr;
     for (int p = 0; p < kMaxPasses; ++p) {
-        const EpochRef ep{ws.d_stage, (uint32_t)p};
         TIMED(ws, kKDepthPass, stream,
-              launch_onesweep(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, 8,
-                              ws.hist + p * kRadix, ws.lookback, ep,
-                              ws.counters + kCntSortTicket0 + p, ws.status, ws.sort_grid, stream));
+              launch_depth_pass(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, ws.tcounts,
+                                ws.hist + p * kRadix, ws.status, ws.sort_grid, stream));
         kin = ws.gkeys[p & 1];
         vin = ws.gvals[p & 1];
     }
