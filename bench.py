@@ -245,9 +245,9 @@ def kernel_bytes(name, n, u, hw):
     stage has to move; see the design notes for the derivation)."""
     P, V, C = u["pairs"], u["visible"], u["runs"]
     return {
-        "preprocess": 44 * n + 192 * V + 96 * n,   # params (+SH of kept) in, records out
+        "preprocess": 44 * n + 192 * V + 104 * n,  # params (+SH of kept) in; records, key, box out
         "depth_pass": 20 * n,                      # count: key in; scatter: key + value in and out
-        "scan_tiles": 12 * n + 16 * V,
+        "scan_tiles": 8 * n,                       # boxes in depth order in, run offsets out
         "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
         "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident
         "tile_scatter_columns": 8 * C + 12 * V,    # column runs out; Gaussian staging in

@@ -134,7 +134,7 @@ void free_workspace(Workspace& w) {
         delete w.prof;
         w.prof = nullptr;
     }
-    void* ptrs[] = {w.rec, w.aux, w.depth_key, w.tiles, w.rect, w.offsets, w.sorted_box, w.gkeys[0],
+    void* ptrs[] = {w.rec, w.aux, w.depth_key, w.offsets, w.gbox, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
@@ -149,7 +149,7 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t pixels = (size_t)max_width * max_height;
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
     const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
-    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 4 + 16 + 36) + P * 12 +
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36) + P * 12 +
            (P / kSortChunk + 2) * 4 + tiles * 12 + pixels * 12 + lb +
            (size_t)kRadix * (kMaxTileGrid + 2) * 4 + 4096;
 }
@@ -184,9 +184,8 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     ALLOC(w.rec, N * kRecFloat4 * sizeof(float4));
     ALLOC(w.aux, N * kAuxFloat4 * sizeof(float4));
     ALLOC(w.depth_key, N * sizeof(uint32_t));
-    ALLOC(w.tiles, N * sizeof(uint32_t));
-    ALLOC(w.rect, N * sizeof(ushort4));
     ALLOC(w.offsets, N * sizeof(uint32_t));
+    ALLOC(w.gbox, N * sizeof(uint32_t));
     ALLOC(w.sorted_box, N * sizeof(uint32_t));
     for (int b = 0; b < 2; ++b) {
         ALLOC(w.gkeys[b], N * sizeof(uint32_t));
@@ -373,7 +372,7 @@ adr_status adr_read_gaussians(adr_ctx* c, float* geom, int32_t* rect, int32_t* t
     if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
     if (!c->have_frame) return fail(ADR_ERR_INVALID, "adr_read_gaussians before adr_preprocess");
     DeviceGuard guard(c->device);
-    launch_read_gaussians(c->ws.rec, c->ws.aux, c->ws.rect, c->ws.tiles, (int)c->fs.n, geom, rect,
+    launch_read_gaussians(c->ws.rec, c->ws.aux, c->ws.gbox, (int)c->fs.n, geom, rect,
                           tiles, (cudaStream_t)stream);
     return check_launch("adr_read_gaussians") == ADR_OK ? ok() : ADR_ERR_CUDA;
 }

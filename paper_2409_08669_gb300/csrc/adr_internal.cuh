@@ -110,10 +110,9 @@ struct Workspace {
     float4* rec = nullptr;                 // [max_n * kRecFloat4]
     float4* aux = nullptr;                 // [max_n * kAuxFloat4]
     uint32_t* depth_key = nullptr;         // [max_n]
-    uint32_t* tiles = nullptr;             // [max_n]
-    ushort4* rect = nullptr;               // [max_n]
     uint32_t* offsets = nullptr;           // [max_n]
-    uint32_t* sorted_box = nullptr;        // [max_n] packed tile rectangle per depth-order position
+    uint32_t* gbox = nullptr;              // [max_n] packed tile rectangle per Gaussian (all ones: none)
+    uint32_t* sorted_box = nullptr;        // [max_n] the same per depth-order position
     uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
     uint2* pruns = nullptr;                // [capacity] column runs grouped by tile column
@@ -177,14 +176,16 @@ void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
                        const float* opac, const float* sh, const FrameParams* fp,
                        uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
-                       uint32_t* tiles, ushort4* rect, cudaStream_t stream);
+                       uint32_t* gbox, cudaStream_t stream);
 
 // One stable 8-bit pass of the depth sort (sort.cu): keys (>> shift) & 255;
 // vals_in == nullptr means the values are 0..n-1.  counts: kRadix x grid
-// words; totals: kRadix words, zeroed before.
+// words; totals: kRadix words, zeroed before.  With pay_out, also writes
+// pay_out[i] = pay_in[vals_out[i]].
 void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                        uint32_t* vals_out, int64_t n, int shift, uint32_t* counts, uint32_t* totals,
-                       uint32_t* status, int grid, cudaStream_t stream);
+                       const uint32_t* pay_in, uint32_t* pay_out, uint32_t* status, int grid,
+                       cudaStream_t stream);
 
 // Inputs of the tile passes.
 struct PairSource {
@@ -227,13 +228,12 @@ void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
 // coordinates and extents fit 8 bits because images are at most 4096 pixels
 // per side).
-// Exclusive scan of the column-run counts (rectangle widths) of the
-// Gaussians in depth order, with decoupled lookback.  Also writes the packed
-// rectangle of each depth-order position with tiles (sorted_box), the run
-// total, visible count and pair total to counters (with the capacity flag),
-// and chunk_first[c] = position of the Gaussian holding run c * kSortChunk.
-void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
-                       int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
+// Exclusive scan of the column-run counts (rectangle widths) over the packed
+// rectangles in depth order (sorted_box, all ones = no tiles), with decoupled
+// lookback.  Also writes the run total, visible count and pair total to
+// counters (with the capacity flag), and chunk_first[c] = position of the
+// Gaussian holding run c * kSortChunk.
+void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, uint32_t* offsets,
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);
 
@@ -248,7 +248,7 @@ void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, c
                             const float* dl_dload, float* g2d, cudaStream_t stream);
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
                                 const float* opac, const float* sh, const FrameParams* fp,
-                                const uint32_t* tiles, const float4* aux,
+                                const uint32_t* gbox, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream);
 void launch_load_loss(const int32_t* load, int64_t hw, double* sums, float weight, float* dl_dload,
@@ -269,9 +269,8 @@ void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStre
 int onesweep_blocks_per_sm();
 int scan_blocks_per_sm();
 
-void launch_read_gaussians(const float4* rec, const float4* aux, const ushort4* rect,
-                           const uint32_t* tiles, int n, float* geom, int32_t* rect_out,
-                           int32_t* tiles_out, cudaStream_t stream);
+void launch_read_gaussians(const float4* rec, const float4* aux, const uint32_t* gbox, int n,
+                           float* geom, int32_t* rect_out, int32_t* tiles_out, cudaStream_t stream);
 
 // Workspace allocation with cudaMalloc (context and serving paths).
 adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_capacity,

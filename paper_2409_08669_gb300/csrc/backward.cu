@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128)
 k_preprocess_backward(int n, const float* __restrict__ means, const float* __restrict__ scales,
                       const float* __restrict__ rots, const float* __restrict__ opac,
                       const float* __restrict__ sh, const FrameParams* __restrict__ fp,
-                      const uint32_t* __restrict__ tiles, const float4* __restrict__ aux,
+                      const uint32_t* __restrict__ gbox, const float4* __restrict__ aux,
                       const float* __restrict__ g2d, float* __restrict__ g_means,
                       float* __restrict__ g_scales, float* __restrict__ g_rots,
                       float* __restrict__ g_opac, float* __restrict__ g_sh) {
@@ -200,7 +200,7 @@ k_preprocess_backward(int n, const float* __restrict__ means, const float* __res
     float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float go = 0.f;
     float* gsh = g_sh + (size_t)i * 48;
-    if (tiles[i] == 0) {
+    if (gbox[i] == 0xFFFFFFFFu) {   // no tiles
         for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
     } else {
         const float* G = g2d + (size_t)i * 9;
@@ -398,12 +398,12 @@ void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, c
 
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
                                 const float* opac, const float* sh, const FrameParams* fp,
-                                const uint32_t* tiles, const float4* aux,
+                                const uint32_t* gbox, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream) {
     if (n <= 0) return;
     k_preprocess_backward<<<(n + 127) / 128, 128, 0, stream>>>(n, means, scales, rots, opac, sh, fp,
-                                                               tiles, aux, g2d, g_means,
+                                                               gbox, aux, g2d, g_means,
                                                                g_scales, g_rots, g_opac, g_sh);
 }
 

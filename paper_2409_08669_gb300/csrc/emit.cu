@@ -9,8 +9,8 @@
 //     kernel after the scan) and the capacity check;
 //   * chunk_first[c] = depth-order position of the Gaussian that holds run
 //     c * 4096, so the tile sort can generate each chunk's runs on chip;
-//   * sorted_box[i] = the packed tile rectangle of depth-order position i.
-// Plus small helpers for the tile ranges.
+// It reads the packed rectangles in depth order, which the last depth-sort
+// pass carries along.  Plus small helpers for the tile ranges.
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -77,11 +77,10 @@ __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, 
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
-             const ushort4* __restrict__ rect, int64_t n, int64_t capacity,
-             uint32_t* __restrict__ offsets, uint32_t* __restrict__ sorted_box,
-             uint32_t* __restrict__ chunk_first, unsigned long long* __restrict__ lookback,
-             EpochRef eref, uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
+k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n, int64_t capacity,
+             uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
+             unsigned long long* __restrict__ lookback, EpochRef eref,
+             uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
     __shared__ uint32_t s_warp[kScanThreads / 32], s_pairs[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
@@ -95,27 +94,18 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
         const int64_t base = (int64_t)chunk * kScanChunk;
         if (base >= n) break;
         // Blocked arrangement: thread t owns items base + t*16 .. +15.
-        uint32_t w[kScanItems], box[kScanItems];
+        uint32_t w[kScanItems];
         uint32_t tsum = 0, psum = 0, nonzero = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + tid * kScanItems + k;
-            uint32_t t = 0;
-            w[k] = 0;
-            box[k] = 0;
-            if (i < n) {
-                const uint32_t g = order[i];
-                t = tiles[g];
-                if (t) {
-                    const ushort4 r = rect[g];
-                    w[k] = (uint32_t)(r.z - r.x);
-                    box[k] = (uint32_t)r.x | ((uint32_t)r.y << 8) | ((w[k] - 1u) << 16) |
-                             ((uint32_t)(r.w - r.y - 1) << 24);
-                }
-            }
+            const uint32_t box = i < n ? sorted_box[i] : 0xFFFFFFFFu;   // all ones: no tiles
+            const bool has = box != 0xFFFFFFFFu;
+            w[k] = has ? ((box >> 16) & 0xFFu) + 1u : 0u;
+            const uint32_t t = has ? w[k] * ((box >> 24) + 1u) : 0u;
             tsum += w[k];   // <= 16 * 256 per thread
             psum += t;      // <= 16 * 2^16 per thread
-            nonzero += t != 0;
+            nonzero += has;
         }
         // Block exclusive scan of the thread run sums, block sum of the pairs.
         uint32_t x = tsum;
@@ -159,7 +149,6 @@ k_scan_tiles(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ti
                 const uint64_t c_max = ((uint64_t)capacity - 1) / kSortChunk;
                 if (c_hi > c_max) c_hi = c_max;
                 for (uint64_t c = c_lo; c <= c_hi; ++c) chunk_first[c] = (uint32_t)i;
-                sorted_box[i] = box[k];
             }
             run = sat_add(run, t);
         }
@@ -199,9 +188,8 @@ k_pair_keys(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorte
 
 __global__ void __launch_bounds__(256)
 k_read_gaussians(const float4* __restrict__ rec, const float4* __restrict__ aux,
-                 const ushort4* __restrict__ rect, const uint32_t* __restrict__ tiles, int n,
-                 float* __restrict__ geom, int32_t* __restrict__ rect_out,
-                 int32_t* __restrict__ tiles_out) {
+                 const uint32_t* __restrict__ gbox, int n, float* __restrict__ geom,
+                 int32_t* __restrict__ rect_out, int32_t* __restrict__ tiles_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 r0 = rec[3 * i + 0], r2 = rec[3 * i + 2];
@@ -211,12 +199,15 @@ k_read_gaussians(const float4* __restrict__ rec, const float4* __restrict__ aux,
         o[0] = r0.x; o[1] = r0.y; o[2] = a0.x; o[3] = a0.y; o[4] = a0.z; o[5] = a0.w;
         o[6] = a1.x; o[7] = a1.y; o[8] = r2.x; o[9] = r2.y; o[10] = r2.z; o[11] = a1.z;
     }
+    const uint32_t box = gbox[i];
+    const bool has = box != 0xFFFFFFFFu;
+    const int32_t x0 = has ? (int32_t)(box & 0xFFu) : 0, y0 = has ? (int32_t)((box >> 8) & 0xFFu) : 0;
+    const int32_t w = has ? (int32_t)((box >> 16) & 0xFFu) + 1 : 0, h = has ? (int32_t)(box >> 24) + 1 : 0;
     if (rect_out) {
-        const ushort4 r = rect[i];
-        rect_out[4 * i + 0] = r.x; rect_out[4 * i + 1] = r.y;
-        rect_out[4 * i + 2] = r.z; rect_out[4 * i + 3] = r.w;
+        rect_out[4 * i + 0] = x0; rect_out[4 * i + 1] = y0;
+        rect_out[4 * i + 2] = x0 + w; rect_out[4 * i + 3] = y0 + h;
     }
-    if (tiles_out) tiles_out[i] = (int32_t)tiles[i];
+    if (tiles_out) tiles_out[i] = w * h;
 }
 
 }  // namespace
@@ -228,14 +219,12 @@ int scan_blocks_per_sm() {
     return b > 0 ? b : 1;
 }
 
-void launch_scan_tiles(const uint32_t* order, const uint32_t* tiles, const ushort4* rect,
-                       int64_t n, int64_t capacity, uint32_t* offsets, uint32_t* sorted_box,
+void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, uint32_t* offsets,
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream) {
     if (n > 0)
-        k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(order, tiles, rect, n, capacity, offsets,
-                                                        sorted_box, chunk_first, lookback, epoch,
-                                                        counters, status);
+        k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(sorted_box, n, capacity, offsets, chunk_first,
+                                                        lookback, epoch, counters, status);
     k_finish_pairs<<<1, 1, 0, stream>>>(counters, capacity, status);
 }
 
@@ -252,12 +241,11 @@ void launch_pair_keys(const uint2* ranges, int num_tiles, const uint32_t* sorted
                                                keys_out, vals_out);
 }
 
-void launch_read_gaussians(const float4* rec, const float4* aux, const ushort4* rect,
-                           const uint32_t* tiles, int n, float* geom, int32_t* rect_out,
-                           int32_t* tiles_out, cudaStream_t stream) {
+void launch_read_gaussians(const float4* rec, const float4* aux, const uint32_t* gbox, int n,
+                           float* geom, int32_t* rect_out, int32_t* tiles_out, cudaStream_t stream) {
     if (n <= 0) return;
-    k_read_gaussians<<<(n + 255) / 256, 256, 0, stream>>>(rec, aux, rect, tiles, n, geom,
-                                                          rect_out, tiles_out);
+    k_read_gaussians<<<(n + 255) / 256, 256, 0, stream>>>(rec, aux, gbox, n, geom, rect_out,
+                                                          tiles_out);
 }
 
 }  // namespace adr

@@ -36,10 +36,9 @@ constexpr size_t kPixels = (size_t)kNaMaxWidth * kNaMaxHeight;
 constexpr size_t kOffRec = 0;
 constexpr size_t kOffAux = align256(kOffRec + kNaMaxGaussians * kRecFloat4 * 16);
 constexpr size_t kOffDepth = align256(kOffAux + kNaMaxGaussians * kAuxFloat4 * 16);
-constexpr size_t kOffTiles = align256(kOffDepth + kNaMaxGaussians * 4);
-constexpr size_t kOffRect = align256(kOffTiles + kNaMaxGaussians * 4);
-constexpr size_t kOffOffsets = align256(kOffRect + kNaMaxGaussians * 8);
-constexpr size_t kOffSortedBox = align256(kOffOffsets + kNaMaxGaussians * 4);
+constexpr size_t kOffOffsets = align256(kOffDepth + kNaMaxGaussians * 4);
+constexpr size_t kOffGBox = align256(kOffOffsets + kNaMaxGaussians * 4);
+constexpr size_t kOffSortedBox = align256(kOffGBox + kNaMaxGaussians * 4);
 constexpr size_t kOffGKeys = align256(kOffSortedBox + kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffPRuns = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
@@ -101,9 +100,8 @@ adr_status setup(int dev, DeviceState*& out) {
         w.rec = reinterpret_cast<float4*>(b + kOffRec);
         w.aux = reinterpret_cast<float4*>(b + kOffAux);
         w.depth_key = reinterpret_cast<uint32_t*>(b + kOffDepth);
-        w.tiles = reinterpret_cast<uint32_t*>(b + kOffTiles);
-        w.rect = reinterpret_cast<ushort4*>(b + kOffRect);
         w.offsets = reinterpret_cast<uint32_t*>(b + kOffOffsets);
+        w.gbox = reinterpret_cast<uint32_t*>(b + kOffGBox);
         w.sorted_box = reinterpret_cast<uint32_t*>(b + kOffSortedBox);
         for (int k = 0; k < 2; ++k) {
             w.gkeys[k] = reinterpret_cast<uint32_t*>(b + kOffGKeys) + k * kNaMaxGaussians;

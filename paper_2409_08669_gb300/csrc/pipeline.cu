@@ -76,7 +76,7 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     // Stage 1: per-Gaussian projection, covariance, colour and early cull.
     TIMED(ws, kKPreprocess, stream,
           launch_preprocess((int)n, means, scales, rots, opac, sh, ws.d_fp, ws.d_stage, ws.rec,
-                            ws.aux, ws.depth_key, ws.tiles, ws.rect, stream));
+                            ws.aux, ws.depth_key, ws.gbox, stream));
     // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
     // carry key 0xFFFFFFFF and end up behind the V that have tiles.
     const uint32_t* kin = ws.depth_key;
@@ -84,7 +84,9 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     for (int p = 0; p < kMaxPasses; ++p) {
         TIMED(ws, kKDepthPass, stream,
               launch_depth_pass(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, ws.tcounts,
-                                ws.hist + p * kRadix, ws.status, ws.sort_grid, stream));
+                                ws.hist + p * kRadix, p + 1 == kMaxPasses ? ws.gbox : nullptr,
+                                p + 1 == kMaxPasses ? ws.sorted_box : nullptr, ws.status,
+                                ws.sort_grid, stream));
         kin = ws.gkeys[p & 1];
         vin = ws.gvals[p & 1];
     }
@@ -92,9 +94,8 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
     const EpochRef ep{ws.d_stage, (uint32_t)kMaxPasses};
     TIMED(ws, kKScanTiles, stream,
-          launch_scan_tiles(fs.order, ws.tiles, ws.rect, n, ws.capacity, ws.offsets,
-                            ws.sorted_box, ws.chunk_first, ws.lookback, ep, ws.counters,
-                            ws.status, ws.scan_grid, stream));
+          launch_scan_tiles(ws.sorted_box, n, ws.capacity, ws.offsets, ws.chunk_first, ws.lookback,
+                            ep, ws.counters, ws.status, ws.scan_grid, stream));
 }
 
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
@@ -157,7 +158,7 @@ void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* me
           launch_render_backward(ws.ranges, fs.sorted_gauss, ws.rec, ws.aux, ws.d_fp, fs.num_tiles,
                                  ws.last, ws.tfin, dl_dimg, dl_dload, ws.g2d, stream));
     TIMED(ws, kKPreprocessBackward, stream,
-          launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, ws.d_fp, ws.tiles,
+          launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, ws.d_fp, ws.gbox,
                                      ws.aux, ws.g2d, g_means, g_scales, g_rots, g_opac, g_sh,
                                      stream));
 }

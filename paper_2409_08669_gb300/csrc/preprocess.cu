@@ -144,7 +144,7 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
              const float* __restrict__ sh, const FrameParams* __restrict__ fp,
              uint32_t* __restrict__ stage, float4* __restrict__ rec,
              float4* __restrict__ aux, uint32_t* __restrict__ depth_key,
-             uint32_t* __restrict__ tiles, ushort4* __restrict__ rect) {
+             uint32_t* __restrict__ gbox) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) atomicAdd(stage, 1u);   // new lookback tag for this call's passes
     if (i >= n) return;
@@ -272,8 +272,10 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
     aux[2 * i + 0] = a0;
     aux[2 * i + 1] = a1;
     depth_key[i] = key;
-    tiles[i] = ntiles;
-    rect[i] = rc;
+    // packed rectangle x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24, all ones if no tiles
+    gbox[i] = ntiles ? (uint32_t)rc.x | ((uint32_t)rc.y << 8) | ((uint32_t)(rc.z - rc.x - 1) << 16) |
+                           ((uint32_t)(rc.w - rc.y - 1) << 24)
+                     : 0xFFFFFFFFu;
 }
 
 }  // namespace
@@ -281,11 +283,11 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
                        const float* opac, const float* sh, const FrameParams* fp,
                        uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
-                       uint32_t* tiles, ushort4* rect, cudaStream_t stream) {
+                       uint32_t* gbox, cudaStream_t stream) {
     if (n <= 0) return;
     const int threads = 256;
     k_preprocess<<<(n + threads - 1) / threads, threads, 0, stream>>>(
-        n, means, scales, rots, opac, sh, fp, stage, rec, aux, depth_key, tiles, rect);
+        n, means, scales, rots, opac, sh, fp, stage, rec, aux, depth_key, gbox);
 }
 
 }  // namespace adr

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kSortThreads, 3)
 k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
                 int shift, const uint32_t* __restrict__ starts, int grid,
+                const uint32_t* __restrict__ pay_in, uint32_t* __restrict__ pay_out,
                 uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortShared& sm = *reinterpret_cast<SortShared*>(smem_raw);
@@ -155,8 +156,10 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             const uint32_t k = sm.keys[s];
             const uint32_t g = sm.dst[(k >> shift) & 0xFFu] + (uint32_t)s;   // exact modulo 2^32
             if ((int64_t)g >= n) { atomicOr(status, kErrRange); continue; }
+            const uint32_t v = sm.vals[s];
             keys_out[g] = k;
-            vals_out[g] = sm.vals[s];
+            vals_out[g] = v;
+            if (pay_out) pay_out[g] = pay_in[v];   // the value's payload, in sorted order
         }
         __syncthreads();
     }
@@ -176,12 +179,14 @@ int onesweep_blocks_per_sm() {
 
 void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                        uint32_t* vals_out, int64_t n, int shift, uint32_t* counts, uint32_t* totals,
-                       uint32_t* status, int grid, cudaStream_t stream) {
+                       const uint32_t* pay_in, uint32_t* pay_out, uint32_t* status, int grid,
+                       cudaStream_t stream) {
     if (n <= 0) return;
     k_digit_counts<<<grid, kSortThreads, 0, stream>>>(keys_in, n, shift, grid, counts, totals);
     launch_tile_count_scan(counts, totals, grid, stream);
     k_digit_scatter<<<grid, kSortThreads, kSortSmem, stream>>>(keys_in, vals_in, keys_out, vals_out, n,
-                                                              shift, counts, grid, status);
+                                                              shift, counts, grid, pay_in, pay_out,
+                                                              status);
 }
 
 }  // namespace adr
