@@ -157,12 +157,25 @@ def max_over_ranks(pg, value):
     return float(t.item())
 
 
+def deal_cameras(cams, rank):
+    """Replica `rank` starts its camera cycle at camera `rank` (replicas render
+    different frames of the same orbit)."""
+    k = rank % len(cams)
+    return cams[k:] + cams[:k]
+
+
+def aggregate_fps(pg, local_seconds, steps, world):
+    """Whole-job frames/s: the frames of all replicas over the slowest
+    replica's time (max over ranks)."""
+    t = max_over_ranks(pg, local_seconds)
+    return steps * world / t, t
+
+
 def build_workload(rank=0):
     kind = WORKLOADS[WORKLOAD][0]
     scene = S.heavy_scene(n=N_GAUSS, seed=2) if kind == "heavy" else S.cluster_scene(n=N_GAUSS, seed=1)
     cams = S.orbit_cameras(N_CAMERAS, radius=4.0, width=WIDTH, height=HEIGHT)
-    cams = cams[rank % N_CAMERAS:] + cams[:rank % N_CAMERAS]
-    return scene, cams
+    return scene, deal_cameras(cams, rank)
 
 
 # ---------------------------------------------------------------------------
@@ -450,19 +463,19 @@ def run_ours(args):
         raise SystemExit(f"device status {status} after the timed region")
     if args.quick:
         rast.close()
+        fps, _ = aggregate_fps(pg, t_adr, args.steps, world)
         if rank == 0:
-            print(json.dumps({"workload": WORKLOAD, "fps": args.steps * world / t_adr,
+            print(json.dumps({"workload": WORKLOAD, "fps": fps,
                               "stages_ms": {k: statistics.mean(v) for k, v in stages.items()}}))
         return
     t_plain, stages_plain, _ = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
                                          stream, pg)
     t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
                                with_stages=False)
-    t_adr = max_over_ranks(pg, t_adr)
+    fps, t_adr = aggregate_fps(pg, t_adr, args.steps, world)
     t_plain = max_over_ranks(pg, t_plain)
     t_circle = max_over_ranks(pg, t_circle)
     frames = args.steps * world
-    fps = frames / t_adr
 
     # Units of work for the roofline (untimed, on the first cameras of the timed cycle).
     nu = min(args.steps, 5)
@@ -532,6 +545,10 @@ def run_ours(args):
                             "plain": statistics.mean(u["pairs"] for u in units_plain)},
         "evals_per_frame": {"adr_aabb": u_mean["evals"],
                             "plain": statistics.mean(u["evals"] for u in units_plain)},
+        "culled_pair_fraction": 1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain),
+        "sort_mpairs_per_s": {"adr_aabb": u_mean["pairs"] / stage_ms["sort_ranges"] / 1e3,
+                              "plain": statistics.mean(u["pairs"] for u in units_plain)
+                              / stage_ms_plain["sort_ranges"] / 1e3},
         "roofline": roofline,
         "kernels": ktable,
         "render_roofline": {"alu": {"achieved": render_alu, "peak": alu_peak,
