@@ -57,10 +57,12 @@ def select_workload(name):
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
-# DRAM bytes (read + write) per Gaussian-tile pair of the tile-sort kernels
-# from an ncu capture (scaled to a launch by the measured P); empty until the
-# current kernels have been captured.
-TRAFFIC_BYTES_PER_PAIR = {}
+# DRAM bytes (read + write) per Gaussian-tile pair of the dominant kernel from
+# a one-pass ncu capture of one launch at the heavy 3M-Gaussian 1080p frame
+# (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md: 128.34 + 576.92 MB),
+# divided by that workload's mean P (1.5958e8) and scaled to a launch by the
+# measured P.
+TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 
 def peaks():
@@ -269,6 +271,32 @@ def kernel_bytes(name, n, u, hw):
         "tile_ranges": 12 * (hw // 256),           # tile counts in, ranges out
         "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
     }[name]
+
+
+def alpha_low_sweep(rast, params, cams, stream, pg, steps, warmup):
+    """Raising the splatting-opacity threshold (the paper's remark that a
+    higher alpha_low speeds rendering up): AdR-AABB frames/s at 1, 2 and 4 /
+    255 (cull and skip both use it) and the largest pixel change against
+    1/255 on three cameras."""
+    import torch
+    base = S.Settings(mode=S.MODE_AABB)
+    ref = []
+    for k in range(3):
+        img, _, _ = rast.forward(params, cams[k], base, stream=stream, want_aux=False)
+        torch.cuda.synchronize()
+        ref.append(img.clone())
+    out = []
+    for num in (1, 2, 4):
+        st = S.Settings(mode=S.MODE_AABB, alpha_low=float(np.float32(num / 255.0)))
+        t, _, _ = time_mode(rast, params, cams, st, steps, warmup, stream, pg, with_stages=False)
+        diff = 0.0
+        for k in range(3):
+            img, _, _ = rast.forward(params, cams[k], st, stream=stream, want_aux=False)
+            torch.cuda.synchronize()
+            diff = max(diff, float((img - ref[k]).abs().max()))
+        out.append({"alpha_low": f"{num}/255", "fps": steps / max_over_ranks(pg, t),
+                    "pairs": rast.num_pairs(), "max_abs_pixel_change_vs_1_255": diff})
+    return out
 
 
 def train_step_rate(local, steps=20, warmup=5):
@@ -546,9 +574,9 @@ def run_ours(args):
         "evals_per_frame": {"adr_aabb": u_mean["evals"],
                             "plain": statistics.mean(u["evals"] for u in units_plain)},
         "culled_pair_fraction": 1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain),
-        "sort_mpairs_per_s": {"adr_aabb": u_mean["pairs"] / stage_ms["sort_ranges"] / 1e3,
+        "sort_gpairs_per_s": {"adr_aabb": u_mean["pairs"] / stage_ms["sort_ranges"] / 1e6,
                               "plain": statistics.mean(u["pairs"] for u in units_plain)
-                              / stage_ms_plain["sort_ranges"] / 1e3},
+                              / stage_ms_plain["sort_ranges"] / 1e6},
         "roofline": roofline,
         "kernels": ktable,
         "render_roofline": {"alu": {"achieved": render_alu, "peak": alu_peak,
@@ -562,6 +590,8 @@ def run_ours(args):
         "gpu_launches": sum(v["launches"] for v in ktable.values()),
         "clocks": clocks,
     }
+    result["alpha_low_sweep"] = alpha_low_sweep(rast, params, cams, stream, pg, min(args.steps, 100),
+                                                args.warmup)
     rast.close()
     del params
     if not args.no_train:
