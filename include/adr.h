@@ -73,16 +73,32 @@ typedef struct adr_camera {
     int32_t width, height;
 } adr_camera;
 
+/* Tile-rectangle rule of Preprocess, for the half-widths (r_x, r_y) the
+ * mode chose around the pixel centre (px, py).
+ *   ADR_RECT_PIXEL : the tiles holding a pixel centre x in
+ *                    [ceil(px - r_x), floor(px + r_x)] clipped to the image
+ *                    (likewise y).  Lossless: no pixel within the half-widths
+ *                    misses the Gaussian.  The default.
+ *   ADR_RECT_3DGS  : the original 3DGS rasterizer's rounding, for comparison
+ *                    with renders of that rasterizer: R = ceil(r_x), tiles
+ *                    [floor((px - R)/16), floor((px + R + 15)/16)) clamped to
+ *                    the tile grid (likewise y).  Not lossless: when
+ *                    px + R lies in [16k, 16k+1) the tile k is dropped
+ *                    although its pixel 16k is within the radius. */
+typedef enum adr_rect_rule { ADR_RECT_PIXEL = 0, ADR_RECT_3DGS = 1 } adr_rect_rule;
+
 /* Render settings.  alpha_low: minimum splatting opacity (paper: 1/255,
  * Sec. 5.1.2); t_min: blending stops before a Gaussian that would take the
  * transmittance below it; lowpass: added to the diagonal of Sigma';
  * jac_clamp: the projection Jacobian uses x/z, y/z clamped to
- * +-jac_clamp*tan(fov/2); bg: background colour; sh_degree: 0..3. */
+ * +-jac_clamp*tan(fov/2); bg: background colour; sh_degree: 0..3;
+ * rect_rule: an adr_rect_rule. */
 typedef struct adr_settings {
     int32_t mode;
     float alpha_low, t_min, lowpass, jac_clamp;
     float bg[3];
     int32_t sh_degree;
+    int32_t rect_rule;
 } adr_settings;
 
 typedef struct adr_ctx adr_ctx;

@@ -51,7 +51,7 @@ def _load():
             P = ctypes.c_void_p
             i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             lib.orc_preprocess.restype = i64
-            lib.orc_preprocess.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, dbl, dbl, dbl,
+            lib.orc_preprocess.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, i32, dbl, dbl, dbl,
                                            dbl, P, P, P, P, P, P]
             lib.orc_emit_pairs.restype = i64
             lib.orc_emit_pairs.argtypes = [i64, P, P, P, i32, P, P, i64]
@@ -102,7 +102,8 @@ def preprocess(scene, camera, settings, tol_rel: float = 1e-6):
     flags = np.zeros(n, np.uint8)
     total = lib.orc_preprocess(n, _p(means), _p(scales), _p(rots), _p(opac), _p(sh),
                                settings.sh_degree, _p(cam), camera.width, camera.height,
-                               settings.mode, settings.alpha_low, settings.lowpass,
+                               settings.mode, settings.rect_rule,
+                               settings.alpha_low, settings.lowpass,
                                settings.jac_clamp, tol_rel, _p(geom), _p(depth), _p(rect),
                                _p(tiles), _p(rgb), _p(flags))
     return dict(geom=geom, depth=depth, rect=rect, tiles=tiles, rgb=rgb, flags=flags,

@@ -28,7 +28,11 @@
  *     clamped to +-jac_clamp*tan(fov/2);
  *   - a pixel has its centre at integer coordinates;
  *   - tile rectangle: x in [ceil(px - r_x), floor(px + r_x)] clipped to the
- *     image, tiles floor(x/16); the same rule for every mode;
+ *     image, tiles floor(x/16); the same rule for every mode.  A second,
+ *     compatibility rule reproduces the original 3DGS rasterizer's rounding
+ *     (integer radius R = ceil(r_x), tiles [floor((px - R)/16),
+ *     floor((px + R + 15)/16)) clamped to the tile grid); it can drop the
+ *     tile of a pixel within the radius, so it is not lossless;
  *   - the adaptive modes emit no pair when sigma < alpha_low (Eq. 7 has no
  *     real radius there); the plain mode keeps such Gaussians, as 3DGS does;
  *   - alpha = min(0.99, sigma*exp(-q/2)); a pair is skipped iff alpha <
@@ -49,6 +53,7 @@
 #endif
 
 enum { ORC_PLAIN = 0, ORC_CIRCLE = 1, ORC_AABB = 2 };
+enum { ORC_RECT_PIXEL = 0, ORC_RECT_3DGS = 1 };
 
 /* Per-Gaussian record written by orc_preprocess (doubles, stride ORC_GEOM). */
 enum {
@@ -180,10 +185,28 @@ static int pixel_interval(double c, double r, int size, long *lo, long *hi)
     return 1;
 }
 
-/* Tile interval [t0, t1) of the pixel interval. */
-static int tile_interval(double c, double r, int size, long *t0, long *t1)
+/* Tile interval [t0, t1) of the 3DGS rounding: the square of integer
+ * half-width R = ceil(r) around c, its low edge rounded down to a tile and its
+ * high edge rounded up (c + R + 15, then down), both clamped to [0, tiles]. */
+static int tile_interval_3dgs(double c, double r, int size, long *t0, long *t1)
+{
+    double tiles = (double)((size + ORC_TILE - 1) / ORC_TILE);
+    double R = ceil(r);
+    double a = floor((c - R) / ORC_TILE), b = floor((c + R + (ORC_TILE - 1)) / ORC_TILE);
+    if (!(a == a) || !(b == b)) return 0;
+    a = fmin(fmax(a, 0.0), tiles);
+    b = fmin(fmax(b, 0.0), tiles);
+    if (!(a < b)) return 0;
+    *t0 = (long)a;
+    *t1 = (long)b;
+    return 1;
+}
+
+/* Tile interval [t0, t1) of the pixel interval (or of the 3DGS rounding). */
+static int tile_interval(double c, double r, int size, long *t0, long *t1, int rule)
 {
     long lo, hi;
+    if (rule == ORC_RECT_3DGS) return tile_interval_3dgs(c, r, size, t0, t1);
     if (!pixel_interval(c, r, size, &lo, &hi)) return 0;
     *t0 = lo / ORC_TILE;
     *t1 = hi / ORC_TILE + 1;
@@ -191,19 +214,19 @@ static int tile_interval(double c, double r, int size, long *t0, long *t1)
 }
 
 /* Does the tile interval change when the edge values move by +-tol? */
-static int interval_fragile(double c, double r, int size, double tol_rel)
+static int interval_fragile(double c, double r, int size, double tol_rel, int rule)
 {
     double lo_v = c - r, hi_v = c + r;
     double dl = tol_rel * fmax(1.0, fabs(lo_v)), dh = tol_rel * fmax(1.0, fabs(hi_v));
     long a0, a1, b0, b1;
-    int e0 = tile_interval(c, r, size, &a0, &a1);
+    int e0 = tile_interval(c, r, size, &a0, &a1, rule);
     /* shrink and grow each edge independently */
     double cs[4][2] = {
         {c + dl / 2, r - dl / 2}, {c - dl / 2, r + dl / 2},   /* lo edge +dl, -dl */
         {c - dh / 2, r - dh / 2}, {c + dh / 2, r + dh / 2},   /* hi edge -dh, +dh */
     };
     for (int k = 0; k < 4; ++k) {
-        int e1 = tile_interval(cs[k][0], cs[k][1], size, &b0, &b1);
+        int e1 = tile_interval(cs[k][0], cs[k][1], size, &b0, &b1, rule);
         if (e1 != e0) return 1;
         if (e0 && (a0 != b0 || a1 != b1)) return 1;
     }
@@ -229,7 +252,7 @@ static int interval_fragile(double c, double r, int size, double tol_rel)
 int64_t orc_preprocess(int64_t n, const double *means, const double *scales, const double *rots,
                        const double *opac, const double *sh, int sh_degree,
                        const float *cam, int width, int height,
-                       int mode, double alpha_low, double lowpass, double jac_clamp,
+                       int mode, int rect_rule, double alpha_low, double lowpass, double jac_clamp,
                        double tol_rel,
                        double *geom, float *depth, int32_t *rect, int64_t *tiles,
                        double *rgb, uint8_t *flags)
@@ -352,9 +375,10 @@ int64_t orc_preprocess(int64_t n, const double *means, const double *scales, con
         g[G_RX] = rx; g[G_RY] = ry;
 
         long tx0, tx1, ty0, ty1;
-        int okx = tile_interval(px, rx, width, &tx0, &tx1);
-        int oky = tile_interval(py, ry, height, &ty0, &ty1);
-        if (interval_fragile(px, rx, width, tol_rel) || interval_fragile(py, ry, height, tol_rel))
+        int okx = tile_interval(px, rx, width, &tx0, &tx1, rect_rule);
+        int oky = tile_interval(py, ry, height, &ty0, &ty1, rect_rule);
+        if (interval_fragile(px, rx, width, tol_rel, rect_rule) ||
+            interval_fragile(py, ry, height, tol_rel, rect_rule))
             flags[i] |= F_NEAR;
         if (okx && oky) {
             rect[i * 4 + 0] = (int32_t)tx0; rect[i * 4 + 1] = (int32_t)ty0;

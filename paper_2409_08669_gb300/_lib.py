@@ -43,7 +43,8 @@ class adr_camera(ctypes.Structure):
 class adr_settings(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("alpha_low", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("lowpass", ctypes.c_float), ("jac_clamp", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
+                ("rect_rule", ctypes.c_int32)]
 
 
 class adr_serve_config(ctypes.Structure):
@@ -152,6 +153,7 @@ def make_settings(st) -> adr_settings:
     for i in range(3):
         s.bg[i] = float(st.bg[i])
     s.sh_degree = int(st.sh_degree)
+    s.rect_rule = int(st.rect_rule)
     return s
 
 

@@ -72,6 +72,8 @@ adr_status make_settings(const adr_settings* s, SetDev& d) {
     if (!s) return fail(ADR_ERR_INVALID, "settings is NULL");
     if (s->mode < ADR_PLAIN || s->mode > ADR_AABB) return fail(ADR_ERR_INVALID, "bad mode %d", s->mode);
     if (s->sh_degree < 0 || s->sh_degree > 3) return fail(ADR_ERR_INVALID, "sh_degree must be 0..3");
+    if (s->rect_rule != ADR_RECT_PIXEL && s->rect_rule != ADR_RECT_3DGS)
+        return fail(ADR_ERR_INVALID, "bad rect_rule %d", s->rect_rule);
     if (!(s->alpha_low > 0.f && s->alpha_low < 1.f)) return fail(ADR_ERR_INVALID, "alpha_low must be in (0,1)");
     if (!(s->t_min >= 0.f && s->t_min < 1.f)) return fail(ADR_ERR_INVALID, "t_min must be in [0,1)");
     if (!(s->lowpass >= 0.f) || !std::isfinite(s->lowpass)) return fail(ADR_ERR_INVALID, "bad lowpass");
@@ -81,6 +83,7 @@ adr_status make_settings(const adr_settings* s, SetDev& d) {
     d.jac_clamp = s->jac_clamp;
     for (int i = 0; i < 3; ++i) d.bg[i] = s->bg[i];
     d.sh_degree = s->sh_degree;
+    d.rect_rule = s->rect_rule;
     return ADR_OK;
 }
 

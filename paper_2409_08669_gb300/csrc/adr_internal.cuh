@@ -35,6 +35,7 @@ struct SetDev {
     float alpha_low, t_min, lowpass, jac_clamp;
     float bg[3];
     int sh_degree;
+    int rect_rule;
 };
 
 // Camera and settings of a frame, read by the kernels from device memory so a

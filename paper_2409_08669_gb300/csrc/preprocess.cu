@@ -134,6 +134,22 @@ __device__ __forceinline__ bool tile_span(float c, float r, int size, int& t0, i
     return true;
 }
 
+// The original 3DGS rasterizer's tile rounding: integer half-width R = ceil(r),
+// tiles [floor((c - R)/16), floor((c + R + 15)/16)) clamped to [0, tiles].
+// Returns false if empty.
+__device__ __forceinline__ bool tile_span_3dgs(float c, float r, int tiles, int& t0, int& t1) {
+    const float R = ceilf(r);
+    float lo = floorf(__fmul_rn(__fsub_rn(c, R), 1.f / kTile));
+    float hi = floorf(__fmul_rn(__fadd_rn(__fadd_rn(c, R), (float)(kTile - 1)), 1.f / kTile));
+    if (!(lo == lo) || !(hi == hi)) return false;   // NaN
+    lo = fminf(fmaxf(lo, 0.f), (float)tiles);
+    hi = fminf(fmaxf(hi, 0.f), (float)tiles);
+    if (!(lo < hi)) return false;
+    t0 = (int)lo;
+    t1 = (int)hi;
+    return true;
+}
+
 // sqrt(log2(e) / 2): w-vectors carry this factor so that
 // (w1.d)^2 + (w2.d)^2 = (log2 e) * q / 2 and alpha = sigma * 2^-(...).
 constexpr float kHalfLog2e = 0.84932180028801907f;
@@ -247,8 +263,12 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
                 }
             }
             int tx0, tx1, ty0, ty1;
-            if (keep && tile_span(px, rx, cam.width, tx0, tx1) &&
-                tile_span(py, ry, cam.height, ty0, ty1)) {
+            const bool span = st.rect_rule == ADR_RECT_3DGS
+                                  ? tile_span_3dgs(px, rx, cam.tiles_x, tx0, tx1) &&
+                                        tile_span_3dgs(py, ry, cam.tiles_y, ty0, ty1)
+                                  : tile_span(px, rx, cam.width, tx0, tx1) &&
+                                        tile_span(py, ry, cam.height, ty0, ty1);
+            if (keep && span) {
                 ntiles = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
                 rc = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1,
                                   (unsigned short)ty1);

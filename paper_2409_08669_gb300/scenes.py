@@ -33,6 +33,11 @@ MODE_CIRCLE = 1
 MODE_AABB = 2
 MODE_NAMES = {MODE_PLAIN: "plain", MODE_CIRCLE: "adr_circle", MODE_AABB: "adr_aabb"}
 
+# Tile-rectangle rules: the pixel-conservative rule (lossless, the default) and
+# the original 3DGS rasterizer's rounding (for comparison with 3DGS renders).
+RECT_PIXEL = 0
+RECT_3DGS = 1
+
 CAMERA_FLOATS = 24
 
 
@@ -91,6 +96,7 @@ class Settings:
     jac_clamp: float = float(np.float32(1.3))          # Jacobian clamp, in units of tan(fov/2)
     bg: tuple = (0.0, 0.0, 0.0)
     sh_degree: int = 3
+    rect_rule: int = RECT_PIXEL
 
     def with_mode(self, mode: int) -> "Settings":
         return dataclasses.replace(self, mode=mode)

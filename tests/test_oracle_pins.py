@@ -283,6 +283,69 @@ def test_pair_tiles_equal_pixel_brute_force(seed):
             assert got == want
 
 
+def _brute_tiles_3dgs(px, py, rx, ry, w, h):
+    """The 3DGS rounding as a point set: with R = ceil(r), the tiles whose span
+    [16t, 16t + 16) meets the real interval [c - R, c + R - 1], kept inside the
+    tile grid.  Sampled every half pixel plus both ends (tiles are 16 wide)."""
+    def axis(c, r, size):
+        R = math.ceil(r)
+        lo, hi = c - R, c + R - 1
+        if hi < lo:
+            return set()
+        pts = np.append(np.arange(lo, hi, 0.5), hi)
+        t = set(np.floor(pts / 16).astype(np.int64).tolist())
+        return {v for v in t if 0 <= v < (size + 15) // 16}
+    tx, ty = axis(px, rx, w), axis(py, ry, h)
+    return {y * ((w + 15) // 16) + x for y in ty for x in tx}
+
+
+@pytest.mark.parametrize("seed", [3, 5])
+def test_3dgs_rect_rule_equals_point_set_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    w, h = 150, 120
+    cam = S.look_at((0, 0, -2.5), width=w, height=h)
+    n_checked = 0
+    for m, s, q, op in _random_gaussians(rng, 25, opac_hi=0.99):
+        sc = _single(m * 2.0, s * 2.0, q, op)
+        for mode in (S.MODE_PLAIN, S.MODE_CIRCLE, S.MODE_AABB):
+            pre = oracle.preprocess(sc, cam, S.Settings(mode=mode, rect_rule=S.RECT_3DGS))
+            keys, _ = oracle.emit_pairs(pre)
+            got = set((keys >> np.uint64(32)).astype(np.int64).tolist()) if pre["tiles"][0] else set()
+            g = pre["geom"][0]
+            if not (pre["flags"][0] & oracle.F_VISIBLE) or g[oracle.G_RX] == 0:
+                assert not got
+                continue
+            want = _brute_tiles_3dgs(g[oracle.G_PX], g[oracle.G_PY], g[oracle.G_RX], g[oracle.G_RY], w, h)
+            assert got == want
+            n_checked += 1
+    assert n_checked > 30
+
+
+def test_3dgs_rect_rule_drops_edge_tiles_and_is_not_lossless():
+    """The 3DGS rounding keeps the lower tiles of the pixel rule (or one more)
+    and loses the last tile when px + R falls in [16k, 16k + 1): the pixel 16k
+    is then within the radius but its tile is not listed, so the image can
+    differ from the lossless render, which equals the per-pixel brute force."""
+    sc = S.tiny_scene(0, n=4000)
+    cam = S.look_at((0, 0, -3), width=128, height=128)
+    pix = oracle.render(sc, cam, S.Settings(mode=S.MODE_PLAIN))
+    cmp = oracle.render(sc, cam, S.Settings(mode=S.MODE_PLAIN, rect_rule=S.RECT_3DGS))
+    rp, rc = pix["pre"]["rect"], cmp["pre"]["rect"]
+    both = (pix["pre"]["tiles"] > 0) & (cmp["pre"]["tiles"] > 0)
+    assert np.all(rc[both, 0] <= rp[both, 0]) and np.all(rc[both, 1] <= rp[both, 1])
+    assert np.all(rc[both, 2] >= rp[both, 2] - 1) and np.all(rc[both, 3] >= rp[both, 3] - 1)
+    g = pix["pre"]["geom"]
+    upper = np.floor(g[:, oracle.G_PX] + g[:, oracle.G_RO])
+    dropped_x = both & (rc[:, 2] == rp[:, 2] - 1)
+    # exactly the predicted edge case (inside the image) drops a column of tiles
+    assert np.all(np.mod(upper[dropped_x], 16) == 0)
+    assert dropped_x.sum() > 0
+    assert np.abs(cmp["img"] - pix["img"]).max() > 1e-3
+    # the compat render is still the render of its own tile lists
+    bf = oracle.render_brute(cmp["pre"], S.Settings(mode=S.MODE_PLAIN), use_rect=True)
+    np.testing.assert_array_equal(cmp["img"], bf["img"])
+
+
 # ----------------------------------------------------------------------------
 # Colour: real SH basis (Condon-Shortley phase) vs scipy
 # ----------------------------------------------------------------------------

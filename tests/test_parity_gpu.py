@@ -87,6 +87,15 @@ def test_ragged_image_many_tiles(rast):
         _check_frame(rast, scene, cam, S.Settings(mode=mode), f"ragged/{mode}")
 
 
+@pytest.mark.parametrize("mode", [S.MODE_PLAIN, S.MODE_CIRCLE, S.MODE_AABB])
+def test_3dgs_rect_rule_parity(rast, mode):
+    """The 3DGS-compatible tile rounding, on the ragged image (250x190)."""
+    scene = S.tiny_scene(11, n=6000)
+    cam = S.look_at((0.3, -0.2, -2.2), width=250, height=190)
+    st = S.Settings(mode=mode, rect_rule=S.RECT_3DGS)
+    _check_frame(rast, scene, cam, st, f"rect3dgs/{S.MODE_NAMES[mode]}")
+
+
 def test_cluster_scene_1080p_subset(rast):
     """A 200k-Gaussian draw of the clustered scene at 1920x1080 (tile grid 120x68)."""
     scene = S.cluster_scene(n=200_000, seed=1)
@@ -187,3 +196,6 @@ def test_invalid_arguments_rejected(rast):
     cam = S.look_at((0, 0, -3), width=64, height=64)
     with pytest.raises(_lib.AdrError):
         rast.forward(upload(scene), cam, S.Settings(mode=7))
+    with pytest.raises(_lib.AdrError) as e:
+        rast.forward(upload(scene), cam, S.Settings(rect_rule=2))
+    assert e.value.status == _lib.ADR_ERR_INVALID
