@@ -129,9 +129,15 @@ adr_status adr_preprocess(adr_ctx *ctx, const float *means, const float *scales,
                           const float *rots, const float *opac, const float *sh, int64_t n,
                           const adr_camera *camera, const adr_settings *settings, void *stream);
 
-/* Stages 4-5: stable sort of the pairs by tile (the Gaussians are already in
- * depth order, so the result is ordered by (tile, depth, index)) and the
- * per-tile ranges [start, end) into the sorted list. */
+/* Stages 4-5: the tile lists, ordered by (tile, depth, index) (the Gaussians
+ * are already in depth order).  The pairs are grouped by column of tiles:
+ * each Gaussian contributes one run per tile column of its rectangle (its
+ * rows in that column), stably sorted by column, with each column's
+ * [start, end).  A tile's list is the runs of its column that cover its row,
+ * in order; adr_render reads it from there, so the pairs are never written
+ * out one by one.  adr_render_backward, adr_read_pairs and adr_read_ranges
+ * first expand the runs into per-tile lists and ranges (a second, stable
+ * pass by tile row), enqueued on their own stream. */
 adr_status adr_sort(adr_ctx *ctx, void *stream);
 
 /* Stage 6: per-tile front-to-back alpha blending (Eq. 2-3) of the sorted
@@ -165,6 +171,24 @@ adr_status adr_render_backward(adr_ctx *ctx, const float *means, const float *sc
  * ready to pass to adr_render_backward. */
 adr_status adr_load_loss(adr_ctx *ctx, const int32_t *load, int64_t hw, float weight,
                          double *stats, float *dl_dload, void *stream);
+
+/* Image loss of the training objective (Sec. 4.4 total loss: the L1 and SSIM
+ * terms beside L_load).  img and ref: [channels, height, width] device fp32
+ * (the render and its target).  SSIM follows Wang et al. 2004: per channel,
+ * local means, variances and covariance under the 11x11 Gaussian window of
+ * standard deviation 1.5 (normalised), extended past the border with zeros so
+ * the SSIM map has the image's size, with C1 = 0.01^2 and C2 = 0.03^2.
+ * Writes stats[0] = mean |img - ref| and stats[1] = mean SSIM over every
+ * element (device doubles).  If dl_dimg is non-NULL it is overwritten with the
+ * gradient of  w_l1 * mean|img - ref| + w_ssim * (1 - mean SSIM)  with respect
+ * to img (the L1 subgradient is 0 where img == ref); scratch must then hold
+ * 3 * channels * height * width floats (device memory, contents clobbered).
+ * Runs on the current CUDA device, which must own the pointers; enqueued on
+ * `stream`.  ADR_ERR_INVALID for NULL pointers, non-positive sizes or more than
+ * 2^31 elements, or a missing scratch. */
+adr_status adr_image_loss(const float *img, const float *ref, int32_t channels, int32_t height,
+                          int32_t width, float w_l1, float w_ssim, double *stats, float *dl_dimg,
+                          float *scratch, void *stream);
 
 /* Waits for the context's last stream and returns the pair count P (the sum
  * of tiles over Gaussians, which may exceed pair_capacity).  Returns

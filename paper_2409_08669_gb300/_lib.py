@@ -80,6 +80,8 @@ _SIGNATURES = {
                                         ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
     "adr_render_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "adr_load_loss": (_I32, [_P, _P, _I64, ctypes.c_float, _P, _P, _P]),
+    "adr_image_loss": (_I32, [_P, _P, _I32, _I32, _I32, ctypes.c_float, ctypes.c_float, _P, _P,
+                              _P, _P]),
     "adr_profile_enable": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -228,6 +230,12 @@ def adr_render_backward(ctx, means, scales, rots, opac, sh, dl_dimg, dl_dload, g
 def adr_load_loss(ctx, load_, hw, weight, stats, dl_dload, stream):
     return check(load().adr_load_loss(ctx, load_, hw, weight, stats, dl_dload, stream),
                  "adr_load_loss")
+
+
+def adr_image_loss(img, ref, channels, height, width, w_l1, w_ssim, stats, dl_dimg, scratch,
+                   stream):
+    return check(load().adr_image_loss(img, ref, channels, height, width, w_l1, w_ssim, stats,
+                                       dl_dimg, scratch, stream), "adr_image_loss")
 
 
 def adr_profile_enable(ctx, enable):

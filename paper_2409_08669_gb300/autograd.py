@@ -6,12 +6,14 @@ as a float tensor; a gradient reaching the load flows back through the
 straight-through reading d l_i / d alpha = 1 (Sec. 4.4).
 LoadBalanceLoss: L_load = std of l_i over the pixels (Eq. 13), computed and
 differentiated by adr_load_loss.
+ImageLoss: w_l1 * L1 + w_ssim * (1 - SSIM) against a target image, computed and
+differentiated by adr_image_loss (the L1 and SSIM terms of the total loss).
 """
 from __future__ import annotations
 
 import torch
 
-from .raster import Rasterizer
+from .raster import Rasterizer, image_loss
 
 
 class AdrRasterize(torch.autograd.Function):
@@ -54,6 +56,20 @@ class LoadBalanceLoss(torch.autograd.Function):
         return grad * g, None
 
 
+class ImageLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, ref, w_l1, w_ssim):
+        stats, grad = image_loss(img.detach(), ref.detach(), w_l1, w_ssim, want_grad=True)
+        ctx.save_for_backward(grad)
+        ctx.stats = stats
+        return (w_l1 * stats[0] + w_ssim * (1.0 - stats[1])).to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None, None, None
+
+
 def rasterize(params, rast: Rasterizer, camera, settings):
     """(img [3,H,W], load [H,W] float, t_final [H,W]) differentiable w.r.t. params."""
     return AdrRasterize.apply(*params, rast, camera, settings)
@@ -61,3 +77,8 @@ def rasterize(params, rast: Rasterizer, camera, settings):
 
 def load_balance_loss(load_f, rast: Rasterizer):
     return LoadBalanceLoss.apply(load_f, rast)
+
+
+def l1_ssim_loss(img, ref, w_l1=0.8, w_ssim=0.2):
+    """w_l1 * mean|img - ref| + w_ssim * (1 - SSIM(img, ref)), differentiable in img."""
+    return ImageLoss.apply(img, ref, float(w_l1), float(w_ssim))

@@ -365,6 +365,8 @@ adr_status adr_read_pairs(adr_ctx* c, uint64_t* keys, uint32_t* vals, int64_t ca
     if (capacity < 0) return fail(ADR_ERR_INVALID, "negative capacity");
     DeviceGuard guard(c->device);
     const int64_t cap = capacity < c->ws.capacity ? capacity : c->ws.capacity;
+    c->last_stream = (cudaStream_t)stream;
+    enqueue_tile_lists(c->ws, c->fs, (cudaStream_t)stream);
     launch_pair_keys(c->ws.ranges, c->fs.num_tiles, c->fs.sorted_gauss, c->ws.depth_key, cap,
                      reinterpret_cast<unsigned long long*>(keys), vals, (cudaStream_t)stream);
     return check_launch("adr_read_pairs") == ADR_OK ? ok() : ADR_ERR_CUDA;
@@ -384,6 +386,8 @@ adr_status adr_read_ranges(adr_ctx* c, uint32_t* ranges, void* stream) {
     if (!c || !ranges) return fail(ADR_ERR_INVALID, "NULL argument");
     if (!c->have_sort) return fail(ADR_ERR_INVALID, "adr_read_ranges before adr_sort");
     DeviceGuard guard(c->device);
+    c->last_stream = (cudaStream_t)stream;
+    enqueue_tile_lists(c->ws, c->fs, (cudaStream_t)stream);
     launch_copy_ranges(c->ws.ranges, c->fs.num_tiles, reinterpret_cast<uint2*>(ranges),
                        (cudaStream_t)stream);
     return check_launch("adr_read_ranges") == ADR_OK ? ok() : ADR_ERR_CUDA;
@@ -417,6 +421,7 @@ adr_status adr_render_backward(adr_ctx* c, const float* means, const float* scal
     DeviceGuard guard(c->device);
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
+    enqueue_tile_lists(c->ws, c->fs, strm);   // the backward walks per-tile lists
     enqueue_backward(c->ws, c->fs, means, scales, rots, opac, sh, dl_dimg, dl_dload, g_means,
                      g_scales, g_rots, g_opac, g_sh, strm);
     return check_launch("adr_render_backward") == ADR_OK ? ok() : ADR_ERR_CUDA;
@@ -433,6 +438,28 @@ adr_status adr_load_loss(adr_ctx* c, const int32_t* load, int64_t hw, float weig
     ADR_CUDA(cudaMemcpyAsync(stats, c->ws.load_sums + 2, 2 * sizeof(double),
                              cudaMemcpyDeviceToDevice, strm));
     return check_launch("adr_load_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
+}
+
+adr_status adr_image_loss(const float* img, const float* ref, int32_t channels, int32_t height,
+                          int32_t width, float w_l1, float w_ssim, double* stats, float* dl_dimg,
+                          float* scratch, void* stream) {
+    if (!img || !ref || !stats) return fail(ADR_ERR_INVALID, "NULL argument");
+    if (channels <= 0 || height <= 0 || width <= 0 || (int64_t)channels * height * width > (1ll << 31))
+        return fail(ADR_ERR_INVALID, "image size %d x %d x %d out of range", channels, height, width);
+    if (dl_dimg && !scratch) return fail(ADR_ERR_INVALID, "scratch is required with dl_dimg");
+    if (!std::isfinite(w_l1) || !std::isfinite(w_ssim)) return fail(ADR_ERR_INVALID, "bad weight");
+    // Gaussian window of standard deviation 1.5 over 11 taps, normalised to sum 1.
+    LossWindow win;
+    double w[11], sum = 0.0;
+    for (int k = 0; k < 11; ++k) {
+        const double d = k - 5;
+        w[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+        sum += w[k];
+    }
+    for (int k = 0; k < 11; ++k) win.w[k] = (float)(w[k] / sum);
+    launch_image_loss(img, ref, channels, height, width, win, w_l1, w_ssim, stats, dl_dimg,
+                      scratch, (cudaStream_t)stream);
+    return check_launch("adr_image_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
 }
 
 adr_status adr_profile_enable(adr_ctx* c, int32_t enable) {

@@ -148,8 +148,25 @@ struct FrameState {
     SetDev st{};
     int num_tiles = 0;
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
-    const uint32_t* sorted_gauss = nullptr;  // pairs' Gaussians by (tile, depth)
+    const uint32_t* sorted_gauss = nullptr;  // list entries' Gaussians by (cell, depth)
+    const uint2* runs = nullptr;             // column runs by (column, depth)
+    // The render lists: kColumnLists = the column runs of each column of tiles;
+    // otherwise the Gaussians of each (band of 2^list_shift tile rows, column)
+    // cell, the tiles themselves when 0.  -1 before the first sort.
+    int list_shift = -1;
 };
+
+// The lists the render reads.  kColumnLists: each column of tiles reads the
+// column runs of the first tile-sort pass directly (in depth order; a tile's
+// own list is the runs covering its row), and the second pass is not run.
+// 0 .. 7: the second pass groups the Gaussians by bands of 2^shift tile rows
+// (0 = per-tile lists).  Per-tile lists are rebuilt on demand for the
+// backward and the pair inspection.
+constexpr int kColumnLists = 8;
+#ifndef ADR_LIST_SHIFT
+#define ADR_LIST_SHIFT 8
+#endif
+constexpr int kListShift = ADR_LIST_SHIFT;
 
 // Counts stage calls on the host; every 2^28 calls (before the device tag
 // wraps) clears the lookback words.
@@ -169,6 +186,9 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                         bool set_params = true);
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream);
+// Rebuilds per-tile lists (list_shift 0) from the column runs if the last
+// sort made band lists; what the backward and the pair inspection read.
+void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream);
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream);
 void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st);
@@ -217,13 +237,13 @@ void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t
 void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
                                  uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
-                            int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
+                            int tiles_x, int num_cells, int shift, uint32_t* counts, uint32_t* totals,
                             uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
                         int64_t capacity, uint2* ranges, cudaStream_t stream);
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
-                              int grid, int tiles_y, cudaStream_t stream);
+                              int grid, int num_bands, int shift, cudaStream_t stream);
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
@@ -238,9 +258,14 @@ void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, 
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);
 
-void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                   const FrameParams* fp, int num_tiles, float* img, float* t_final,
-                   int32_t* load, int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream);
+void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
+                   const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
+                   int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
+                   int32_t* trav, float* tfin, cudaStream_t stream);
+// Column ranges [start, end) of the first tile-sort pass's runs, from its
+// per-column totals (empty on pair overflow).  One CTA.
+void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* counters,
+                          int64_t capacity, uint2* ranges, cudaStream_t stream);
 
 // Backward (backward.cu).
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
@@ -252,6 +277,13 @@ void launch_preprocess_backward(int n, const float* means, const float* scales, 
                                 const uint32_t* gbox, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream);
+// 1-D taps of the SSIM window (the 2-D window is their outer product).
+struct LossWindow {
+    float w[11];
+};
+void launch_image_loss(const float* img, const float* ref, int channels, int H, int W,
+                       const LossWindow& win, float w_l1, float w_ssim, double* stats,
+                       float* dl_dimg, float* scratch, cudaStream_t stream);
 void launch_load_loss(const int32_t* load, int64_t hw, double* sums, float weight, float* dl_dload,
                       int sm_count, cudaStream_t stream);
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,

@@ -98,12 +98,38 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                             ep, ws.counters, ws.status, ws.scan_grid, stream));
 }
 
+// Stage 4, pass 2 and stage 5 for lists of 2^shift tile rows: entries grouped
+// by band (ty >> shift) over the column-sorted runs, then the cells' ranges.
+static void enqueue_lists(const Workspace& ws, FrameState& fs, int shift, cudaStream_t stream) {
+    const int bands = ((fs.cam.tiles_y - 1) >> shift) + 1;
+    const int cells = bands * fs.cam.tiles_x;
+    cudaMemsetAsync(ws.ttotals + kRadix, 0, kRadix * sizeof(uint32_t), stream);
+    cudaMemsetAsync(ws.tile_counts, 0, (size_t)cells * sizeof(uint32_t), stream);
+    if (fs.n > 0 && fs.order) {
+        // The runs' entry counts vary, so the pass uses many small run ranges
+        // (kMaxTileGrid CTAs) that the hardware schedules as CTAs finish.
+        const int G2 = kMaxTileGrid;
+        TIMED(ws, kKTileCountRows, stream,
+              launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x, cells, shift,
+                                     ws.tcounts, ws.ttotals + kRadix, ws.tile_counts, ws.status, G2,
+                                     stream));
+        TIMED(ws, kKTileCountScan, stream,
+              launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G2, stream));
+        TIMED(ws, kKTileScatterRows, stream,
+              launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
+                                       ws.status, G2, bands, shift, stream));
+    }
+    // Stage 5: every cell's [start, end) from its entry count.
+    TIMED(ws, kKTileRanges, stream,
+          launch_tile_ranges(ws.tile_counts, cells, ws.counters, ws.capacity, ws.ranges, stream));
+    fs.sorted_gauss = ws.pgauss;
+    fs.list_shift = shift;
+}
+
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream) {
     (void)epoch;   // the tile sort has no lookback words
-    fs.sorted_gauss = ws.pgauss;
-    cudaMemsetAsync(ws.ttotals, 0, 2 * kRadix * sizeof(uint32_t), stream);
-    cudaMemsetAsync(ws.tile_counts, 0, (size_t)fs.num_tiles * sizeof(uint32_t), stream);
+    cudaMemsetAsync(ws.ttotals, 0, kRadix * sizeof(uint32_t), stream);
     const int G = ws.tile_grid;
     if (fs.n > 0 && fs.order) {
         PairSource src;
@@ -120,32 +146,32 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
         TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
         TIMED(ws, kKTileScatterColumns, stream,
               launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
-        // Stage 4, pass 2: pairs expanded from the runs, grouped by ty.  The
-        // runs' pair counts vary, so the pass uses many small run ranges
-        // (kMaxTileGrid CTAs) that the hardware schedules as CTAs finish.
-        const int G2 = kMaxTileGrid;
-        TIMED(ws, kKTileCountRows, stream,
-              launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x,
-                                     fs.num_tiles, ws.tcounts, ws.ttotals + kRadix, ws.tile_counts,
-                                     ws.status, G2, stream));
-        TIMED(ws, kKTileCountScan, stream,
-              launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G2, stream));
-        TIMED(ws, kKTileScatterRows, stream,
-              launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
-                                       ws.status, G2, fs.cam.tiles_y, stream));
     }
-    // Stage 5: every tile's [start, end) from its pair count.
-    TIMED(ws, kKTileRanges, stream,
-          launch_tile_ranges(ws.tile_counts, fs.num_tiles, ws.counters, ws.capacity, ws.ranges,
-                             stream));
+    fs.runs = ws.pruns;
+    if (kListShift == kColumnLists) {
+        // Stage 5: the render reads each column's runs; their ranges come from
+        // the pass's per-column totals.
+        TIMED(ws, kKTileRanges, stream,
+              launch_column_ranges(ws.ttotals, fs.cam.tiles_x, ws.counters, ws.capacity, ws.ranges,
+                                   stream));
+        fs.sorted_gauss = nullptr;
+        fs.list_shift = kColumnLists;
+    } else {
+        enqueue_lists(ws, fs, kListShift, stream);
+    }
+}
+
+void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
+    if (fs.list_shift != 0) enqueue_lists(ws, fs, 0, stream);
 }
 
 void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream) {
     // Stage 6.
     TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, fs.sorted_gauss, ws.rec, ws.d_fp, fs.num_tiles, img, t_final,
-                        load, ws.last, ws.trav, ws.tfin, stream));
+          launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
+                        ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
+                        stream));
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,

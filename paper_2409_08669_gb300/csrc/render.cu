@@ -3,11 +3,16 @@
 // alpha < alpha_low skip, early termination and the per-pixel load l_i
 // (Sec. 4.4, Eq. 12).
 //
-// One CTA of 256 threads per 16x16 tile.  The tile's list is walked in batches
-// of 256 Gaussians staged in shared memory (one Gaussian per thread); the CTA
-// leaves as soon as every pixel has terminated (__syncthreads_count).  Pixel
-// offsets are taken relative to the tile origin so the float-float centre
-// collapses to one well-conditioned float per Gaussian per tile.
+// One CTA of 256 threads per 16x16 tile.  The tile reads a depth-ordered list
+// that holds its own list as a subsequence -- the column runs of its column
+// of tiles (kRuns), or the Gaussians of its column and band of 2^list_shift
+// tile rows -- in batches of 256 entries (one per thread); the entries whose
+// tile rectangle holds the tile's row are compacted, in list order, into
+// shared memory, and every pixel walks them.  Pixels stop early (transmittance
+// below t_min), so a tile usually reads only the front of its list.  The CTA leaves as soon as every
+// pixel has terminated (__syncthreads_count).  Pixel offsets are taken
+// relative to the tile origin so the float-float centre collapses to one
+// well-conditioned float per Gaussian per tile.
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -15,14 +20,20 @@ namespace {
 
 constexpr int kRenderThreads = kTilePixels;
 
+template <bool kRuns>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
-         const float4* __restrict__ rec, const FrameParams* __restrict__ fp, float* __restrict__ img,
+         const uint2* __restrict__ runs, const float4* __restrict__ rec,
+         const uint32_t* __restrict__ gbox, int list_shift,
+         const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
          int32_t* __restrict__ trav_out, float* __restrict__ tfin) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
+    __shared__ uint32_t s_gid[kRenderThreads];
+    __shared__ uint32_t s_wcnt[4][kRenderThreads / 32];
+    __shared__ uint32_t s_next;
 
     const CamDev cam = fp->cam;
     const SetDev st = fp->st;
@@ -34,26 +45,85 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
     const float fx = (float)lx, fy = (float)ly;
 
-    const uint2 range = ranges[tile];
+    // The list of the tile's cell: its column, its (band, column), or the tile itself.
+    const uint2 range = ranges[kRuns ? tx : (ty >> list_shift) * cam.tiles_x + tx];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int32_t count = 0, last = 0, trav = 0;
     bool done = !inside;
     const float alpha_low = st.alpha_low, t_min = st.t_min;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
 
-    for (uint32_t base = range.x; base < range.y; base += kRenderThreads) {
+    // Each batch reads kFill list entries per thread (list order: entry
+    // base + k * 256 + thread) and stages the first 256 kept ones; the list
+    // resumes at the first kept entry not staged.
+    constexpr int kFill = kRuns ? 4 : 1;
+    uint32_t base = range.x;
+    while (base < range.y) {
         if (__syncthreads_count(done) == kRenderThreads) break;
-        const uint32_t idx = base + threadIdx.x;
-        if (idx < range.y) {
-            const uint32_t g = sorted_gauss[idx];
-            const float4 r0 = rec[3 * (size_t)g + 0];
+        uint32_t g[kFill], kept[kFill];
+        bool keep[kFill];
+#pragma unroll
+        for (int k = 0; k < kFill; ++k) {
+            const uint32_t idx = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
+            g[k] = 0;
+            keep[k] = idx < range.y;
+            if (keep[k]) {
+                if (kRuns) {   // run record: Gaussian, y0 | (h - 1) << 8 | tx << 16
+                    const uint2 r = runs[idx];
+                    g[k] = r.x;
+                    keep[k] = (uint32_t)ty - (r.y & 0xFFu) <= ((r.y >> 8) & 0xFFu);
+                } else {
+                    g[k] = sorted_gauss[idx];
+                    if (list_shift) {   // does the Gaussian's rectangle hold this tile row?
+                        const uint32_t box = gbox[g[k]];
+                        keep[k] = (uint32_t)ty - ((box >> 8) & 0xFFu) <= (box >> 24);
+                    }
+                }
+            }
+        }
+        // Stable compaction: ballots per (k, warp), then their exclusive prefix.
+#pragma unroll
+        for (int k = 0; k < kFill; ++k) {
+            kept[k] = __ballot_sync(0xffffffffu, keep[k]);
+            if (lane == 0) s_wcnt[k][warp] = __popc(kept[k]);
+        }
+        __syncthreads();
+        uint32_t total = 0, before[kFill];
+#pragma unroll
+        for (int k = 0; k < kFill; ++k) {
+#pragma unroll
+            for (int w = 0; w < kRenderThreads / 32; ++w) {
+                const uint32_t cw = s_wcnt[k][w];
+                if (w == warp) before[k] = total;
+                total += cw;
+            }
+        }
+        const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int k = 0; k < kFill; ++k) {
+            if (keep[k]) {
+                const uint32_t slot = before[k] + __popc(kept[k] & lt);
+                if (slot < (uint32_t)kRenderThreads) s_gid[slot] = g[k];
+                else if (slot == (uint32_t)kRenderThreads)
+                    s_next = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
+            }
+        }
+        const int m = (int)min(total, (uint32_t)kRenderThreads);
+        __syncthreads();
+        const uint32_t next = total > (uint32_t)kRenderThreads
+                                  ? s_next
+                                  : min(range.y, base + (uint32_t)(kFill * kRenderThreads));
+        if ((int)threadIdx.x < m) {
+            const uint32_t gi = s_gid[threadIdx.x];
+            const float4 r0 = rec[3 * (size_t)gi + 0];
             // centre relative to the tile origin: (hi - origin) is exact, one rounding for lo
             s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
                                             __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
-            s_w[threadIdx.x] = rec[3 * (size_t)g + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
+            s_w[threadIdx.x] = rec[3 * (size_t)gi + 1];
+            s_c[threadIdx.x] = rec[3 * (size_t)gi + 2];
         }
         __syncthreads();
-        const int m = min((uint32_t)kRenderThreads, range.y - base);
         if (!done) {
             int j = 0;
             for (; j < m; ++j) {
@@ -74,10 +144,12 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 C2 = fmaf(col.z, wgt, C2);
                 T = test_T;
                 ++count;
-                last = (int32_t)(base - range.x) + j + 1;
+                last = fbase + j + 1;
             }
             trav += j;
         }
+        fbase += m;
+        base = next;
     }
     if (inside) {
         const size_t hw = (size_t)cam.width * cam.height;
@@ -95,13 +167,20 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
 }  // namespace
 
-void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
-                   const FrameParams* fp, int num_tiles, float* img, float* t_final,
-                   int32_t* load, int32_t* last, int32_t* trav, float* tfin, cudaStream_t stream) {
+void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
+                   const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
+                   int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
+                   int32_t* trav, float* tfin, cudaStream_t stream) {
     const int tiles = num_tiles;
     if (tiles <= 0) return;
-    k_render<<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, rec, fp, img,
-                                                   t_final, load, last, trav, tfin);
+    if (list_shift == kColumnLists)
+        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
+                                                             list_shift, fp, img, t_final, load,
+                                                             last, trav, tfin);
+    else
+        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
+                                                              list_shift, fp, img, t_final, load,
+                                                              last, trav, tfin);
 }
 
 }  // namespace adr

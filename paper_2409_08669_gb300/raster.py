@@ -28,6 +28,26 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+def image_loss(img, ref, w_l1=1.0, w_ssim=0.0, want_grad=True, stream=None, scratch=None):
+    """(stats, grad): stats = device float64 [mean |img - ref|, mean SSIM] and
+    grad = d(w_l1 * L1 + w_ssim * (1 - SSIM)) / d img (None unless want_grad),
+    computed by adr_image_loss.  img, ref: [C, H, W] float32 on one device."""
+    img, ref = img.contiguous(), ref.contiguous()
+    assert img.dtype == torch.float32 and ref.dtype == torch.float32 and img.shape == ref.shape
+    assert img.dim() == 3
+    c, h, w = img.shape
+    stats = torch.empty(2, dtype=torch.float64, device=img.device)
+    grad = None
+    if want_grad:
+        grad = torch.empty_like(img)
+        if scratch is None or scratch.numel() < 3 * img.numel():
+            scratch = torch.empty(3 * img.numel(), dtype=torch.float32, device=img.device)
+    with torch.cuda.device(img.device):
+        _lib.adr_image_loss(_ptr(img), _ptr(ref), c, h, w, float(w_l1), float(w_ssim), _ptr(stats),
+                            _ptr(grad), _ptr(scratch) if want_grad else 0, _stream(stream))
+    return stats, grad
+
+
 class Rasterizer:
     """One library context: workspace for up to `max_gaussians` Gaussians,
     `pair_capacity` Gaussian-tile pairs and images up to max_width x max_height."""
