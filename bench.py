@@ -58,11 +58,12 @@ def select_workload(name):
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
-# DRAM bytes (read + write) per Gaussian-tile pair of the dominant kernel from
-# a one-pass ncu capture of one launch at the heavy 3M-Gaussian 1080p frame
-# (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md: 128.34 + 576.92 MB),
-# divided by that workload's mean P (1.5958e8) and scaled to a launch by the
-# measured P.
+# DRAM bytes (read + write) of one launch from one-pass ncu captures at the
+# heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
+# 103.82 + 51.44 MB, one frame) and the per-tile list pass
+# (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md, 128.34 + 576.92 MB over
+# P = 1.5958e8 pairs, scaled by the measured P).
+TRAFFIC_BYTES_PER_LAUNCH = {"render": 103.82e6 + 51.44e6}
 TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 
@@ -551,7 +552,7 @@ def run_ours(args):
     dominant = max(ktable, key=lambda k: ktable[k]["ms_per_launch"] * ktable[k]["launches"])
     dk = ktable[dominant]
     tpp = TRAFFIC_BYTES_PER_PAIR.get(dominant)
-    traffic = tpp * u_mean["pairs"] if tpp else None
+    traffic = tpp * u_mean["pairs"] if tpp else TRAFFIC_BYTES_PER_LAUNCH.get(dominant)
     if dominant == "render":
         alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
         achieved = u_mean["evals"] * EVAL_FP32_OPS / (dk["ms_per_launch"] / 1e3) / 1e12

@@ -277,6 +277,30 @@ void launch_preprocess_backward(int n, const float* means, const float* scales, 
                                 const uint32_t* gbox, const float4* aux,
                                 const float* g2d, float* g_means, float* g_scales, float* g_rots,
                                 float* g_opac, float* g_sh, cudaStream_t stream);
+// 2^x with the hardware's approximate base-2 exponential (PTX ex2.approx.ftz:
+// relative error ~2^-22, results below 2^-126 flushed to zero).  Render and its
+// backward both evaluate a Gaussian's alpha with it, so they take the same
+// alpha < alpha_low skip decisions; a flushed result is below alpha_low anyway.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The eigen-form quadratic of a Gaussian at a pixel, shared by Render and its
+// backward so both take identical decisions: with the centre c relative to the
+// tile origin, w = (w1, w2) and the pixel offset f from the origin,
+// u_i = w_i . (c - f) is evaluated as k_i - w_i . f with k_i = w_i . c formed
+// once per (Gaussian, tile); returns log2(sigma) - (u1^2 + u2^2).
+__device__ __forceinline__ float2 quad_k(float2 c, float4 w) {
+    return make_float2(fmaf(w.x, c.x, w.y * c.y), fmaf(w.z, c.x, w.w * c.y));
+}
+__device__ __forceinline__ float quad_exponent(float2 k, float4 w, float log2_sigma, float fx, float fy) {
+    const float u1 = fmaf(-w.x, fx, fmaf(-w.y, fy, k.x));
+    const float u2 = fmaf(-w.z, fx, fmaf(-w.w, fy, k.y));
+    return fmaf(-u1, u1, fmaf(-u2, u2, log2_sigma));
+}
+
 // 1-D taps of the SSIM window (the 2-D window is their outer product).
 struct LossWindow {
     float w[11];

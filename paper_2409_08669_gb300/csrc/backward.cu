@@ -99,9 +99,7 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                     const float4 w = s_w[j];
                     const float4 col = s_c[j];
                     const float dx = c.x - fx, dy = c.y - fy;
-                    const float u1 = fmaf(w.x, dx, w.y * dy);
-                    const float u2 = fmaf(w.z, dx, w.w * dy);
-                    const float raw = exp2f(fmaf(-u1, u1, fmaf(-u2, u2, col.w)));
+                    const float raw = ex2_approx(quad_exponent(quad_k(c, w), w, col.w, fx, fy));
                     const float alpha = fminf(0.99f, raw);
                     if (alpha >= alpha_low) {
                         contrib = true;

@@ -4,12 +4,13 @@
 // (Sec. 4.4, Eq. 12).
 //
 // One CTA of 256 threads per 16x16 tile.  The tile reads a depth-ordered list
-// that holds its own list as a subsequence -- the column runs of its column
-// of tiles (kRuns), or the Gaussians of its column and band of 2^list_shift
-// tile rows -- in batches of 256 entries (one per thread); the entries whose
-// tile rectangle holds the tile's row are compacted, in list order, into
-// shared memory, and every pixel walks them.  Pixels stop early (transmittance
-// below t_min), so a tile usually reads only the front of its list.  The CTA leaves as soon as every
+// that holds its own list as a subsequence -- the column runs of its column of
+// tiles (kRuns), or the Gaussians of its column and band of 2^list_shift tile
+// rows (the tile itself when 0).  Each batch reads up to 1024 entries (4 per
+// thread), keeps those whose rows hold the tile's row, compacts the first 256
+// kept ones stably into shared memory with their records, and every pixel
+// blends them.  Pixels stop early (transmittance below t_min), so a tile
+// usually reads only the front of its list; the CTA leaves as soon as every
 // pixel has terminated (__syncthreads_count).  Pixel offsets are taken
 // relative to the tile origin so the float-float centre collapses to one
 // well-conditioned float per Gaussian per tile.
@@ -21,7 +22,7 @@ namespace {
 constexpr int kRenderThreads = kTilePixels;
 
 template <bool kRuns>
-__global__ void __launch_bounds__(kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, 5)   // 5 CTAs per SM: <= 51 registers
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const uint2* __restrict__ runs, const float4* __restrict__ rec,
          const uint32_t* __restrict__ gbox, int list_shift,
@@ -117,24 +118,21 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         if ((int)threadIdx.x < m) {
             const uint32_t gi = s_gid[threadIdx.x];
             const float4 r0 = rec[3 * (size_t)gi + 0];
+            const float4 w = rec[3 * (size_t)gi + 1];
             // centre relative to the tile origin: (hi - origin) is exact, one rounding for lo
-            s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
-                                            __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
-            s_w[threadIdx.x] = rec[3 * (size_t)gi + 1];
+            const float2 c = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
+                                         __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
+            s_xy[threadIdx.x] = quad_k(c, w);
+            s_w[threadIdx.x] = w;
             s_c[threadIdx.x] = rec[3 * (size_t)gi + 2];
         }
         __syncthreads();
         if (!done) {
             int j = 0;
             for (; j < m; ++j) {
-                const float2 c = s_xy[j];
-                const float4 w = s_w[j];
-                const float dx = c.x - fx, dy = c.y - fy;
-                const float u1 = fmaf(w.x, dx, w.y * dy);
-                const float u2 = fmaf(w.z, dx, w.w * dy);
                 const float4 col = s_c[j];
-                const float e = fmaf(-u1, u1, fmaf(-u2, u2, col.w));   // log2(sigma) - q log2(e)/2
-                const float alpha = fminf(0.99f, exp2f(e));
+                const float e = quad_exponent(s_xy[j], s_w[j], col.w, fx, fy);   // log2(sigma) - q log2(e)/2
+                const float alpha = fminf(0.99f, ex2_approx(e));
                 if (alpha < alpha_low) continue;
                 const float test_T = T * (1.f - alpha);
                 if (test_T < t_min) { done = true; ++j; break; }
