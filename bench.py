@@ -340,10 +340,11 @@ def train_step_rate(local, steps=20, warmup=5):
 def finetune_measure(local, steps=500):
     """The load-balancing fine-tune (Sec. 4.4) on the 1M-Gaussian clustered
     scene at 1280x720: the scene is fitted to renders of its perturbed copy
-    from 10 orbit cameras for `steps` iterations, once with the paper's
-    weights (lambda_load = 0.45) and once without the load term (L1 0.8,
-    SSIM 0.2); frames/s, load std, PSNR and SSIM are measured on 10 other
-    orbit cameras before and after."""
+    from 10 orbit cameras for `steps` iterations with the paper's weights
+    (lambda_load = 0.45) under both readings of d l_i / d alpha
+    (straight-through; through the early stop) and once without the load
+    term (L1 0.8, SSIM 0.2); frames/s, load std, PSNR and SSIM are measured
+    on the training cameras and on 10 other orbit cameras, before and after."""
     import torch
     from paper_2409_08669_gb300.finetune import (FinetuneConfig, Finetuner, evaluate,
                                                  render_targets)
@@ -359,18 +360,26 @@ def finetune_measure(local, steps=500):
     tparams = upload(target, dev)
     train_tgt = render_targets(rast, tparams, train_cams, st)
     eval_tgt = render_targets(rast, tparams, eval_cams, st)
+    b = upload(base, dev)
     out = {"workload": "cluster-1M-720p", "steps": steps, "train_cameras": len(train_cams),
            "eval_cameras": len(eval_cams),
-           "before": evaluate(rast, upload(base, dev), eval_cams, eval_tgt, st)}
-    for name, cfg in (("lambda_load_0.45", FinetuneConfig(steps=steps)),
-                      ("lambda_load_0", FinetuneConfig(steps=steps, lambda_l1=0.8, lambda_ssim=0.2,
-                                                       lambda_load=0.0))):
-        ft = Finetuner(base, train_cams, train_tgt, rast, st, cfg)
+           "before": {"train": evaluate(rast, b, train_cams, train_tgt, st),
+                      "eval": evaluate(rast, b, eval_cams, eval_tgt, st)}}
+    del b
+    st_stop = S.Settings(mode=S.MODE_AABB, load_grad=S.LOAD_GRAD_TERMINATION)
+    for name, cfg, s in (
+            ("lambda_load_0.45_straight", FinetuneConfig(steps=steps), st),
+            ("lambda_load_0.45_termination", FinetuneConfig(steps=steps), st_stop),
+            ("lambda_load_0", FinetuneConfig(steps=steps, lambda_l1=0.8, lambda_ssim=0.2,
+                                             lambda_load=0.0), st)):
+        ft = Finetuner(base, train_cams, train_tgt, rast, s, cfg)
         for _ in range(steps):
             ft.step()
         torch.cuda.synchronize()
-        out[name] = evaluate(rast, ft.activated_copy(), eval_cams, eval_tgt, st)
-        del ft
+        p = ft.activated_copy()
+        out[name] = {"train": evaluate(rast, p, train_cams, train_tgt, st),
+                     "eval": evaluate(rast, p, eval_cams, eval_tgt, st)}
+        del ft, p
     rast.close()
     return out
 

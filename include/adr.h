@@ -87,18 +87,34 @@ typedef struct adr_camera {
  *                    although its pixel 16k is within the radius. */
 typedef enum adr_rect_rule { ADR_RECT_PIXEL = 0, ADR_RECT_3DGS = 1 } adr_rect_rule;
 
+/* How the per-pixel load l_i (Eq. 12, an integer count) passes a gradient to
+ * the opacities alpha_k of the Gaussians blended into the pixel in
+ * adr_render_backward; the paper does not say.
+ *   ADR_LOAD_GRAD_STRAIGHT    : d l_i / d alpha_k = 1 (straight-through).  The
+ *                               default.
+ *   ADR_LOAD_GRAD_TERMINATION : the same for pixels that reached the end of
+ *                               their list; for a pixel that stopped early
+ *                               (transmittance below t_min),
+ *                               d l_i / d alpha_k = -l_i / (-ln T_final) / (1 - alpha_k):
+ *                               raising any alpha_k by d(-ln(1 - alpha_k))
+ *                               brings the stop forward by that much optical
+ *                               depth, -ln T_final / l_i per blended Gaussian
+ *                               on average. */
+typedef enum adr_load_grad { ADR_LOAD_GRAD_STRAIGHT = 0, ADR_LOAD_GRAD_TERMINATION = 1 } adr_load_grad;
+
 /* Render settings.  alpha_low: minimum splatting opacity (paper: 1/255,
  * Sec. 5.1.2); t_min: blending stops before a Gaussian that would take the
  * transmittance below it; lowpass: added to the diagonal of Sigma';
  * jac_clamp: the projection Jacobian uses x/z, y/z clamped to
  * +-jac_clamp*tan(fov/2); bg: background colour; sh_degree: 0..3;
- * rect_rule: an adr_rect_rule. */
+ * rect_rule: an adr_rect_rule; load_grad: an adr_load_grad. */
 typedef struct adr_settings {
     int32_t mode;
     float alpha_low, t_min, lowpass, jac_clamp;
     float bg[3];
     int32_t sh_degree;
     int32_t rect_rule;
+    int32_t load_grad;
 } adr_settings;
 
 typedef struct adr_ctx adr_ctx;

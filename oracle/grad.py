@@ -10,8 +10,10 @@ here, so the gradient follows the branches the forward path took.
 
 The per-pixel load l_i (Eq. 12) is an integer count; its gradient uses the
 straight-through reading d l_i / d alpha_ik = 1 for every blended pair,
-so dL_load/d alpha_ik = dL/d l_i (parity unpinned beyond this reading: the
-paper does not say how L_load back-propagates).
+so dL_load/d alpha_ik = dL/d l_i, or, with settings.load_grad = 1, for a
+pixel that stopped early d l_i / d(-ln(1 - alpha_ik)) = -l_i / (-ln T_final)
+(parity unpinned beyond these readings: the paper does not say how L_load
+back-propagates).
 
 Only tests may import this module.
 """
@@ -130,6 +132,7 @@ def render_torch(params, camera, settings, structure=None):
         T = torch.ones_like(Xp)
         C = torch.zeros((3, Xp.shape[0]), dtype=torch.float64)
         L = torch.zeros_like(Xp)
+        S = torch.zeros_like(Xp)    # optical depth of the blended Gaussians, sum of -ln(1 - alpha)
         done = torch.zeros(Xp.shape[0], dtype=torch.bool)
         for k in range(int(ranges[tile, 0]), int(ranges[tile, 1])):
             if bool(done.all()):
@@ -148,6 +151,14 @@ def render_torch(params, camera, settings, structure=None):
             C = C + rgb[g][:, None] * (alpha * T * bw)[None]                # Eq. 3
             T = torch.where(blend, test_T, T)
             L = L + bw * (1.0 + (alpha - a_det))                            # Eq. 12, straight-through
+            S = S + bw * -torch.log1p(-alpha)
+        if settings.load_grad == 1:
+            # Pixels that stopped early: d l / d(-ln(1 - alpha_k)) = -l / (-ln T_final),
+            # the count itself unchanged in value.
+            cnt = L.detach()
+            stopped = done & (cnt > 0)
+            theta = S.detach().clamp_min(1e-300)
+            L = torch.where(stopped, cnt - cnt / theta * (S - S.detach()), L)
         h, w = len(ys), len(xs)
         img[:, y0:y0 + h, x0:x0 + w] = (C + T[None] * bg[:, None]).reshape(3, h, w)
         Tout[y0:y0 + h, x0:x0 + w] = T.reshape(h, w)

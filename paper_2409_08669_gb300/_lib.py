@@ -44,7 +44,7 @@ class adr_settings(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("alpha_low", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("lowpass", ctypes.c_float), ("jac_clamp", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
-                ("rect_rule", ctypes.c_int32)]
+                ("rect_rule", ctypes.c_int32), ("load_grad", ctypes.c_int32)]
 
 
 class adr_serve_config(ctypes.Structure):
@@ -156,6 +156,7 @@ def make_settings(st) -> adr_settings:
         s.bg[i] = float(st.bg[i])
     s.sh_degree = int(st.sh_degree)
     s.rect_rule = int(st.rect_rule)
+    s.load_grad = int(st.load_grad)
     return s
 
 

@@ -74,6 +74,8 @@ adr_status make_settings(const adr_settings* s, SetDev& d) {
     if (s->sh_degree < 0 || s->sh_degree > 3) return fail(ADR_ERR_INVALID, "sh_degree must be 0..3");
     if (s->rect_rule != ADR_RECT_PIXEL && s->rect_rule != ADR_RECT_3DGS)
         return fail(ADR_ERR_INVALID, "bad rect_rule %d", s->rect_rule);
+    if (s->load_grad != ADR_LOAD_GRAD_STRAIGHT && s->load_grad != ADR_LOAD_GRAD_TERMINATION)
+        return fail(ADR_ERR_INVALID, "bad load_grad %d", s->load_grad);
     if (!(s->alpha_low > 0.f && s->alpha_low < 1.f)) return fail(ADR_ERR_INVALID, "alpha_low must be in (0,1)");
     if (!(s->t_min >= 0.f && s->t_min < 1.f)) return fail(ADR_ERR_INVALID, "t_min must be in [0,1)");
     if (!(s->lowpass >= 0.f) || !std::isfinite(s->lowpass)) return fail(ADR_ERR_INVALID, "bad lowpass");
@@ -84,6 +86,7 @@ adr_status make_settings(const adr_settings* s, SetDev& d) {
     for (int i = 0; i < 3; ++i) d.bg[i] = s->bg[i];
     d.sh_degree = s->sh_degree;
     d.rect_rule = s->rect_rule;
+    d.load_grad = s->load_grad;
     return ADR_OK;
 }
 
@@ -139,7 +142,7 @@ void free_workspace(Workspace& w) {
     }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.offsets, w.gbox, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
-                    w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.g2d, w.load_sums,
+                    w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.lstat, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -153,7 +156,7 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
     const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
     return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36) + P * 12 +
-           (P / kSortChunk + 2) * 4 + tiles * 12 + pixels * 12 + lb +
+           (P / kSortChunk + 2) * 4 + tiles * 12 + pixels * 16 + lb +
            (size_t)kRadix * (kMaxTileGrid + 2) * 4 + 4096;
 }
 
@@ -204,6 +207,7 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     ALLOC(w.last, pixels * sizeof(int32_t));
     ALLOC(w.trav, pixels * sizeof(int32_t));
     ALLOC(w.tfin, pixels * sizeof(float));
+    ALLOC(w.lstat, pixels * sizeof(int32_t));
     ALLOC(w.g2d, N * 9 * sizeof(float));
     ALLOC(w.load_sums, 4 * sizeof(double));
     ALLOC(w.hist, kHistWords * sizeof(uint32_t));

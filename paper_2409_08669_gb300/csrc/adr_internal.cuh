@@ -36,6 +36,7 @@ struct SetDev {
     float bg[3];
     int sh_degree;
     int rect_rule;
+    int load_grad;
 };
 
 // Camera and settings of a frame, read by the kernels from device memory so a
@@ -80,7 +81,8 @@ enum Counter : int {
     kCntVisible = 1,      // Gaussians with at least one tile (they sort first by depth)
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
     kCntRuns = 3,         // number of column runs C (sum of rectangle widths), saturating
-    kCntSortTicket0 = 4,  // words 4-7: unused
+    kCntDepthKept = 4,    // Gaussians with tiles, counted by the first depth pass
+                          // words 5-7: unused
     kCntPairs64 = 8,      // words 8-9: P as a 64-bit sum
     kCntSlots = 16
 };
@@ -126,6 +128,7 @@ struct Workspace {
     int32_t* last = nullptr;               // [max pixels]
     int32_t* trav = nullptr;               // [max pixels]
     float* tfin = nullptr;                 // [max pixels] final transmittance of the last render
+    int32_t* lstat = nullptr;              // [max pixels] l_i | terminated << 31 of the last render
     float* g2d = nullptr;                  // [max_n * 9] backward: dL/d(px, py, conic, sigma, rgb)
     double* load_sums = nullptr;           // [4] load-balancing loss moments
     uint32_t* hist = nullptr;              // [kHistWords]
@@ -203,10 +206,13 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
 // vals_in == nullptr means the values are 0..n-1.  counts: kRadix x grid
 // words; totals: kRadix words, zeroed before.  With pay_out, also writes
 // pay_out[i] = pay_in[vals_out[i]].
+// One stable 8-bit pass of the depth sort.  first: all n keys in, keys
+// 0xFFFFFFFF (no tiles) dropped and the kept ones counted into *kept; later
+// passes sort the *kept keys.
 void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                       uint32_t* vals_out, int64_t n, int shift, uint32_t* counts, uint32_t* totals,
-                       const uint32_t* pay_in, uint32_t* pay_out, uint32_t* status, int grid,
-                       cudaStream_t stream);
+                       uint32_t* vals_out, int64_t n, uint32_t* kept, bool first, int shift,
+                       uint32_t* counts, uint32_t* totals, const uint32_t* pay_in,
+                       uint32_t* pay_out, uint32_t* status, int grid, cudaStream_t stream);
 
 // Inputs of the tile passes.
 struct PairSource {
@@ -261,7 +267,7 @@ void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
                    const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
                    int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, cudaStream_t stream);
+                   int32_t* trav, float* tfin, int32_t* lstat, cudaStream_t stream);
 // Column ranges [start, end) of the first tile-sort pass's runs, from its
 // per-column totals (empty on pair overflow).  One CTA.
 void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* counters,
@@ -270,8 +276,9 @@ void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* c
 // Backward (backward.cu).
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                             const float4* aux, const FrameParams* fp, int num_tiles,
-                            const int32_t* last, const float* t_final, const float* dl_dimg,
-                            const float* dl_dload, float* g2d, cudaStream_t stream);
+                            const int32_t* last, const float* t_final, const int32_t* lstat,
+                            const float* dl_dimg, const float* dl_dload, float* g2d,
+                            cudaStream_t stream);
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,
                                 const float* opac, const float* sh, const FrameParams* fp,
                                 const uint32_t* gbox, const float4* aux,

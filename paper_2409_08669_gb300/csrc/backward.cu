@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kBwdThreads)
 k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
                   const float4* __restrict__ rec, const float4* __restrict__ aux,
                   const FrameParams* __restrict__ fp, const int32_t* __restrict__ last_pos,
-                  const float* __restrict__ t_final,
+                  const float* __restrict__ t_final, const int32_t* __restrict__ lstat,
                   const float* __restrict__ dl_dimg, const float* __restrict__ dl_dload,
                   float* __restrict__ g2d) {
     __shared__ float2 s_xy[kBwdThreads];
@@ -59,6 +59,17 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
         g1 = dl_dimg[hw + pix];
         g2 = dl_dimg[2 * hw + pix];
         if (dl_dload) gl = dl_dload[pix];
+    }
+    // d l_i / d alpha_k per blended Gaussian k: 1 (straight-through), or, with
+    // the termination reading, -l_i / (-ln T_final) / (1 - alpha_k) for a pixel
+    // that stopped (a more opaque Gaussian makes it stop sooner).
+    float gl_stop = 0.f;
+    if (st.load_grad == ADR_LOAD_GRAD_TERMINATION && inside && gl != 0.f && lstat) {
+        const int32_t ls = lstat[pix];
+        if (ls < 0 && T < 1.f) {
+            gl_stop = gl * -(float)(ls & 0x7FFFFFFF) / -logf(T);
+            gl = 0.f;
+        }
     }
     float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];   // colour behind the current Gaussian
     const float alpha_low = st.alpha_low;
@@ -110,7 +121,7 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                         d_g = wgt * g1;
                         d_b = wgt * g2;
                         float dalpha = T * ((col.x - acc0) * g0 + (col.y - acc1) * g1 + (col.z - acc2) * g2);
-                        dalpha += gl;                                     // straight-through load term
+                        dalpha += gl + gl_stop / one_m;                   // load term
                         acc0 = fmaf(col.x, alpha, one_m * acc0);
                         acc1 = fmaf(col.y, alpha, one_m * acc1);
                         acc2 = fmaf(col.z, alpha, one_m * acc2);
@@ -386,12 +397,13 @@ k_load_grad(const int32_t* __restrict__ load, int64_t hw, double* __restrict__ s
 
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,
                             const float4* aux, const FrameParams* fp, int num_tiles,
-                            const int32_t* last, const float* t_final, const float* dl_dimg,
-                            const float* dl_dload, float* g2d, cudaStream_t stream) {
+                            const int32_t* last, const float* t_final, const int32_t* lstat,
+                            const float* dl_dimg, const float* dl_dload, float* g2d,
+                            cudaStream_t stream) {
     const int tiles = num_tiles;
     if (tiles <= 0) return;
     k_render_backward<<<tiles, kBwdThreads, 0, stream>>>(ranges, sorted_gauss, rec, aux, fp,
-                                                         last, t_final, dl_dimg, dl_dload, g2d);
+                                                         last, t_final, lstat, dl_dimg, dl_dload, g2d);
 }
 
 void launch_preprocess_backward(int n, const float* means, const float* scales, const float* rots,

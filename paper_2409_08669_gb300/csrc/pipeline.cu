@@ -77,13 +77,17 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     TIMED(ws, kKPreprocess, stream,
           launch_preprocess((int)n, means, scales, rots, opac, sh, ws.d_fp, ws.d_stage, ws.rec,
                             ws.aux, ws.depth_key, ws.gbox, stream));
-    // Gaussians by view depth: 4 stable 8-bit passes; Gaussians without tiles
-    // carry key 0xFFFFFFFF and end up behind the V that have tiles.
+    // Gaussians by view depth: 4 stable 8-bit passes over the V Gaussians with
+    // tiles (the first pass drops the others, key 0xFFFFFFFF).  The last pass
+    // carries the packed rectangles into depth order; the slots behind the V
+    // keep the no-tiles sentinel the run scan skips.
+    if (n > 0) cudaMemsetAsync(ws.sorted_box, 0xFF, (size_t)n * sizeof(uint32_t), stream);
     const uint32_t* kin = ws.depth_key;
     const uint32_t* vin = nullptr;
     for (int p = 0; p < kMaxPasses; ++p) {
         TIMED(ws, kKDepthPass, stream,
-              launch_depth_pass(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n, 8 * p, ws.tcounts,
+              launch_depth_pass(kin, vin, ws.gkeys[p & 1], ws.gvals[p & 1], n,
+                                ws.counters + kCntDepthKept, p == 0, 8 * p, ws.tcounts,
                                 ws.hist + p * kRadix, p + 1 == kMaxPasses ? ws.gbox : nullptr,
                                 p + 1 == kMaxPasses ? ws.sorted_box : nullptr, ws.status,
                                 ws.sort_grid, stream));
@@ -171,7 +175,7 @@ void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float
     TIMED(ws, kKRender, stream,
           launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
                         ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
-                        stream));
+                        ws.lstat, stream));
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,
@@ -182,7 +186,7 @@ void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* me
     cudaMemsetAsync(ws.g2d, 0, (size_t)fs.n * 9 * sizeof(float), stream);
     TIMED(ws, kKRenderBackward, stream,
           launch_render_backward(ws.ranges, fs.sorted_gauss, ws.rec, ws.aux, ws.d_fp, fs.num_tiles,
-                                 ws.last, ws.tfin, dl_dimg, dl_dload, ws.g2d, stream));
+                                 ws.last, ws.tfin, ws.lstat, dl_dimg, dl_dload, ws.g2d, stream));
     TIMED(ws, kKPreprocessBackward, stream,
           launch_preprocess_backward((int)fs.n, means, scales, rots, opac, sh, ws.d_fp, ws.gbox,
                                      ws.aux, ws.g2d, g_means, g_scales, g_rots, g_opac, g_sh,

@@ -28,7 +28,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
          const uint32_t* __restrict__ gbox, int list_shift,
          const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
-         int32_t* __restrict__ trav_out, float* __restrict__ tfin) {
+         int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
@@ -50,7 +50,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const uint2 range = ranges[kRuns ? tx : (ty >> list_shift) * cam.tiles_x + tx];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int32_t count = 0, last = 0, trav = 0;
-    bool done = !inside;
+    bool done = !inside, stopped = false;
     const float alpha_low = st.alpha_low, t_min = st.t_min;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
@@ -135,7 +135,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 const float alpha = fminf(0.99f, ex2_approx(e));
                 if (alpha < alpha_low) continue;
                 const float test_T = T * (1.f - alpha);
-                if (test_T < t_min) { done = true; ++j; break; }
+                if (test_T < t_min) { done = stopped = true; ++j; break; }
                 const float wgt = alpha * T;
                 C0 = fmaf(col.x, wgt, C0);
                 C1 = fmaf(col.y, wgt, C1);
@@ -160,6 +160,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         if (last_out) last_out[pix] = last;
         if (trav_out) trav_out[pix] = trav;
         if (tfin) tfin[pix] = T;
+        if (lstat) lstat[pix] = count | (stopped ? (int32_t)0x80000000u : 0);
     }
 }
 
@@ -168,17 +169,17 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
                    const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
                    int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, cudaStream_t stream) {
+                   int32_t* trav, float* tfin, int32_t* lstat, cudaStream_t stream) {
     const int tiles = num_tiles;
     if (tiles <= 0) return;
     if (list_shift == kColumnLists)
         k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
                                                              list_shift, fp, img, t_final, load,
-                                                             last, trav, tfin);
+                                                             last, trav, tfin, lstat);
     else
         k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
                                                               list_shift, fp, img, t_final, load,
-                                                              last, trav, tfin);
+                                                              last, trav, tfin, lstat);
 }
 
 }  // namespace adr

@@ -9,6 +9,9 @@
 //      stably (warp match_any), groups them by digit in shared memory and
 //      writes every digit's run contiguously from the CTA's running offset.
 // No CTA waits for another one, so a pass has no lookback chain.
+// The first pass drops the Gaussians without tiles (key 0xFFFFFFFF, which
+// would sort last anyway) and counts the others; the later passes sort only
+// those, reading their number from device memory.
 #include <cstddef>
 
 #include "adr_internal.cuh"
@@ -26,6 +29,7 @@ struct alignas(16) SortShared {
     uint32_t local[kRadix + 1];              // exclusive prefix of this chunk's digit counts
     uint32_t dst[kRadix];                    // global position of local slot 0, per digit
     uint32_t wsum[kWarps];
+    uint32_t kept;                           // items of the chunk that are written
 };
 constexpr size_t kSortSmem = sizeof(SortShared);
 
@@ -33,6 +37,13 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+constexpr uint32_t kNoTiles = 0xFFFFFFFFu;   // depth key of a Gaussian without tiles
+
+// Items of a pass: the host count, or the device count of the kept keys.
+__device__ __forceinline__ int64_t pass_items(int64_t n, const uint32_t* n_dev) {
+    return n_dev ? min(n, (int64_t)*n_dev) : n;
 }
 
 // The chunks [c0, c1) of CTA blockIdx.x.
@@ -44,11 +55,14 @@ __device__ __forceinline__ void chunk_span(int64_t n, int grid, uint32_t& c0, ui
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-k_digit_counts(const uint32_t* __restrict__ keys, int64_t n, int shift, int grid,
-               uint32_t* __restrict__ counts, uint32_t* __restrict__ totals) {
-    __shared__ uint32_t s_cnt[kRadix];
+k_digit_counts(const uint32_t* __restrict__ keys, int64_t n_host, const uint32_t* __restrict__ n_dev,
+               bool drop, int shift, int grid, uint32_t* __restrict__ counts,
+               uint32_t* __restrict__ totals, uint32_t* __restrict__ kept_total) {
+    __shared__ uint32_t s_cnt[kRadix + 1];   // + the dropped keys
     const int tid = threadIdx.x;
+    const int64_t n = pass_items(n_host, n_dev);
     s_cnt[tid] = 0;
+    if (tid == 0) s_cnt[kRadix] = 0;
     __syncthreads();
     uint32_t c0, c1;
     chunk_span(n, grid, c0, c1);
@@ -57,30 +71,41 @@ k_digit_counts(const uint32_t* __restrict__ keys, int64_t n, int shift, int grid
         const int64_t B = min((int64_t)c1 * kSortChunk, n);   // > A
         const int64_t Bv = A + ((B - A) & ~(int64_t)3);         // A is 16-byte aligned
         const uint4* k4 = reinterpret_cast<const uint4*>(keys + A);
+        auto digit = [&](uint32_t k) { return (drop && k == kNoTiles) ? (uint32_t)kRadix : (k >> shift) & 0xFFu; };
         for (int64_t j = tid; A + 4 * j < Bv; j += kSortThreads) {
             const uint4 q = k4[j];
-            atomicAdd(&s_cnt[(q.x >> shift) & 0xFFu], 1u);
-            atomicAdd(&s_cnt[(q.y >> shift) & 0xFFu], 1u);
-            atomicAdd(&s_cnt[(q.z >> shift) & 0xFFu], 1u);
-            atomicAdd(&s_cnt[(q.w >> shift) & 0xFFu], 1u);
+            atomicAdd(&s_cnt[digit(q.x)], 1u);
+            atomicAdd(&s_cnt[digit(q.y)], 1u);
+            atomicAdd(&s_cnt[digit(q.z)], 1u);
+            atomicAdd(&s_cnt[digit(q.w)], 1u);
         }
-        for (int64_t i = Bv + tid; i < B; i += kSortThreads) atomicAdd(&s_cnt[(keys[i] >> shift) & 0xFFu], 1u);
+        for (int64_t i = Bv + tid; i < B; i += kSortThreads) atomicAdd(&s_cnt[digit(keys[i])], 1u);
     }
     __syncthreads();
     const uint32_t c = s_cnt[tid];
     counts[(size_t)tid * grid + blockIdx.x] = c;
     if (c) atomicAdd(totals + tid, c);
+    if (kept_total && c0 < c1) {   // the kept keys of this CTA: its range minus the dropped ones
+        if (tid == 0) {
+            const int64_t A = (int64_t)c0 * kSortChunk, B = min((int64_t)c1 * kSortChunk, n);
+            atomicAdd(kept_total, (uint32_t)(B - A) - s_cnt[kRadix]);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kSortThreads, 3)
 k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
-                int shift, const uint32_t* __restrict__ starts, int grid,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n_host,
+                const uint32_t* __restrict__ n_dev, bool drop, int shift,
+                const uint32_t* __restrict__ starts, int grid,
                 const uint32_t* __restrict__ pay_in, uint32_t* __restrict__ pay_out,
                 uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortShared& sm = *reinterpret_cast<SortShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = pass_items(n_host, n_dev);
+    // Output positions are bounded by the kept keys (all of them if nothing is dropped).
+    const int64_t n_out = drop ? n_host : n;
     uint32_t c0, c1;
     chunk_span(n, grid, c0, c1);
     if (c0 >= c1) return;
@@ -99,11 +124,13 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             val[q] = ok ? (vals_in ? vals_in[base + s] : (uint32_t)(base + s)) : 0u;
         }
         __syncwarp();
-        // Stable warp-level ranking with match_any (digit kRadix = out of range).
+        // Stable warp-level ranking with match_any (digit kRadix = out of range
+        // or dropped).
 #pragma unroll
         for (int q = 0; q < kSortItems; ++q) {
             const int s = warp * (kSortItems * 32) + q * 32 + lane;
-            const uint32_t d = s < count ? ((key[q] >> shift) & 0xFFu) : (uint32_t)kRadix;
+            const bool in = s < count && !(drop && key[q] == kNoTiles);
+            const uint32_t d = in ? ((key[q] >> shift) & 0xFFu) : (uint32_t)kRadix;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t before = sm.warp_cnt[warp][d];
             rank[q] = before + __popc(peers & lanemask_lt());
@@ -134,6 +161,7 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             for (int w = 0; w < warp; ++w) wbase += sm.wsum[w];
             loc = wbase + x - cnt;
             sm.local[tid] = loc;
+            if (tid == kSortThreads - 1) sm.kept = wbase + x;   // all digits' items
         }
         const uint32_t r = sm.run[tid];
         sm.dst[tid] = r - loc;
@@ -143,7 +171,7 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
         for (int q = 0; q < kSortItems; ++q) {
             const int s = warp * (kSortItems * 32) + q * 32 + lane;
-            if (s < count) {
+            if (s < count && !(drop && key[q] == kNoTiles)) {
                 const uint32_t d = (key[q] >> shift) & 0xFFu;
                 const uint32_t pos = sm.local[d] + sm.warp_cnt[warp][d] + rank[q];
                 sm.keys[pos] = key[q];
@@ -152,10 +180,11 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         }
         __syncthreads();
         // Coalesced write-out: each digit's run goes to consecutive addresses.
-        for (int s = tid; s < count; s += kSortThreads) {
+        const int kept = (int)sm.kept;
+        for (int s = tid; s < kept; s += kSortThreads) {
             const uint32_t k = sm.keys[s];
             const uint32_t g = sm.dst[(k >> shift) & 0xFFu] + (uint32_t)s;   // exact modulo 2^32
-            if ((int64_t)g >= n) { atomicOr(status, kErrRange); continue; }
+            if ((int64_t)g >= n_out) { atomicOr(status, kErrRange); continue; }
             const uint32_t v = sm.vals[s];
             keys_out[g] = k;
             vals_out[g] = v;
@@ -178,15 +207,19 @@ int onesweep_blocks_per_sm() {
 }
 
 void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                       uint32_t* vals_out, int64_t n, int shift, uint32_t* counts, uint32_t* totals,
-                       const uint32_t* pay_in, uint32_t* pay_out, uint32_t* status, int grid,
-                       cudaStream_t stream) {
+                       uint32_t* vals_out, int64_t n, uint32_t* kept, bool first, int shift,
+                       uint32_t* counts, uint32_t* totals, const uint32_t* pay_in,
+                       uint32_t* pay_out, uint32_t* status, int grid, cudaStream_t stream) {
     if (n <= 0) return;
-    k_digit_counts<<<grid, kSortThreads, 0, stream>>>(keys_in, n, shift, grid, counts, totals);
+    // First pass: all n keys in, the kept ones counted into *kept.  Later
+    // passes: the *kept keys.
+    const uint32_t* n_dev = first ? nullptr : kept;
+    k_digit_counts<<<grid, kSortThreads, 0, stream>>>(keys_in, n, n_dev, first, shift, grid, counts,
+                                                      totals, first ? kept : nullptr);
     launch_tile_count_scan(counts, totals, grid, stream);
     k_digit_scatter<<<grid, kSortThreads, kSortSmem, stream>>>(keys_in, vals_in, keys_out, vals_out, n,
-                                                              shift, counts, grid, pay_in, pay_out,
-                                                              status);
+                                                              n_dev, first, shift, counts, grid,
+                                                              pay_in, pay_out, status);
 }
 
 }  // namespace adr

@@ -38,6 +38,11 @@ MODE_NAMES = {MODE_PLAIN: "plain", MODE_CIRCLE: "adr_circle", MODE_AABB: "adr_aa
 RECT_PIXEL = 0
 RECT_3DGS = 1
 
+# Readings of d l_i / d alpha for the load-balancing loss: straight-through
+# (the default) or through the early stop of pixels that terminated.
+LOAD_GRAD_STRAIGHT = 0
+LOAD_GRAD_TERMINATION = 1
+
 CAMERA_FLOATS = 24
 
 
@@ -97,6 +102,7 @@ class Settings:
     bg: tuple = (0.0, 0.0, 0.0)
     sh_degree: int = 3
     rect_rule: int = RECT_PIXEL
+    load_grad: int = LOAD_GRAD_STRAIGHT
 
     def with_mode(self, mode: int) -> "Settings":
         return dataclasses.replace(self, mode=mode)

@@ -56,7 +56,7 @@ def test_binding_covers_every_declared_symbol(libpath):
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.adr_camera) == (16 + 4 + 1 + 3) * 4 + 2 * 4
-    assert ctypes.sizeof(_lib.adr_settings) == 4 + 4 * 4 + 3 * 4 + 4 + 4
+    assert ctypes.sizeof(_lib.adr_settings) == 4 + 4 * 4 + 3 * 4 + 4 + 4 + 4
     assert ctypes.sizeof(_lib.adr_serve_config) == 8 + 3 * 8 + 4 * 4
 
 

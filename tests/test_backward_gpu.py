@@ -66,10 +66,11 @@ def test_backward_matches_oracle_gradient_2k_64px(rast, mode):
         assert _rel(a, b) <= 1e-3, (name, _rel(a, b))
 
 
-def test_backward_with_load_term_and_background(rast):
+@pytest.mark.parametrize("load_grad", [S.LOAD_GRAD_STRAIGHT, S.LOAD_GRAD_TERMINATION])
+def test_backward_with_load_term_and_background(rast, load_grad):
     sc = _scene(seed=9, n=1500)
     cam = S.look_at((-0.3, 0.2, -2.4), width=80, height=48)
-    st = S.Settings(mode=S.MODE_AABB, bg=(0.2, 0.5, 0.1))
+    st = S.Settings(mode=S.MODE_AABB, bg=(0.2, 0.5, 0.1), load_grad=load_grad)
     rng = np.random.default_rng(4)
     w = rng.normal(size=(3, 48, 80))
     v = rng.normal(size=(48, 80)) * 0.05
