@@ -263,7 +263,10 @@ def kernel_bytes(name, n, u, hw):
     P, V, C = u["pairs"], u["visible"], u["runs"]
     return {
         "preprocess": 44 * n + 192 * V + 104 * n,  # params (+SH of kept) in; records, key, box out
-        "depth_pass": 20 * n,                      # count: key in; scatter: key + value in and out
+        # per launch, averaged over the 4 passes: the first reads the n keys twice and
+        # writes the V kept keys + values; the others count, read and write V keys +
+        # values; the last also gathers and writes the V packed rectangles
+        "depth_pass": 2 * n + 19 * V,
         "scan_tiles": 8 * n,                       # boxes in depth order in, run offsets out
         "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
         "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident

@@ -1,9 +1,10 @@
 """The load-balancing fine-tune (Sec. 4.4 total loss) on a small heavy-load
-scene: the image loss falls and the training views fit their targets better,
-with and without the load term, and the load term changes the per-pixel load
-distribution.  Which way the load std moves depends on the reading of
-d l_i / d alpha (under the straight-through reading it can rise: lowering
-alpha delays early termination); it is reported, not asserted."""
+scene.  Without the load term the image loss falls and the training views fit
+their targets better.  With lambda_load = 0.45 the load gradient's reading
+decides the outcome: under the early-stop reading the load spreads less than
+without the load term (lower std of l_i on the training views), which is the
+paper's aim; the straight-through reading is run and reported (it can raise
+the spread: lowering alpha delays the early stop)."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -11,7 +12,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_finetune_fits_targets_and_load_term_acts():
+def test_finetune_fits_targets_and_load_term_balances():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2409_08669_gb300 import scenes as S
@@ -21,15 +22,17 @@ def test_finetune_fits_targets_and_load_term_acts():
     target = S.perturbed_scene(base, seed=4)
     cams = S.orbit_cameras(8, width=320, height=240)
     st = S.Settings(mode=S.MODE_AABB)
+    st_stop = S.Settings(mode=S.MODE_AABB, load_grad=S.LOAD_GRAD_TERMINATION)
     rast = Rasterizer(max_gaussians=base.n, pair_capacity=1 << 24, max_width=320, max_height=240)
     try:
         tgt = render_targets(rast, upload(target), cams, st)
         before = evaluate(rast, upload(base), cams, tgt, st, repeats=1)
         res = {}
-        for name, cfg in (("load", FinetuneConfig(steps=80)),
-                          ("plain", FinetuneConfig(steps=80, lambda_l1=0.8, lambda_ssim=0.2,
-                                                   lambda_load=0.0))):
-            ft = Finetuner(base, cams, tgt, rast, st, cfg)
+        for name, cfg, s in (("plain", FinetuneConfig(steps=80, lambda_l1=0.8, lambda_ssim=0.2,
+                                                      lambda_load=0.0), st),
+                             ("straight", FinetuneConfig(steps=80), st),
+                             ("stop", FinetuneConfig(steps=80), st_stop)):
+            ft = Finetuner(base, cams, tgt, rast, s, cfg)
             first = float(ft.step())
             for _ in range(cfg.steps - 1):
                 last = ft.step()
@@ -41,5 +44,5 @@ def test_finetune_fits_targets_and_load_term_acts():
     print(before, res)
     assert res["plain"]["last_loss"] < res["plain"]["first_loss"]
     assert res["plain"]["psnr_db"] > before["psnr_db"] + 1.0
-    assert res["load"]["psnr_db"] > before["psnr_db"]
-    assert abs(res["load"]["load_mean"] - res["plain"]["load_mean"]) > 0.005 * res["plain"]["load_mean"]
+    assert res["stop"]["psnr_db"] > before["psnr_db"]
+    assert res["stop"]["load_std"] < res["plain"]["load_std"]
