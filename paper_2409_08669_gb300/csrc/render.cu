@@ -38,8 +38,9 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
     const CamDev cam = fp->cam;
     const SetDev st = fp->st;
-    const int tile = blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    // CTAs walk the tiles column by column: the tiles in flight at once share
+    // a few columns' run lists and Gaussian records in L2.
+    const int ty = (int)(blockIdx.x % cam.tiles_y), tx = (int)(blockIdx.x / cam.tiles_y);
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const bool inside = x < cam.width && y < cam.height;
