@@ -6,7 +6,7 @@
 // One CTA of 256 threads per 16x16 tile.  The tile reads a depth-ordered list
 // that holds its own list as a subsequence -- the column runs of its column of
 // tiles (kRuns), or the Gaussians of its column and band of 2^list_shift tile
-// rows (the tile itself when 0).  Each batch reads up to 1024 entries (4 per
+// rows (the tile itself when 0).  Each batch reads up to 2048 entries (8 per
 // thread), keeps those whose rows hold the tile's row, compacts the first 256
 // kept ones stably into shared memory with their records, and every pixel
 // blends them.  Pixels stop early (transmittance below t_min), so a tile
@@ -21,8 +21,10 @@ namespace {
 
 constexpr int kRenderThreads = kTilePixels;
 
+constexpr int kRunFill = 8;   // list entries each thread reads per batch (column runs)
+
 template <bool kRuns>
-__global__ void __launch_bounds__(kRenderThreads, 5)   // 5 CTAs per SM: <= 51 registers
+__global__ void __launch_bounds__(kRenderThreads, 4)   // 4 CTAs per SM: <= 64 registers
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const uint2* __restrict__ runs, const float4* __restrict__ rec,
          const uint32_t* __restrict__ gbox, int list_shift,
@@ -33,7 +35,9 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
     __shared__ uint32_t s_gid[kRenderThreads];
-    __shared__ uint32_t s_wcnt[4][kRenderThreads / 32];
+    __shared__ uint32_t s_wcnt[kRunFill][kRenderThreads / 32];   // kept per (k, warp)
+    __shared__ uint32_t s_off[kRunFill * (kRenderThreads / 32)];  // their exclusive prefix
+    __shared__ uint32_t s_total;
     __shared__ uint32_t s_next;
 
     const CamDev cam = fp->cam;
@@ -59,7 +63,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     // Each batch reads kFill list entries per thread (list order: entry
     // base + k * 256 + thread) and stages the first 256 kept ones; the list
     // resumes at the first kept entry not staged.
-    constexpr int kFill = kRuns ? 4 : 1;
+    constexpr int kFill = kRuns ? kRunFill : 1;
     uint32_t base = range.x;
     while (base < range.y) {
         if (__syncthreads_count(done) == kRenderThreads) break;
@@ -84,23 +88,44 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 }
             }
         }
-        // Stable compaction: ballots per (k, warp), then their exclusive prefix.
+        // Stable compaction: ballots per (k, warp); warp 0 scans their counts
+        // in list order (k-major).
 #pragma unroll
         for (int k = 0; k < kFill; ++k) {
             kept[k] = __ballot_sync(0xffffffffu, keep[k]);
             if (lane == 0) s_wcnt[k][warp] = __popc(kept[k]);
         }
         __syncthreads();
-        uint32_t total = 0, before[kFill];
+        if (warp == 0) {
+            constexpr int kN = kFill * (kRenderThreads / 32);
+            constexpr int kPer = (kN + 31) / 32;                 // counts per lane
+            uint32_t v[kPer], t = 0;
 #pragma unroll
-        for (int k = 0; k < kFill; ++k) {
-#pragma unroll
-            for (int w = 0; w < kRenderThreads / 32; ++w) {
-                const uint32_t cw = s_wcnt[k][w];
-                if (w == warp) before[k] = total;
-                total += cw;
+            for (int e = 0; e < kPer; ++e) {
+                const int i = lane * kPer + e;
+                v[e] = i < kN ? (&s_wcnt[0][0])[i] : 0u;
+                t += v[e];
             }
+            uint32_t x = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t run = x - t;
+#pragma unroll
+            for (int e = 0; e < kPer; ++e) {
+                const int i = lane * kPer + e;
+                if (i < kN) s_off[i] = run;
+                run += v[e];
+            }
+            if (lane == 31) s_total = x;
         }
+        __syncthreads();
+        const uint32_t total = s_total;
+        uint32_t before[kFill];
+#pragma unroll
+        for (int k = 0; k < kFill; ++k) before[k] = s_off[k * (kRenderThreads / 32) + warp];
         const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
         for (int k = 0; k < kFill; ++k) {
