@@ -60,10 +60,10 @@ def select_workload(name):
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
-# 103.82 + 51.44 MB, one frame) and the per-tile list pass
+# 105.58 + 43.83 MB, one frame) and the per-tile list pass
 # (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md, 128.34 + 576.92 MB over
 # P = 1.5958e8 pairs, scaled by the measured P).
-TRAFFIC_BYTES_PER_LAUNCH = {"render": 103.82e6 + 51.44e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"render": 105.58e6 + 43.83e6}
 TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 

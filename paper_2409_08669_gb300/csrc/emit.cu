@@ -77,11 +77,13 @@ __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, 
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n, int64_t capacity,
+k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t capacity,
              uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
              unsigned long long* __restrict__ lookback, EpochRef eref,
              uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
+    // The depth sort kept only the Gaussians with tiles: scan those.
+    const int64_t n = min(n_host, (int64_t)counters[kCntDepthKept]);
     __shared__ uint32_t s_warp[kScanThreads / 32], s_pairs[kScanThreads / 32];
     __shared__ uint32_t s_chunk, s_prefix;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -78,10 +78,8 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
           launch_preprocess((int)n, means, scales, rots, opac, sh, ws.d_fp, ws.d_stage, ws.rec,
                             ws.aux, ws.depth_key, ws.gbox, stream));
     // Gaussians by view depth: 4 stable 8-bit passes over the V Gaussians with
-    // tiles (the first pass drops the others, key 0xFFFFFFFF).  The last pass
-    // carries the packed rectangles into depth order; the slots behind the V
-    // keep the no-tiles sentinel the run scan skips.
-    if (n > 0) cudaMemsetAsync(ws.sorted_box, 0xFF, (size_t)n * sizeof(uint32_t), stream);
+    // tiles (the first pass drops the others, key 0xFFFFFFFF, and counts the
+    // V).  The last pass carries the packed rectangles into depth order.
     const uint32_t* kin = ws.depth_key;
     const uint32_t* vin = nullptr;
     for (int p = 0; p < kMaxPasses; ++p) {
@@ -95,7 +93,8 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
         vin = ws.gvals[p & 1];
     }
     fs.order = vin;
-    // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order.
+    // Stage 2 (+ bookkeeping for stage 3): scan of tile counts in depth order
+    // over the V Gaussians with tiles.
     const EpochRef ep{ws.d_stage, (uint32_t)kMaxPasses};
     TIMED(ws, kKScanTiles, stream,
           launch_scan_tiles(ws.sorted_box, n, ws.capacity, ws.offsets, ws.chunk_first, ws.lookback,
