@@ -1,6 +1,7 @@
 """GPU parity at the full benchmark size: the heavy-load scene of 3M Gaussians
 at 1920x1080 (AdR-AABB), in the launch configuration the benchmark times
-(one context with a 2^29-pair capacity, one camera of the orbit).
+(one context with a 2^29-pair capacity, one camera of the orbit); and a
+600k-Gaussian heavy scene at 3840x2160 (the 4K configuration's tile grid).
 
 The oracle cannot sort 1.5e8 pairs in seconds, so it checks:
   * every Gaussian: depth keys bit-exact, tile counts and rectangles exact
@@ -27,15 +28,33 @@ torch = pytest.importorskip("torch")
 TILE = 16
 
 
-def test_heavy_3m_1080p_sampled_parity():
+def _need_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2409_08669_gb300 import _lib
-    from paper_2409_08669_gb300.raster import Rasterizer, upload
+
+
+def test_heavy_3m_1080p_sampled_parity():
+    _need_gpu()
     scene = S.heavy_scene(n=3_000_000, seed=2)
     cam = S.orbit_cameras(50, radius=4.0, width=1920, height=1080)[5]
+    _sampled_parity(scene, cam, 1 << 29, "heavy-3M-1080p")
+
+
+def test_heavy_600k_4k_sampled_parity():
+    """3840x2160: a 240 x 135 tile grid, near the 256-column limit of the
+    column pass and the 8-bit row fields of the run records."""
+    _need_gpu()
+    scene = S.heavy_scene(n=600_000, seed=7)
+    cam = S.orbit_cameras(50, radius=4.0, width=3840, height=2160)[11]
+    _sampled_parity(scene, cam, 1 << 28, "heavy-600k-4k")
+
+
+def _sampled_parity(scene, cam, capacity, label):
+    from paper_2409_08669_gb300 import _lib
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
     st = S.Settings(mode=S.MODE_AABB)
-    rast = Rasterizer(max_gaussians=scene.n, pair_capacity=1 << 29, max_width=1920, max_height=1080)
+    rast = Rasterizer(max_gaussians=scene.n, pair_capacity=capacity, max_width=cam.width,
+                      max_height=cam.height)
     try:
         params = upload(scene)
         img, t_final, load = rast.forward(params, cam, st)
@@ -113,6 +132,6 @@ def test_heavy_3m_1080p_sampled_parity():
         excl[y0:y0 + TILE, x0:x0 + TILE] = True
     assert not np.any(mism & ~excl), f"{int((mism & ~excl).sum())} pixels differ in sampled tiles"
     kept = mask & ~excl
-    print(f"heavy-3M-1080p: P={P} sampled tiles={sample.size} (lists with near-threshold "
+    print(f"{label}: P={P} sampled tiles={sample.size} (lists with near-threshold "
           f"differences: {logged}) max|err| kept={err[kept].max():.2e} "
           f"near pixels={int((mism & excl).sum())}/{int(mask.sum())}")
