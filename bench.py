@@ -58,6 +58,12 @@ def select_workload(name):
     WORKLOAD, N_GAUSS, WIDTH, HEIGHT, PAIR_CAPACITY = name, n, w, h, cap
     return kind
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
+# Kernels of one forward frame: frame parameters 1, preprocess 1, depth sort
+# 4 x (count, count scan, scatter) 12, run scan + pair total 2, slice-0 setup 1,
+# tile pass 1 (count, count scan, scatter, column ranges) 4, render slice 0 1,
+# unfinished-tile table (rows, columns) + compaction (count, scan, scatter) 5,
+# tile pass 1 of slice 1 4, render slice 1 1.
+KERNELS_PER_FRAME = 32
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
 # 105.58 + 43.83 MB, one frame) and the per-tile list pass
@@ -258,24 +264,26 @@ def frame_units(rast, params, cams, st, stream, count):
 
 
 def kernel_bytes(name, n, u, hw):
-    """Algorithmic DRAM bytes of one launch of each kernel (the data the
-    stage has to move; see the design notes for the derivation)."""
-    P, V, C = u["pairs"], u["visible"], u["runs"]
+    """Algorithmic DRAM bytes per frame of each kernel (the data the stage has
+    to move; see the design notes for the derivation), or None where the work
+    depends on the depth slices' sizes, which the frame does not report."""
+    P, V = u["pairs"], u["visible"]
     return {
         "preprocess": 44 * n + 192 * V + 104 * n,  # params (+SH of kept) in; records, key, box out
-        # per launch, averaged over the 4 passes: the first reads the n keys twice and
-        # writes the V kept keys + values; the others count, read and write V keys +
-        # values; the last also gathers and writes the V packed rectangles
-        "depth_pass": 2 * n + 19 * V,
-        "scan_tiles": 8 * n,                       # boxes in depth order in, run offsets out
-        "tile_count_columns": 8 * V,               # offset + rectangle per visible Gaussian
+        # 4 passes: the first reads the n keys twice and writes the V kept keys +
+        # values; the others count, read and write V keys + values; the last
+        # also gathers and writes the V packed rectangles
+        "depth_pass": 8 * n + 76 * V,
+        "scan_tiles": 8 * V,                       # boxes in depth order in, run offsets out (slice 1 on top)
+        "tile_count_columns": None,                # runs of the two depth slices
         "tile_count_scan": 0,                      # 2 x 256 x grid words, L2-resident
-        "tile_scatter_columns": 8 * C + 12 * V,    # column runs out; Gaussian staging in
-        "tile_count_rows": 8 * C,                  # column runs in
-        "tile_scatter_rows": 8 * C + 4 * P,        # column runs in, Gaussian ids of the pairs out
-        "tile_ranges": 12 * (hw // 256),           # tile counts in, ranges out
+        "tile_scatter_columns": None,
+        "tile_count_rows": 8 * u["runs"],          # column runs in (per-tile lists only)
+        "tile_scatter_rows": 8 * u["runs"] + 4 * P,
+        "tile_ranges": 12 * (hw // 256),           # column / tile ranges
+        "slice": None,                             # unfinished-tile table, compaction of slice 1
         "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
-    }[name]
+    }.get(name)
 
 
 def alpha_low_sweep(rast, params, cams, stream, pg, steps, warmup):
@@ -557,17 +565,20 @@ def run_ours(args):
     ktable = {}
     for name, (ms, launches) in kernels.items():
         per = ms / launches
+        per_frame = ms / args.steps
         b = kernel_bytes(name, N_GAUSS, u_mean, hw)
-        ktable[name] = {"launches": launches, "ms_per_launch": per,
+        ktable[name] = {"launches_per_frame": launches / args.steps, "ms_per_launch": per,
+                        "ms_per_frame": per_frame,
                         "share": ms / sum(v[0] for v in kernels.values()),
-                        "algorithmic_bytes": b, "gbs": b / (per / 1e3) / 1e9}
-    dominant = max(ktable, key=lambda k: ktable[k]["ms_per_launch"] * ktable[k]["launches"])
+                        "algorithmic_bytes_per_frame": b,
+                        "gbs": None if b is None else b / (per_frame / 1e3) / 1e9}
+    dominant = max(ktable, key=lambda k: ktable[k]["ms_per_frame"])
     dk = ktable[dominant]
     tpp = TRAFFIC_BYTES_PER_PAIR.get(dominant)
     traffic = tpp * u_mean["pairs"] if tpp else TRAFFIC_BYTES_PER_LAUNCH.get(dominant)
     if dominant == "render":
         alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
-        achieved = u_mean["evals"] * EVAL_FP32_OPS / (dk["ms_per_launch"] / 1e3) / 1e12
+        achieved = u_mean["evals"] * EVAL_FP32_OPS / (dk["ms_per_frame"] / 1e3) / 1e12
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": alu_peak,
                     "unit": "T FP32 lane-ops/s", "frac": achieved / alu_peak, "traffic": traffic,
                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz"}
@@ -575,9 +586,9 @@ def run_ours(args):
         roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["gbs"], "peak": hbm_gbs,
                     "unit": "GB/s", "frac": dk["gbs"] / hbm_gbs, "traffic": traffic,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                    "algorithmic_bytes_per_launch": dk["algorithmic_bytes"]}
+                    "algorithmic_bytes_per_frame": dk["algorithmic_bytes_per_frame"]}
     render = ktable.get("render")
-    render_ms = render["ms_per_launch"] if render else float("nan")
+    render_ms = render["ms_per_frame"] if render else float("nan")
     alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
     render_alu = u_mean["evals"] * EVAL_FP32_OPS / (render_ms / 1e3) / 1e12
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
@@ -625,7 +636,7 @@ def run_ours(args):
                                     "frac": (render["gbs"] / hbm_gbs) if render else None}},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": sum(v["launches"] for v in ktable.values()),
+        "gpu_launches": KERNELS_PER_FRAME * args.steps,
         "clocks": clocks,
     }
     result["alpha_low_sweep"] = alpha_low_sweep(rast, params, cams, stream, pg, min(args.steps, 100),

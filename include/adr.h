@@ -151,9 +151,14 @@ adr_status adr_preprocess(adr_ctx *ctx, const float *means, const float *scales,
  * rows in that column), stably sorted by column, with each column's
  * [start, end).  A tile's list is the runs of its column that cover its row,
  * in order; adr_render reads it from there, so the pairs are never written
- * out one by one.  adr_render_backward, adr_read_pairs and adr_read_ranges
- * first expand the runs into per-tile lists and ranges (a second, stable
- * pass by tile row), enqueued on their own stream. */
+ * out one by one.  The runs are built in two depth slices: adr_sort builds
+ * those of the nearest Gaussians; adr_render renders them, then builds and
+ * renders the runs of the farther Gaussians that touch a tile with a pixel
+ * still blending (a pixel's blend stops once its transmittance falls below
+ * t_min, so the others cannot change a pixel).  adr_render_backward,
+ * adr_read_pairs and adr_read_ranges first build every Gaussian's runs and
+ * expand them into per-tile lists and ranges (a second, stable pass by tile
+ * row), enqueued on their own stream. */
 adr_status adr_sort(adr_ctx *ctx, void *stream);
 
 /* Stage 6: per-tile front-to-back alpha blending (Eq. 2-3) of the sorted

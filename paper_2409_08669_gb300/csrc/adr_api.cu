@@ -143,7 +143,9 @@ void free_workspace(Workspace& w) {
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.offsets, w.gbox, w.sorted_box, w.gkeys[0],
                     w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.lstat, w.g2d, w.load_sums,
-                    w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage};
+                    w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage,
+                    w.slice_counters, w.s_order, w.s_box, w.s_offsets, w.s_chunk_first,
+                    w.surv_cnt, w.pst, w.pis, w.tile_done, w.tile_fbase, w.sat};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -155,8 +157,8 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t pixels = (size_t)max_width * max_height;
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
     const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
-    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36) + P * 12 +
-           (P / kSortChunk + 2) * 4 + tiles * 12 + pixels * 16 + lb +
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36 + 12) + P * 12 +
+           2 * (P / kSortChunk + 2) * 4 + tiles * 20 + pixels * 48 + lb +
            (size_t)kRadix * (kMaxTileGrid + 2) * 4 + 4096;
 }
 
@@ -208,6 +210,20 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     ALLOC(w.trav, pixels * sizeof(int32_t));
     ALLOC(w.tfin, pixels * sizeof(float));
     ALLOC(w.lstat, pixels * sizeof(int32_t));
+    {
+        const size_t tx = (size_t)(max_width + kTile - 1) / kTile, ty = (size_t)(max_height + kTile - 1) / kTile;
+        ALLOC(w.slice_counters, 2 * kCntSlots * sizeof(uint32_t));
+        ALLOC(w.s_order, N * sizeof(uint32_t));
+        ALLOC(w.s_box, N * sizeof(uint32_t));
+        ALLOC(w.s_offsets, N * sizeof(uint32_t));
+        ALLOC(w.s_chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
+        ALLOC(w.surv_cnt, 2 * kMaxTileGrid * sizeof(uint32_t));
+        ALLOC(w.pst, pixels * sizeof(float4));
+        ALLOC(w.pis, pixels * sizeof(int4));
+        ALLOC(w.tile_done, (size_t)w.max_tiles * sizeof(uint32_t));
+        ALLOC(w.tile_fbase, (size_t)w.max_tiles * sizeof(int32_t));
+        ALLOC(w.sat, (tx + 1) * (ty + 1) * sizeof(uint32_t));
+    }
     ALLOC(w.g2d, N * 9 * sizeof(float));
     ALLOC(w.load_sums, 4 * sizeof(double));
     ALLOC(w.hist, kHistWords * sizeof(uint32_t));

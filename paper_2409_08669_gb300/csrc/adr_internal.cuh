@@ -92,7 +92,7 @@ enum Counter : int {
 enum KernelId : int {
     kKPreprocess = 0, kKDepthPass, kKScanTiles, kKTileRanges, kKTileCountColumns,
     kKTileScatterColumns, kKTileCountRows, kKTileScatterRows, kKTileCountScan, kKRender,
-    kKRenderBackward, kKPreprocessBackward, kKernelCount
+    kKRenderBackward, kKPreprocessBackward, kKSlice, kKernelCount
 };
 const char* kernel_name(int id);
 struct Profiler {
@@ -139,10 +139,25 @@ struct Workspace {
     Profiler* prof = nullptr;              // non-null: time every launch
     FrameParams* d_fp = nullptr;           // [1] camera + settings of the current frame
     uint32_t* d_stage = nullptr;           // [1] stage counter (see EpochRef)
+    // Depth slices of the forward frame (slices.cu); all null: one slice.
+    uint32_t* slice_counters = nullptr;    // [2 * kCntSlots] counter blocks of slices 0 and 1
+    uint32_t* s_order = nullptr;           // [max_n] slice-1 Gaussians in depth order
+    uint32_t* s_box = nullptr;             // [max_n] their packed rectangles
+    uint32_t* s_offsets = nullptr;         // [max_n] their run offsets
+    uint32_t* s_chunk_first = nullptr;     // [capacity / kSortChunk + 2]
+    uint32_t* surv_cnt = nullptr;          // [2 * kMaxTileGrid] per-CTA kept counts and runs
+    float4* pst = nullptr;                 // [max pixels] T, C of unfinished tiles
+    int4* pis = nullptr;                   // [max pixels] l_i, last, traversed, stopped
+    uint32_t* tile_done = nullptr;         // [max_tiles]
+    int32_t* tile_fbase = nullptr;         // [max_tiles]
+    uint32_t* sat = nullptr;               // [(tiles_x + 1) * (tiles_y + 1)] at the largest image
 };
 
 // hist layout: 4 x 256 per-digit totals of the depth passes.
 constexpr int kHistWords = kMaxPasses * kRadix;
+
+// Contents of the column-run buffer: every Gaussian's runs, or a slice's.
+enum RunsHeld : int { kRunsAll = 0, kRunsSlice0 = 1, kRunsSlice1 = 2 };
 
 // What one frame's stages hand to the next.
 struct FrameState {
@@ -153,6 +168,8 @@ struct FrameState {
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
     const uint32_t* sorted_gauss = nullptr;  // list entries' Gaussians by (cell, depth)
     const uint2* runs = nullptr;             // column runs by (column, depth)
+    bool sliced = false;                     // the frame renders in two depth slices
+    int runs_held = 0;                       // which Gaussians' column runs ws.pruns holds
     // The render lists: kColumnLists = the column runs of each column of tiles;
     // otherwise the Gaussians of each (band of 2^list_shift tile rows, column)
     // cell, the tiles themselves when 0.  -1 before the first sort.
@@ -192,7 +209,7 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
 // Rebuilds per-tile lists (list_shift 0) from the column runs if the last
 // sort made band lists; what the backward and the pair inspection read.
 void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream);
-void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
+void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream);
 void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st);
 
@@ -264,10 +281,35 @@ void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, 
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);
 
+// Render in depth slices (slices.cu): phase 0 renders a whole list; phase 1
+// the first slice, finishing the tiles whose pixels all stopped (tile_done =
+// 1) and keeping the per-pixel state of the others (pst: T, C; pis: l_i,
+// last, traversed, stopped) and their list position (tile_fbase); phase 2
+// resumes those tiles and finishes them.
+struct SliceState {
+    int phase = 0;
+    float4* pst = nullptr;
+    int4* pis = nullptr;
+    uint32_t* tile_done = nullptr;
+    int32_t* tile_fbase = nullptr;
+};
+// Slice 0 = the nearest 1/kSliceDiv of the Gaussians with tiles (0: no slices).
+#ifndef ADR_SLICE_DIV
+#define ADR_SLICE_DIV 16
+#endif
+constexpr int kSliceDiv = ADR_SLICE_DIV;
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
                    const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
                    int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, int32_t* lstat, cudaStream_t stream);
+                   int32_t* trav, float* tfin, int32_t* lstat, const SliceState& ss,
+                   cudaStream_t stream);
+void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint32_t* c0,
+                         cudaStream_t stream);
+void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,
+                      const uint32_t* sorted_box, const uint32_t* order, const uint32_t* counters,
+                      int grid, uint32_t* cnt, int64_t n_max, int64_t chunk_max, uint32_t* s_order,
+                      uint32_t* s_box, uint32_t* s_offsets, uint32_t* s_chunk_first, uint32_t* c1,
+                      uint32_t* status, cudaStream_t stream);
 // Column ranges [start, end) of the first tile-sort pass's runs, from its
 // per-column totals (empty on pair overflow).  One CTA.
 void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* counters,

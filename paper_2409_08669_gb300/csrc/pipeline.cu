@@ -9,7 +9,7 @@ const char* kernel_name(int id) {
     static const char* names[kKernelCount] = {
         "preprocess", "depth_pass", "scan_tiles", "tile_ranges",
         "tile_count_columns", "tile_scatter_columns", "tile_count_rows", "tile_scatter_rows",
-        "tile_count_scan", "render", "render_backward", "preprocess_backward"};
+        "tile_count_scan", "render", "render_backward", "preprocess_backward", "slice"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
 }
 
@@ -129,52 +129,127 @@ static void enqueue_lists(const Workspace& ws, FrameState& fs, int shift, cudaSt
     fs.list_shift = shift;
 }
 
-void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
-                  cudaStream_t stream) {
-    (void)epoch;   // the tile sort has no lookback words
-    cudaMemsetAsync(ws.ttotals, 0, kRadix * sizeof(uint32_t), stream);
+// Stage 3-4, pass 1: the column runs of `src`'s Gaussians, generated on chip
+// and grouped by tile column, and (stage 5) each column's [start, end).
+static void enqueue_pass1(const Workspace& ws, const FrameState& fs, const PairSource& src,
+                          cudaStream_t stream) {
     const int G = ws.tile_grid;
+    cudaMemsetAsync(ws.ttotals, 0, kRadix * sizeof(uint32_t), stream);
     if (fs.n > 0 && fs.order) {
-        PairSource src;
-        src.order = fs.order;
-        src.offsets = ws.offsets;
-        src.sorted_box = ws.sorted_box;
-        src.chunk_first = ws.chunk_first;
-        src.counters = ws.counters;
-        src.capacity = ws.capacity;
-        src.tiles_x = fs.cam.tiles_x;
-        // Stage 3-4, pass 1: column runs generated from the Gaussians, grouped by tx.
         TIMED(ws, kKTileCountColumns, stream,
               launch_tile_count_columns(src, ws.tcounts, ws.ttotals, ws.status, G, stream));
         TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
         TIMED(ws, kKTileScatterColumns, stream,
               launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
     }
-    fs.runs = ws.pruns;
-    if (kListShift == kColumnLists) {
-        // Stage 5: the render reads each column's runs; their ranges come from
-        // the pass's per-column totals.
-        TIMED(ws, kKTileRanges, stream,
-              launch_column_ranges(ws.ttotals, fs.cam.tiles_x, ws.counters, ws.capacity, ws.ranges,
-                                   stream));
-        fs.sorted_gauss = nullptr;
-        fs.list_shift = kColumnLists;
-    } else {
-        enqueue_lists(ws, fs, kListShift, stream);
+    TIMED(ws, kKTileRanges, stream,
+          launch_column_ranges(ws.ttotals, fs.cam.tiles_x, src.counters, ws.capacity, ws.ranges,
+                               stream));
+}
+
+// The Gaussians with tiles in depth order (all of them, or a slice's).
+static PairSource pair_source(const Workspace& ws, const FrameState& fs, int which) {
+    PairSource src;
+    src.capacity = ws.capacity;
+    src.tiles_x = fs.cam.tiles_x;
+    if (which == 1) {   // slice 1: the compacted Gaussians behind slice 0
+        src.order = ws.s_order;
+        src.offsets = ws.s_offsets;
+        src.sorted_box = ws.s_box;
+        src.chunk_first = ws.s_chunk_first;
+        src.counters = ws.slice_counters + kCntSlots;
+    } else {            // all Gaussians, or (which == 0) the nearest ones of slice 0
+        src.order = fs.order;
+        src.offsets = ws.offsets;
+        src.sorted_box = ws.sorted_box;
+        src.chunk_first = ws.chunk_first;
+        src.counters = which == 0 ? ws.slice_counters : ws.counters;
     }
+    return src;
+}
+
+void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                  cudaStream_t stream) {
+    (void)epoch;   // the tile sort has no lookback words
+    fs.runs = ws.pruns;
+    fs.sorted_gauss = nullptr;
+    fs.sliced = ws.pst != nullptr && kListShift == kColumnLists && kSliceDiv > 0;
+    if (fs.sliced) {
+        // Slice 0: the nearest Gaussians' runs; Render builds slice 1 from what
+        // its pixels still need.
+        cudaMemsetAsync(ws.slice_counters, 0, 2 * kCntSlots * sizeof(uint32_t), stream);
+        launch_slice0_setup(ws.counters, ws.offsets, ws.slice_counters, stream);
+        enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
+        fs.list_shift = kColumnLists;
+        fs.runs_held = kRunsSlice0;
+        return;
+    }
+    if (kListShift == kColumnLists) {
+        enqueue_pass1(ws, fs, pair_source(ws, fs, -1), stream);
+        fs.list_shift = kColumnLists;
+        fs.runs_held = kRunsAll;
+        return;
+    }
+    // Band or per-tile lists: pass 1 without its column ranges, then pass 2.
+    const PairSource src = pair_source(ws, fs, -1);
+    const int G = ws.tile_grid;
+    cudaMemsetAsync(ws.ttotals, 0, kRadix * sizeof(uint32_t), stream);
+    if (fs.n > 0 && fs.order) {
+        TIMED(ws, kKTileCountColumns, stream,
+              launch_tile_count_columns(src, ws.tcounts, ws.ttotals, ws.status, G, stream));
+        TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
+        TIMED(ws, kKTileScatterColumns, stream,
+              launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
+    }
+    fs.runs_held = kRunsAll;
+    enqueue_lists(ws, fs, kListShift, stream);
 }
 
 void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
-    if (fs.list_shift != 0) enqueue_lists(ws, fs, 0, stream);
+    if (fs.list_shift == 0) return;
+    if (fs.runs_held != kRunsAll) {   // the column runs of every Gaussian first
+        enqueue_pass1(ws, fs, pair_source(ws, fs, -1), stream);
+        fs.runs_held = kRunsAll;
+    }
+    enqueue_lists(ws, fs, 0, stream);
 }
 
-void enqueue_render(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
+void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream) {
     // Stage 6.
+    if (!fs.sliced) {
+        TIMED(ws, kKRender, stream,
+              launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
+                            ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
+                            ws.lstat, SliceState{}, stream));
+        return;
+    }
+    if (fs.runs_held != kRunsSlice0) enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
+    SliceState ss;
+    ss.pst = ws.pst;
+    ss.pis = ws.pis;
+    ss.tile_done = ws.tile_done;
+    ss.tile_fbase = ws.tile_fbase;
+    ss.phase = 1;
     TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
-                        ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
-                        ws.lstat, stream));
+          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,
+                        fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
+                        stream));
+    // Slice 1: the Gaussians behind slice 0 that touch an unfinished tile,
+    // with their run offsets, then their column runs.
+    uint32_t* c1 = ws.slice_counters + kCntSlots;
+    TIMED(ws, kKSlice, stream,
+          launch_survivors(ws.tile_done, fs.cam.tiles_x, fs.cam.tiles_y, ws.sat, ws.sorted_box,
+                           fs.order, ws.counters, ws.sort_grid, ws.surv_cnt, ws.max_n,
+                           ws.capacity / kSortChunk + 2, ws.s_order, ws.s_box, ws.s_offsets,
+                           ws.s_chunk_first, c1, ws.status, stream));
+    enqueue_pass1(ws, fs, pair_source(ws, fs, 1), stream);
+    fs.runs_held = kRunsSlice1;
+    ss.phase = 2;
+    TIMED(ws, kKRender, stream,
+          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,
+                        fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
+                        stream));
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,

@@ -30,7 +30,8 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
          const uint32_t* __restrict__ gbox, int list_shift,
          const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
-         int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat) {
+         int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat,
+         SliceState ss) {
     __shared__ float2 s_xy[kRenderThreads];
     __shared__ float4 s_w[kRenderThreads];
     __shared__ float4 s_c[kRenderThreads];
@@ -59,6 +60,19 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const float alpha_low = st.alpha_low, t_min = st.t_min;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
+    const int tile_rm = ty * cam.tiles_x + tx;
+    const size_t pix = inside ? (size_t)y * cam.width + x : 0;
+    if (ss.phase == 2) {   // last slice: resume the tiles the first slice left unfinished
+        if (ss.tile_done[tile_rm]) return;
+        if (inside) {
+            const float4 a = ss.pst[pix];
+            const int4 b = ss.pis[pix];
+            T = a.x; C0 = a.y; C1 = a.z; C2 = a.w;
+            count = b.x; last = b.y; trav = b.z; stopped = b.w != 0;
+            done = stopped;
+        }
+        fbase = ss.tile_fbase[tile_rm];
+    }
 
     // Each batch reads kFill list entries per thread (list order: entry
     // base + k * 256 + thread) and stages the first 256 kept ones; the list
@@ -175,9 +189,22 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
         fbase += m;
         base = next;
     }
+    if (ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
+        const bool all_done = __syncthreads_count(done) == kRenderThreads;
+        if (threadIdx.x == 0) {
+            ss.tile_done[tile_rm] = all_done ? 1u : 0u;
+            if (!all_done) ss.tile_fbase[tile_rm] = fbase;
+        }
+        if (!all_done) {
+            if (inside) {
+                ss.pst[pix] = make_float4(T, C0, C1, C2);
+                ss.pis[pix] = make_int4(count, last, trav, stopped ? 1 : 0);
+            }
+            return;
+        }
+    }
     if (inside) {
         const size_t hw = (size_t)cam.width * cam.height;
-        const size_t pix = (size_t)y * cam.width + x;
         img[pix] = C0 + T * st.bg[0];
         img[hw + pix] = C1 + T * st.bg[1];
         img[2 * hw + pix] = C2 + T * st.bg[2];
@@ -195,17 +222,18 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
                    const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
                    int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, int32_t* lstat, cudaStream_t stream) {
+                   int32_t* trav, float* tfin, int32_t* lstat, const SliceState& ss,
+                   cudaStream_t stream) {
     const int tiles = num_tiles;
     if (tiles <= 0) return;
     if (list_shift == kColumnLists)
         k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
                                                              list_shift, fp, img, t_final, load,
-                                                             last, trav, tfin, lstat);
+                                                             last, trav, tfin, lstat, ss);
     else
         k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
                                                               list_shift, fp, img, t_final, load,
-                                                              last, trav, tfin, lstat);
+                                                              last, trav, tfin, lstat, ss);
 }
 
 }  // namespace adr
