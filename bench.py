@@ -60,10 +60,10 @@ def select_workload(name):
 EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation in Render
 # Kernels of one forward frame: frame parameters 1, preprocess 1, depth sort
 # 4 x (count, count scan, scatter) 12, run scan + pair total 2, slice-0 setup 1,
-# tile pass 1 (count, count scan, scatter, column ranges) 4, render slice 0 1,
+# tile pass 1 (count, count scan, scatter) 3, render slice 0 1,
 # unfinished-tile table (rows, columns) + compaction (count, scan, scatter) 5,
-# tile pass 1 of slice 1 4, render slice 1 1.
-KERNELS_PER_FRAME = 32
+# tile pass 1 of slice 1 3, render slice 1 1 (each render derives its column ranges).
+KERNELS_PER_FRAME = 30
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
 # 105.58 + 43.83 MB, one frame) and the per-tile list pass

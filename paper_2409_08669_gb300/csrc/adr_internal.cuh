@@ -292,6 +292,11 @@ struct SliceState {
     int4* pis = nullptr;
     uint32_t* tile_done = nullptr;
     int32_t* tile_fbase = nullptr;
+    // Column lists: the pass's per-column run totals and the counters whose
+    // pair count flags an overflow (the lists are then empty).
+    const uint32_t* col_totals = nullptr;
+    const uint32_t* col_counters = nullptr;
+    int64_t capacity = 0;
 };
 // Slice 0 = the nearest 1/kSliceDiv of the Gaussians with tiles (0: no slices).
 #ifndef ADR_SLICE_DIV
@@ -310,10 +315,7 @@ void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint3
                       int grid, uint32_t* cnt, int64_t n_max, int64_t chunk_max, uint32_t* s_order,
                       uint32_t* s_box, uint32_t* s_offsets, uint32_t* s_chunk_first, uint32_t* c1,
                       uint32_t* status, cudaStream_t stream);
-// Column ranges [start, end) of the first tile-sort pass's runs, from its
-// per-column totals (empty on pair overflow).  One CTA.
-void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* counters,
-                          int64_t capacity, uint2* ranges, cudaStream_t stream);
+
 
 // Backward (backward.cu).
 void launch_render_backward(const uint2* ranges, const uint32_t* sorted_gauss, const float4* rec,

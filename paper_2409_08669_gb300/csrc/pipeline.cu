@@ -130,7 +130,8 @@ static void enqueue_lists(const Workspace& ws, FrameState& fs, int shift, cudaSt
 }
 
 // Stage 3-4, pass 1: the column runs of `src`'s Gaussians, generated on chip
-// and grouped by tile column, and (stage 5) each column's [start, end).
+// and grouped by tile column (stage 5, each column's [start, end), is the
+// prefix of the per-column totals, which Render takes itself).
 static void enqueue_pass1(const Workspace& ws, const FrameState& fs, const PairSource& src,
                           cudaStream_t stream) {
     const int G = ws.tile_grid;
@@ -142,9 +143,6 @@ static void enqueue_pass1(const Workspace& ws, const FrameState& fs, const PairS
         TIMED(ws, kKTileScatterColumns, stream,
               launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
     }
-    TIMED(ws, kKTileRanges, stream,
-          launch_column_ranges(ws.ttotals, fs.cam.tiles_x, src.counters, ws.capacity, ws.ranges,
-                               stream));
 }
 
 // The Gaussians with tiles in depth order (all of them, or a slice's).
@@ -217,19 +215,23 @@ void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream
 void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream) {
     // Stage 6.
+    SliceState ss;
+    ss.col_totals = ws.ttotals;
+    ss.capacity = ws.capacity;
     if (!fs.sliced) {
+        ss.col_counters = ws.counters;
         TIMED(ws, kKRender, stream,
               launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
                             ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
-                            ws.lstat, SliceState{}, stream));
+                            ws.lstat, ss, stream));
         return;
     }
     if (fs.runs_held != kRunsSlice0) enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
-    SliceState ss;
     ss.pst = ws.pst;
     ss.pis = ws.pis;
     ss.tile_done = ws.tile_done;
     ss.tile_fbase = ws.tile_fbase;
+    ss.col_counters = ws.slice_counters;
     ss.phase = 1;
     TIMED(ws, kKRender, stream,
           launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,
@@ -245,6 +247,7 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
                            ws.s_chunk_first, c1, ws.status, stream));
     enqueue_pass1(ws, fs, pair_source(ws, fs, 1), stream);
     fs.runs_held = kRunsSlice1;
+    ss.col_counters = c1;
     ss.phase = 2;
     TIMED(ws, kKRender, stream,
           launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,

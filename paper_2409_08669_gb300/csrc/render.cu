@@ -40,6 +40,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     __shared__ uint32_t s_off[kRunFill * (kRenderThreads / 32)];  // their exclusive prefix
     __shared__ uint32_t s_total;
     __shared__ uint32_t s_next;
+    __shared__ uint2 s_range;
 
     const CamDev cam = fp->cam;
     const SetDev st = fp->st;
@@ -52,8 +53,9 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
     const float fx = (float)lx, fy = (float)ly;
 
-    // The list of the tile's cell: its column, its (band, column), or the tile itself.
-    const uint2 range = ranges[kRuns ? tx : (ty >> list_shift) * cam.tiles_x + tx];
+    // The list of the tile's cell: its (band, column) or the tile itself; for
+    // column runs, see below.
+    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[(ty >> list_shift) * cam.tiles_x + tx];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int32_t count = 0, last = 0, trav = 0;
     bool done = !inside, stopped = false;
@@ -72,6 +74,20 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
             done = stopped;
         }
         fbase = ss.tile_fbase[tile_rm];
+    }
+    if (kRuns) {   // column tx's runs start after the runs of the columns before it
+        if (warp == 0) {
+            uint32_t before = 0;
+            for (int c = lane; c < tx; c += 32) before += ss.col_totals[c];
+            before = __reduce_add_sync(0xffffffffu, before);
+            if (lane == 0) {
+                const bool overflow = (int64_t)ss.col_counters[kCntPairs] > ss.capacity;
+                s_range = overflow ? make_uint2(0u, 0u)
+                                   : make_uint2(before, before + ss.col_totals[tx]);
+            }
+        }
+        __syncthreads();
+        range = s_range;
     }
 
     // Each batch reads kFill list entries per thread (list order: entry

@@ -656,26 +656,6 @@ void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32
     k_tile_ranges<<<1, kRangeThreads, 0, stream>>>(tile_counts, num_tiles, counters, capacity, ranges);
 }
 
-// Column ranges from the first pass's per-column run totals: one thread per
-// column (tiles_x <= 256), exclusive scan over the columns.
-__global__ void __launch_bounds__(kRadix)
-k_column_ranges(const uint32_t* __restrict__ totals, int tiles_x, const uint32_t* __restrict__ counters,
-                int64_t capacity, uint2* __restrict__ ranges) {
-    __shared__ uint32_t s_w[kRadix / 32];
-    const bool overflow = (int64_t)counters[kCntPairs] > capacity;
-    const int tid = threadIdx.x;
-    const uint32_t v = (tid < tiles_x && !overflow) ? totals[tid] : 0u;
-    uint32_t total;
-    const uint32_t start = block_exclusive_scan(v, s_w, total);
-    if (tid < tiles_x) ranges[tid] = make_uint2(start, start + v);
-}
-
-void launch_column_ranges(const uint32_t* totals, int tiles_x, const uint32_t* counters,
-                          int64_t capacity, uint2* ranges, cudaStream_t stream) {
-    if (tiles_x <= 0) return;
-    k_column_ranges<<<1, kRadix, 0, stream>>>(totals, tiles_x, counters, capacity, ranges);
-}
-
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
                               int grid, int num_bands, int shift, cudaStream_t stream) {
