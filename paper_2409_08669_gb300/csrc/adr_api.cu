@@ -145,7 +145,7 @@ void free_workspace(Workspace& w) {
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.lstat, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage,
                     w.slice_counters, w.s_order, w.s_box, w.s_offsets, w.s_chunk_first,
-                    w.surv_cnt, w.pst, w.pis, w.tile_done, w.tile_fbase, w.sat};
+                    w.surv_cnt, w.surv_flag, w.pst, w.pis, w.tile_done, w.tile_fbase, w.sat};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -218,6 +218,7 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
         ALLOC(w.s_offsets, N * sizeof(uint32_t));
         ALLOC(w.s_chunk_first, (P / kSortChunk + 2) * sizeof(uint32_t));
         ALLOC(w.surv_cnt, 2 * kMaxTileGrid * sizeof(uint32_t));
+        ALLOC(w.surv_flag, N);
         ALLOC(w.pst, pixels * sizeof(float4));
         ALLOC(w.pis, pixels * sizeof(int4));
         ALLOC(w.tile_done, (size_t)w.max_tiles * sizeof(uint32_t));

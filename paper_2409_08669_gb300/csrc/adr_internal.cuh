@@ -146,6 +146,7 @@ struct Workspace {
     uint32_t* s_offsets = nullptr;         // [max_n] their run offsets
     uint32_t* s_chunk_first = nullptr;     // [capacity / kSortChunk + 2]
     uint32_t* surv_cnt = nullptr;          // [2 * kMaxTileGrid] per-CTA kept counts and runs
+    uint8_t* surv_flag = nullptr;          // [max_n] kept flag per depth-order position
     float4* pst = nullptr;                 // [max pixels] T, C of unfinished tiles
     int4* pis = nullptr;                   // [max pixels] l_i, last, traversed, stopped
     uint32_t* tile_done = nullptr;         // [max_tiles]
@@ -312,9 +313,9 @@ void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint
                          cudaStream_t stream);
 void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,
                       const uint32_t* sorted_box, const uint32_t* order, const uint32_t* counters,
-                      int grid, uint32_t* cnt, int64_t n_max, int64_t chunk_max, uint32_t* s_order,
-                      uint32_t* s_box, uint32_t* s_offsets, uint32_t* s_chunk_first, uint32_t* c1,
-                      uint32_t* status, cudaStream_t stream);
+                      int grid, uint32_t* cnt, uint8_t* keep_flag, int64_t n_max, int64_t chunk_max,
+                      uint32_t* s_order, uint32_t* s_box, uint32_t* s_offsets,
+                      uint32_t* s_chunk_first, uint32_t* c1, uint32_t* status, cudaStream_t stream);
 
 
 // Backward (backward.cu).

@@ -242,7 +242,7 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
     uint32_t* c1 = ws.slice_counters + kCntSlots;
     TIMED(ws, kKSlice, stream,
           launch_survivors(ws.tile_done, fs.cam.tiles_x, fs.cam.tiles_y, ws.sat, ws.sorted_box,
-                           fs.order, ws.counters, ws.sort_grid, ws.surv_cnt, ws.max_n,
+                           fs.order, ws.counters, ws.sort_grid, ws.surv_cnt, ws.surv_flag, ws.max_n,
                            ws.capacity / kSortChunk + 2, ws.s_order, ws.s_box, ws.s_offsets,
                            ws.s_chunk_first, c1, ws.status, stream));
     enqueue_pass1(ws, fs, pair_source(ws, fs, 1), stream);

@@ -126,14 +126,17 @@ __device__ __forceinline__ uint32_t box_runs(uint32_t box) { return ((box >> 16)
 // Per CTA: the kept Gaussians and their column runs (cnt[b], cnt[grid + b]).
 __global__ void __launch_bounds__(kSurvThreads)
 k_surv_count(const uint32_t* __restrict__ sorted_box, const uint32_t* __restrict__ counters,
-             const uint32_t* __restrict__ sat, int tiles_x, int grid, uint32_t* __restrict__ cnt) {
+             const uint32_t* __restrict__ sat, int tiles_x, int grid, uint32_t* __restrict__ cnt,
+             uint8_t* __restrict__ keep_flag) {
     __shared__ uint32_t s_w[2][kSurvThreads / 32];
     uint32_t a, e;
     surv_span(counters, grid, a, e);
     uint32_t c = 0, r = 0;
     for (uint32_t i = a + threadIdx.x; i < e; i += kSurvThreads) {
         const uint32_t box = sorted_box[i];
-        if (survives(box, sat, tiles_x + 1)) {
+        const bool keep = survives(box, sat, tiles_x + 1);
+        keep_flag[i] = keep ? 1 : 0;
+        if (keep) {
             ++c;
             r += box_runs(box);
         }
@@ -208,7 +211,7 @@ k_surv_scan(uint32_t* __restrict__ cnt, int grid, const uint32_t* __restrict__ c
 // that starts inside a Gaussian's runs, that Gaussian's position.
 __global__ void __launch_bounds__(kSurvThreads)
 k_surv_scatter(const uint32_t* __restrict__ sorted_box, const uint32_t* __restrict__ order,
-               const uint32_t* __restrict__ counters, const uint32_t* __restrict__ sat, int tiles_x,
+               const uint32_t* __restrict__ counters, const uint8_t* __restrict__ keep_flag,
                int grid, const uint32_t* __restrict__ starts, int64_t n_max, int64_t chunk_max,
                uint32_t* __restrict__ s_order, uint32_t* __restrict__ s_box,
                uint32_t* __restrict__ s_offsets, uint32_t* __restrict__ s_chunk_first,
@@ -220,8 +223,8 @@ k_surv_scatter(const uint32_t* __restrict__ sorted_box, const uint32_t* __restri
     uint32_t out = starts[blockIdx.x], roff = starts[grid + blockIdx.x];
     for (uint32_t b0 = a; b0 < e; b0 += kSurvThreads) {
         const uint32_t i = b0 + tid;
-        const uint32_t box = i < e ? sorted_box[i] : 0xFFFFFFFFu;
-        const bool keep = i < e && survives(box, sat, tiles_x + 1);
+        const bool keep = i < e && keep_flag[i] != 0;
+        const uint32_t box = keep ? sorted_box[i] : 0xFFFFFFFFu;
         const uint32_t w = keep ? box_runs(box) : 0u;
         const uint32_t m = __ballot_sync(0xffffffffu, keep);
         const uint32_t wr = warp_incl_scan(w, lane);
@@ -268,17 +271,18 @@ void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint
 
 void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,
                       const uint32_t* sorted_box, const uint32_t* order, const uint32_t* counters,
-                      int grid, uint32_t* cnt, int64_t n_max, int64_t chunk_max, uint32_t* s_order,
-                      uint32_t* s_box, uint32_t* s_offsets, uint32_t* s_chunk_first, uint32_t* c1,
-                      uint32_t* status, cudaStream_t stream) {
+                      int grid, uint32_t* cnt, uint8_t* keep_flag, int64_t n_max, int64_t chunk_max,
+                      uint32_t* s_order, uint32_t* s_box, uint32_t* s_offsets,
+                      uint32_t* s_chunk_first, uint32_t* c1, uint32_t* status, cudaStream_t stream) {
     const int warps = kSurvThreads / 32;
     k_sat_rows<<<(tiles_y + 1 + warps - 1) / warps, kSurvThreads, 0, stream>>>(tile_done, tiles_x,
                                                                                tiles_y, sat);
     k_sat_cols<<<(tiles_x + 1 + warps - 1) / warps, kSurvThreads, 0, stream>>>(tiles_x, tiles_y, sat);
-    k_surv_count<<<grid, kSurvThreads, 0, stream>>>(sorted_box, counters, sat, tiles_x, grid, cnt);
+    k_surv_count<<<grid, kSurvThreads, 0, stream>>>(sorted_box, counters, sat, tiles_x, grid, cnt,
+                                                    keep_flag);
     k_surv_scan<<<1, kMaxTileGrid / 8, 0, stream>>>(cnt, grid, counters, c1);
-    k_surv_scatter<<<grid, kSurvThreads, 0, stream>>>(sorted_box, order, counters, sat, tiles_x,
-                                                      grid, cnt, n_max, chunk_max, s_order, s_box,
+    k_surv_scatter<<<grid, kSurvThreads, 0, stream>>>(sorted_box, order, counters, keep_flag, grid,
+                                                      cnt, n_max, chunk_max, s_order, s_box,
                                                       s_offsets, s_chunk_first, status);
 }
 
