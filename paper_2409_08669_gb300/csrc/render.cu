@@ -14,6 +14,10 @@
 // pixel has terminated (__syncthreads_count).  Pixel offsets are taken
 // relative to the tile origin so the float-float centre collapses to one
 // well-conditioned float per Gaussian per tile.
+//
+// With depth slices (slices.cu) the kernel runs twice per frame: phase 1 over
+// slice 0's runs finishes the tiles whose pixels all stopped and saves the
+// state of the others; phase 2 resumes those over slice 1's runs.
 #include "adr_internal.cuh"
 
 namespace adr {
