@@ -623,9 +623,13 @@ def run_ours(args):
         "evals_per_frame": {"adr_aabb": u_mean["evals"],
                             "plain": statistics.mean(u["evals"] for u in units_plain)},
         "culled_pair_fraction": 1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain),
-        "sort_gpairs_per_s": {"adr_aabb": u_mean["pairs"] / stage_ms["sort_ranges"] / 1e6,
-                              "plain": statistics.mean(u["pairs"] for u in units_plain)
-                              / stage_ms_plain["sort_ranges"] / 1e6},
+        # Pairs put in (tile, depth) order per second by the sorting kernels of a
+        # frame (depth sort, run scan, tile pass 1 of both slices, slice-1
+        # selection); the pairs behind every tile's last stop are never written.
+        "sort_gpairs_per_s": u_mean["pairs"] / sum(
+            ktable[k]["ms_per_frame"] for k in ("depth_pass", "scan_tiles", "tile_count_columns",
+                                                "tile_count_scan", "tile_scatter_columns", "slice")
+            if k in ktable) / 1e6,
         "roofline": roofline,
         "kernels": ktable,
         "render_roofline": {"alu": {"achieved": render_alu, "peak": alu_peak,

@@ -171,23 +171,14 @@ struct FrameState {
     const uint2* runs = nullptr;             // column runs by (column, depth)
     bool sliced = false;                     // the frame renders in two depth slices
     int runs_held = 0;                       // which Gaussians' column runs ws.pruns holds
-    // The render lists: kColumnLists = the column runs of each column of tiles;
-    // otherwise the Gaussians of each (band of 2^list_shift tile rows, column)
-    // cell, the tiles themselves when 0.  -1 before the first sort.
-    int list_shift = -1;
+    int lists = -1;                          // a ListKind; -1 before the first sort
 };
 
-// The lists the render reads.  kColumnLists: each column of tiles reads the
-// column runs of the first tile-sort pass directly (in depth order; a tile's
-// own list is the runs covering its row), and the second pass is not run.
-// 0 .. 7: the second pass groups the Gaussians by bands of 2^shift tile rows
-// (0 = per-tile lists).  Per-tile lists are rebuilt on demand for the
-// backward and the pair inspection.
-constexpr int kColumnLists = 8;
-#ifndef ADR_LIST_SHIFT
-#define ADR_LIST_SHIFT 8
-#endif
-constexpr int kListShift = ADR_LIST_SHIFT;
+// The lists Render reads: the column runs of the first tile-sort pass (each
+// column of tiles reads its runs in depth order; a tile's own list is the
+// runs covering its row, and the second pass is not run), or per-tile lists
+// (the second pass; built on demand for the backward and the pair inspection).
+enum ListKind : int { kListsTiles = 0, kListsColumns = 1 };
 
 // Counts stage calls on the host; every 2^28 calls (before the device tag
 // wraps) clears the lookback words.
@@ -207,8 +198,8 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                         bool set_params = true);
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream);
-// Rebuilds per-tile lists (list_shift 0) from the column runs if the last
-// sort made band lists; what the backward and the pair inspection read.
+// Builds per-tile lists (from every Gaussian's column runs) if the last sort
+// made column lists; what the backward and the pair inspection read.
 void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream);
 void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream);
@@ -261,13 +252,13 @@ void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t
 void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
                                  uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
-                            int tiles_x, int num_cells, int shift, uint32_t* counts, uint32_t* totals,
+                            int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
                             uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
                         int64_t capacity, uint2* ranges, cudaStream_t stream);
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
-                              int grid, int num_bands, int shift, cudaStream_t stream);
+                              int grid, int tiles_y, cudaStream_t stream);
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream);
 
 // Packed tile rectangle: x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24 (tile
@@ -305,10 +296,9 @@ struct SliceState {
 #endif
 constexpr int kSliceDiv = ADR_SLICE_DIV;
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
-                   const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
-                   int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, int32_t* lstat, const SliceState& ss,
-                   cudaStream_t stream);
+                   const float4* rec, int lists, const FrameParams* fp, int num_tiles, float* img,
+                   float* t_final, int32_t* load, int32_t* last, int32_t* trav, float* tfin,
+                   int32_t* lstat, const SliceState& ss, cudaStream_t stream);
 void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint32_t* c0,
                          cudaStream_t stream);
 void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,

@@ -101,32 +101,30 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
                             ep, ws.counters, ws.status, ws.scan_grid, stream));
 }
 
-// Stage 4, pass 2 and stage 5 for lists of 2^shift tile rows: entries grouped
-// by band (ty >> shift) over the column-sorted runs, then the cells' ranges.
-static void enqueue_lists(const Workspace& ws, FrameState& fs, int shift, cudaStream_t stream) {
-    const int bands = ((fs.cam.tiles_y - 1) >> shift) + 1;
-    const int cells = bands * fs.cam.tiles_x;
+// Stage 4, pass 2 and stage 5: the pairs of the column runs grouped by tile
+// row (per-tile lists), then every tile's [start, end).
+static void enqueue_tile_pass2(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
     cudaMemsetAsync(ws.ttotals + kRadix, 0, kRadix * sizeof(uint32_t), stream);
-    cudaMemsetAsync(ws.tile_counts, 0, (size_t)cells * sizeof(uint32_t), stream);
+    cudaMemsetAsync(ws.tile_counts, 0, (size_t)fs.num_tiles * sizeof(uint32_t), stream);
     if (fs.n > 0 && fs.order) {
-        // The runs' entry counts vary, so the pass uses many small run ranges
+        // The runs' pair counts vary, so the pass uses many small run ranges
         // (kMaxTileGrid CTAs) that the hardware schedules as CTAs finish.
         const int G2 = kMaxTileGrid;
         TIMED(ws, kKTileCountRows, stream,
-              launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x, cells, shift,
+              launch_tile_count_rows(ws.pruns, ws.counters, ws.capacity, fs.cam.tiles_x, fs.num_tiles,
                                      ws.tcounts, ws.ttotals + kRadix, ws.tile_counts, ws.status, G2,
                                      stream));
         TIMED(ws, kKTileCountScan, stream,
               launch_tile_count_scan(ws.tcounts, ws.ttotals + kRadix, G2, stream));
         TIMED(ws, kKTileScatterRows, stream,
               launch_tile_scatter_rows(ws.pruns, ws.counters, ws.capacity, ws.tcounts, ws.pgauss,
-                                       ws.status, G2, bands, shift, stream));
+                                       ws.status, G2, fs.cam.tiles_y, stream));
     }
-    // Stage 5: every cell's [start, end) from its entry count.
     TIMED(ws, kKTileRanges, stream,
-          launch_tile_ranges(ws.tile_counts, cells, ws.counters, ws.capacity, ws.ranges, stream));
+          launch_tile_ranges(ws.tile_counts, fs.num_tiles, ws.counters, ws.capacity, ws.ranges,
+                             stream));
     fs.sorted_gauss = ws.pgauss;
-    fs.list_shift = shift;
+    fs.lists = kListsTiles;
 }
 
 // Stage 3-4, pass 1: the column runs of `src`'s Gaussians, generated on chip
@@ -171,45 +169,28 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
     (void)epoch;   // the tile sort has no lookback words
     fs.runs = ws.pruns;
     fs.sorted_gauss = nullptr;
-    fs.sliced = ws.pst != nullptr && kListShift == kColumnLists && kSliceDiv > 0;
+    fs.lists = kListsColumns;
+    fs.sliced = ws.pst != nullptr && kSliceDiv > 0;
     if (fs.sliced) {
         // Slice 0: the nearest Gaussians' runs; Render builds slice 1 from what
         // its pixels still need.
         cudaMemsetAsync(ws.slice_counters, 0, 2 * kCntSlots * sizeof(uint32_t), stream);
         launch_slice0_setup(ws.counters, ws.offsets, ws.slice_counters, stream);
         enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
-        fs.list_shift = kColumnLists;
         fs.runs_held = kRunsSlice0;
-        return;
-    }
-    if (kListShift == kColumnLists) {
+    } else {
         enqueue_pass1(ws, fs, pair_source(ws, fs, -1), stream);
-        fs.list_shift = kColumnLists;
         fs.runs_held = kRunsAll;
-        return;
     }
-    // Band or per-tile lists: pass 1 without its column ranges, then pass 2.
-    const PairSource src = pair_source(ws, fs, -1);
-    const int G = ws.tile_grid;
-    cudaMemsetAsync(ws.ttotals, 0, kRadix * sizeof(uint32_t), stream);
-    if (fs.n > 0 && fs.order) {
-        TIMED(ws, kKTileCountColumns, stream,
-              launch_tile_count_columns(src, ws.tcounts, ws.ttotals, ws.status, G, stream));
-        TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
-        TIMED(ws, kKTileScatterColumns, stream,
-              launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
-    }
-    fs.runs_held = kRunsAll;
-    enqueue_lists(ws, fs, kListShift, stream);
 }
 
 void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
-    if (fs.list_shift == 0) return;
+    if (fs.lists == kListsTiles) return;
     if (fs.runs_held != kRunsAll) {   // the column runs of every Gaussian first
         enqueue_pass1(ws, fs, pair_source(ws, fs, -1), stream);
         fs.runs_held = kRunsAll;
     }
-    enqueue_lists(ws, fs, 0, stream);
+    enqueue_tile_pass2(ws, fs, stream);
 }
 
 void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
@@ -221,9 +202,9 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
     if (!fs.sliced) {
         ss.col_counters = ws.counters;
         TIMED(ws, kKRender, stream,
-              launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, ws.gbox, fs.list_shift,
-                            ws.d_fp, fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin,
-                            ws.lstat, ss, stream));
+              launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, fs.lists, ws.d_fp,
+                            fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
+                            stream));
         return;
     }
     if (fs.runs_held != kRunsSlice0) enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
@@ -234,9 +215,8 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
     ss.col_counters = ws.slice_counters;
     ss.phase = 1;
     TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,
-                        fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
-                        stream));
+          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, kListsColumns, ws.d_fp, fs.num_tiles,
+                        img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss, stream));
     // Slice 1: the Gaussians behind slice 0 that touch an unfinished tile,
     // with their run offsets, then their column runs.
     uint32_t* c1 = ws.slice_counters + kCntSlots;
@@ -250,9 +230,8 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
     ss.col_counters = c1;
     ss.phase = 2;
     TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, ws.gbox, kColumnLists, ws.d_fp,
-                        fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
-                        stream));
+          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, kListsColumns, ws.d_fp, fs.num_tiles,
+                        img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss, stream));
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,

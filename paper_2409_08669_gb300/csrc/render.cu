@@ -5,8 +5,7 @@
 //
 // One CTA of 256 threads per 16x16 tile.  The tile reads a depth-ordered list
 // that holds its own list as a subsequence -- the column runs of its column of
-// tiles (kRuns), or the Gaussians of its column and band of 2^list_shift tile
-// rows (the tile itself when 0).  Each batch reads up to 2048 entries (8 per
+// tiles (kRuns) -- or its own list.  Each batch reads up to 2048 runs (8 per
 // thread), keeps those whose rows hold the tile's row, compacts the first 256
 // kept ones stably into shared memory with their records, and every pixel
 // blends them.  Pixels stop early (transmittance below t_min), so a tile
@@ -31,7 +30,6 @@ template <bool kRuns>
 __global__ void __launch_bounds__(kRenderThreads, 4)   // 4 CTAs per SM: <= 64 registers
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const uint2* __restrict__ runs, const float4* __restrict__ rec,
-         const uint32_t* __restrict__ gbox, int list_shift,
          const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
          int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat,
@@ -57,9 +55,8 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
     const float fx = (float)lx, fy = (float)ly;
 
-    // The list of the tile's cell: its (band, column) or the tile itself; for
-    // column runs, see below.
-    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[(ty >> list_shift) * cam.tiles_x + tx];
+    // The tile's own list; for column runs, see below.
+    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[ty * cam.tiles_x + tx];
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int32_t count = 0, last = 0, trav = 0;
     bool done = !inside, stopped = false;
@@ -115,10 +112,6 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                     keep[k] = (uint32_t)ty - (r.y & 0xFFu) <= ((r.y >> 8) & 0xFFu);
                 } else {
                     g[k] = sorted_gauss[idx];
-                    if (list_shift) {   // does the Gaussian's rectangle hold this tile row?
-                        const uint32_t box = gbox[g[k]];
-                        keep[k] = (uint32_t)ty - ((box >> 8) & 0xFFu) <= (box >> 24);
-                    }
                 }
             }
         }
@@ -240,20 +233,19 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 }  // namespace
 
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
-                   const float4* rec, const uint32_t* gbox, int list_shift, const FrameParams* fp,
-                   int num_tiles, float* img, float* t_final, int32_t* load, int32_t* last,
-                   int32_t* trav, float* tfin, int32_t* lstat, const SliceState& ss,
-                   cudaStream_t stream) {
+                   const float4* rec, int lists, const FrameParams* fp, int num_tiles, float* img,
+                   float* t_final, int32_t* load, int32_t* last, int32_t* trav, float* tfin,
+                   int32_t* lstat, const SliceState& ss, cudaStream_t stream) {
     const int tiles = num_tiles;
     if (tiles <= 0) return;
-    if (list_shift == kColumnLists)
-        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
-                                                             list_shift, fp, img, t_final, load,
-                                                             last, trav, tfin, lstat, ss);
+    if (lists == kListsColumns)
+        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, fp, img,
+                                                             t_final, load, last, trav, tfin, lstat,
+                                                             ss);
     else
-        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, gbox,
-                                                              list_shift, fp, img, t_final, load,
-                                                              last, trav, tfin, lstat, ss);
+        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, fp,
+                                                              img, t_final, load, last, trav, tfin,
+                                                              lstat, ss);
 }
 
 }  // namespace adr

@@ -366,26 +366,16 @@ k_scatter_columns(PairSource src, const uint32_t* __restrict__ starts, uint2* __
 // Pass 2: pairs grouped by ty.
 // ---------------------------------------------------------------------------
 
-// Row interval of a run in units of 2^shift tile rows ("bands"): the bands
-// [y0 >> shift, ((y0 + h - 1) >> shift) + 1).  shift = 0 gives the tile rows.
-__device__ __forceinline__ void run_band_span(uint32_t y, int shift, uint32_t& b0, uint32_t& hb) {
-    const uint32_t y0 = run_y0(y), h = run_h(y);
-    b0 = y0 >> shift;
-    hb = ((y0 + h - 1u) >> shift) + 1u - b0;
-}
-
-// Counts of the band (ty >> shift) over the entries of this CTA's runs (each
-// run adds its band interval to a difference array), and the entries of every
-// (band, column) cell: runs of column tx meeting the band.  With shift = 0 the
-// bands are the tile rows and the cells the tiles.  Runs arrive grouped by tx,
-// so the CTA's first kColSlots columns are counted on chip; runs beyond them
-// (only in columns with few runs) add to cell_counts directly.
+// Counts of ty over the pairs of this CTA's runs (each run adds its row
+// interval to a difference array), and the pairs of every tile: runs of
+// column tx covering row ty.  Runs arrive grouped by tx, so the CTA's first
+// kColSlots columns are counted on chip; runs beyond them (only in columns
+// with few runs) add to tile_counts directly.
 __global__ void __launch_bounds__(kSortThreads)
 k_count_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters, int64_t capacity,
-             int grid, int tiles_x, int num_cells, int shift, uint32_t* __restrict__ counts,
+             int grid, int tiles_x, int num_tiles, uint32_t* __restrict__ counts,
              uint32_t* __restrict__ totals, uint32_t* __restrict__ tile_counts,
              uint32_t* __restrict__ status) {
-    const int num_tiles = num_cells;
     __shared__ int s_diff[kRadix + 1];
     __shared__ int s_col[kColSlots][kRadix + 1];
     __shared__ uint32_t s_wsum[kWarps];
@@ -401,10 +391,8 @@ k_count_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counte
         tx0 = run_tx(runs[A].y);
         for (int64_t i = A + tid; i < B; i += kSortThreads) {
             const uint32_t y = runs[i].y;
-            const uint32_t tx = run_tx(y);
-            uint32_t y0, h;
-            run_band_span(y, shift, y0, h);
-            if (run_y0(y) + run_h(y) > (uint32_t)kRadix || tx >= (uint32_t)tiles_x) {   // not a pass-1 record
+            const uint32_t y0 = run_y0(y), h = run_h(y), tx = run_tx(y);
+            if (y0 + h > (uint32_t)kRadix || tx >= (uint32_t)tiles_x) {   // not a pass-1 record
                 atomicOr(status, kErrRange);
                 continue;
             }
@@ -491,7 +479,7 @@ k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
 __global__ void __launch_bounds__(kSortThreads, 8)   // 8 CTAs per SM: 32 registers, 22 KB shared
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
-               int grid, int tiles_y, int shift, uint32_t* __restrict__ status) {
+               int grid, int tiles_y, uint32_t* __restrict__ status) {
     __shared__ RowShared sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Span sp = cta_span(run_count(counters, capacity), grid);
@@ -508,9 +496,7 @@ k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ coun
             uint32_t rows = 0u, gid = 0u;   // rows [0, 0): covers nothing
             if (j < avail) {
                 const uint2 rec = runs[r + j];
-                uint32_t b0, hb;
-                run_band_span(rec.y, shift, b0, hb);
-                rows = b0 | ((b0 + hb) << 16);
+                rows = run_y0(rec.y) | ((run_y0(rec.y) + run_h(rec.y)) << 16);
                 gid = rec.x;
             }
             sm.rows[j] = rows;
@@ -644,10 +630,10 @@ void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, 
 }
 
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
-                            int tiles_x, int num_cells, int shift, uint32_t* counts, uint32_t* totals,
+                            int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
                             uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream) {
-    k_count_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, grid, tiles_x, num_cells,
-                                                    shift, counts, totals, tile_counts, status);
+    k_count_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, grid, tiles_x, num_tiles,
+                                                    counts, totals, tile_counts, status);
 }
 
 void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
@@ -658,9 +644,9 @@ void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32
 
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
-                              int grid, int num_bands, int shift, cudaStream_t stream) {
+                              int grid, int tiles_y, cudaStream_t stream) {
     k_scatter_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, starts, gauss_out,
-                                                      grid, num_bands, shift, status);
+                                                      grid, tiles_y, status);
 }
 
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream) {
