@@ -155,7 +155,11 @@ adr_status adr_preprocess(adr_ctx *ctx, const float *means, const float *scales,
  * those of the nearest Gaussians; adr_render renders them, then builds and
  * renders the runs of the farther Gaussians that touch a tile with a pixel
  * still blending (a pixel's blend stops once its transmittance falls below
- * t_min, so the others cannot change a pixel).  adr_render_backward,
+ * t_min, so the others cannot change a pixel).  A context slices a frame when
+ * the last sliced frame's two slices held fewer than half of all runs (read
+ * back without waiting), and every 16th frame to measure again; otherwise it
+ * builds every Gaussian's runs at once.  Either way the image is the same.
+ * adr_render_backward,
  * adr_read_pairs and adr_read_ranges first build every Gaussian's runs and
  * expand them into per-tile lists and ranges (a second, stable pass by tile
  * row), enqueued on their own stream. */

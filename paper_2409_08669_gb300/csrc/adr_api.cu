@@ -118,7 +118,16 @@ struct adr_ctx {
     std::atomic<uint32_t> epoch{0};
     bool have_frame = false, have_sort = false, have_render = false;
     cudaStream_t last_stream = nullptr;
-    uint32_t* host_words = nullptr;  // pinned: counters + status readback
+    uint32_t* host_words = nullptr;  // pinned: counters + status readback (words 0-31),
+                                     // runs of the last sliced frame (words 40-42)
+    // Depth slices pay only when most tiles stop within the nearest Gaussians.
+    // After a sliced frame its run counts (all, slice 0, slice 1) come back
+    // asynchronously; the next frame slices if the two slices made fewer than
+    // half of all runs, and every kSliceProbe-th frame slices to measure again.
+    cudaEvent_t slice_ev = nullptr;
+    bool slice_probe = false;        // a readback is in flight
+    bool slices_pay = true;
+    uint32_t frames = 0;
     // host-path staging (adr_render_host), allocated on its first use
     float* stage = nullptr;
     float* stage_img = nullptr;
@@ -254,6 +263,7 @@ void free_ctx(adr_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_words) cudaFreeHost(c->host_words);
+    if (c->slice_ev) cudaEventDestroy(c->slice_ev);
     delete c;
 }
 
@@ -291,6 +301,8 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
     }
     cudaError_t e = cudaHostAlloc((void**)&c->host_words, 64 * sizeof(uint32_t), cudaHostAllocDefault);
     if (e != cudaSuccess) { free_ctx(c); return fail(ADR_ERR_CUDA, "cudaHostAlloc: %s", cudaGetErrorString(e)); }
+    e = cudaEventCreateWithFlags(&c->slice_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { free_ctx(c); return fail(ADR_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
     *out = c;
     return ok();
 }
@@ -329,6 +341,18 @@ adr_status adr_sort(adr_ctx* c, void* stream) {
     DeviceGuard guard(c->device);
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
+    if (c->slice_probe) {   // the last sliced frame's run counts, if they are back
+        const cudaError_t q = cudaEventQuery(c->slice_ev);
+        if (q == cudaSuccess) {
+            const uint64_t all = c->host_words[40], used = (uint64_t)c->host_words[41] + c->host_words[42];
+            c->slices_pay = 2 * used < all;
+            c->slice_probe = false;
+        } else if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady) {
+            cudaGetLastError();   // not an error: clear it
+        }
+    }
+    c->fs.allow_slices = c->slices_pay || (c->frames % kSliceProbe) == 0;
+    ++c->frames;
     enqueue_sort(c->ws, c->fs, c->epoch, strm);
     adr_status s;
     if ((s = check_launch("adr_sort")) != ADR_OK) return s;
@@ -344,6 +368,16 @@ adr_status adr_render(adr_ctx* c, float* img, float* t_final, int32_t* load, voi
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
     enqueue_render(c->ws, c->fs, img, t_final, load, strm);
+    if (c->fs.sliced && !c->slice_probe) {
+        // Runs of every Gaussian, of slice 0 and of slice 1, back to the host.
+        const uint32_t* src[3] = {c->ws.counters + kCntRuns, c->ws.slice_counters + kCntRuns,
+                                  c->ws.slice_counters + kCntSlots + kCntRuns};
+        for (int k = 0; k < 3; ++k)
+            ADR_CUDA(cudaMemcpyAsync(c->host_words + 40 + k, src[k], sizeof(uint32_t),
+                                     cudaMemcpyDeviceToHost, strm));
+        ADR_CUDA(cudaEventRecord(c->slice_ev, strm));
+        c->slice_probe = true;
+    }
     adr_status s;
     if ((s = check_launch("adr_render")) != ADR_OK) return s;
     c->have_render = true;

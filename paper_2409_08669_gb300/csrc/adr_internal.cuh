@@ -169,6 +169,7 @@ struct FrameState {
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
     const uint32_t* sorted_gauss = nullptr;  // list entries' Gaussians by (cell, depth)
     const uint2* runs = nullptr;             // column runs by (column, depth)
+    bool allow_slices = true;                // the caller's choice for the next sort
     bool sliced = false;                     // the frame renders in two depth slices
     int runs_held = 0;                       // which Gaussians' column runs ws.pruns holds
     int lists = -1;                          // a ListKind; -1 before the first sort
@@ -295,6 +296,7 @@ struct SliceState {
 #define ADR_SLICE_DIV 16
 #endif
 constexpr int kSliceDiv = ADR_SLICE_DIV;
+constexpr uint32_t kSliceProbe = 16;   // a context re-measures the slices every 16 frames
 void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
                    const float4* rec, int lists, const FrameParams* fp, int num_tiles, float* img,
                    float* t_final, int32_t* load, int32_t* last, int32_t* trav, float* tfin,

@@ -170,7 +170,7 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
     fs.runs = ws.pruns;
     fs.sorted_gauss = nullptr;
     fs.lists = kListsColumns;
-    fs.sliced = ws.pst != nullptr && kSliceDiv > 0;
+    fs.sliced = fs.allow_slices && ws.pst != nullptr && kSliceDiv > 0;
     if (fs.sliced) {
         // Slice 0: the nearest Gaussians' runs; Render builds slice 1 from what
         // its pixels still need.
