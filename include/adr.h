@@ -145,6 +145,16 @@ adr_status adr_preprocess(adr_ctx *ctx, const float *means, const float *scales,
                           const float *rots, const float *opac, const float *sh, int64_t n,
                           const adr_camera *camera, const adr_settings *settings, void *stream);
 
+/* Depth slices of adr_sort / adr_render (see adr_sort): never, always, or
+ * (the default) when the context's last sliced frame shows they pay.  The
+ * images are the same in every mode; only the time differs. */
+typedef enum adr_slice_mode {
+    ADR_SLICES_NEVER = 0, ADR_SLICES_ALWAYS = 1, ADR_SLICES_ADAPTIVE = 2
+} adr_slice_mode;
+/* Sets the context's adr_slice_mode for the following frames.  ADR_ERR_INVALID
+ * for an unknown mode. */
+adr_status adr_set_depth_slices(adr_ctx *ctx, int32_t mode);
+
 /* Stages 4-5: the tile lists, ordered by (tile, depth, index) (the Gaussians
  * are already in depth order).  The pairs are grouped by column of tiles:
  * each Gaussian contributes one run per tile column of its rectangle (its

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "adr_image_loss": (_I32, [_P, _P, _I32, _I32, _I32, ctypes.c_float, ctypes.c_float, _P, _P,
                               _P, _P]),
     "adr_profile_enable": (_I32, [_P, _I32]),
+    "adr_set_depth_slices": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
     "adr_serve_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(adr_serve_config)]),
@@ -237,6 +238,10 @@ def adr_image_loss(img, ref, channels, height, width, w_l1, w_ssim, stats, dl_di
                    stream):
     return check(load().adr_image_loss(img, ref, channels, height, width, w_l1, w_ssim, stats,
                                        dl_dimg, scratch, stream), "adr_image_loss")
+
+
+def adr_set_depth_slices(ctx, mode):
+    return check(load().adr_set_depth_slices(ctx, int(mode)), "adr_set_depth_slices")
 
 
 def adr_profile_enable(ctx, enable):

@@ -128,6 +128,7 @@ struct adr_ctx {
     bool slice_probe = false;        // a readback is in flight
     bool slices_pay = true;
     uint32_t frames = 0;
+    int32_t slice_mode = ADR_SLICES_ADAPTIVE;
     // host-path staging (adr_render_host), allocated on its first use
     float* stage = nullptr;
     float* stage_img = nullptr;
@@ -351,7 +352,9 @@ adr_status adr_sort(adr_ctx* c, void* stream) {
             cudaGetLastError();   // not an error: clear it
         }
     }
-    c->fs.allow_slices = c->slices_pay || (c->frames % kSliceProbe) == 0;
+    c->fs.allow_slices = c->slice_mode == ADR_SLICES_ALWAYS ||
+                         (c->slice_mode == ADR_SLICES_ADAPTIVE &&
+                          (c->slices_pay || (c->frames % kSliceProbe) == 0));
     ++c->frames;
     enqueue_sort(c->ws, c->fs, c->epoch, strm);
     adr_status s;
@@ -515,6 +518,14 @@ adr_status adr_image_loss(const float* img, const float* ref, int32_t channels, 
     launch_image_loss(img, ref, channels, height, width, win, w_l1, w_ssim, stats, dl_dimg,
                       scratch, (cudaStream_t)stream);
     return check_launch("adr_image_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
+}
+
+adr_status adr_set_depth_slices(adr_ctx* c, int32_t mode) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (mode != ADR_SLICES_NEVER && mode != ADR_SLICES_ALWAYS && mode != ADR_SLICES_ADAPTIVE)
+        return fail(ADR_ERR_INVALID, "bad depth-slice mode %d", mode);
+    c->slice_mode = mode;
+    return ok();
 }
 
 adr_status adr_profile_enable(adr_ctx* c, int32_t enable) {

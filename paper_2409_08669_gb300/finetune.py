@@ -94,8 +94,11 @@ def render_targets(rast: Rasterizer, params, cameras, settings):
 
 def evaluate(rast: Rasterizer, params, cameras, targets, settings, repeats=5):
     """Frames/s of the whole frame (preprocess + sort + render, CUDA events over
-    `repeats` passes of the cameras), mean and std of the per-pixel load
-    l_i, and PSNR / SSIM against the targets, averaged over the cameras."""
+    `repeats` passes of the cameras, without depth slices so that the frame's
+    work does not depend on the context's slicing history), mean and std of
+    the per-pixel load l_i, and PSNR / SSIM against the targets, averaged over
+    the cameras."""
+    rast.set_depth_slices(Rasterizer.SLICES_NEVER)
     stds, means, psnr, ssim = [], [], [], []
     for cam, tgt in zip(cameras, targets):
         img, _, load = rast.forward(params, cam, settings)
@@ -118,6 +121,7 @@ def evaluate(rast: Rasterizer, params, cameras, targets, settings, repeats=5):
             rast.forward(params, cam, settings, want_aux=False)
     ev1.record()
     torch.cuda.synchronize(rast.device)
+    rast.set_depth_slices(Rasterizer.SLICES_ADAPTIVE)
     frames = repeats * len(cameras)
     k = len(cameras)
     return {"fps": frames * 1e3 / ev0.elapsed_time(ev1), "load_mean": sum(means) / k,

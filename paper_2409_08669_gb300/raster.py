@@ -105,6 +105,13 @@ class Rasterizer:
         self.sort(stream)
         return self.render(stream=stream, **kw)
 
+    SLICES_NEVER, SLICES_ALWAYS, SLICES_ADAPTIVE = 0, 1, 2
+
+    def set_depth_slices(self, mode):
+        """Depth slices of the frame: SLICES_NEVER, SLICES_ALWAYS or SLICES_ADAPTIVE
+        (default); the images are the same, only the time differs."""
+        _lib.adr_set_depth_slices(self.ctx, mode)
+
     def backward(self, params, dl_dimg, dl_dload=None, stream=None):
         """Gradients of the last rendered frame: (g_means, g_scales, g_rots, g_opac, g_sh)."""
         grads = tuple(torch.empty_like(p) for p in params)

@@ -199,3 +199,26 @@ def test_invalid_arguments_rejected(rast):
     with pytest.raises(_lib.AdrError) as e:
         rast.forward(upload(scene), cam, S.Settings(rect_rule=2))
     assert e.value.status == _lib.ADR_ERR_INVALID
+
+
+def test_depth_slice_modes_render_identical_frames(rast):
+    """The depth slices only skip Gaussians no pixel reaches: the image, T,
+    l_i and the per-pixel list positions are bit-identical with and without."""
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
+    for scene, cam in ((S.tiny_scene(11, n=6000), S.look_at((0.3, -0.2, -2.2), width=250, height=190)),
+                       (S.heavy_scene(n=200_000, seed=4), S.orbit_cameras(50, width=960, height=540)[9])):
+        params = upload(scene)
+        st = S.Settings(mode=S.MODE_AABB)
+        out = []
+        for mode in (Rasterizer.SLICES_NEVER, Rasterizer.SLICES_ALWAYS):
+            rast.set_depth_slices(mode)
+            img, t_final, load = rast.forward(params, cam, st)
+            torch.cuda.synchronize()
+            last, trav = rast.read_pixel_stats()
+            out.append((img.cpu().numpy(), t_final.cpu().numpy(), load.cpu().numpy(), last, trav))
+        rast.set_depth_slices(Rasterizer.SLICES_ADAPTIVE)
+        for a, b in zip(*out):
+            np.testing.assert_array_equal(a, b)
+    from paper_2409_08669_gb300 import _lib
+    with pytest.raises(_lib.AdrError):
+        rast.set_depth_slices(7)
