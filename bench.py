@@ -66,10 +66,10 @@ EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation i
 KERNELS_PER_FRAME = 30
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
-# its two launches of one frame, 63.8 MB) and the per-tile list pass
+# its two launches of one frame, 63.5 MB) and the per-tile list pass
 # (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md, 128.34 + 576.92 MB over
 # P = 1.5958e8 pairs, scaled by the measured P).
-TRAFFIC_BYTES_PER_FRAME = {"render": (11.10e6 + 9.04e6) + (43.41e6 + 0.24e6)}
+TRAFFIC_BYTES_PER_FRAME = {"render": (11.10e6 + 8.57e6) + (43.41e6 + 0.40e6)}
 TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 
