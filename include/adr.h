@@ -169,10 +169,9 @@ adr_status adr_set_depth_slices(adr_ctx *ctx, int32_t mode);
  * the last sliced frame's two slices held fewer than half of all runs (read
  * back without waiting), and every 16th frame to measure again; otherwise it
  * builds every Gaussian's runs at once.  Either way the image is the same.
- * adr_render_backward,
- * adr_read_pairs and adr_read_ranges first build every Gaussian's runs and
- * expand them into per-tile lists and ranges (a second, stable pass by tile
- * row), enqueued on their own stream. */
+ * adr_render_backward, adr_read_pairs and adr_read_ranges first build every
+ * Gaussian's runs and expand them into per-tile lists and ranges (a second,
+ * stable pass by tile row), enqueued on their own stream. */
 adr_status adr_sort(adr_ctx *ctx, void *stream);
 
 /* Stage 6: per-tile front-to-back alpha blending (Eq. 2-3) of the sorted
