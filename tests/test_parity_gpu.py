@@ -44,8 +44,12 @@ def _check_frame(rast, scene, cam, st, label=""):
     flags = pre["flags"]
     near = (flags & oracle.F_NEAR) != 0
     geom, rect, tiles = rast.read_gaussians()
-    # depth sort keys: bit-exact for every Gaussian
-    np.testing.assert_array_equal(geom[:, 11].view(np.uint32), pre["depth"].view(np.uint32))
+    # depth sort keys: bit-exact for every Gaussian (a NaN depth, whose payload
+    # bits are not fixed, only has to be NaN on both sides)
+    gd, od = geom[:, 11], pre["depth"]
+    np.testing.assert_array_equal(np.isnan(gd), np.isnan(od))
+    fin = ~np.isnan(od)
+    np.testing.assert_array_equal(gd[fin].view(np.uint32), od[fin].view(np.uint32))
     # tile counts and rectangles: exact except near-threshold Gaussians
     tbad = np.nonzero((tiles != pre["tiles"]) & ~near)[0]
     assert tbad.size == 0, f"{label}: {tbad.size} Gaussians with different tile counts, e.g. {tbad[:5]}"
@@ -222,3 +226,16 @@ def test_depth_slice_modes_render_identical_frames(rast):
     from paper_2409_08669_gb300 import _lib
     with pytest.raises(_lib.AdrError):
         rast.set_depth_slices(7)
+
+
+def test_degenerate_gaussians_are_culled(rast):
+    """Gaussians with NaN centres or zero-norm rotations never reach a tile
+    (their depth or det(Sigma') fails the cull), on both sides; the rest of the
+    frame keeps parity with the oracle."""
+    scene = S.tiny_scene(13, n=3000)
+    scene.means[:6] = np.nan
+    scene.rots[6:12] = 0.0
+    cam = S.look_at((0, 0, -3), width=128, height=96)
+    _check_frame(rast, scene, cam, S.Settings(mode=S.MODE_AABB), "degenerate")
+    _, _, tiles = rast.read_gaussians()
+    assert np.all(tiles[:12] == 0)
