@@ -3,8 +3,8 @@
 Its forward must equal the C oracle's (which is pinned against closed forms
 and brute force), and its autograd gradient of L = <w, image> must equal
 central finite differences of the C oracle's FP64 forward.  The load term's
-straight-through gradient has no finite-difference counterpart (the load is a
-count): parity unpinned beyond its definition."""
+gradient has no finite-difference counterpart (the load is a count): parity
+unpinned beyond the two readings' definitions, checked on closed-form cases."""
 import numpy as np
 import pytest
 
@@ -105,3 +105,35 @@ def test_load_term_straight_through_definition():
     sigma = float(np.float32(0.4))
     expect = float((v * (load > 0) * alpha / sigma).sum())
     assert grads[3][0] == pytest.approx(expect, rel=1e-10)
+
+
+def test_load_term_early_stop_reading_on_a_stack():
+    """The early-stop reading (load_grad = 1) on a column of identical
+    Gaussians in front of the camera: the centre pixel stops after l blends,
+    and raising any blended Gaussian's opacity brings the stop forward, so
+    d l / d sigma < 0 there (the straight-through reading gives > 0).  Its size:
+    -l / (-ln T_final) * d(-ln(1 - alpha_k))/d sigma summed over the blended k."""
+    k = 30
+    means = np.zeros((k, 3)); means[:, 2] = np.linspace(-0.5, 0.5, k)
+    sc = S.Scene(*(np.ascontiguousarray(a, dtype=np.float32) for a in (
+        means, np.full((k, 3), 0.08), np.tile([1.0, 0.0, 0.0, 0.0], (k, 1)), np.full(k, 0.5),
+        np.zeros((k, 16, 3)))))
+    cam = S.look_at((0, 0, -3), width=17, height=17)
+    v = np.zeros((17, 17)); v[8, 8] = 1.0
+    out = {}
+    for lg in (S.LOAD_GRAD_STRAIGHT, S.LOAD_GRAD_TERMINATION):
+        st = S.Settings(mode=S.MODE_AABB, load_grad=lg)
+        grads, img, load = og.gradients(sc, cam, st, np.zeros((3, 17, 17)), dl_dload=v)
+        out[lg] = (grads[3], load)
+    ref = oracle.render(sc, cam, S.Settings(mode=S.MODE_AABB))
+    l = int(ref["load"][8, 8])
+    assert 0 < l < k and ref["t_final"][8, 8] < 1e-3           # the centre pixel stopped early
+    g_st, g_stop = out[S.LOAD_GRAD_STRAIGHT][0].sum(), out[S.LOAD_GRAD_TERMINATION][0].sum()
+    assert g_st > 0 and g_stop < 0
+    # magnitude: each blended Gaussian is centred on the pixel (on the optical
+    # axis), so its alpha there is sigma itself and T_final = (1 - sigma)^l
+    sigma = 0.5
+    t_final = ref["t_final"][8, 8]
+    assert t_final == pytest.approx((1.0 - sigma) ** l, rel=1e-9)
+    expect = -l / -np.log(t_final) * l * (1.0 / (1.0 - sigma))   # d alpha/d sigma = 1
+    assert g_stop == pytest.approx(expect, rel=1e-6)
