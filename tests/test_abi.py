@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2409_08669_gb300 import _lib, build
@@ -81,3 +82,15 @@ def test_serve_config_rejected_without_gpu(libpath):
     cfg.max_slots, cfg.max_width = 2, 8192
     assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
     assert lib.adr_serve_poll(None, 1, 0) == _lib.ADR_ERR_INVALID
+
+
+def test_settings_marshalling_carries_every_field():
+    from paper_2409_08669_gb300 import scenes as S
+    st = S.Settings(mode=S.MODE_CIRCLE, alpha_low=float(np.float32(2 / 255)), t_min=1e-3,
+                    lowpass=0.2, jac_clamp=1.1, bg=(0.1, 0.2, 0.3), sh_degree=2,
+                    rect_rule=S.RECT_3DGS, load_grad=S.LOAD_GRAD_TERMINATION)
+    c = _lib.make_settings(st)
+    assert (c.mode, c.sh_degree, c.rect_rule, c.load_grad) == (1, 2, 1, 1)
+    assert c.alpha_low == pytest.approx(2 / 255, rel=1e-6) and c.t_min == pytest.approx(1e-3)
+    assert (c.lowpass, c.jac_clamp) == (pytest.approx(0.2), pytest.approx(1.1))
+    assert list(c.bg) == [pytest.approx(0.1), pytest.approx(0.2), pytest.approx(0.3)]
