@@ -6,8 +6,12 @@ of a scene against target images under
 lambda_L1 + lambda_ssim + lambda_load = 1, with lambda_load = 0.45 and the
 remaining 0.55 split 4:1 between L1 and SSIM (the 0.8 / 0.2 weighting of the
 3DGS objective the paper starts from).  L_load (Eq. 13) is the standard
-deviation over the pixels of the per-pixel load l_i (Eq. 12); it reaches the
-Gaussians through the straight-through reading d l_i / d alpha = 1.
+deviation over the pixels of the per-pixel load l_i (Eq. 12).  The paper gives
+no derivative of the integer count l_i; the settings pick the reading: the
+straight-through one (d l_i / d alpha_k = 1 for every Gaussian blended into the
+pixel) or the termination one (for a pixel that stopped early,
+d l_i / d alpha_k = -l_i / (-ln T_final) / (1 - alpha_k): a more opaque Gaussian
+brings the stop forward and shortens l_i).
 
 Every loss term and every gradient of the rasterizer runs in libadr.so
 (adr_render / adr_render_backward, adr_image_loss, adr_load_loss); PyTorch
