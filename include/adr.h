@@ -120,8 +120,9 @@ typedef struct adr_settings {
 typedef struct adr_ctx adr_ctx;
 
 /* Create a context on `device` with workspace for up to `max_gaussians`
- * Gaussians, `pair_capacity` Gaussian-tile pairs (at most 2^30) and images
- * up to max_width x max_height (at most 2^16 tiles, e.g. 4096 x 4096).  All
+ * Gaussians (at most 2^29), `pair_capacity` Gaussian-tile pairs (at most
+ * 2^30) and images up to max_width x max_height (at most 2^16 tiles, e.g.
+ * 4096 x 4096).  All
  * workspace is allocated here (cudaMalloc); no later call allocates, except
  * the first adr_render_host, which allocates its staging buffers.  Returns ADR_ERR_INVALID for sizes <= 0 or too
  * large, ADR_ERR_CUDA if allocation fails (nothing leaks). */
@@ -335,7 +336,7 @@ typedef struct adr_serve_config {
     int32_t max_slots;            /* 1..64 concurrent frames */
     int64_t mem_budget_bytes;     /* admission budget, > 0 */
     int64_t slot_pair_capacity;   /* Gaussian-tile pairs per slot, 1..2^30 */
-    int64_t slot_max_gaussians;   /* largest scene, > 0 */
+    int64_t slot_max_gaussians;   /* largest scene, 1..2^29 */
     int32_t max_width, max_height;/* largest image, <= 4096 each */
     int32_t use_graphs;           /* 0: plain launches; else graph replay */
     int32_t device;               /* CUDA device ordinal */

@@ -291,8 +291,8 @@ adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacit
                       int32_t max_width, int32_t max_height, int32_t device) {
     if (!out) return fail(ADR_ERR_INVALID, "ctx out-pointer is NULL");
     *out = nullptr;
-    if (max_gaussians <= 0 || max_gaussians > (int64_t(1) << 30))
-        return fail(ADR_ERR_INVALID, "max_gaussians must be in 1..2^30");
+    if (max_gaussians <= 0 || max_gaussians > kMaxGaussians)
+        return fail(ADR_ERR_INVALID, "max_gaussians must be in 1..2^29");
     if (pair_capacity <= 0 || pair_capacity > (int64_t(1) << 30))
         return fail(ADR_ERR_INVALID, "pair_capacity must be in 1..2^30");
     if (max_width <= 0 || max_height <= 0 || max_width > 4096 || max_height > 4096)

@@ -74,6 +74,9 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;                           // up to 32 key bits
 constexpr int kMaxTiles = 1 << 16;                      // tile ids sort in two 8-bit passes
 constexpr int kMaxTileGrid = 2048;                      // CTAs of a tile-sort pass (bounds tcounts)
+// Largest scene a context or serving slot accepts: the per-Gaussian kernels
+// index their packed arrays as 4 * i + c with a 32-bit thread index i.
+constexpr int64_t kMaxGaussians = int64_t(1) << 29;
 
 // Per-call counters kept on the device.
 enum Counter : int {

@@ -281,6 +281,7 @@ adr_status adr_serve_create(adr_server** out, const adr_serve_config* cfg) {
     *out = nullptr;
     if (cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->slot_pair_capacity <= 0 ||
         cfg->slot_pair_capacity > (int64_t(1) << 30) || cfg->slot_max_gaussians <= 0 ||
+        cfg->slot_max_gaussians > kMaxGaussians ||
         cfg->max_width <= 0 || cfg->max_height <= 0 || cfg->max_width > 4096 ||
         cfg->max_height > 4096 || cfg->mem_budget_bytes <= 0)
         return report_error(ADR_ERR_INVALID, "adr_serve_create: configuration out of range");

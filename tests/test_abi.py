@@ -71,6 +71,21 @@ def test_version_and_error_without_gpu(libpath):
     assert b"max_gaussians" in lib.adr_last_error()
 
 
+def test_scene_size_limit_rejected_without_gpu(libpath):
+    # the per-Gaussian kernels index 4 * i + c in 32 bits: 2^29 is the largest scene
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    for n in ((1 << 29) + 1, 1 << 30, 1 << 40):
+        assert lib.adr_create(ctypes.byref(out), n, 1 << 20, 64, 64, 0) == _lib.ADR_ERR_INVALID
+        assert b"2^29" in lib.adr_last_error()
+        assert not out.value
+    cfg = _lib.adr_serve_config(max_slots=1, mem_budget_bytes=1 << 30, slot_pair_capacity=1 << 20,
+                                slot_max_gaussians=(1 << 29) + 1, max_width=256, max_height=256,
+                                use_graphs=1, device=0)
+    assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
+    assert not out.value
+
+
 def test_serve_config_rejected_without_gpu(libpath):
     lib = _lib.load()
     cfg = _lib.adr_serve_config(max_slots=0, mem_budget_bytes=1 << 30, slot_pair_capacity=1 << 20,
