@@ -64,7 +64,9 @@ typedef enum adr_mode { ADR_PLAIN = 0, ADR_CIRCLE = 1, ADR_AABB = 2 } adr_mode;
 
 /* Pinhole camera.  view: row-major world->camera matrix with OpenCV axes
  * (x right, y down, z forward).  A pixel (i, j) has its centre at integer
- * coordinates.  near: Gaussians with view depth <= near are culled. */
+ * coordinates.  near_z (> 0, finite): Gaussians with view depth <= near_z
+ * are culled.  fx, fy must be positive and finite; width, height within the
+ * context's maximum (else ADR_ERR_INVALID). */
 typedef struct adr_camera {
     float view[16];
     float fx, fy, cx, cy;

@@ -67,6 +67,9 @@ adr_status make_cam(int max_w, int max_h, const adr_camera* cam, CamDev& d) {
                     max_w, max_h);
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !std::isfinite(cam->fx) || !std::isfinite(cam->fy))
         return fail(ADR_ERR_INVALID, "focal lengths must be positive and finite");
+    // a Gaussian at depth 0 would project to infinity: the near plane must be in front
+    if (!(cam->near_z > 0.f) || !std::isfinite(cam->near_z))
+        return fail(ADR_ERR_INVALID, "near_z must be positive and finite");
     for (int i = 0; i < 12; ++i) d.v[i] = cam->view[i];
     d.fx = cam->fx; d.fy = cam->fy; d.cx = cam->cx; d.cy = cam->cy;
     d.near_z = cam->near_z;

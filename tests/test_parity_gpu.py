@@ -203,6 +203,11 @@ def test_invalid_arguments_rejected(rast):
     with pytest.raises(_lib.AdrError) as e:
         rast.forward(upload(scene), cam, S.Settings(rect_rule=2))
     assert e.value.status == _lib.ADR_ERR_INVALID
+    for near in (0.0, -1.0, float("inf")):   # the near plane must be in front of the camera
+        with pytest.raises(_lib.AdrError) as e:
+            rast.forward(upload(scene), S.look_at((0, 0, -3), width=64, height=64, near=near),
+                         S.Settings())
+        assert e.value.status == _lib.ADR_ERR_INVALID
 
 
 def test_depth_slice_modes_render_identical_frames(rast):
