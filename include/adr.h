@@ -372,7 +372,8 @@ adr_status adr_serve_submit(adr_server *server, int32_t scene_id, const adr_came
  * the wait ran out (the ticket stays valid), or the request's own error
  * (ADR_ERR_CAPACITY: more pairs than slot_pair_capacity, image incomplete;
  * ADR_ERR_TIMEOUT: a bounded device wait gave up; ADR_ERR_CUDA), which also
- * releases the ticket.  ADR_ERR_INVALID for an unknown ticket. */
+ * releases the ticket.  ADR_ERR_INVALID for an unknown ticket or a negative
+ * timeout_us (the ticket is left as it was). */
 adr_status adr_serve_poll(adr_server *server, uint64_t ticket, int64_t timeout_us);
 /* Statistics since creation, first min(n, 10) of: completed requests, p50
  * latency ms, p99 latency ms, mean latency ms (submit to completion seen by

@@ -368,6 +368,7 @@ adr_status adr_serve_submit(adr_server* s, int32_t scene_id, const adr_camera* c
 
 adr_status adr_serve_poll(adr_server* s, uint64_t ticket, int64_t timeout_us) {
     if (!s) return report_error(ADR_ERR_INVALID, "adr_serve_poll: NULL server");
+    if (timeout_us < 0) return report_error(ADR_ERR_INVALID, "adr_serve_poll: negative timeout");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->requests.find(ticket);
     if (it == s->requests.end()) return report_error(ADR_ERR_INVALID, "adr_serve_poll: unknown ticket");

@@ -132,6 +132,7 @@ def test_poll_pending_timeout_and_unknown_ticket(env):
     tickets = [srv.submit(ids[2], c, o) for c, o in zip(cams, outs)]
     last = tickets[-1]
     assert srv.poll(last, 0) == _lib.ADR_PENDING
+    assert srv._lib.adr_serve_poll(srv._h, last, -5) == _lib.ADR_ERR_INVALID
     assert srv.poll(last, 1) in (_lib.ADR_ERR_TIMEOUT, _lib.ADR_OK)
     for t in tickets:
         st = srv.poll(t)
