@@ -12,8 +12,9 @@ The per-pixel load l_i (Eq. 12) is an integer count; its gradient uses the
 straight-through reading d l_i / d alpha_ik = 1 for every blended pair,
 so dL_load/d alpha_ik = dL/d l_i, or, with settings.load_grad = 1, for a
 pixel that stopped early d l_i / d(-ln(1 - alpha_ik)) = -l_i / (-ln T_final)
-(parity unpinned beyond these readings: the paper does not say how L_load
-back-propagates).
+(the paper does not say how L_load back-propagates; the tests pin the
+straight-through reading to its definition and the early-stop reading to the
+slope of the count l_i that the C oracle renders as opacities rise).
 
 Only tests may import this module.
 """
