@@ -109,3 +109,11 @@ def test_settings_marshalling_carries_every_field():
     assert c.alpha_low == pytest.approx(2 / 255, rel=1e-6) and c.t_min == pytest.approx(1e-3)
     assert (c.lowpass, c.jac_clamp) == (pytest.approx(0.2), pytest.approx(1.1))
     assert list(c.bg) == [pytest.approx(0.1), pytest.approx(0.2), pytest.approx(0.3)]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without libadr.so the binding raises instead of computing
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib._build, "LIB", str(tmp_path / "libadr.so"))
+    with pytest.raises(RuntimeError, match="libadr.so not found"):
+        _lib.load(build_if_missing=False)
