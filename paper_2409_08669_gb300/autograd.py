@@ -3,7 +3,8 @@
 AdrRasterize: forward = adr_preprocess + adr_sort + adr_render, backward =
 adr_render_backward.  Outputs the image and the per-pixel load l_i (Eq. 12)
 as a float tensor; a gradient reaching the load flows back through the
-straight-through reading d l_i / d alpha = 1 (Sec. 4.4).
+reading settings.load_grad selects (straight-through d l_i / d alpha = 1, or
+the early-stop reading for pixels that terminated; Sec. 4.4).
 LoadBalanceLoss: L_load = std of l_i over the pixels (Eq. 13), computed and
 differentiated by adr_load_loss.
 ImageLoss: w_l1 * L1 + w_ssim * (1 - SSIM) against a target image, computed and
