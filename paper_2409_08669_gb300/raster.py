@@ -28,13 +28,54 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+# values per Gaussian of (means, scales, rots, opacity, SH) in the C ABI's layout
+PARAM_NAMES = ("means", "scales", "rots", "opac", "sh")
+PARAM_WIDTHS = (3, 3, 4, 1, 48)
+
+
+def check_tensor(name, t, numel, dtype=torch.float32, device=None):
+    """Raise unless `t` is a contiguous `dtype` tensor of `numel` values (on
+    cuda:`device` when given): the kernels read and write exactly that many
+    values behind the pointer, so a mismatch must not reach them."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} holds {t.numel()} values, expected {numel}")
+    if device is not None and (not t.is_cuda or t.device.index != device):
+        raise ValueError(f"{name} must be on cuda:{device}, got {t.device}")
+
+
+def check_params(params, device=None):
+    """Validates (means [n,3], scales [n,3], rots [n,4], opac [n], sh [n,16,3]),
+    float32 and contiguous (on cuda:`device` when given); returns n."""
+    if len(params) != 5:
+        raise ValueError(f"expected 5 parameter tensors, got {len(params)}")
+    means = params[0]
+    if not isinstance(means, torch.Tensor) or means.dim() != 2 or means.shape[1] != 3:
+        raise ValueError("means must be an [n, 3] tensor")
+    n = int(means.shape[0])
+    for name, t, width in zip(PARAM_NAMES, params, PARAM_WIDTHS):
+        check_tensor(name, t, width * n, device=device)
+    return n
+
+
 def image_loss(img, ref, w_l1=1.0, w_ssim=0.0, want_grad=True, stream=None, scratch=None):
     """(stats, grad): stats = device float64 [mean |img - ref|, mean SSIM] and
     grad = d(w_l1 * L1 + w_ssim * (1 - SSIM)) / d img (None unless want_grad),
     computed by adr_image_loss.  img, ref: [C, H, W] float32 on one device."""
     img, ref = img.contiguous(), ref.contiguous()
-    assert img.dtype == torch.float32 and ref.dtype == torch.float32 and img.shape == ref.shape
-    assert img.dim() == 3
+    if img.dim() != 3:
+        raise ValueError(f"img must be [C, H, W], got shape {tuple(img.shape)}")
+    if ref.shape != img.shape:
+        raise ValueError(f"ref shape {tuple(ref.shape)} differs from img {tuple(img.shape)}")
+    if not img.is_cuda:
+        raise ValueError(f"img must be a CUDA tensor, got {img.device}")
+    check_tensor("img", img, img.numel(), device=img.device.index)
+    check_tensor("ref", ref, img.numel(), device=img.device.index)
     c, h, w = img.shape
     stats = torch.empty(2, dtype=torch.float64, device=img.device)
     grad = None
@@ -75,9 +116,7 @@ class Rasterizer:
     # -- stages -----------------------------------------------------------------
     def preprocess(self, params, camera, settings, stream=None):
         means, scales, rots, opac, sh = params
-        n = int(means.shape[0])
-        for t in params:
-            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        n = check_params(params, self.device)
         self.n = n
         self.camera = camera
         self.frame += 1
@@ -97,6 +136,11 @@ class Rasterizer:
             t_final = torch.empty((h, w), dtype=torch.float32, device=dev)
         if want_aux and load is None:
             load = torch.empty((h, w), dtype=torch.int32, device=dev)
+        check_tensor("img", img, 3 * h * w, device=self.device)
+        if t_final is not None:
+            check_tensor("t_final", t_final, h * w, device=self.device)
+        if load is not None:
+            check_tensor("load", load, h * w, dtype=torch.int32, device=self.device)
         _lib.adr_render(self.ctx, _ptr(img), _ptr(t_final), _ptr(load), _stream(stream))
         return img, t_final, load
 
@@ -114,10 +158,15 @@ class Rasterizer:
 
     def backward(self, params, dl_dimg, dl_dload=None, stream=None):
         """Gradients of the last rendered frame: (g_means, g_scales, g_rots, g_opac, g_sh)."""
+        if check_params(params, self.device) != self.n:
+            raise ValueError(f"backward needs the {self.n} Gaussians of the last frame")
+        h, w = self.camera.height, self.camera.width
         grads = tuple(torch.empty_like(p) for p in params)
         dl_dimg = dl_dimg.contiguous().float()
+        check_tensor("dl_dimg", dl_dimg, 3 * h * w, device=self.device)
         if dl_dload is not None:
             dl_dload = dl_dload.contiguous().float()
+            check_tensor("dl_dload", dl_dload, h * w, device=self.device)
         _lib.adr_render_backward(self.ctx, *(_ptr(p) for p in params), _ptr(dl_dimg),
                                  _ptr(dl_dload), *(_ptr(g) for g in grads), _stream(stream))
         return grads
@@ -125,7 +174,7 @@ class Rasterizer:
     def load_loss(self, load, weight=1.0, want_grad=True, stream=None):
         """(mean, std) of the per-pixel load and weight * dL_load/dl (Eq. 13)."""
         load = load.contiguous()
-        assert load.dtype == torch.int32
+        check_tensor("load", load, load.numel(), dtype=torch.int32, device=self.device)
         stats = torch.empty(2, dtype=torch.float64, device=load.device)
         grad = torch.empty(load.shape, dtype=torch.float32, device=load.device) if want_grad else None
         _lib.adr_load_loss(self.ctx, _ptr(load), load.numel(), float(weight), _ptr(stats), _ptr(grad),

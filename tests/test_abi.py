@@ -117,3 +117,31 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib._build, "LIB", str(tmp_path / "libadr.so"))
     with pytest.raises(RuntimeError, match="libadr.so not found"):
         _lib.load(build_if_missing=False)
+
+
+def test_parameter_checks_reject_what_the_kernels_would_overrun():
+    # the binding's checks run before any C call: sizes, dtypes and layout
+    import torch
+    from paper_2409_08669_gb300.raster import check_params, check_tensor
+    n = 5
+    good = [torch.zeros(n, 3), torch.ones(n, 3), torch.ones(n, 4), torch.ones(n), torch.zeros(n, 16, 3)]
+    assert check_params(good) == n
+    assert check_params([torch.zeros(0, 3), torch.zeros(0, 3), torch.zeros(0, 4), torch.zeros(0),
+                         torch.zeros(0, 16, 3)]) == 0
+    bad_sh = good[:4] + [torch.zeros(n, 9, 3)]            # degree-2 SH: 27 values, not 48
+    with pytest.raises(ValueError, match="sh holds 135 values, expected 240"):
+        check_params(bad_sh)
+    with pytest.raises(ValueError, match="float32"):
+        check_params(good[:3] + [torch.ones(n, dtype=torch.float64)] + good[4:])
+    with pytest.raises(ValueError, match="contiguous"):
+        check_params([torch.zeros(3, n).t()] + good[1:])
+    with pytest.raises(ValueError, match=r"\[n, 3\]"):
+        check_params([torch.zeros(3 * n)] + good[1:])
+    with pytest.raises(ValueError, match="expected 5"):
+        check_params(good[:4])
+    with pytest.raises(ValueError, match="must be on cuda:0"):
+        check_params(good, device=0)                      # CPU tensors
+    with pytest.raises(ValueError, match="int32"):
+        check_tensor("load", torch.zeros(4), 4, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        check_tensor("img", np.zeros(4, np.float32), 4)
