@@ -113,6 +113,6 @@ def test_autograd_image_loss_backward():
     loss = l1_ssim_loss(xd, torch.from_numpy(y).cuda(), 0.44, 0.11)
     (2.0 * loss).backward()
     l1, ms, go = O.image_loss(x, y, 0.44, 0.11)
-    assert float(loss) == pytest.approx(0.44 * l1 + 0.11 * (1 - ms), rel=1e-5)
+    assert float(loss.detach()) == pytest.approx(0.44 * l1 + 0.11 * (1 - ms), rel=1e-5)
     g = xd.grad.cpu().numpy()
     assert np.abs(g - 2.0 * go).max() <= 4e-3 * np.abs(go).max()
