@@ -8,6 +8,7 @@ import ctypes
 import torch
 
 from . import _lib
+from .raster import check_params, check_tensor
 
 STAT_NAMES = ("completed", "p50_ms", "p99_ms", "mean_ms", "max_inflight", "admitted_while_busy",
               "rejected", "frames_per_s", "capacity_errors", "graph_replays")
@@ -32,22 +33,26 @@ class Server:
         self.device = dev
         self._scenes = []   # keep the borrowed tensors alive
 
+    def _check_out(self, camera, out):
+        """The request's image [3, H, W] is written in full by the device."""
+        check_tensor("out", out, 3 * camera.height * camera.width, device=self.device)
+        if tuple(out.shape) != (3, camera.height, camera.width):
+            raise ValueError(f"out must be [3, {camera.height}, {camera.width}], got {tuple(out.shape)}")
+
     def add_scene(self, params, settings) -> int:
         means, scales, rots, opac, sh = params
-        for t in params:
-            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        n = check_params(params, self.device)
         sid = ctypes.c_int32()
         st = _lib.make_settings(settings)
         _lib.check(self._lib.adr_serve_add_scene(self._h, means.data_ptr(), scales.data_ptr(),
                                                  rots.data_ptr(), opac.data_ptr(), sh.data_ptr(),
-                                                 means.shape[0], ctypes.byref(st), ctypes.byref(sid)),
+                                                 n, ctypes.byref(st), ctypes.byref(sid)),
                    "adr_serve_add_scene")
         self._scenes.append(params)
         return sid.value
 
     def submit(self, scene_id: int, camera, out: torch.Tensor) -> int:
-        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
-        assert tuple(out.shape) == (3, camera.height, camera.width)
+        self._check_out(camera, out)
         c = _lib.make_camera(camera)
         t = ctypes.c_uint64()
         _lib.check(self._lib.adr_serve_submit(self._h, scene_id, ctypes.byref(c), out.data_ptr(),
@@ -55,7 +60,8 @@ class Server:
         return t.value
 
     def submit_status(self, scene_id: int, camera, out: torch.Tensor) -> int:
-        """Like submit but returns the raw status (no exception)."""
+        """Like submit but returns the raw status (no exception from the library)."""
+        self._check_out(camera, out)
         c = _lib.make_camera(camera)
         t = ctypes.c_uint64()
         return self._lib.adr_serve_submit(self._h, scene_id, ctypes.byref(c), out.data_ptr(),
