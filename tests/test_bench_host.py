@@ -1,0 +1,53 @@
+"""Host logic of bench.py that needs no GPU: the parsing of the nvidia-smi
+clock samples taken during the timed region (a run that saw a thermal or
+hardware slowdown must say so) and the algorithmic-bytes table of the
+roofline."""
+import os
+import tempfile
+
+import bench
+
+
+def _summary(lines):
+    clk = bench.ClockSampler(0)
+    clk.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    clk.file.write("\n".join(lines) + "\n")
+    clk.proc = object()          # stands in for the finished nvidia-smi process
+    out = clk.summary()
+    assert not os.path.exists(clk.file.name)
+    return out
+
+
+def test_clock_summary_median_max_and_no_reasons():
+    na = "Not Active"
+    rows = [f"0, {mhz}, 2070, 950.0, 0x0000000000000000, {na}, {na}, {na}, {na}"
+            for mhz in (2070, 2055, 1987, 2070, 2070)]
+    out = _summary(rows)
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
+
+
+def test_clock_summary_reports_every_active_reason():
+    na, a = "Not Active", "Active"
+    rows = [f"0, 1800, 2070, 1400.0, 0x4, {na}, {na}, {na}, {a}",
+            f"0, 1500, 2070, 1400.0, 0x48, {a}, {na}, {a}, {na}",
+            "garbage line",
+            f"0, [N/A], 2070, 1400.0, 0x0, {na}, {na}, {na}, {na}"]
+    out = _summary(rows)
+    assert out["samples"] == 2 and out["sm_mhz"] == 1650.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples():
+    assert _summary([])["reasons"] == ["no samples"]
+    clk = bench.ClockSampler(0)
+    assert clk.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_algorithmic_bytes_table():
+    u = {"pairs": 1000, "visible": 100, "runs": 50, "evals": 0, "loaded": 10}
+    hw = 1920 * 1080
+    assert bench.kernel_bytes("preprocess", 200, u, hw) == 44 * 200 + 192 * 100 + 104 * 200
+    assert bench.kernel_bytes("tile_scatter_rows", 200, u, hw) == 8 * 50 + 4 * 1000
+    assert bench.kernel_bytes("render", 200, u, hw) == 52 * 10 + 12 * hw
+    assert bench.kernel_bytes("slice", 200, u, hw) is None       # depends on the slices' sizes
+    assert bench.kernel_bytes("no_such_kernel", 200, u, hw) is None
