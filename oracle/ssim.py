@@ -17,7 +17,8 @@ training, on which the paper builds), and L_ssim = 1 - mean S.
 The window sums are written out as the 121 shifted copies of the zero-padded
 image, with no separable split; the gradient is the chain rule through the
 three local moments mu_x, E[x^2], E[xy] and the adjoint of the window sum.
-Only tests (and the benchmark's CPU baseline) may import this module.
+Only tests and __graft_entry__.smoke() may import this module (TEST
+INFRASTRUCTURE: the product path never loads it).
 """
 from __future__ import annotations
 
