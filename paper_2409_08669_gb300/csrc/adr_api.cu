@@ -208,6 +208,7 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
     do {                                                                                    \
         e = cudaMalloc((void**)&(ptr), (bytes));                                           \
         if (e != cudaSuccess) {                                                             \
+            (void)cudaGetLastError(); /* not sticky: clear it for the next launch check */  \
             free_workspace(w);                                                              \
             return fail(ADR_ERR_CUDA, "cudaMalloc(%zu) for %s: %s", (size_t)(bytes), #ptr,  \
                         cudaGetErrorString(e));                                             \
@@ -608,10 +609,22 @@ adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, 
     cudaStream_t strm = (cudaStream_t)stream;
     const size_t N = (size_t)c->ws.max_n;
     const size_t per = 3 + 3 + 4 + 1 + 48;   // floats per Gaussian
-    if (!c->stage) {
-        ADR_CUDA(cudaMalloc((void**)&c->stage, N * per * sizeof(float)));
-        ADR_CUDA(cudaMalloc((void**)&c->stage_img, (size_t)c->max_w * c->max_h * 4 * sizeof(float)));
-        ADR_CUDA(cudaMalloc((void**)&c->stage_load, (size_t)c->max_w * c->max_h * sizeof(int32_t)));
+    if (!c->stage) {   // all three staging buffers, or none (a later call retries)
+        float *stage = nullptr, *stage_img = nullptr;
+        int32_t* stage_load = nullptr;
+        const size_t px = (size_t)c->max_w * c->max_h;
+        cudaError_t e = cudaMalloc((void**)&stage, N * per * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&stage_img, px * 4 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&stage_load, px * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();   // clear it, or the next launch check would report it
+            if (stage) cudaFree(stage);
+            if (stage_img) cudaFree(stage_img);
+            return fail(ADR_ERR_CUDA, "adr_render_host staging allocation: %s", cudaGetErrorString(e));
+        }
+        c->stage = stage;
+        c->stage_img = stage_img;
+        c->stage_load = stage_load;
     }
     // Device layout: sh first (16-byte aligned), then rots, means, scales, opac.
     float* d_sh = c->stage;

@@ -299,6 +299,7 @@ adr_status adr_serve_create(adr_server** out, const adr_serve_config* cfg) {
             cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc((void**)&sl->img, (size_t)3 * cfg->max_width * cfg->max_height * sizeof(float)) != cudaSuccess ||
             cudaHostAlloc((void**)&sl->host_words, 16, cudaHostAllocDefault) != cudaSuccess) {
+            (void)cudaGetLastError();   // an allocation error is not sticky: clear it
             destroy_server(s);
             return report_error(ADR_ERR_CUDA, "adr_serve_create: slot allocation failed");
         }
