@@ -35,13 +35,13 @@ class Server:
 
     def _check_out(self, camera, out):
         """The request's image [3, H, W] is written in full by the device."""
+        if not isinstance(out, torch.Tensor) or tuple(out.shape) != (3, camera.height, camera.width):
+            raise ValueError(f"out must be a [3, {camera.height}, {camera.width}] tensor")
         check_tensor("out", out, 3 * camera.height * camera.width, device=self.device)
-        if tuple(out.shape) != (3, camera.height, camera.width):
-            raise ValueError(f"out must be [3, {camera.height}, {camera.width}], got {tuple(out.shape)}")
 
     def add_scene(self, params, settings) -> int:
-        means, scales, rots, opac, sh = params
         n = check_params(params, self.device)
+        means, scales, rots, opac, sh = params
         sid = ctypes.c_int32()
         st = _lib.make_settings(settings)
         _lib.check(self._lib.adr_serve_add_scene(self._h, means.data_ptr(), scales.data_ptr(),

@@ -145,3 +145,18 @@ def test_parameter_checks_reject_what_the_kernels_would_overrun():
         check_tensor("load", torch.zeros(4), 4, dtype=torch.int32)
     with pytest.raises(TypeError):
         check_tensor("img", np.zeros(4, np.float32), 4)
+
+
+def test_serving_request_image_checked_before_submit():
+    import torch
+    from paper_2409_08669_gb300 import scenes as S
+    from paper_2409_08669_gb300.serve import Server
+    srv = Server.__new__(Server)          # no server: only the binding's checks run
+    srv.device, srv._h = 0, None
+    cam = S.look_at((0, 0, -3), width=32, height=24)
+    with pytest.raises(ValueError, match=r"\[3, 24, 32\]"):
+        srv._check_out(cam, torch.empty(3, 32, 24))
+    with pytest.raises(ValueError, match="cuda:0"):
+        srv._check_out(cam, torch.empty(3, 24, 32))
+    with pytest.raises(ValueError, match="expected 5 parameter tensors"):
+        srv.add_scene([torch.zeros(1, 3)], S.Settings())
