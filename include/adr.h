@@ -123,11 +123,11 @@ typedef struct adr_ctx adr_ctx;
 
 /* Create a context on `device` with workspace for up to `max_gaussians`
  * Gaussians (at most 2^29), `pair_capacity` Gaussian-tile pairs (at most
- * 2^30) and images up to max_width x max_height (at most 2^16 tiles, e.g.
- * 4096 x 4096).  All
- * workspace is allocated here (cudaMalloc); no later call allocates, except
- * the first adr_render_host, which allocates its staging buffers.  Returns ADR_ERR_INVALID for sizes <= 0 or too
- * large, ADR_ERR_CUDA if allocation fails (nothing leaks). */
+ * 2^30) and images up to max_width x max_height (at most 4096 per side).
+ * All workspace is allocated here (cudaMalloc); no later call allocates,
+ * except the first adr_render_host, which allocates its staging buffers.
+ * Returns ADR_ERR_INVALID for sizes <= 0 or too large (checked before any
+ * CUDA call), ADR_ERR_CUDA if allocation fails (nothing leaks). */
 adr_status adr_create(adr_ctx **ctx, int64_t max_gaussians, int64_t pair_capacity,
                       int32_t max_width, int32_t max_height, int32_t device);
 
@@ -187,8 +187,9 @@ adr_status adr_render(adr_ctx *ctx, float *img, float *t_final, int32_t *load, v
 
 /* Backward of the last adr_render (the differentiable path the paper trains
  * through, Sec. 4.4 total loss): given dL/dimg [3,H,W] and optionally
- * dL/dload [H,W] (the straight-through reading of Eq. 12: d l_i / d alpha_ik = 1
- * for every blended pair; may be NULL), writes dL/d means [n,3], scales [n,3],
+ * dL/dload [H,W] (may be NULL; it reaches the opacities through the reading
+ * of d l_i / d alpha_ik that the frame's settings->load_grad selects, see
+ * adr_load_grad), writes dL/d means [n,3], scales [n,3],
  * rots [n,4] (w,x,y,z; 16-byte aligned), opac [n] and sh [n,16,3] (coefficients
  * above sh_degree get 0).  The parameter arrays must be the ones passed to
  * adr_preprocess for this frame, unchanged.  Gradient buffers are overwritten.
