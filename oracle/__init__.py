@@ -31,44 +31,56 @@ F_VISIBLE = 1
 F_NEAR = 2
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc a C source of the oracle into a shared library (IEEE double, no FMA
+    contraction).  The tests also compile deliberately broken copies with it."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile adr_oracle.c with gcc (IEEE double, no FMA contraction)."""
+    """Compile adr_oracle.c (when the library is missing or older than it)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+        compile_library(_SRC, _LIB_PATH)
     return _LIB_PATH
+
+
+def load_library(path: str):
+    """Open a compiled oracle and declare its functions' signatures."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.orc_preprocess.restype = i64
+    lib.orc_preprocess.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, i32, dbl, dbl, dbl,
+                                   dbl, P, P, P, P, P, P]
+    lib.orc_emit_pairs.restype = i64
+    lib.orc_emit_pairs.argtypes = [i64, P, P, P, i32, P, P, i64]
+    lib.orc_sort_pairs.restype = None
+    lib.orc_sort_pairs.argtypes = [i64, P, P]
+    lib.orc_tile_ranges.restype = None
+    lib.orc_tile_ranges.argtypes = [i64, P, i32, P]
+    lib.orc_render_tiled.restype = None
+    lib.orc_render_tiled.argtypes = [i32, i32, P, P, P, P, dbl, dbl, P, dbl, dbl,
+                                     P, P, P, P, P, P]
+    lib.orc_render_brute.restype = None
+    lib.orc_render_brute.argtypes = [i64, i32, i32, P, P, P, P, P, dbl, dbl, P, P, P, P]
+    lib.orc_load_std.restype = dbl
+    lib.orc_load_std.argtypes = [i64, P]
+    lib.orc_real_sh.restype = dbl
+    lib.orc_real_sh.argtypes = [i32, i32, P]
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
-            lib.orc_preprocess.restype = i64
-            lib.orc_preprocess.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, i32, dbl, dbl, dbl,
-                                           dbl, P, P, P, P, P, P]
-            lib.orc_emit_pairs.restype = i64
-            lib.orc_emit_pairs.argtypes = [i64, P, P, P, i32, P, P, i64]
-            lib.orc_sort_pairs.restype = None
-            lib.orc_sort_pairs.argtypes = [i64, P, P]
-            lib.orc_tile_ranges.restype = None
-            lib.orc_tile_ranges.argtypes = [i64, P, i32, P]
-            lib.orc_render_tiled.restype = None
-            lib.orc_render_tiled.argtypes = [i32, i32, P, P, P, P, dbl, dbl, P, dbl, dbl,
-                                             P, P, P, P, P, P]
-            lib.orc_render_brute.restype = None
-            lib.orc_render_brute.argtypes = [i64, i32, i32, P, P, P, P, P, dbl, dbl, P, P, P, P]
-            lib.orc_load_std.restype = dbl
-            lib.orc_load_std.argtypes = [i64, P]
-            lib.orc_real_sh.restype = dbl
-            lib.orc_real_sh.argtypes = [i32, i32, P]
-            _lib = lib
+            _lib = load_library(build())
     return _lib
 
 

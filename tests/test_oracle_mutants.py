@@ -1,0 +1,82 @@
+"""Planted mistakes in the oracle (CPU only).
+
+Each case compiles a copy of oracle/adr_oracle.c with one plausible error --
+a dropped term, a wrong sign or index, a swapped axis, a transposed operand,
+a condition moved -- swaps it in for the real oracle and checks that one of
+the pins in test_oracle_pins.py fails.  The pin is first run on the real
+oracle, where it must pass.  A site string that no longer occurs in the
+source fails the test, so the cases follow edits of the oracle."""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "adr_oracle.c")
+
+# (name, text in adr_oracle.c, replacement, the pin that must catch it)
+MUTANTS = [
+    ("rotation_sign", "R[0][1] = 2 * (x * y - w * z);", "R[0][1] = 2 * (x * y + w * z);",
+     lambda: pins.test_cov2d_closed_form_at_centre(0.3)),
+    ("lowpass_dropped_on_x", "double a = C2[0][0] + lowpass, b = C2[0][1], c = C2[1][1] + lowpass;",
+     "double a = C2[0][0], b = C2[0][1], c = C2[1][1] + lowpass;",
+     lambda: pins.test_cov2d_closed_form_at_centre(0.0)),
+    ("jacobian_unclamped", "double txz = fmin(limx, fmax(-limx, p[0] / z)) * z;", "double txz = p[0];",
+     pins.test_jacobian_clamp_freezes_offaxis_term),
+    ("depth_sum_order", "d32 = d32 + cam[9] * yf;\n        d32 = d32 + cam[10] * zf;",
+     "d32 = d32 + cam[10] * zf;\n        d32 = d32 + cam[9] * yf;",
+     pins.test_depth_bits_follow_the_fixed_float32_order),
+    ("conic_offdiagonal_sign", "g[G_CONIC_B] = -b / det;", "g[G_CONIC_B] = b / det;",
+     lambda: pins.test_single_gaussian_image_closed_form(0.7, 0.9)),
+    ("pixel_centre_half_offset", "double px = fx * p[0] / z + cx,", "double px = fx * p[0] / z + cx + 0.5,",
+     lambda: pins.test_single_gaussian_image_closed_form(0.0, 0.3)),
+    ("adaptive_radius_factor_two_dropped", "double r_ad = sqrt(2.0 * lam * L);",
+     "double r_ad = sqrt(lam * L);",
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0)),
+    ("aabb_axes_swapped", "double x_max = sqrt(2.0 * a * L);", "double x_max = sqrt(2.0 * c * L);",
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0)),
+    ("r_o_cap_dropped", "rx = ry = fmin(r_ad, r_o);", "rx = ry = r_ad;",
+     pins.test_rcap_binds_for_opaque_gaussians),
+    ("tile_interval_rounds_down", "double a = ceil(c - r), b = floor(c + r);",
+     "double a = floor(c - r), b = floor(c + r);",
+     lambda: pins.test_pair_tiles_equal_pixel_brute_force(3)),
+    ("tile_key_transposed", "keys[off] = ((uint64_t)(ty * tiles_x + tx) << 32)",
+     "keys[off] = ((uint64_t)(tx * tiles_x + ty) << 32)",
+     lambda: pins.test_pair_tiles_equal_pixel_brute_force(3)),
+    ("sort_ties_reversed", "if (x->v != y->v) return x->v < y->v ? -1 : 1;",
+     "if (x->v != y->v) return x->v > y->v ? -1 : 1;",
+     pins.test_sort_ties_keep_index_order),
+    ("sh_cos_for_sin", "if (m > 0) return sqrt(2.0) * K * P * cos(m * phi);",
+     "if (m > 0) return sqrt(2.0) * K * P * sin(m * phi);",
+     pins.test_real_sh_matches_scipy),
+    ("sh_sqrt2_dropped", "if (m < 0) return sqrt(2.0) * K * P * sin(am * phi);",
+     "if (m < 0) return K * P * sin(am * phi);",
+     pins.test_real_sh_orthonormal_by_quadrature),
+    ("opacity_clamp_dropped", "double alpha = fmin(0.99, a_raw);", "double alpha = a_raw;",
+     pins.test_early_termination_worked_example),
+    ("alpha_low_skip_dropped", "if (alpha < alpha_low) return;", "if (alpha < 0.0) return;",
+     lambda: pins.test_single_gaussian_image_closed_form(0.0, 0.3)),
+    ("skipped_pairs_counted", "if (alpha < alpha_low) return;",
+     "if (alpha < alpha_low) { s->load += 1; return; }",
+     lambda: pins.test_single_gaussian_image_closed_form(-1.2, 0.05)),
+    ("stop_after_blending", "if (test_T < t_min) { s->done = 1; return; }",
+     "if (test_T < t_min) { s->done = 1; }",
+     pins.test_early_termination_worked_example),
+    ("blend_weight_without_transmittance", "s->C[c] += rgb[c] * alpha * s->T;",
+     "s->C[c] += rgb[c] * alpha;",
+     pins.test_two_gaussian_stack_worked_example),
+]
+
+
+@pytest.mark.parametrize("site,replacement,pin", [m[1:] for m in MUTANTS], ids=[m[0] for m in MUTANTS])
+def test_a_pin_catches_the_planted_mistake(site, replacement, pin, tmp_path, monkeypatch):
+    pin()                                            # passes on the real oracle
+    src = open(SRC).read()
+    assert src.count(site) == 1, f"mutation site not found once in adr_oracle.c: {site!r}"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(site, replacement))
+    lib = oracle.load_library(oracle.compile_library(str(path), str(tmp_path / "libmutant.so")))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    with pytest.raises(AssertionError):
+        pin()

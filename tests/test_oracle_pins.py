@@ -506,6 +506,42 @@ def test_sort_and_ranges_against_numpy():
     assert int((ranges[:, 1] - ranges[:, 0]).sum()) == skeys.shape[0]
 
 
+def test_sort_ties_keep_index_order():
+    """Gaussians at one position share their depth bits, so their pairs have
+    equal keys; the stable sort (Sec. 3.2, over index-order emission) keeps
+    them in index order, as numpy's stable argsort does."""
+    base = S.tiny_scene(1, n=40)
+    idx = np.repeat(np.arange(8), 5)            # 8 positions, 5 Gaussians each
+    sc = base.subset(np.arange(40))
+    sc.means[:] = base.means[idx]
+    cam = S.look_at((0.3, -0.2, -3), width=96, height=80)
+    pre = oracle.preprocess(sc, cam, S.Settings(mode=S.MODE_PLAIN))
+    keys, vals = oracle.emit_pairs(pre)
+    skeys, svals = oracle.sort_pairs(keys, vals)
+    assert np.unique(skeys).size < skeys.size   # ties present
+    order = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(svals, vals[order])
+
+
+def test_depth_bits_follow_the_fixed_float32_order():
+    """The sort depth is ((v20 x + v21 y) + v22 z) + v23 in float32, each
+    product and sum rounded, in that order, for any camera orientation."""
+    rng = np.random.default_rng(8)
+    sc = S.tiny_scene(2, n=400)
+    for _ in range(4):
+        eye = rng.normal(size=3)
+        eye = 3.0 * eye / np.linalg.norm(eye)
+        cam = S.look_at(tuple(eye), width=64, height=48)
+        pre = oracle.preprocess(sc, cam, S.Settings())
+        v = cam.view.astype(np.float32)
+        x, y, z = (sc.means[:, k].astype(np.float32) for k in range(3))
+        d = v[2, 0] * x
+        d = (d + v[2, 1] * y).astype(np.float32)
+        d = (d + v[2, 2] * z).astype(np.float32)
+        d = (d + v[2, 3]).astype(np.float32)
+        np.testing.assert_array_equal(pre["depth"].view(np.uint32), d.view(np.uint32))
+
+
 # ----------------------------------------------------------------------------
 # Brute force, losslessness and nested culling (Sec. 4.2-4.3, Sec. 5.4)
 # ----------------------------------------------------------------------------
