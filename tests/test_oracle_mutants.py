@@ -1,17 +1,22 @@
 """Planted mistakes in the oracle (CPU only).
 
-Each case compiles a copy of oracle/adr_oracle.c with one plausible error --
-a dropped term, a wrong sign or index, a swapped axis, a transposed operand,
-a condition moved -- swaps it in for the real oracle and checks that one of
-the pins in test_oracle_pins.py fails.  The pin is first run on the real
-oracle, where it must pass.  A site string that no longer occurs in the
-source fails the test, so the cases follow edits of the oracle."""
+Each case makes a copy of the oracle with one plausible error -- a dropped
+term, a wrong sign or index, a swapped axis, a transposed operand, a
+condition moved -- puts it in place of the real one and checks that one of
+the pins fails: the C forward path (oracle/adr_oracle.c, compiled with gcc,
+pins in test_oracle_pins.py) and the image loss (oracle/ssim.py, pins in
+test_ssim_oracle.py).  The pin is first run on the real oracle, where it must
+pass.  A site string that no longer occurs in the source fails the test, so
+the cases follow edits of the oracle."""
+import importlib.util
 import os
 
 import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_ssim_oracle as ssim_pins
+from oracle import ssim as ossim
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "adr_oracle.c")
 
@@ -78,5 +83,47 @@ def test_a_pin_catches_the_planted_mistake(site, replacement, pin, tmp_path, mon
     path.write_text(src.replace(site, replacement))
     lib = oracle.load_library(oracle.compile_library(str(path), str(tmp_path / "libmutant.so")))
     monkeypatch.setattr(oracle, "_lib", lib)
+    with pytest.raises(AssertionError):
+        pin()
+
+
+# The image-loss oracle: a mutated copy of oracle/ssim.py is loaded and put in
+# place of the module the SSIM pins use.
+SSIM_MUTANTS = [
+    ("c1_not_squared", "C1 = 0.01 ** 2", "C1 = 0.01",
+     lambda: ssim_pins.test_constant_images_interior_closed_form(0.2, 0.7)),
+    ("c2_not_squared", "C2 = 0.03 ** 2", "C2 = 0.03",
+     lambda: ssim_pins.test_checkerboard_against_constant_closed_form(0.5, 0.3, 0.2)),
+    ("window_sigma", "SIGMA = 1.5", "SIGMA = 1.0", ssim_pins.test_window_sum_matches_scipy_gaussian_filter),
+    ("window_radius", "RADIUS = 5", "RADIUS = 4", ssim_pins.test_window_sum_matches_scipy_gaussian_filter),
+    ("edge_padding", "    p = np.zeros((h + 2 * RADIUS, wd + 2 * RADIUS))\n"
+                     "    p[RADIUS:RADIUS + h, RADIUS:RADIUS + wd] = a\n",
+     "    p = np.pad(a, RADIUS, mode=\"edge\")\n", ssim_pins.test_window_sum_per_pixel_double_loop),
+    ("covariance_without_means", "exy - mx * my", "exy",
+     lambda: ssim_pins.test_checkerboard_against_constant_closed_form(0.5, 0.3, 0.2)),
+    ("gradient_dxy_factor", "d_xy = 2 * s / a2", "d_xy = s / a2",
+     lambda: ssim_pins.test_gradient_matches_central_differences(0.0, 1.0)),
+    ("gradient_dxx_sign", "d_xx = -s / b2", "d_xx = s / b2",
+     lambda: ssim_pins.test_gradient_matches_central_differences(0.0, 1.0)),
+    ("gradient_second_moment_factor", "window_sum(d_mu) + 2 * x[c] * window_sum(d_xx)",
+     "window_sum(d_mu) + x[c] * window_sum(d_xx)",
+     lambda: ssim_pins.test_gradient_matches_central_differences(0.44, 0.11)),
+    ("l1_gradient_not_averaged", "grad += w_l1 / n * np.sign(x - y)", "grad += w_l1 * np.sign(x - y)",
+     ssim_pins.test_l1_subgradient_zero_at_ties),
+]
+
+
+@pytest.mark.parametrize("site,replacement,pin", [m[1:] for m in SSIM_MUTANTS],
+                         ids=[m[0] for m in SSIM_MUTANTS])
+def test_a_pin_catches_the_planted_image_loss_mistake(site, replacement, pin, tmp_path, monkeypatch):
+    pin()                                            # passes on the real oracle
+    src = open(ossim.__file__).read()
+    assert site in src, f"mutation site not found in ssim.py: {site!r}"
+    path = tmp_path / "ssim_mutant.py"
+    path.write_text(src.replace(site, replacement))
+    spec = importlib.util.spec_from_file_location("ssim_mutant", path)
+    mutant = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mutant)
+    monkeypatch.setattr(ssim_pins, "O", mutant)
     with pytest.raises(AssertionError):
         pin()

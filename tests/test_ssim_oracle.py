@@ -61,6 +61,28 @@ def test_constant_images_interior_closed_form(a, b):
     np.testing.assert_allclose(s[5:-5, 5:-5], want, rtol=1e-11)   # E[x^2] - mu^2 rounds to ~1e-17, over C2
 
 
+@pytest.mark.parametrize("a,d,b", [(0.5, 0.3, 0.2), (0.4, 0.05, 0.9)])
+def test_checkerboard_against_constant_closed_form(a, d, b):
+    """x = a + d (-1)^(i+j) against the constant b.  Away from the border the
+    window's mean of x is a + d s (-1)^(i+j), with s = (sum_u g_u (-1)^u /
+    sum_u g_u)^2 for the 1-D taps g_u = exp(-u^2 / (2 * 1.5^2)), |u| <= 5; its
+    variance is d^2 (1 - s^2); the covariance with a constant is 0.  So
+    S = (2 mu_x b + C1) C2 / ((mu_x^2 + b^2 + C1) (d^2 (1 - s^2) + C2)),
+    which, unlike the constant-image case, depends on C2."""
+    h, w = 16, 18
+    ii, jj = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    sign = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
+    x = (a + d * sign)[None]
+    y = np.full((1, h, w), b)
+    g = [math.exp(-u * u / (2 * 1.5 ** 2)) for u in range(-5, 6)]
+    s = (sum(gu * (-1) ** u for gu, u in zip(g, range(-5, 6))) / sum(g)) ** 2
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    mu = a + d * s * sign
+    want = (2 * mu * b + c1) * c2 / ((mu * mu + b * b + c1) * (d * d * (1 - s * s) + c2))
+    got = O.ssim_map(x, y)[0]
+    np.testing.assert_allclose(got[5:-5, 5:-5], want[5:-5, 5:-5], rtol=1e-9)
+
+
 def test_ssim_symmetric_and_bounded():
     x, y = _pair(3)
     s_xy, s_yx = O.ssim_map(x, y), O.ssim_map(y, x)
