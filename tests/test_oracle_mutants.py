@@ -6,16 +6,20 @@ condition moved -- puts it in place of the real one and checks that one of
 the pins fails: the C forward path (oracle/adr_oracle.c, compiled with gcc,
 pins in test_oracle_pins.py) and the image loss (oracle/ssim.py, pins in
 test_ssim_oracle.py).  The pin is first run on the real oracle, where it must
-pass.  A site string that no longer occurs in the source fails the test, so
-the cases follow edits of the oracle."""
+pass.  The gradient oracle (oracle/grad.py, pins in test_grad_oracle.py) is
+treated the same way.  A site string that no longer occurs in the source
+fails the test, so the cases follow edits of the oracle."""
 import importlib.util
 import os
 
 import pytest
 
 import oracle
+from paper_2409_08669_gb300 import scenes as S
+import test_grad_oracle as grad_pins
 import test_oracle_pins as pins
 import test_ssim_oracle as ssim_pins
+from oracle import grad as ograd
 from oracle import ssim as ossim
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "adr_oracle.c")
@@ -125,5 +129,44 @@ def test_a_pin_catches_the_planted_image_loss_mistake(site, replacement, pin, tm
     mutant = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mutant)
     monkeypatch.setattr(ssim_pins, "O", mutant)
+    with pytest.raises(AssertionError):
+        pin()
+
+
+# The gradient oracle: a mutated copy of oracle/grad.py, loaded inside the
+# oracle package (it imports the C oracle's wrappers relatively), is put in
+# place of the module the gradient pins use.
+GRAD_MUTANTS = [
+    ("blend_weight_without_transmittance", "C = C + rgb[g][:, None] * (alpha * T * bw)[None]",
+     "C = C + rgb[g][:, None] * (alpha * bw)[None]",
+     lambda: grad_pins.test_torch_forward_equals_c_oracle(S.MODE_AABB)),
+    ("conic_cross_term_factor", "q = conic[g, 0] * dx * dx + 2 * conic[g, 1] * dx * dy",
+     "q = conic[g, 0] * dx * dx + conic[g, 1] * dx * dy",
+     lambda: grad_pins.test_torch_forward_equals_c_oracle(S.MODE_PLAIN)),
+    ("straight_through_sign", "L = L + bw * (1.0 + (alpha - a_det))", "L = L + bw * (1.0 - (alpha - a_det))",
+     grad_pins.test_load_term_straight_through_definition),
+    ("early_stop_sign", "cnt - cnt / theta * (S - S.detach())", "cnt + cnt / theta * (S - S.detach())",
+     grad_pins.test_load_term_early_stop_reading_follows_the_slope_of_the_count),
+    ("early_stop_without_optical_depth", "cnt - cnt / theta * (S - S.detach())",
+     "cnt - cnt * (S - S.detach())",
+     grad_pins.test_load_term_early_stop_reading_follows_the_slope_of_the_count),
+    ("optical_depth_as_alpha", "S = S + bw * -torch.log1p(-alpha)", "S = S + bw * alpha",
+     grad_pins.test_load_term_early_stop_reading_on_a_stack),
+]
+
+
+@pytest.mark.parametrize("site,replacement,pin", [m[1:] for m in GRAD_MUTANTS],
+                         ids=[m[0] for m in GRAD_MUTANTS])
+def test_a_pin_catches_the_planted_gradient_mistake(site, replacement, pin, tmp_path, monkeypatch):
+    pin()                                            # passes on the real oracle
+    src = open(ograd.__file__).read()
+    assert src.count(site) == 1, f"mutation site not found once in grad.py: {site!r}"
+    path = tmp_path / "grad_mutant.py"
+    path.write_text(src.replace(site, replacement))
+    spec = importlib.util.spec_from_file_location("oracle.grad_mutant", path)
+    mutant = importlib.util.module_from_spec(spec)
+    mutant.__package__ = "oracle"
+    spec.loader.exec_module(mutant)
+    monkeypatch.setattr(grad_pins, "og", mutant)
     with pytest.raises(AssertionError):
         pin()
