@@ -75,6 +75,19 @@ MUTANTS = [
     ("blend_weight_without_transmittance", "s->C[c] += rgb[c] * alpha * s->T;",
      "s->C[c] += rgb[c] * alpha;",
      pins.test_two_gaussian_stack_worked_example),
+    ("near_plane_at_zero", "if (!(d32 > near_z)) continue;", "if (!(d32 > 0.0f)) continue;",
+     pins.test_near_plane_cull_and_depth_bits),
+    ("eigenvalue_without_offdiagonal", "sqrt(0.25 * (a - c) * (a - c) + b * b);",
+     "sqrt(0.25 * (a - c) * (a - c));",
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(1)),
+    ("rect_3dgs_high_edge_not_rounded_up", "b = floor((c + R + (ORC_TILE - 1)) / ORC_TILE);",
+     "b = floor((c + R) / ORC_TILE);",
+     lambda: pins.test_3dgs_rect_rule_equals_point_set_brute_force(3)),
+    ("tile_range_end_off_by_one", "ranges[2 * tile + 1] = (uint32_t)(i + 1);",
+     "ranges[2 * tile + 1] = (uint32_t)i;",
+     pins.test_sort_and_ranges_against_numpy),
+    ("load_std_sample_form", "return sqrt(var / (double)hw);", "return sqrt(var / (double)(hw - 1));",
+     pins.test_load_std_population_form),
 ]
 
 
