@@ -51,3 +51,19 @@ def test_algorithmic_bytes_table():
     assert bench.kernel_bytes("render", 200, u, hw) == 52 * 10 + 12 * hw
     assert bench.kernel_bytes("slice", 200, u, hw) is None       # depends on the slices' sizes
     assert bench.kernel_bytes("no_such_kernel", 200, u, hw) is None
+
+
+def test_oracle_frame_sample_scales_to_a_full_frame():
+    # the CPU baseline / reference arm: a Gaussian sample and a tile sample of
+    # one frame, each timed and scaled by its sampling factor
+    from paper_2409_08669_gb300 import scenes as S
+    scene = S.tiny_scene(0, n=4000)
+    cam = S.look_at((0, 0, -3), width=128, height=96)
+    of = bench.OracleFrame(scene, g_div=4, t_div=8, seed=1)
+    assert of.sub.n == 1000
+    secs = of.frame_seconds(cam, S.Settings(mode=S.MODE_AABB), key=0)
+    assert 0.0 < secs < 60.0
+    _, ranges, _, tile_scale = of.cache[0]
+    assert tile_scale == (8 * 6) / (8 * 6 // 8)           # 48 tiles, 6 sampled
+    base = bench.cpu_baseline(scene, [cam], S.Settings(mode=S.MODE_AABB), budget_s=0.0)
+    assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
