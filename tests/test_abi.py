@@ -160,3 +160,19 @@ def test_serving_request_image_checked_before_submit():
         srv._check_out(cam, torch.empty(3, 24, 32))
     with pytest.raises(ValueError, match="expected 5 parameter tensors"):
         srv.add_scene([torch.zeros(1, 3)], S.Settings())
+
+
+def test_product_path_never_touches_the_oracle():
+    # the package and its CUDA sources name neither the oracle package nor its library
+    pkg = os.path.join(ROOT, "paper_2409_08669_gb300")
+    offenders = []
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for fn in files:
+            if not fn.endswith((".py", ".cu", ".cuh", ".h")):
+                continue
+            text = open(os.path.join(dirpath, fn)).read()
+            if re.search(r"^\s*(import oracle|from oracle\b)|liboracle|adr_oracle", text, re.M):
+                offenders.append(os.path.relpath(os.path.join(dirpath, fn), ROOT))
+    assert not offenders, offenders
