@@ -176,3 +176,12 @@ def test_product_path_never_touches_the_oracle():
             if re.search(r"^\s*(import oracle|from oracle\b)|liboracle|adr_oracle", text, re.M):
                 offenders.append(os.path.relpath(os.path.join(dirpath, fn), ROOT))
     assert not offenders, offenders
+
+
+def test_oracle_never_touches_the_product():
+    # the oracle imports nothing from the package and includes none of its headers
+    odir = os.path.join(ROOT, "oracle")
+    for fn in os.listdir(odir):
+        if fn.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(odir, fn)).read()
+            assert not re.search(r"paper_2409_08669_gb300|adr_internal|libadr|include/adr", text), fn
