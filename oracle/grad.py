@@ -167,6 +167,50 @@ def render_torch(params, camera, settings, structure=None):
     return img, Tout, load
 
 
+def clamp_near_pixels(scene, camera, settings, tol=1e-5):
+    """[H,W] bool: pixels where a Gaussian that is blended (Eq. 3) has an
+    unclamped opacity sigma * exp(-q/2) within `tol` (relative) of the 0.99
+    clamp of Eq. 2.  The clamp switches that pair's opacity derivative off, so
+    a path that evaluates the exponential with a relative error near `tol` may
+    take the other side of min(0.99, .) there and differ by the whole term.
+    Same traversal as render_torch, without autograd."""
+    params = leaf_params(scene)
+    structure = frame_structure(params, camera, settings)
+    with torch.no_grad():
+        px, py, conic, opac, _ = gaussian_quantities(params, camera, settings)
+    W, H = camera.width, camera.height
+    tx = (W + TILE - 1) // TILE
+    ranges, vals = structure["ranges"], structure["vals"]
+    out = np.zeros((H, W), bool)
+    for tile in range(ranges.shape[0]):
+        y0, x0 = (tile // tx) * TILE, (tile % tx) * TILE
+        ys = torch.arange(y0, min(y0 + TILE, H), dtype=torch.float64)
+        xs = torch.arange(x0, min(x0 + TILE, W), dtype=torch.float64)
+        Yp, Xp = torch.meshgrid(ys, xs, indexing="ij")
+        Yp, Xp = Yp.reshape(-1), Xp.reshape(-1)
+        T = torch.ones_like(Xp)
+        done = torch.zeros(Xp.shape[0], dtype=torch.bool)
+        hit = torch.zeros(Xp.shape[0], dtype=torch.bool)
+        for k in range(int(ranges[tile, 0]), int(ranges[tile, 1])):
+            if bool(done.all()):
+                break
+            g = int(vals[k])
+            dx, dy = px[g] - Xp, py[g] - Yp
+            q = conic[g, 0] * dx * dx + 2.0 * conic[g, 1] * dx * dy + conic[g, 2] * dy * dy
+            raw = opac[g] * torch.exp(-0.5 * q)
+            alpha = torch.clamp_max(raw, 0.99)
+            live = (~done) & (alpha >= settings.alpha_low)
+            test_T = T * (1 - alpha)
+            stop = live & (test_T < settings.t_min)
+            done = done | stop
+            blend = live & ~stop
+            hit |= blend & (torch.abs(raw - 0.99) <= tol * 0.99)
+            T = torch.where(blend, test_T, T)
+        h, w = len(ys), len(xs)
+        out[y0:y0 + h, x0:x0 + w] = hit.reshape(h, w).numpy()
+    return out
+
+
 class _ArrScene:
     def __init__(self, arrays):
         self.means, self.scales, self.rots, self.opac, self.sh = arrays

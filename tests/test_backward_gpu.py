@@ -2,14 +2,26 @@
 analytic gradient (oracle/grad.py, pinned to finite differences of the FP64
 oracle in tests/test_grad_oracle.py).
 
-Bar: relative error of each gradient tensor, ||g_gpu - g_ref|| / ||g_ref||,
-at most 1e-3, with the same seeded inputs.  (FP32 vs FP64: the recovered
-transmittance T_k = T_{k+1} / (1 - alpha_k) and the atomic accumulation carry
-~1e-6 relative error; a handful of near-threshold blend decisions can differ,
-which the norm-wise bound absorbs.)"""
+Bar, element by element for every parameter of every Gaussian:
+|g_gpu - g_ref| <= 1e-3 |g_ref| + 1e-3 max|g_ref| (the max over that
+parameter tensor), with the same seeded inputs.  FP32 against FP64: the
+recovered transmittance T_k = T_{k+1} / (1 - alpha_k) carries ~1e-5 relative
+error after a hundred blends, and the warp sums and atomics add per-pixel
+terms of both signs in FP32, whose rounding the absolute floor covers.
+Pixels where a blend decision of the FP64 oracle lies within tolerance of
+its threshold (alpha vs alpha_low, T(1 - alpha) vs t_min, and a blended
+pair's opacity at the 0.99 clamp) get a zero upstream gradient, so the side
+FP32 takes there cannot change any gradient; these are the forward tests'
+near-threshold pixels.
+
+Cases: uniform scenes at 64x64 and 80x48, and a dense cluster at 136x120
+(lists of up to ~3.5k Gaussians per tile, ~50 blended per pixel), where many
+pixels of a warp blend the same Gaussian and the warp-reduce-then-atomic
+accumulation runs under contention."""
 import numpy as np
 import pytest
 
+import oracle
 from oracle import grad as og
 from paper_2409_08669_gb300 import scenes as S
 
@@ -36,8 +48,29 @@ def _scene(seed=5, n=2000, spread=0.6):
     return sc
 
 
-def _rel(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30))
+def _dense_scene(seed=21, n=6000):
+    """All Gaussians in the heavy scene's dense cluster (means N(0, 0.22),
+    log-scales N(-3, 0.7)), seen from distance ~1.5 so it fills the image."""
+    return S.heavy_scene(n=n, seed=seed, dense_fraction=1.0)
+
+
+def _near_pixels(sc, cam, st):
+    ref = oracle.render(sc, cam, st)
+    return (ref["near"] != 0) | og.clamp_near_pixels(sc, cam, st)
+
+
+def _check_elementwise(got, ref, label):
+    for name, a, b in zip(NAMES, got, ref):
+        assert np.isfinite(a).all(), (label, name)
+        a, b = a.reshape(a.shape[0], -1), b.reshape(b.shape[0], -1)
+        err = np.abs(a - b)
+        tol = 1e-3 * np.abs(b) + 1e-3 * np.abs(b).max()
+        bad = err > tol
+        if bad.any():
+            i, j = np.argwhere(bad)[0]
+            raise AssertionError(f"{label}/{name}: {int(bad.sum())} of {b.size} elements differ; "
+                                 f"first Gaussian {i} [{j}]: gpu {a[i, j]:.6e} oracle {b[i, j]:.6e} "
+                                 f"(max|oracle| {np.abs(b).max():.3e})")
 
 
 def _gpu_grads(rast, sc, cam, st, w, v=None):
@@ -59,11 +92,10 @@ def test_backward_matches_oracle_gradient_2k_64px(rast, mode):
     cam = S.look_at((0.2, -0.1, -2.2), width=64, height=64)
     st = S.Settings(mode=mode)
     w = np.random.default_rng(1).normal(size=(3, 64, 64))
+    w[:, _near_pixels(sc, cam, st)] = 0.0
     got = _gpu_grads(rast, sc, cam, st, w)
     ref, _, _ = og.gradients(sc, cam, st, w)
-    for name, a, b in zip(NAMES, got, ref):
-        assert np.isfinite(a).all(), name
-        assert _rel(a, b) <= 1e-3, (name, _rel(a, b))
+    _check_elementwise(got, ref, f"2k-64px/{S.MODE_NAMES[mode]}")
 
 
 @pytest.mark.parametrize("load_grad", [S.LOAD_GRAD_STRAIGHT, S.LOAD_GRAD_TERMINATION])
@@ -74,10 +106,36 @@ def test_backward_with_load_term_and_background(rast, load_grad):
     rng = np.random.default_rng(4)
     w = rng.normal(size=(3, 48, 80))
     v = rng.normal(size=(48, 80)) * 0.05
+    near = _near_pixels(sc, cam, st)
+    w[:, near] = 0.0
+    v[near] = 0.0
     got = _gpu_grads(rast, sc, cam, st, w, v)
     ref, _, _ = og.gradients(sc, cam, st, w, dl_dload=v)
-    for name, a, b in zip(NAMES, got, ref):
-        assert _rel(a, b) <= 1e-3, (name, _rel(a, b))
+    _check_elementwise(got, ref, f"load-term/{load_grad}")
+
+
+@pytest.mark.parametrize("mode,load_grad", [(S.MODE_AABB, None), (S.MODE_PLAIN, None),
+                                            (S.MODE_AABB, S.LOAD_GRAD_TERMINATION)])
+def test_backward_dense_cluster_elementwise(rast, mode, load_grad):
+    """6000 Gaussians of the dense cluster at 136x120 (ragged last tile row and
+    column): hundreds to thousands of Gaussians per tile list, up to ~130
+    blended per pixel, so every warp reduces and atomically adds the
+    gradients of Gaussians that most of its pixels blend."""
+    sc = _dense_scene()
+    cam = S.look_at((0.3, -0.2, -1.5), width=136, height=120)
+    st = S.Settings(mode=mode, bg=(0.05, 0.1, 0.2),
+                    load_grad=S.LOAD_GRAD_STRAIGHT if load_grad is None else load_grad)
+    rng = np.random.default_rng(8)
+    w = rng.normal(size=(3, 120, 136))
+    v = None if load_grad is None else rng.normal(size=(120, 136)) * 0.02
+    near = _near_pixels(sc, cam, st)
+    w[:, near] = 0.0
+    if v is not None:
+        v[near] = 0.0
+    got = _gpu_grads(rast, sc, cam, st, w, v)
+    ref, _, load = og.gradients(sc, cam, st, w, dl_dload=v)
+    assert load.max() >= 80, "the case must blend many Gaussians per pixel"
+    _check_elementwise(got, ref, f"dense/{S.MODE_NAMES[mode]}/{load_grad}")
 
 
 def test_load_loss_kernel(rast):

@@ -170,3 +170,17 @@ def test_load_term_early_stop_reading_follows_the_slope_of_the_count():
         got[lg] = float(grads[3].sum())
     assert got[S.LOAD_GRAD_TERMINATION] == pytest.approx(slope, rel=0.10)
     assert got[S.LOAD_GRAD_STRAIGHT] > 0 > slope
+
+
+def test_clamp_near_pixels_single_gaussian_on_a_pixel_centre():
+    """One Gaussian centred exactly on pixel (32, 32) of a 65x65 image: its
+    unclamped opacity there is sigma itself (q = 0), so with sigma = 0.99 the
+    centre pixel is flagged and pixels where exp(-q/2) has fallen by more
+    than the tolerance are not; with sigma = 0.5 the clamp is never near."""
+    cam = S.look_at((0, 0, -3), width=65, height=65)
+    assert cam.cx == 32.0 and cam.cy == 32.0
+    for sigma, flagged in ((0.99, True), (0.5, False)):
+        sc = S.isolated_gaussian((0, 0, 0), (0.05, 0.05, 0.05), (1, 0, 0, 0), sigma, (0.5, 0.5, 0.5))
+        m = og.clamp_near_pixels(sc, cam, S.Settings(mode=S.MODE_AABB))
+        assert bool(m[32, 32]) == flagged
+        assert int(m.sum()) == (1 if flagged else 0)

@@ -23,6 +23,7 @@ from oracle import grad as ograd
 from oracle import ssim as ossim
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "adr_oracle.c")
+A1 = S.Settings().alpha_low   # the paper's 1/255
 
 # (name, text in adr_oracle.c, replacement, the pin that must catch it)
 MUTANTS = [
@@ -42,9 +43,9 @@ MUTANTS = [
      lambda: pins.test_single_gaussian_image_closed_form(0.0, 0.3)),
     ("adaptive_radius_factor_two_dropped", "double r_ad = sqrt(2.0 * lam * L);",
      "double r_ad = sqrt(lam * L);",
-     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0)),
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0, A1)),
     ("aabb_axes_swapped", "double x_max = sqrt(2.0 * a * L);", "double x_max = sqrt(2.0 * c * L);",
-     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0)),
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(0, A1)),
     ("r_o_cap_dropped", "rx = ry = fmin(r_ad, r_o);", "rx = ry = r_ad;",
      pins.test_rcap_binds_for_opaque_gaussians),
     ("tile_interval_rounds_down", "double a = ceil(c - r), b = floor(c + r);",
@@ -79,7 +80,7 @@ MUTANTS = [
      pins.test_near_plane_cull_and_depth_bits),
     ("eigenvalue_without_offdiagonal", "sqrt(0.25 * (a - c) * (a - c) + b * b);",
      "sqrt(0.25 * (a - c) * (a - c));",
-     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(1)),
+     lambda: pins.test_adaptive_radius_and_aabb_against_sampled_ellipse(1, A1)),
     ("rect_3dgs_high_edge_not_rounded_up", "b = floor((c + R + (ORC_TILE - 1)) / ORC_TILE);",
      "b = floor((c + R) / ORC_TILE);",
      lambda: pins.test_3dgs_rect_rule_equals_point_set_brute_force(3)),

@@ -189,17 +189,22 @@ def _random_gaussians(rng, k, opac_hi=0.3):
     return out
 
 
+@pytest.mark.parametrize("alpha_low", [float(np.float32(1 / 255)), float(np.float32(4 / 255))],
+                         ids=["1/255", "4/255"])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_adaptive_radius_and_aabb_against_sampled_ellipse(seed):
+def test_adaptive_radius_and_aabb_against_sampled_ellipse(seed, alpha_low):
     rng = np.random.default_rng(seed)
     cam = S.look_at((0, 0, -3), width=256, height=256)
     for m, s, q, op in _random_gaussians(rng, 20):
         sc = _single(m, s, q, op)
-        circ = oracle.preprocess(sc, cam, S.Settings(mode=S.MODE_CIRCLE))["geom"][0]
-        aabb = oracle.preprocess(sc, cam, S.Settings(mode=S.MODE_AABB))["geom"][0]
+        circ = oracle.preprocess(sc, cam, S.Settings(mode=S.MODE_CIRCLE, alpha_low=alpha_low))["geom"][0]
+        aabb = oracle.preprocess(sc, cam, S.Settings(mode=S.MODE_AABB, alpha_low=alpha_low))["geom"][0]
         cov = np.array([[circ[oracle.G_COV_A], circ[oracle.G_COV_B]],
                         [circ[oracle.G_COV_B], circ[oracle.G_COV_C]]])
-        L = math.log(float(np.float32(op)) / S.Settings().alpha_low)
+        L = math.log(float(np.float32(op)) / alpha_low)
+        if L <= 0:   # sigma <= alpha_low: no real radius, no pairs
+            assert circ[oracle.G_RX] == 0 and aabb[oracle.G_RX] == 0
+            continue
         rmax, xmax, ymax = _boundary_extremes(cov, L)
         # sigma <= 0.3 < alpha_low * e^4.5, so the r_o cap does not bind
         assert circ[oracle.G_RX] < circ[oracle.G_RO]
@@ -557,6 +562,24 @@ def test_tiled_equals_brute_force_when_ro_does_not_bind():
         np.testing.assert_array_equal(out["img"], bf["img"])
         np.testing.assert_array_equal(out["load"], bf["load"])
         np.testing.assert_array_equal(out["t_final"], bf["t_final"])
+
+
+def test_tiled_equals_brute_force_at_alpha_low_4_255_in_every_mode():
+    """At alpha_low = 4/255 > e^-4.5 the 3-sigma radius r_o never binds: a
+    pixel outside it has q > 9, so alpha <= sigma e^-4.5 < 4/255 for any
+    sigma <= 1.  The tiled render (every mode, opacities up to 1) must then
+    equal the per-pixel brute force over all Gaussians, with no tiles."""
+    a4 = float(np.float32(4 / 255))
+    assert a4 > math.exp(-4.5)
+    sc = S.tiny_scene(6, n=1500)
+    assert sc.opac.max() > 0.9
+    cam = S.look_at((0.1, 0, -2.8), width=72, height=56)
+    for mode in (S.MODE_PLAIN, S.MODE_CIRCLE, S.MODE_AABB):
+        st = S.Settings(mode=mode, alpha_low=a4)
+        out = oracle.render(sc, cam, st)
+        bf = oracle.render_brute(out["pre"], st)
+        np.testing.assert_array_equal(out["img"], bf["img"])
+        np.testing.assert_array_equal(out["load"], bf["load"])
 
 
 def test_tiled_equals_rect_brute_force_general_scene():

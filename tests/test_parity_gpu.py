@@ -107,6 +107,31 @@ def test_cluster_scene_1080p_subset(rast):
     _check_frame(rast, scene, cam, S.Settings(mode=S.MODE_AABB), "cluster1080")
 
 
+# The alpha_low sweep (raising the splatting-opacity threshold above 1/255
+# trades a little accuracy for speed, Sec. 5.4.1): the cull radii (Eq. 7,
+# Eq. 10) and the per-pixel skip both move with alpha_low, and the oracle
+# takes the same setting.
+ALPHA_LOWS = [float(np.float32(2.0 / 255.0)), float(np.float32(4.0 / 255.0))]
+
+
+@pytest.mark.parametrize("alpha_low", ALPHA_LOWS, ids=["2/255", "4/255"])
+@pytest.mark.parametrize("mode", [S.MODE_PLAIN, S.MODE_AABB])
+def test_alpha_low_sweep_tiny_parity(rast, mode, alpha_low):
+    scene = S.tiny_scene(0)
+    cam = S.look_at((0, 0, -3), width=256, height=256)
+    st = S.Settings(mode=mode, alpha_low=alpha_low)
+    _check_frame(rast, scene, cam, st, f"tiny/{S.MODE_NAMES[mode]}/alpha_low={alpha_low:.5f}")
+
+
+@pytest.mark.parametrize("alpha_low", ALPHA_LOWS, ids=["2/255", "4/255"])
+@pytest.mark.parametrize("mode", [S.MODE_PLAIN, S.MODE_AABB])
+def test_alpha_low_sweep_cluster_1080p_parity(rast, mode, alpha_low):
+    scene = S.cluster_scene(n=200_000, seed=1)
+    cam = S.orbit_cameras(50, width=1920, height=1080)[7]
+    st = S.Settings(mode=mode, alpha_low=alpha_low)
+    _check_frame(rast, scene, cam, st, f"cluster1080/{S.MODE_NAMES[mode]}/alpha_low={alpha_low:.5f}")
+
+
 def test_modes_render_identical_images_on_gpu(rast):
     """Losslessness (Sec. 5.2-5.3): culling changes no pixel."""
     from paper_2409_08669_gb300.raster import upload
