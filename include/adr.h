@@ -46,7 +46,8 @@ typedef enum adr_status {
     ADR_ERR_INVALID = 1,    /* bad argument (NULL, size out of range, bad mode) */
     ADR_ERR_CAPACITY = 2,   /* more pairs than pair_capacity; nothing written out of bounds */
     ADR_ERR_CUDA = 3,       /* a CUDA runtime call failed */
-    ADR_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (output not valid) */
+    ADR_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up: the frame's later stages
+                               were skipped and its image holds only the background */
     ADR_PENDING = 5,        /* serving: request not finished yet */
     ADR_ERR_ADMISSION = 6   /* serving: request can never fit the memory budget */
 } adr_status;
@@ -272,9 +273,32 @@ adr_status adr_profile_read(adr_ctx *ctx, int32_t max_kernels, int32_t *kernel_i
                             double *total_ms, int32_t *launches, int32_t *num_kernels);
 const char *adr_profile_kernel_name(int32_t kernel_id);
 
-/* Waits for the context's work and reports device-side flags as a status
- * (ADR_ERR_CAPACITY, ADR_ERR_TIMEOUT or ADR_OK); clears them.  SYNCHRONISES. */
+/* Waits for the context's work and reports device-side flags as a status;
+ * clears them.  SYNCHRONISES.  In order of precedence: ADR_ERR_TIMEOUT (a
+ * bounded lookback wait of the run scan gave up; that frame's later stages
+ * were skipped), ADR_ERR_CAPACITY (more pairs than pair_capacity), ADR_ERR_CUDA
+ * (a device-side consistency check failed: a scatter index fell outside its
+ * buffer and the write was skipped; not expected from valid inputs), else
+ * ADR_OK. */
 adr_status adr_sync_status(adr_ctx *ctx);
+
+/* Testing hook for failure detection (the paper has no counterpart).  Every
+ * device-side wait of the library is bounded: a decoupled-lookback wait of the
+ * run-count scan (stage 2) that sees no progress for 2^22 polls gives up, flags
+ * the frame and lets its kernels return, and the frame's later stages skip
+ * their work; adr_sync_status, adr_render_frame_noalloc and adr_serve_poll then
+ * return ADR_ERR_TIMEOUT.  This hook makes that happen on purpose, so tests can
+ * drive the path without a fault: while withheld_chunk >= 0, the scan's chunk
+ * `withheld_chunk` (4096 Gaussians with tiles per chunk, in depth order) never
+ * publishes its prefix and every lookback wait gives up after spin_limit
+ * (1..2^22) polls, so the next chunk's wait runs out (frames whose Gaussians
+ * with tiles fill fewer than withheld_chunk + 2 chunks are unaffected).
+ * withheld_chunk < 0 restores normal operation (spin_limit ignored).  The
+ * setting is process-wide, applies to kernels launched after the call (a CUDA
+ * graph captured meanwhile keeps it) and is not thread-safe with respect to
+ * launches in flight on other threads.  ADR_ERR_INVALID for a spin_limit out
+ * of range. */
+adr_status adr_test_lookback_expiry(int32_t withheld_chunk, int32_t spin_limit);
 
 /* End-to-end frame from HOST memory: copies the scene arrays (HOST pointers,
  * ideally pinned) into the context's device staging buffers, runs
@@ -295,10 +319,17 @@ adr_status adr_render_host(adr_ctx *ctx, const float *means, const float *scales
  * synchronisation -- and so cannot create an adr_ctx.
  * It runs the same stages as adr_preprocess + adr_sort + adr_render with all
  * intermediates in one static device array compiled into the library (about
- * 20 MB, held by every GPU that loads the library until the process exits).
+ * 20 MB).  CUDA loads the array and the kernels it uses onto a device when they
+ * are first used there (by default lazily, at the first call on that device);
+ * from then on that device holds the array until the process exits.  That
+ * first load is the driver's one-time allocation and may synchronise, so
+ * callers that cannot take it make their first call on each device during
+ * start-up, or set CUDA_MODULE_LOADING=EAGER.
  * Limits: n <= 32768 Gaussians, width and height <= 512, at most 1048576
  * Gaussian-tile pairs; larger sizes are rejected with ADR_ERR_INVALID, and a
  * frame that produces more pairs returns ADR_ERR_CAPACITY (image incomplete).
+ * A bounded device wait that gave up returns ADR_ERR_TIMEOUT (checked first)
+ * and a failed device-side consistency check ADR_ERR_CUDA.
  * Arguments are as for adr_preprocess and adr_render (device memory, the
  * caller's inputs and outputs; t_final and load may be NULL); the frame runs
  * on the current CUDA device.  The first call on a device looks up the

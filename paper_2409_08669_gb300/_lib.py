@@ -73,6 +73,7 @@ _SIGNATURES = {
     "adr_read_gaussians": (_I32, [_P, _P, _P, _P, _P]),
     "adr_read_ranges": (_I32, [_P, _P, _P]),
     "adr_sync_status": (_I32, [_P]),
+    "adr_test_lookback_expiry": (_I32, [_I32, _I32]),
     "adr_read_pixel_stats": (_I32, [_P, _P, _P, _P]),
     "adr_render_host": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_camera),
                                ctypes.POINTER(adr_settings), _P, _P, _P, _P]),
@@ -213,6 +214,11 @@ def adr_read_pixel_stats(ctx, last, traversed, stream):
 
 def adr_sync_status(ctx):
     return load().adr_sync_status(ctx)
+
+
+def adr_test_lookback_expiry(withheld_chunk, spin_limit=64):
+    """Testing hook: make the run scan's lookback waits give up (see adr.h)."""
+    return load().adr_test_lookback_expiry(int(withheld_chunk), int(spin_limit))
 
 
 def adr_render_host(ctx, means, scales, rots, opac, sh, n, camera, settings, img, t_final, load_,

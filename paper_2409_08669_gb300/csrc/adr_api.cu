@@ -149,8 +149,20 @@ struct adr_ctx {
     int32_t* stage_load = nullptr;
 };
 
+namespace {
+// Process-wide testing hook of the bounded lookback waits (adr_test_lookback_expiry).
+std::atomic<uint32_t> g_lb_withhold{0xFFFFFFFFu};
+std::atomic<int> g_lb_spins{kLookbackSpinLimit};
+}  // namespace
+
 namespace adr {
 // Shared with the other translation units (declared in adr_internal.cuh).
+LookbackTest lookback_test() {
+    LookbackTest t;
+    t.withhold = g_lb_withhold.load();
+    t.spin_limit = g_lb_spins.load();
+    return t;
+}
 adr_status report_error(adr_status st, const char* msg) { return fail(st, "%s", msg); }
 adr_status report_ok() { return ok(); }
 adr_status camera_to_dev(const adr_camera* cam, int max_w, int max_h, CamDev& d) {
@@ -289,7 +301,20 @@ extern "C" {
 
 const char* adr_last_error(void) { return g_last_error.c_str(); }
 
-const char* adr_version(void) { return "adr-gb300 0.2 (sm_103a)"; }
+const char* adr_version(void) { return "adr-gb300 0.3 (sm_103a)"; }
+
+adr_status adr_test_lookback_expiry(int32_t withheld_chunk, int32_t spin_limit) {
+    if (withheld_chunk < 0) {
+        g_lb_withhold.store(0xFFFFFFFFu);
+        g_lb_spins.store(kLookbackSpinLimit);
+        return ok();
+    }
+    if (spin_limit < 1 || spin_limit > kLookbackSpinLimit)
+        return fail(ADR_ERR_INVALID, "spin_limit must be in 1..%d", kLookbackSpinLimit);
+    g_lb_spins.store(spin_limit);
+    g_lb_withhold.store((uint32_t)withheld_chunk);
+    return ok();
+}
 
 adr_status adr_create(adr_ctx** out, int64_t max_gaussians, int64_t pair_capacity,
                       int32_t max_width, int32_t max_height, int32_t device) {
@@ -412,9 +437,8 @@ adr_status adr_sync_status(adr_ctx* c) {
     ADR_CUDA(cudaMemcpy(c->host_words, c->ws.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     const uint32_t bits = c->host_words[0];
     ADR_CUDA(cudaMemset(c->ws.status, 0, sizeof(uint32_t)));
-    if (bits & kErrLookback) return fail(ADR_ERR_TIMEOUT, "a device-side lookback wait gave up");
-    if (bits & kErrCapacity) return fail(ADR_ERR_CAPACITY, "pair count exceeded pair_capacity");
-    if (bits & kErrRange) return fail(ADR_ERR_TIMEOUT, "a scatter index was out of range (skipped)");
+    const StatusReport r = status_from_bits(bits, 0, c->ws.capacity);
+    if (r.status != ADR_OK) return fail(r.status, "%s", r.message);
     return ok();
 }
 

@@ -8,16 +8,12 @@
 #include <atomic>
 
 #include "adr.h"
+#include "status_bits.h"   // device-side error word bits and their adr_status
 
 namespace adr {
 
 constexpr int kTile = ADR_TILE;          // 16x16 pixel tiles (Sec. 3.2)
 constexpr int kTilePixels = kTile * kTile;
-
-// Device-side error word bits (ctx->d_status[0]).
-constexpr uint32_t kErrCapacity = 1u;    // more Gaussian-tile pairs than pair_capacity
-constexpr uint32_t kErrLookback = 2u;    // a decoupled-lookback wait hit its iteration limit
-constexpr uint32_t kErrRange = 4u;       // a scatter index fell outside its buffer (skipped)
 
 // Camera as the kernels see it.
 struct CamDev {
@@ -54,6 +50,19 @@ struct EpochRef {
     uint32_t pass;
 };
 
+// Bounded waits: a decoupled-lookback wait polls at most kLookbackSpinLimit
+// times (about 0.1-0.4 s with its back-off) before it gives up, sets
+// kErrLookback and lets the kernel return.
+constexpr int kLookbackSpinLimit = 1 << 22;
+// Testing hook of that failure path (adr_test_lookback_expiry): chunk
+// `withhold` of the run scan never publishes its prefix, and every wait gives
+// up after `spin_limit` polls.  withhold = 0xFFFFFFFF: normal operation.
+struct LookbackTest {
+    uint32_t withhold = 0xFFFFFFFFu;
+    int spin_limit = kLookbackSpinLimit;
+};
+LookbackTest lookback_test();
+
 // Per-Gaussian render record, three float4 per Gaussian:
 //   rec[3g+0] = (px_hi, py_hi, px_lo, py_lo)   pixel centre as a float-float pair
 //   rec[3g+1] = (w1x, w1y, w2x, w2y)           q(d) = d^T Sigma'^-1 d = 2/log2(e) *
@@ -85,7 +94,9 @@ enum Counter : int {
     kCntScanTicket = 2,   // chunk ticket of the tile-count scan
     kCntRuns = 3,         // number of column runs C (sum of rectangle widths), saturating
     kCntDepthKept = 4,    // Gaussians with tiles, counted by the first depth pass
-                          // words 5-7: unused
+    kCntScanFailed = 5,   // non-zero: a lookback wait of the run scan gave up (the frame
+                          // is then skipped: its pair count reads as saturated)
+                          // words 6-7: unused
     kCntPairs64 = 8,      // words 8-9: P as a 64-bit sum
     kCntSlots = 16
 };
@@ -273,6 +284,9 @@ void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, 
 // lookback.  Also writes the run total, visible count and pair total to
 // counters (with the capacity flag), and chunk_first[c] = position of the
 // Gaussian holding run c * kSortChunk.
+// A wait that gives up sets kErrLookback and counters[kCntScanFailed]; the
+// pair total then reads as saturated, so every later stage of the frame
+// skips its work exactly as after a capacity overflow.
 void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, uint32_t* offsets,
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream);

@@ -21,7 +21,6 @@ constexpr int kScanItems = 16;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 constexpr uint32_t kSat = 0x7FFFFFFFu;   // running sums saturate here (> any capacity)
 constexpr unsigned long long kScanInc = 1ull << 31;
-constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
     const uint32_t s = a + b;
@@ -31,17 +30,22 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
 // Exclusive prefix of chunk `chunk` by decoupled lookback, run by one warp:
 // lane l reads the word of chunk j - l, so each round trip covers 32
 // predecessors; the words up to the nearest inclusive prefix are summed.
-// Lane 0 publishes this chunk's aggregate first and its inclusive prefix last.
+// Lane 0 publishes this chunk's aggregate first and its inclusive prefix last
+// (except the chunk the testing hook withholds).  A wait that makes no
+// progress for lt.spin_limit polls gives up: it flags the status word and the
+// frame's counters and returns the partial prefix.
 __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, uint32_t total,
-                                  uint32_t epoch, uint32_t* status) {
+                                  uint32_t epoch, uint32_t* status, uint32_t* counters,
+                                  LookbackTest lt) {
     const int lane = threadIdx.x & 31;
     const unsigned long long tag = (unsigned long long)epoch << 32;
     volatile unsigned long long* lb = lookback;
+    const bool publish = chunk != lt.withhold;
     if (chunk == 0) {
-        if (lane == 0) lb[0] = tag | kScanInc | min(total, kSat);
+        if (lane == 0 && publish) lb[0] = tag | kScanInc | min(total, kSat);
         return 0;
     }
-    if (lane == 0) lb[chunk] = tag | min(total, kSat);
+    if (lane == 0 && publish) lb[chunk] = tag | min(total, kSat);
     uint64_t excl = 0;
     int64_t j = (int64_t)chunk - 1;   // the nearest predecessor not yet summed
     int spins = 0;
@@ -63,8 +67,11 @@ __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, 
         if (first_inc < first_nr) break;
         j -= take;
         if (take == 0) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) atomicOr(status, kErrLookback);
+            if (++spins > lt.spin_limit) {
+                if (lane == 0) {
+                    atomicOr(status, kErrLookback);
+                    atomicExch(counters + kCntScanFailed, 1u);
+                }
                 break;
             }
             __nanosleep(32);
@@ -72,7 +79,7 @@ __device__ uint32_t warp_lookback(unsigned long long* lookback, uint32_t chunk, 
     }
     const uint32_t e = (uint32_t)min(excl, (uint64_t)kSat);
     __threadfence();
-    if (lane == 0) lb[chunk] = tag | kScanInc | sat_add(e, total);
+    if (lane == 0 && publish) lb[chunk] = tag | kScanInc | sat_add(e, total);
     return e;
 }
 
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t capacity,
              uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
              unsigned long long* __restrict__ lookback, EpochRef eref,
-             uint32_t* __restrict__ counters, uint32_t* __restrict__ status) {
+             uint32_t* __restrict__ counters, uint32_t* __restrict__ status, LookbackTest lt) {
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
     // The depth sort kept only the Gaussians with tiles: scan those.
     const int64_t n = min(n_host, (int64_t)counters[kCntDepthKept]);
@@ -129,7 +136,7 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
         const uint32_t texcl = wbase + x - tsum;
         if (warp == 0) {
             if (lane == 0 && pairs) atomicAdd(pairs64, (unsigned long long)pairs);
-            const uint32_t excl = warp_lookback(lookback, chunk, total, epoch, status);
+            const uint32_t excl = warp_lookback(lookback, chunk, total, epoch, status, counters, lt);
             if (lane == 0) {
                 s_prefix = excl;
                 if (base + kScanChunk >= n) counters[kCntRuns] = sat_add(excl, total);
@@ -158,10 +165,17 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
     }
 }
 
-// After the scan: the pair total P (saturated to 31 bits) and the capacity flag.
+// After the scan: the pair total P (saturated to 31 bits) and the capacity
+// flag.  If a lookback wait gave up, the run offsets are not a valid scan:
+// P reads as saturated (above any capacity), so every later stage skips its
+// work as after an overflow, and only kErrLookback reports it.
 __global__ void k_finish_pairs(uint32_t* __restrict__ counters, int64_t capacity,
                                uint32_t* __restrict__ status) {
     const unsigned long long p = *reinterpret_cast<const unsigned long long*>(counters + kCntPairs64);
+    if (counters[kCntScanFailed] != 0u) {
+        counters[kCntPairs] = kSat;
+        return;
+    }
     counters[kCntPairs] = (uint32_t)min(p, (unsigned long long)kSat);
     if (p > (unsigned long long)capacity) atomicOr(status, kErrCapacity);
 }
@@ -226,7 +240,8 @@ void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, 
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream) {
     if (n > 0)
         k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(sorted_box, n, capacity, offsets, chunk_first,
-                                                        lookback, epoch, counters, status);
+                                                        lookback, epoch, counters, status,
+                                                        lookback_test());
     k_finish_pairs<<<1, 1, 0, stream>>>(counters, capacity, status);
 }
 

@@ -12,9 +12,15 @@
 // scratch lives in the library image itself.
 //
 // The array is sized for at most kNaMaxGaussians Gaussians, kNaMaxPairs
-// Gaussian-tile pairs and kNaMaxWidth x kNaMaxHeight images (about 20 MB);
-// every GPU that loads the library holds it until the process exits.
+// Gaussian-tile pairs and kNaMaxWidth x kNaMaxHeight images (about 20 MB).
+// CUDA loads this file's module (the array and its kernels) on a device when
+// the module is first used there, by default lazily at the first call on that
+// device; from then on that device holds the array until the process exits.
+// Callers for whom that first load (a one-time allocation by the driver, and
+// possibly a synchronisation) is unacceptable make the first call during
+// start-up, or run with CUDA_MODULE_LOADING=EAGER.
 #include <atomic>
+#include <cstdio>
 #include <mutex>
 
 #include "adr_internal.cuh"
@@ -181,11 +187,17 @@ extern "C" adr_status adr_render_frame_noalloc(const float* means, const float* 
         cudaMemcpyAsync(&words[1], ws.counters + kCntPairs, 4, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
         cudaStreamSynchronize(strm) != cudaSuccess)
         return report_error(ADR_ERR_CUDA, "adr_render_frame_noalloc: status readback failed");
-    if (words[0] & (kErrLookback | kErrRange))
-        return report_error(ADR_ERR_TIMEOUT, "adr_render_frame_noalloc: a device-side wait gave up");
-    if ((words[0] & kErrCapacity) || words[1] > kNaMaxPairs)
+    // A wait that gave up skips the frame and reads its pair count as
+    // saturated, so it is reported before the capacity check.
+    const StatusReport r = status_from_bits(words[0], (int64_t)words[1], kNaMaxPairs);
+    if (r.status == ADR_ERR_CAPACITY)
         return report_error(ADR_ERR_CAPACITY,
                             "adr_render_frame_noalloc: more than 1048576 Gaussian-tile pairs "
                             "(static scratch limit); the image is incomplete");
+    if (r.status != ADR_OK) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "adr_render_frame_noalloc: %s", r.message);
+        return report_error(r.status, msg);
+    }
     return report_ok();
 }

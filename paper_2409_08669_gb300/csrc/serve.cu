@@ -197,15 +197,21 @@ void scheduler(adr_server* s) {
             Request* r = sl->req;
             const uint32_t bits = sl->host_words[0], pairs = sl->host_words[1];
             r->t_done = now_ms();
-            if (q != cudaSuccess) r->result = ADR_ERR_CUDA;
-            else if (bits & kErrLookback) r->result = ADR_ERR_TIMEOUT;
-            else if ((bits & kErrCapacity) || (int64_t)pairs > s->cfg.slot_pair_capacity) {
-                r->result = ADR_ERR_CAPACITY;
-                s->capacity_errors++;
+            if (q != cudaSuccess) {
+                r->result = ADR_ERR_CUDA;
+                snprintf(s->error, sizeof(s->error), "frame: %s", cudaGetErrorString(q));
+            } else {
+                const StatusReport rep = status_from_bits(bits, (int64_t)pairs, s->cfg.slot_pair_capacity);
+                r->result = rep.status;
+                if (rep.status == ADR_ERR_CAPACITY) s->capacity_errors++;
+                if (rep.status == ADR_ERR_CUDA) snprintf(s->error, sizeof(s->error), "%s", rep.message);
             }
             Scene& sc = s->scenes[r->scene];
-            const double ppp = (double)pairs / ((double)r->cam.width * r->cam.height);
-            sc.pairs_per_pixel = sc.pairs_per_pixel < 0 ? ppp : std::max(ppp, 0.9 * sc.pairs_per_pixel + 0.1 * ppp);
+            if (!(bits & kErrLookback)) {   // a skipped frame's pair count is not a measurement
+                const double ppp = (double)pairs / ((double)r->cam.width * r->cam.height);
+                sc.pairs_per_pixel = sc.pairs_per_pixel < 0 ? ppp
+                                                            : std::max(ppp, 0.9 * sc.pairs_per_pixel + 0.1 * ppp);
+            }
             r->state = kDone;
             s->latencies.push_back(r->t_done - r->t_submit);
             s->t_last_done = r->t_done;
@@ -390,6 +396,9 @@ adr_status adr_serve_poll(adr_server* s, uint64_t ticket, int64_t timeout_us) {
         snprintf(msg, sizeof(msg), "adr_serve_poll: the request failed (%s)", s->error);
         return report_error(res, msg);
     }
+    if (res == ADR_ERR_TIMEOUT)
+        return report_error(res, "adr_serve_poll: a device-side lookback wait gave up; the "
+                                 "request's frame was skipped (ticket released)");
     if (res != ADR_OK) return report_error(res, "adr_serve_poll: the request failed on the device");
     return report_ok();
 }

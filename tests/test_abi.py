@@ -185,3 +185,54 @@ def test_oracle_never_touches_the_product():
         if fn.endswith((".py", ".c", ".h")):
             text = open(os.path.join(odir, fn)).read()
             assert not re.search(r"paper_2409_08669_gb300|adr_internal|libadr|include/adr", text), fn
+
+
+def test_lookback_expiry_hook_checks_its_arguments_without_gpu(libpath):
+    lib = _lib.load()
+    assert lib.adr_test_lookback_expiry(0, 0) == _lib.ADR_ERR_INVALID
+    assert lib.adr_test_lookback_expiry(1, (1 << 22) + 1) == _lib.ADR_ERR_INVALID
+    assert b"spin_limit" in lib.adr_last_error()
+    assert lib.adr_test_lookback_expiry(-1, 0) == _lib.ADR_OK
+
+
+_STATUS_MAP_SRC = r"""
+#include <cstdio>
+#include "status_bits.h"
+int main() {
+    for (unsigned bits = 0; bits < 8; ++bits)
+        for (int over = 0; over < 2; ++over) {
+            const adr::StatusReport r = adr::status_from_bits(bits, over ? 11 : 10, 10);
+            std::printf("%u %d %d %d\n", bits, over, (int)r.status, r.message[0] != 0);
+        }
+    return 0;
+}
+"""
+
+
+def test_device_status_word_maps_to_one_status_in_every_entry_point(tmp_path):
+    """The mapping adr_sync_status, adr_render_frame_noalloc and the serving
+    scheduler share (host code, compiled here with g++): a wait that gave up
+    wins (its frame reads as saturated), then a pair overflow (flag or count
+    above the capacity), then a failed consistency check; every error has a
+    message."""
+    src = tmp_path / "status_map.cpp"
+    exe = tmp_path / "status_map"
+    src.write_text(_STATUS_MAP_SRC)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run(["g++", "-std=c++17", f"-I{os.path.join(root, 'include')}",
+                    f"-I{os.path.join(root, 'paper_2409_08669_gb300', 'csrc')}", str(src), "-o", str(exe)],
+                   check=True)
+    rows = [tuple(map(int, line.split())) for line in
+            subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    assert len(rows) == 16
+    for bits, over, status, has_msg in rows:
+        if bits & 2:
+            want = _lib.ADR_ERR_TIMEOUT
+        elif (bits & 1) or over:
+            want = _lib.ADR_ERR_CAPACITY
+        elif bits & 4:
+            want = _lib.ADR_ERR_CUDA
+        else:
+            want = _lib.ADR_OK
+        assert status == want, (bits, over, status)
+        assert has_msg == (want != _lib.ADR_OK)
