@@ -82,17 +82,24 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region, every 50 ms
-    (the first arrives ~10 ms after start), so a 0.2 s timed region holds
-    several samples."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock/throttle samples, every ~50 ms (the first arrives ~10 ms
+    after start).  The sampler starts before the warm-up frames and waits (up
+    to 2 s) for its first sample; `mark()` brackets the timed region, whose own
+    samples are counted separately (a 20-frame region lasts ~20 ms, so it holds
+    one at most; the window around it runs the same frames)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index=0):
+    def __init__(self, gpu_index=0, window="warm-up and timed frames"):
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.window = window
+        self.marks = []
+
+    def mark(self):
+        self.marks.append(time.time())
 
     def __enter__(self):
         try:
@@ -101,6 +108,9 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 2.0 and os.path.getsize(self.file.name) == 0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -117,22 +127,44 @@ class ClockSampler:
         if self.proc is None or self.file is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.file.flush()
-        rows = []
-        for line in open(self.file.name):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        rows = parse_clock_rows(open(self.file.name).read().splitlines())
         os.unlink(self.file.name)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return summarise_clocks(rows, self.marks, self.window)
+
+
+def parse_clock_rows(lines):
+    """(epoch seconds or None, sm MHz, max sm MHz, [hw, hw_thermal, sw_thermal,
+    sw_power_cap] flags) per nvidia-smi line of ClockSampler.FIELDS."""
+    import datetime
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        try:
+            rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+        except ValueError:
+            continue
+    return rows
+
+
+def summarise_clocks(rows, marks=(), window=""):
+    """Median SM clock, max clock, active throttle reasons and sample counts
+    (all samples of the window, and those inside the first two marks)."""
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for _, _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+    out = {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+           "reasons": reasons, "samples": len(rows), "window": window}
+    if len(marks) >= 2:
+        out["samples_in_timed_region"] = sum(1 for r in rows if r[0] is not None and
+                                             marks[0] <= r[0] <= marks[1])
+    return out
 
 
 def dist_setup(args):
@@ -195,7 +227,7 @@ def build_workload(rank=0):
 # ---------------------------------------------------------------------------
 
 def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stages=True,
-              kernel_times=False):
+              kernel_times=False, clock=None):
     """Returns (seconds for `steps` frames, per-stage ms lists, per-kernel times).
 
     With kernel_times the library records CUDA events around each of its kernel
@@ -210,6 +242,8 @@ def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stage
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device="cuda")
+    if clock is not None:
+        clock.mark()
     start.record(stream)
     for k in range(steps):
         cam = cams[(warmup + k) % len(cams)]
@@ -226,6 +260,8 @@ def time_mode(rast, params, cams, st, steps, warmup, stream, pg=None, with_stage
             ev[k][3].record(stream)
     stop.record(stream)
     barrier(pg)
+    if clock is not None:
+        clock.mark()
     total = start.elapsed_time(stop) / 1e3
     stages = None
     if with_stages:
@@ -260,8 +296,14 @@ def frame_units(rast, params, cams, st, stream, count):
         length = ranges[:, 1] - ranges[:, 0]
         loaded = np.minimum(length, ((tmax + 255) // 256) * 256)
         runs = int((rect[:, 2].astype(np.int64) - rect[:, 0])[tiles > 0].sum())
+        # the runs the tile sort built (both depth slices, or all), from the
+        # forward frame itself: render it again without the inspection reads
+        rast.forward(params, cams[k], st, stream=stream, want_aux=False)
+        fc = rast.frame_counts()
+        built = fc["runs_slice0"] + fc["runs_slice1"] if fc["sliced"] else fc["runs"]
         out.append(dict(pairs=p, visible=v, runs=runs, evals=int(trav.astype(np.int64).sum()),
-                        loaded=int(loaded.sum())))
+                        loaded=int(loaded.sum()), runs_built=built, sliced=fc["sliced"],
+                        visible_slice1=fc["visible_slice1"]))
     return out
 
 
@@ -286,6 +328,21 @@ def kernel_bytes(name, n, u, hw):
         "slice": None,                             # unfinished-tile table, compaction of slice 1
         "render": 52 * u["loaded"] + 12 * hw,      # records + ids of loaded prefixes, image out
     }.get(name)
+
+
+def sort_throughput(ktable, u):
+    """Items per second of the depth sort (Gaussians with tiles over its four
+    passes) and of tile pass 1 (column runs built over its count, count scan
+    and scatter kernels), from the live kernel table."""
+    ms = lambda names: sum(ktable[k]["ms_per_frame"] for k in names if k in ktable)
+    depth_ms = ms(("depth_pass",))
+    pass1_ms = ms(("tile_count_columns", "tile_count_scan", "tile_scatter_columns"))
+    return {"depth_sort_gaussians_per_s": u["visible"] / (depth_ms / 1e3) if depth_ms else None,
+            "depth_sort_ms_per_frame": depth_ms,
+            "tile_pass1_runs_per_s": u["runs_built"] / (pass1_ms / 1e3) if pass1_ms else None,
+            "tile_pass1_ms_per_frame": pass1_ms,
+            "runs_built_per_frame": u["runs_built"], "runs_all_gaussians_per_frame": u["runs"],
+            "visible_per_frame": u["visible"]}
 
 
 def alpha_low_sweep(rast, params, cams, stream, pg, steps, warmup):
@@ -530,9 +587,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     rast.num_pairs()
 
-    with ClockSampler(local) as clk:
+    window = "warm-up and timed AdR frames" + ("" if args.quick else ", then the plain and circle legs")
+    with ClockSampler(local, window) as clk:
         t_adr, stages, kernels = time_mode(rast, params, cams, st_adr, args.steps, args.warmup,
-                                           stream, pg, kernel_times=True)
+                                           stream, pg, kernel_times=True, clock=clk)
+        if not args.quick:
+            t_plain, stages_plain, _ = time_mode(rast, params, cams, st_plain, args.steps,
+                                                 args.warmup, stream, pg)
+            t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup,
+                                       stream, pg, with_stages=False)
     clocks = clk.summary()
     status = rast.sync_status()
     if status != 0:
@@ -544,10 +607,6 @@ def run_ours(args):
             print(json.dumps({"workload": WORKLOAD, "fps": fps,
                               "stages_ms": {k: statistics.mean(v) for k, v in stages.items()}}))
         return
-    t_plain, stages_plain, _ = time_mode(rast, params, cams, st_plain, args.steps, args.warmup,
-                                         stream, pg)
-    t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup, stream, pg,
-                               with_stages=False)
     fps, t_adr = aggregate_fps(pg, t_adr, args.steps, world)
     t_plain = max_over_ranks(pg, t_plain)
     t_circle = max_over_ranks(pg, t_circle)
@@ -625,13 +684,11 @@ def run_ours(args):
         "evals_per_frame": {"adr_aabb": u_mean["evals"],
                             "plain": statistics.mean(u["evals"] for u in units_plain)},
         "culled_pair_fraction": 1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain),
-        # Pairs put in (tile, depth) order per second by the sorting kernels of a
-        # frame (depth sort, run scan, tile pass 1 of both slices, slice-1
-        # selection); the pairs behind every tile's last stop are never written.
-        "sort_gpairs_per_s": u_mean["pairs"] / sum(
-            ktable[k]["ms_per_frame"] for k in ("depth_pass", "scan_tiles", "tile_count_columns",
-                                                "tile_count_scan", "tile_scatter_columns", "slice")
-            if k in ktable) / 1e6,
+        # What the sorting kernels move: the depth sort orders the V Gaussians
+        # with tiles (4 passes); tile pass 1 groups the column runs it builds
+        # (both depth slices' runs when sliced) by tile column.  The pairs
+        # themselves are never written on the forward path.
+        "sort_throughput": sort_throughput(ktable, u_mean),
         "roofline": roofline,
         "kernels": ktable,
         "render_roofline": {"alu": {"achieved": render_alu, "peak": alu_peak,

@@ -235,6 +235,15 @@ adr_status adr_image_loss(const float *img, const float *ref, int32_t channels, 
  * wait gave up (device flags are cleared).  SYNCHRONISES that stream. */
 adr_status adr_num_pairs(adr_ctx *ctx, int64_t *num_pairs);
 
+/* Inspection: sizes of the last rendered frame, first min(n, 7) of (HOST
+ * int64 array): the pair count P, the Gaussians with tiles V, the column runs
+ * of all of them C, whether the frame rendered in two depth slices (0/1), the
+ * runs the tile sort built for slice 0 and for slice 1, and the Gaussians of
+ * slice 1 (the last three 0 for an unsliced frame).  A sliced frame's tile
+ * sort moves the runs of its two slices only.  SYNCHRONISES the context's
+ * last stream.  ADR_ERR_INVALID before the first adr_render. */
+adr_status adr_frame_counts(adr_ctx *ctx, int64_t *out, int32_t n);
+
 /* Inspection (tests, debugging).  Copy the sorted pairs as 64-bit keys
  * (tile << 32) | bits(depth) and Gaussian indices into caller device buffers
  * of `capacity` entries (at most min(P, capacity) written).  Enqueued on

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "adr_sort": (_I32, [_P, _P]),
     "adr_render": (_I32, [_P, _P, _P, _P, _P]),
     "adr_num_pairs": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "adr_frame_counts": (_I32, [_P, _P, _I32]),
     "adr_read_pairs": (_I32, [_P, _P, _P, _I64, _P]),
     "adr_read_gaussians": (_I32, [_P, _P, _P, _P, _P]),
     "adr_read_ranges": (_I32, [_P, _P, _P]),

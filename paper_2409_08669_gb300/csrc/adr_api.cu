@@ -458,6 +458,26 @@ adr_status adr_num_pairs(adr_ctx* c, int64_t* num_pairs) {
     return ok();
 }
 
+adr_status adr_frame_counts(adr_ctx* c, int64_t* out, int32_t n) {
+    if (!c || !out || n < 1) return fail(ADR_ERR_INVALID, "bad argument");
+    if (!c->have_render) return fail(ADR_ERR_INVALID, "adr_frame_counts before adr_render");
+    DeviceGuard guard(c->device);
+    ADR_CUDA(cudaStreamSynchronize(c->last_stream));
+    uint32_t w[3 * kCntSlots] = {0};
+    ADR_CUDA(cudaMemcpy(w, c->ws.counters, kCntSlots * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (c->fs.sliced)
+        ADR_CUDA(cudaMemcpy(w + kCntSlots, c->ws.slice_counters, 2 * kCntSlots * sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost));
+    const uint32_t* s0 = w + kCntSlots;
+    const uint32_t* s1 = w + 2 * kCntSlots;
+    const int64_t vals[7] = {(int64_t)w[kCntPairs], (int64_t)w[kCntVisible], (int64_t)w[kCntRuns],
+                             c->fs.sliced ? 1 : 0, c->fs.sliced ? (int64_t)s0[kCntRuns] : 0,
+                             c->fs.sliced ? (int64_t)s1[kCntRuns] : 0,
+                             c->fs.sliced ? (int64_t)s1[kCntVisible] : 0};
+    for (int i = 0; i < n && i < 7; ++i) out[i] = vals[i];
+    return ok();
+}
+
 adr_status adr_read_pairs(adr_ctx* c, uint64_t* keys, uint32_t* vals, int64_t capacity,
                           void* stream) {
     if (!c || !keys || !vals) return fail(ADR_ERR_INVALID, "NULL argument");

@@ -4,6 +4,8 @@ PyTorch provides device memory and streams; every stage runs in libadr.so.
 """
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import torch
 
@@ -185,6 +187,16 @@ class Rasterizer:
     def num_pairs(self, raise_on_error=True):
         p, st = _lib.adr_num_pairs(self.ctx, raise_on_error)
         return (p, st) if not raise_on_error else p
+
+    FRAME_COUNT_NAMES = ("pairs", "visible", "runs", "sliced", "runs_slice0", "runs_slice1",
+                         "visible_slice1")
+
+    def frame_counts(self):
+        """Sizes of the last rendered frame (adr_frame_counts) as a dict."""
+        buf = (ctypes.c_int64 * len(self.FRAME_COUNT_NAMES))()
+        _lib.check(_lib.load().adr_frame_counts(self.ctx, ctypes.addressof(buf), len(buf)),
+                   "adr_frame_counts")
+        return dict(zip(self.FRAME_COUNT_NAMES, (int(v) for v in buf)))
 
     def read_pairs(self, count=None, stream=None):
         p = self.num_pairs() if count is None else count

@@ -8,8 +8,12 @@ import tempfile
 import bench
 
 
-def _summary(lines):
-    clk = bench.ClockSampler(0)
+TS = "2026/12/04 06:00:00.{:03d}"
+
+
+def _summary(lines, marks=()):
+    clk = bench.ClockSampler(0, "test window")
+    clk.marks = list(marks)
     clk.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
     clk.file.write("\n".join(lines) + "\n")
     clk.proc = object()          # stands in for the finished nvidia-smi process
@@ -20,18 +24,28 @@ def _summary(lines):
 
 def test_clock_summary_median_max_and_no_reasons():
     na = "Not Active"
-    rows = [f"0, {mhz}, 2070, 950.0, 0x0000000000000000, {na}, {na}, {na}, {na}"
-            for mhz in (2070, 2055, 1987, 2070, 2070)]
+    rows = [f"{TS.format(100 * k)}, 0, {mhz}, 2070, 950.0, 0x0000000000000000, {na}, {na}, {na}, {na}"
+            for k, mhz in enumerate((2070, 2055, 1987, 2070, 2070))]
     out = _summary(rows)
-    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5,
+                   "window": "test window"}
+
+
+def test_clock_summary_counts_the_samples_inside_the_timed_region():
+    import datetime
+    na = "Not Active"
+    rows = [f"{TS.format(100 * k)}, 0, 2070, 2070, 950.0, 0x0, {na}, {na}, {na}, {na}" for k in range(6)]
+    t = lambda ms: datetime.datetime.strptime(TS.format(ms), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    out = _summary(rows, marks=(t(150), t(420)))
+    assert out["samples"] == 6 and out["samples_in_timed_region"] == 3   # at 200, 300, 400 ms
 
 
 def test_clock_summary_reports_every_active_reason():
     na, a = "Not Active", "Active"
-    rows = [f"0, 1800, 2070, 1400.0, 0x4, {na}, {na}, {na}, {a}",
-            f"0, 1500, 2070, 1400.0, 0x48, {a}, {na}, {a}, {na}",
+    rows = [f"{TS.format(0)}, 0, 1800, 2070, 1400.0, 0x4, {na}, {na}, {na}, {a}",
+            f"{TS.format(50)}, 0, 1500, 2070, 1400.0, 0x48, {a}, {na}, {a}, {na}",
             "garbage line",
-            f"0, [N/A], 2070, 1400.0, 0x0, {na}, {na}, {na}, {na}"]
+            f"{TS.format(99)}, 0, [N/A], 2070, 1400.0, 0x0, {na}, {na}, {na}, {na}"]
     out = _summary(rows)
     assert out["samples"] == 2 and out["sm_mhz"] == 1650.0
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
@@ -67,3 +81,13 @@ def test_oracle_frame_sample_scales_to_a_full_frame():
     assert tile_scale == (8 * 6) / (8 * 6 // 8)           # 48 tiles, 6 sampled
     base = bench.cpu_baseline(scene, [cam], S.Settings(mode=S.MODE_AABB), budget_s=0.0)
     assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
+
+
+def test_sort_throughput_counts_what_the_kernels_move():
+    kt = {"depth_pass": {"ms_per_frame": 0.1}, "tile_count_columns": {"ms_per_frame": 0.02},
+          "tile_count_scan": {"ms_per_frame": 0.01}, "tile_scatter_columns": {"ms_per_frame": 0.02}}
+    u = {"visible": 1_000_000, "runs_built": 500_000, "runs": 9_000_000}
+    out = bench.sort_throughput(kt, u)
+    assert out["depth_sort_gaussians_per_s"] == 1_000_000 / 1e-4
+    assert abs(out["tile_pass1_runs_per_s"] - 500_000 / 5e-5) < 1e-3 * 1e10
+    assert out["runs_built_per_frame"] == 500_000
