@@ -400,11 +400,71 @@ def train_step_rate(local, steps=20, warmup=5):
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
+    # Per-kernel device time of the library's launches over as many more steps
+    # (CUDA events on the launching stream), then the work units of the
+    # backward on the same cameras: the list positions each pixel walks back
+    # (its last blend) and the blended pairs (l_i).
+    rast.profile(True)
+    rast.profile_read()
+    for _ in range(steps):
+        ft.step()
+    kernels = rast.profile_read()
+    rast.profile(False)
+    walked, blended = [], []
+    with torch.no_grad():
+        p = ft.activated_copy()
+        for cam in cams:
+            _, _, load = rast.forward(p, cam, st)
+            last, _ = rast.read_pixel_stats()
+            walked.append(int(last.astype(np.int64).sum()))
+            blended.append(int(load.to(torch.int64).sum().item()))
+    n_vis = int(np.count_nonzero(rast.read_gaussians()[2]))
     rast.close()
+    table = {name: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
+                    "share": v[0] / sum(x[0] for x in kernels.values())}
+             for name, v in kernels.items()}
+    u = {"walked": statistics.mean(walked), "blended": statistics.mean(blended),
+         "visible": n_vis, "gaussians": base.n}
     return {"workload": "cluster-1M-720p", "steps_per_s": 1e3 / ms, "ms_per_step": ms,
             "final_loss": float(loss.item()),
             "step": "forward + L1/SSIM + L_load (lambda 0.44/0.11/0.45) + adr_render_backward + "
-                    "Adam on 1M Gaussians, 1280x720"}
+                    "Adam on 1M Gaussians, 1280x720",
+            "kernels": table, "units": u, "backward_roofline": backward_roofline(table, u)}
+
+
+# FP32 lane operations of the Render backward: per list position a pixel walks
+# back, the forward's evaluation (eigen-form quadratic with its k term, the
+# exponential, clamp and skip test); per blended pair the transmittance
+# recovery, the colour, opacity and conic terms and the colour behind.
+BWD_OPS_PER_WALKED = 15
+BWD_OPS_PER_BLENDED = 35
+# Preprocess backward, bytes per Gaussian with tiles: parameters (236 B), the
+# forward's conic record (32 B), the 2D gradients (36 B) and the tile box in,
+# the parameter gradients (236 B) out; without tiles only the box in and zeros out.
+BWD_PRE_BYTES_VISIBLE = 236 + 32 + 36 + 4 + 236
+BWD_PRE_BYTES_CULLED = 4 + 236
+
+
+def backward_roofline(table, u, sm_count=152, clk_mhz=2070.0):
+    out = {}
+    hbm_gbs, _, src = peaks()
+    rb = table.get("render_backward")
+    if rb:
+        ops = BWD_OPS_PER_WALKED * u["walked"] + BWD_OPS_PER_BLENDED * u["blended"]
+        ach = ops / (rb["ms_per_step"] / 1e3) / 1e12
+        peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
+        out["render_backward"] = {"bound": "alu", "achieved": ach, "peak": peak,
+                                  "unit": "T FP32 lane-ops/s", "frac": ach / peak,
+                                  "work": f"{BWD_OPS_PER_WALKED} per walked position + "
+                                          f"{BWD_OPS_PER_BLENDED} per blended pair"}
+    pb = table.get("preprocess_backward")
+    if pb:
+        b = BWD_PRE_BYTES_VISIBLE * u["visible"] + BWD_PRE_BYTES_CULLED * (u["gaussians"] - u["visible"])
+        ach = b / (pb["ms_per_step"] / 1e3) / 1e9
+        out["preprocess_backward"] = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs,
+                                      "unit": "GB/s", "frac": ach / hbm_gbs,
+                                      "algorithmic_bytes_per_step": b, "peak_source": src}
+    return out
 
 
 def finetune_measure(local, steps=500):
@@ -768,21 +828,56 @@ class OracleFrame:
         t1 = time.perf_counter()
         o.render_tiled(full, ranges, svals, st)
         t_render = time.perf_counter() - t1
+        self.last_split = (t_pre * self.g_div, t_render * tile_scale)
         return t_pre * self.g_div + t_render * tile_scale
+
+
+def render_all_cores(of, cam, st, key, threads):
+    """Seconds of the oracle's tiled render of the same tile sample on
+    `threads` host threads, each rendering its share of the sampled tiles (the
+    other tiles' ranges emptied) into its own buffers.  The C oracle holds no
+    global state and ctypes releases the GIL during the call, so the threads
+    run in parallel; the oracle itself is unchanged."""
+    from concurrent.futures import ThreadPoolExecutor
+    o = of.oracle
+    full, ranges, svals, tile_scale = of._tile_lists(key, cam, st)
+    tiles = np.nonzero(ranges[:, 1] > ranges[:, 0])[0]
+    parts = [p for p in np.array_split(tiles, threads) if p.size]
+    subs = []
+    for p in parts:
+        r = np.zeros_like(ranges)
+        r[p] = ranges[p]
+        subs.append(r)
+    with ThreadPoolExecutor(max_workers=len(subs)) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda r: o.render_tiled(full, r, svals, st), subs))
+        return (time.perf_counter() - t0) * tile_scale
 
 
 def cpu_baseline(scene, cams, st, budget_s=30.0):
     of = OracleFrame(scene)
     t0 = time.perf_counter()
-    secs = []
+    secs, pre, ren = [], [], []
     for i, cam in enumerate(cams):
         secs.append(of.frame_seconds(cam, st, key=i))
+        pre.append(of.last_split[0])
+        ren.append(of.last_split[1])
         if time.perf_counter() - t0 > budget_s:
             break
+    cores = os.cpu_count() or 1
+    par = [render_all_cores(of, cams[i], st, i, cores) for i in range(len(secs))]
+    t_par = statistics.mean(pre) + statistics.mean(par)
     return {"value": 1.0 / statistics.mean(secs), "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": (f"{len(secs)} frame(s): preprocess+emit+sort of a 1/{of.g_div} Gaussian "
                        f"sample and render of a 1/{of.t_div} tile sample, each scaled to the "
-                       f"full frame; single-threaded FP64 C")}
+                       f"full frame; single-threaded FP64 C"),
+            "render_s_per_frame_1_core": statistics.mean(ren),
+            "all_cores": {"value": 1.0 / t_par, "unit": "frames/s", "cores": cores,
+                          "render_s_per_frame": statistics.mean(par),
+                          "preprocess_emit_sort_s_per_frame": statistics.mean(pre),
+                          "how": f"the same tile sample rendered on {cores} host threads over "
+                                 f"disjoint tile subsets; preprocess, emission and the pair sort "
+                                 f"(qsort) stay single-threaded"}}
 
 
 def run_reference(args):

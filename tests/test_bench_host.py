@@ -81,6 +81,30 @@ def test_oracle_frame_sample_scales_to_a_full_frame():
     assert tile_scale == (8 * 6) / (8 * 6 // 8)           # 48 tiles, 6 sampled
     base = bench.cpu_baseline(scene, [cam], S.Settings(mode=S.MODE_AABB), budget_s=0.0)
     assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
+    ac = base["all_cores"]
+    assert ac["cores"] == (os.cpu_count() or 1) and ac["value"] > 0
+
+
+def test_all_cores_render_renders_every_sampled_tile_once():
+    """The threads' tile subsets partition the sampled tiles: summing their
+    images gives the single-threaded render of the sample."""
+    import numpy as np
+    import oracle
+    from paper_2409_08669_gb300 import scenes as S
+    scene = S.tiny_scene(2, n=3000)
+    cam = S.look_at((0, 0, -3), width=96, height=80)
+    st = S.Settings(mode=S.MODE_AABB)
+    of = bench.OracleFrame(scene, g_div=4, t_div=2, seed=3)
+    full, ranges, svals, _ = of._tile_lists(0, cam, st)
+    one = oracle.render_tiled(full, ranges, svals, st)["img"]
+    tiles = np.nonzero(ranges[:, 1] > ranges[:, 0])[0]
+    acc = np.zeros_like(one)
+    for p in np.array_split(tiles, 3):
+        r = np.zeros_like(ranges)
+        r[p] = ranges[p]
+        acc += oracle.render_tiled(full, r, svals, st)["img"]
+    np.testing.assert_array_equal(acc, one)
+    assert bench.render_all_cores(of, cam, st, 0, 3) > 0.0
 
 
 def test_sort_throughput_counts_what_the_kernels_move():
