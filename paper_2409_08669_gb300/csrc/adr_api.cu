@@ -96,6 +96,7 @@ adr_status make_settings(const adr_settings* s, SetDev& d) {
     if (!(s->jac_clamp > 0.f)) return fail(ADR_ERR_INVALID, "jac_clamp must be positive");
     d.mode = s->mode;
     d.alpha_low = s->alpha_low; d.t_min = s->t_min; d.lowpass = s->lowpass;
+    d.e_low = (float)std::log2((double)s->alpha_low);
     d.jac_clamp = s->jac_clamp;
     for (int i = 0; i < 3; ++i) d.bg[i] = s->bg[i];
     d.sh_degree = s->sh_degree;

@@ -29,6 +29,11 @@ struct CamDev {
 struct SetDev {
     int mode;
     float alpha_low, t_min, lowpass, jac_clamp;
+    // log2(alpha_low) rounded once to FP32 on the host: Render and its
+    // backward take a pair's alpha < alpha_low skip as e < e_low on the
+    // exponent e of alpha = min(0.99, 2^e), so both decide it identically
+    // without evaluating 2^e for the pairs they skip.
+    float e_low;
     float bg[3];
     int sh_degree;
     int rect_rule;
@@ -351,14 +356,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // The eigen-form quadratic of a Gaussian at a pixel, shared by Render and its
 // backward so both take identical decisions: with the centre c relative to the
 // tile origin, w = (w1, w2) and the pixel offset f from the origin,
-// u_i = w_i . (c - f) is evaluated as k_i - w_i . f with k_i = w_i . c formed
-// once per (Gaussian, tile); returns log2(sigma) - (u1^2 + u2^2).
+// u_i = w_i . (c - f) is evaluated as (k_i - w_ix fx) - w_iy fy with
+// k_i = w_i . c formed once per (Gaussian, tile), the fx-term first (Render's
+// two pixels of a thread share fx); returns log2(sigma) - (u1^2 + u2^2).
 __device__ __forceinline__ float2 quad_k(float2 c, float4 w) {
     return make_float2(fmaf(w.x, c.x, w.y * c.y), fmaf(w.z, c.x, w.w * c.y));
 }
 __device__ __forceinline__ float quad_exponent(float2 k, float4 w, float log2_sigma, float fx, float fy) {
-    const float u1 = fmaf(-w.x, fx, fmaf(-w.y, fy, k.x));
-    const float u2 = fmaf(-w.z, fx, fmaf(-w.w, fy, k.y));
+    const float u1 = fmaf(-w.y, fy, fmaf(-w.x, fx, k.x));
+    const float u2 = fmaf(-w.w, fy, fmaf(-w.z, fx, k.y));
     return fmaf(-u1, u1, fmaf(-u2, u2, log2_sigma));
 }
 

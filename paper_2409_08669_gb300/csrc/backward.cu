@@ -72,7 +72,7 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
         }
     }
     float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];   // colour behind the current Gaussian
-    const float alpha_low = st.alpha_low;
+    const float e_low = st.e_low;   // alpha >= alpha_low as 2^e >= alpha_low, decided on e
 
     if (range.x < range.y) {
         // The longest prefix any pixel of the tile needs.
@@ -110,9 +110,10 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                     const float4 w = s_w[j];
                     const float4 col = s_c[j];
                     const float dx = c.x - fx, dy = c.y - fy;
-                    const float raw = ex2_approx(quad_exponent(quad_k(c, w), w, col.w, fx, fy));
-                    const float alpha = fminf(0.99f, raw);
-                    if (alpha >= alpha_low) {
+                    const float e = quad_exponent(quad_k(c, w), w, col.w, fx, fy);
+                    if (e >= e_low) {
+                        const float raw = ex2_approx(e);
+                        const float alpha = fminf(0.99f, raw);
                         contrib = true;
                         const float one_m = 1.f - alpha;
                         T = T / one_m;                                    // T before this blend

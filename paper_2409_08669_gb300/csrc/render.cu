@@ -22,24 +22,59 @@
 namespace adr {
 namespace {
 
-constexpr int kRenderThreads = kTilePixels;
+// One CTA of 128 threads per 16x16 tile.  Warp w renders the 8x8 quadrant
+// (w mod 2, w div 2) of the tile; lane l owns the two vertically adjacent
+// pixels (l mod 8, 2 (l div 8)) and (l mod 8, 2 (l div 8) + 1) of it, so
+// both share fx.  Each pixel's two eigen components u_i = (k_i - w_ix fx) -
+// w_iy fy advance together in one paired FP32 FMA (fma.rn.f32x2, each lane
+// rounding as the scalar fmaf does), the fx-term is formed once for both
+// pixels, and the blend of the two pixels is one paired sequence without
+// branches: every pixel takes exactly the decisions of quad_exponent's scalar
+// evaluation, which the backward uses too.
+constexpr int kRenderThreads = kTilePixels / 2;
+constexpr int kStage = kTilePixels;          // Gaussians staged per batch
+constexpr int kRenderWarps = kRenderThreads / 32;
 
-constexpr int kRunFill = 8;   // list entries each thread reads per batch (column runs)
+constexpr int kRunFill = 16;   // list entries each thread reads per batch (column runs)
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 
 template <bool kRuns>
-__global__ void __launch_bounds__(kRenderThreads, 4)   // 4 CTAs per SM: <= 64 registers
+__global__ void __launch_bounds__(kRenderThreads, 8)   // 8 CTAs per SM: <= 64 registers
 k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
          const uint2* __restrict__ runs, const float4* __restrict__ rec,
          const FrameParams* __restrict__ fp, float* __restrict__ img,
          float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
          int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat,
          SliceState ss) {
-    __shared__ float2 s_xy[kRenderThreads];
-    __shared__ float4 s_w[kRenderThreads];
-    __shared__ float4 s_c[kRenderThreads];
-    __shared__ uint32_t s_gid[kRenderThreads];
-    __shared__ uint32_t s_wcnt[kRunFill][kRenderThreads / 32];   // kept per (k, warp)
-    __shared__ uint32_t s_off[kRunFill * (kRenderThreads / 32)];  // their exclusive prefix
+    constexpr int kFill = kRuns ? kRunFill : kStage / kRenderThreads;
+    __shared__ float4 s_kl[kStage];    // k1, k2, log2(sigma), -
+    __shared__ float4 s_nw[kStage];    // -w1x, -w2x, -w1y, -w2y
+    __shared__ float4 s_rg[kStage];    // red, red, green, green
+    __shared__ float2 s_bb[kStage];    // blue, blue
+    __shared__ uint32_t s_gid[kStage];
+    __shared__ uint32_t s_cand[kFill][kRenderThreads];  // this batch's list entries' Gaussians
+    __shared__ uint32_t s_mask[kFill][kRenderWarps];    // kept entries per (k, warp), by lane
+    __shared__ uint32_t s_wcnt[kFill][kRenderWarps];    // their number
+    __shared__ uint32_t s_off[kFill * kRenderWarps];    // their exclusive prefix
     __shared__ uint32_t s_total;
     __shared__ uint32_t s_next;
     __shared__ uint2 s_range;
@@ -49,30 +84,38 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     // CTAs walk the tiles column by column: the tiles in flight at once share
     // a few columns' run lists and Gaussian records in L2.
     const int ty = (int)(blockIdx.x % cam.tiles_y), tx = (int)(blockIdx.x / cam.tiles_y);
-    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
-    const int x = tx * kTile + lx, y = ty * kTile + ly;
-    const bool inside = x < cam.width && y < cam.height;
-    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
-    const float fx = (float)lx, fy = (float)ly;
-
-    // The tile's own list; for column runs, see below.
-    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[ty * cam.tiles_x + tx];
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int32_t count = 0, last = 0, trav = 0;
-    bool done = !inside, stopped = false;
-    const float alpha_low = st.alpha_low, t_min = st.t_min;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 8 + 2 * (lane >> 3);
+    const int x = tx * kTile + lx, ya = ty * kTile + ly, yb = ya + 1;
+    const bool in_a = x < cam.width && ya < cam.height, in_b = x < cam.width && yb < cam.height;
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const float2 fx2 = make_float2((float)lx, (float)lx);
+    const float2 fya2 = make_float2((float)ly, (float)ly), fyb2 = make_float2((float)(ly + 1), (float)(ly + 1));
+
+    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[ty * cam.tiles_x + tx];
+    // Per-pixel blend state: pixel a in .x, pixel b in .y.
+    float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
+    int32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, stop_a = 0, stop_b = 0;
+    bool done_a = !in_a, done_b = !in_b, stopped_a = false, stopped_b = false;
+    const float e_low = st.e_low, t_min = st.t_min;
     int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
     const int tile_rm = ty * cam.tiles_x + tx;
-    const size_t pix = inside ? (size_t)y * cam.width + x : 0;
+    const size_t pixa = in_a ? (size_t)ya * cam.width + x : 0;
+    const size_t pixb = in_b ? (size_t)yb * cam.width + x : 0;
     if (ss.phase == 2) {   // last slice: resume the tiles the first slice left unfinished
         if (ss.tile_done[tile_rm]) return;
-        if (inside) {
-            const float4 a = ss.pst[pix];
-            const int4 b = ss.pis[pix];
-            T = a.x; C0 = a.y; C1 = a.z; C2 = a.w;
-            count = b.x; last = b.y; trav = b.z; stopped = b.w != 0;
-            done = stopped;
+        // a pixel that stopped keeps its traversal as its stop position
+        if (in_a) {
+            const float4 a = ss.pst[pixa];
+            const int4 b = ss.pis[pixa];
+            T.x = a.x; C0.x = a.y; C1.x = a.z; C2.x = a.w;
+            cnt_a = b.x; last_a = b.y; stopped_a = done_a = b.w != 0; stop_a = stopped_a ? b.z : 0;
+        }
+        if (in_b) {
+            const float4 a = ss.pst[pixb];
+            const int4 b = ss.pis[pixb];
+            T.y = a.x; C0.y = a.y; C1.y = a.z; C2.y = a.w;
+            cnt_b = b.x; last_b = b.y; stopped_b = done_b = b.w != 0; stop_b = stopped_b ? b.z : 0;
         }
         fbase = ss.tile_fbase[tile_rm];
     }
@@ -92,39 +135,37 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     }
 
     // Each batch reads kFill list entries per thread (list order: entry
-    // base + k * 256 + thread) and stages the first 256 kept ones; the list
+    // base + k * 128 + thread) and stages the first 256 kept ones; the list
     // resumes at the first kept entry not staged.
-    constexpr int kFill = kRuns ? kRunFill : 1;
     uint32_t base = range.x;
     while (base < range.y) {
-        if (__syncthreads_count(done) == kRenderThreads) break;
-        uint32_t g[kFill], kept[kFill];
-        bool keep[kFill];
-#pragma unroll
+        if (__syncthreads_count(done_a && done_b) == kRenderThreads) break;
+#pragma unroll 4
         for (int k = 0; k < kFill; ++k) {
             const uint32_t idx = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
-            g[k] = 0;
-            keep[k] = idx < range.y;
-            if (keep[k]) {
+            bool keep = idx < range.y;
+            uint32_t g = 0;
+            if (keep) {
                 if (kRuns) {   // run record: Gaussian, y0 | (h - 1) << 8 | tx << 16
                     const uint2 r = runs[idx];
-                    g[k] = r.x;
-                    keep[k] = (uint32_t)ty - (r.y & 0xFFu) <= ((r.y >> 8) & 0xFFu);
+                    g = r.x;
+                    keep = (uint32_t)ty - (r.y & 0xFFu) <= ((r.y >> 8) & 0xFFu);
                 } else {
-                    g[k] = sorted_gauss[idx];
+                    g = sorted_gauss[idx];
                 }
             }
-        }
-        // Stable compaction: ballots per (k, warp); warp 0 scans their counts
-        // in list order (k-major).
-#pragma unroll
-        for (int k = 0; k < kFill; ++k) {
-            kept[k] = __ballot_sync(0xffffffffu, keep[k]);
-            if (lane == 0) s_wcnt[k][warp] = __popc(kept[k]);
+            s_cand[k][threadIdx.x] = g;
+            // Stable compaction: one ballot per (k, warp), kept in shared
+            // memory; warp 0 scans their counts in list order (k-major).
+            const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) {
+                s_mask[k][warp] = mask;
+                s_wcnt[k][warp] = __popc(mask);
+            }
         }
         __syncthreads();
         if (warp == 0) {
-            constexpr int kN = kFill * (kRenderThreads / 32);
+            constexpr int kN = kFill * kRenderWarps;
             constexpr int kPer = (kN + 31) / 32;                 // counts per lane
             uint32_t v[kPer], t = 0;
 #pragma unroll
@@ -133,100 +174,140 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
                 v[e] = i < kN ? (&s_wcnt[0][0])[i] : 0u;
                 t += v[e];
             }
-            uint32_t x = t;
+            uint32_t xs = t;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
+                const uint32_t yv = __shfl_up_sync(0xffffffffu, xs, o);
+                if (lane >= o) xs += yv;
             }
-            uint32_t run = x - t;
+            uint32_t run = xs - t;
 #pragma unroll
             for (int e = 0; e < kPer; ++e) {
                 const int i = lane * kPer + e;
                 if (i < kN) s_off[i] = run;
                 run += v[e];
             }
-            if (lane == 31) s_total = x;
+            if (lane == 31) s_total = xs;
         }
         __syncthreads();
         const uint32_t total = s_total;
-        uint32_t before[kFill];
-#pragma unroll
-        for (int k = 0; k < kFill; ++k) before[k] = s_off[k * (kRenderThreads / 32) + warp];
         const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
         for (int k = 0; k < kFill; ++k) {
-            if (keep[k]) {
-                const uint32_t slot = before[k] + __popc(kept[k] & lt);
-                if (slot < (uint32_t)kRenderThreads) s_gid[slot] = g[k];
-                else if (slot == (uint32_t)kRenderThreads)
+            const uint32_t mask = s_mask[k][warp];
+            if ((mask >> lane) & 1u) {
+                const uint32_t slot = s_off[k * kRenderWarps + warp] + __popc(mask & lt);
+                if (slot < (uint32_t)kStage) s_gid[slot] = s_cand[k][threadIdx.x];
+                else if (slot == (uint32_t)kStage)
                     s_next = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
             }
         }
-        const int m = (int)min(total, (uint32_t)kRenderThreads);
+        const int m = (int)min(total, (uint32_t)kStage);
         __syncthreads();
-        const uint32_t next = total > (uint32_t)kRenderThreads
+        const uint32_t next = total > (uint32_t)kStage
                                   ? s_next
                                   : min(range.y, base + (uint32_t)(kFill * kRenderThreads));
-        if ((int)threadIdx.x < m) {
-            const uint32_t gi = s_gid[threadIdx.x];
+        for (int sl = threadIdx.x; sl < m; sl += kRenderThreads) {
+            const uint32_t gi = s_gid[sl];
             const float4 r0 = rec[3 * (size_t)gi + 0];
             const float4 w = rec[3 * (size_t)gi + 1];
+            const float4 col = rec[3 * (size_t)gi + 2];
             // centre relative to the tile origin: (hi - origin) is exact, one rounding for lo
             const float2 c = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
                                          __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
-            s_xy[threadIdx.x] = quad_k(c, w);
-            s_w[threadIdx.x] = w;
-            s_c[threadIdx.x] = rec[3 * (size_t)gi + 2];
+            const float2 k = quad_k(c, w);
+            s_kl[sl] = make_float4(k.x, k.y, col.w, 0.f);
+            s_nw[sl] = make_float4(-w.x, -w.z, -w.y, -w.w);
+            s_rg[sl] = make_float4(col.x, col.x, col.y, col.y);
+            s_bb[sl] = make_float2(col.z, col.z);
         }
         __syncthreads();
-        if (!done) {
-            int j = 0;
-            for (; j < m; ++j) {
-                const float4 col = s_c[j];
-                const float e = quad_exponent(s_xy[j], s_w[j], col.w, fx, fy);   // log2(sigma) - q log2(e)/2
-                const float alpha = fminf(0.99f, ex2_approx(e));
-                if (alpha < alpha_low) continue;
-                const float test_T = T * (1.f - alpha);
-                if (test_T < t_min) { done = stopped = true; ++j; break; }
-                const float wgt = alpha * T;
-                C0 = fmaf(col.x, wgt, C0);
-                C1 = fmaf(col.y, wgt, C1);
-                C2 = fmaf(col.z, wgt, C2);
+        if (!__all_sync(0xffffffffu, done_a && done_b)) {   // warp-uniform: the loop votes
+            for (int j = 0; j < m; ++j) {
+                const float4 kl = s_kl[j];
+                const float4 nw = s_nw[j];
+                // u = (k - w_x fx) - w_y fy, the fx-term shared, as quad_exponent
+                const float2 in = ffma2(make_float2(nw.x, nw.y), fx2, make_float2(kl.x, kl.y));
+                const float2 ua = ffma2(make_float2(nw.z, nw.w), fya2, in);
+                const float2 ub = ffma2(make_float2(nw.z, nw.w), fyb2, in);
+                // e = log2(sigma) - q log2(e) / 2; alpha = min(0.99, 2^e) (Eq. 2) reaches
+                // alpha_low iff e >= e_low
+                const float ea = fmaf(-ua.x, ua.x, fmaf(-ua.y, ua.y, kl.z));
+                const float eb = fmaf(-ub.x, ub.x, fmaf(-ub.y, ub.y, kl.z));
+                bool la = !done_a && ea >= e_low, lb = !done_b && eb >= e_low;
+                if (!__any_sync(0xffffffffu, la || lb)) {   // no pixel of the warp reaches alpha_low
+                    if (__all_sync(0xffffffffu, done_a && done_b)) break;
+                    continue;
+                }
+                // Front-to-back step (Eq. 3), both pixels at once: a pixel that
+                // skips has alpha 0 here, so T and C stay as they are.
+                float2 alpha = make_float2(la ? fminf(0.99f, ex2_approx(ea)) : 0.f,
+                                           lb ? fminf(0.99f, ex2_approx(eb)) : 0.f);
+                float2 test_T = fmul2(T, ffma2(alpha, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+                const int32_t pos = fbase + j + 1;
+                const bool sa = test_T.x < t_min, sb = test_T.y < t_min;
+                if (__any_sync(0xffffffffu, sa || sb)) {
+                    // rare: a pixel stops before this Gaussian, which it does not blend
+                    if (sa) { alpha.x = 0.f; test_T.x = T.x; la = false; stop_a = pos; done_a = true; }
+                    if (sb) { alpha.y = 0.f; test_T.y = T.y; lb = false; stop_b = pos; done_b = true; }
+                }
+                const float2 wgt = fmul2(alpha, T);
+                const float4 rg = s_rg[j];
+                C0 = ffma2(make_float2(rg.x, rg.y), wgt, C0);
+                C1 = ffma2(make_float2(rg.z, rg.w), wgt, C1);
+                C2 = ffma2(s_bb[j], wgt, C2);
                 T = test_T;
-                ++count;
-                last = fbase + j + 1;
+                if (la) { ++cnt_a; last_a = pos; }
+                if (lb) { ++cnt_b; last_b = pos; }
             }
-            trav += j;
         }
         fbase += m;
         base = next;
     }
+    stopped_a = stop_a != 0;
+    stopped_b = stop_b != 0;
+    // Traversal (positions evaluated): up to the stop, else the whole list seen.
+    const int32_t trav_a = stopped_a ? stop_a : fbase, trav_b = stopped_b ? stop_b : fbase;
     if (ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
-        const bool all_done = __syncthreads_count(done) == kRenderThreads;
+        const bool all_done = __syncthreads_count(done_a && done_b) == kRenderThreads;
         if (threadIdx.x == 0) {
             ss.tile_done[tile_rm] = all_done ? 1u : 0u;
             if (!all_done) ss.tile_fbase[tile_rm] = fbase;
         }
         if (!all_done) {
-            if (inside) {
-                ss.pst[pix] = make_float4(T, C0, C1, C2);
-                ss.pis[pix] = make_int4(count, last, trav, stopped ? 1 : 0);
+            if (in_a) {
+                ss.pst[pixa] = make_float4(T.x, C0.x, C1.x, C2.x);
+                ss.pis[pixa] = make_int4(cnt_a, last_a, trav_a, stopped_a ? 1 : 0);
+            }
+            if (in_b) {
+                ss.pst[pixb] = make_float4(T.y, C0.y, C1.y, C2.y);
+                ss.pis[pixb] = make_int4(cnt_b, last_b, trav_b, stopped_b ? 1 : 0);
             }
             return;
         }
     }
-    if (inside) {
-        const size_t hw = (size_t)cam.width * cam.height;
-        img[pix] = C0 + T * st.bg[0];
-        img[hw + pix] = C1 + T * st.bg[1];
-        img[2 * hw + pix] = C2 + T * st.bg[2];
-        if (t_final) t_final[pix] = T;
-        if (load) load[pix] = count;
-        if (last_out) last_out[pix] = last;
-        if (trav_out) trav_out[pix] = trav;
-        if (tfin) tfin[pix] = T;
-        if (lstat) lstat[pix] = count | (stopped ? (int32_t)0x80000000u : 0);
+    const size_t hw = (size_t)cam.width * cam.height;
+    if (in_a) {
+        img[pixa] = C0.x + T.x * st.bg[0];
+        img[hw + pixa] = C1.x + T.x * st.bg[1];
+        img[2 * hw + pixa] = C2.x + T.x * st.bg[2];
+        if (t_final) t_final[pixa] = T.x;
+        if (load) load[pixa] = cnt_a;
+        if (last_out) last_out[pixa] = last_a;
+        if (trav_out) trav_out[pixa] = trav_a;
+        if (tfin) tfin[pixa] = T.x;
+        if (lstat) lstat[pixa] = cnt_a | (stopped_a ? (int32_t)0x80000000u : 0);
+    }
+    if (in_b) {
+        img[pixb] = C0.y + T.y * st.bg[0];
+        img[hw + pixb] = C1.y + T.y * st.bg[1];
+        img[2 * hw + pixb] = C2.y + T.y * st.bg[2];
+        if (t_final) t_final[pixb] = T.y;
+        if (load) load[pixb] = cnt_b;
+        if (last_out) last_out[pixb] = last_b;
+        if (trav_out) trav_out[pixb] = trav_b;
+        if (tfin) tfin[pixb] = T.y;
+        if (lstat) lstat[pixb] = cnt_b | (stopped_b ? (int32_t)0x80000000u : 0);
     }
 }
 
