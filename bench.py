@@ -514,21 +514,26 @@ def finetune_measure(local, steps=500):
     return out
 
 
-def serve_measure(local, n_requests=2000, warmup_requests=200, rate=200.0, seed=21):
+SERVE_SCENES = (6_000_000, 3_000_000, 1_000_000, 500_000)
+
+
+def serve_measure(local, n_requests=2000, warmup_requests=200, rate=200.0, seed=21, max_batch=1,
+                  slots=16, params=None):
     """Serving: 4 resident clustered scenes (0.5M, 1M, 3M, 6M Gaussians), a
     Poisson stream of `rate` requests/s, each a random camera on the radius-4
     sphere at a resolution drawn from {800x800, 1280x720, 1920x1080}, through
-    the continuous-batching server (adr_serve_*).  Latency is submit to
-    completion; a closed-loop burst of the same request mix gives the
-    saturation throughput."""
+    the continuous-batching server (adr_serve_*) with `slots` frame slots in
+    groups of `max_batch` (1: frames overlap, each request its own launches;
+    4: up to four requests on one scene share one batched frame).  Latency is
+    submit to completion; a closed-loop burst of the same request mix gives
+    the saturation throughput."""
     import torch
-    from paper_2409_08669_gb300.raster import upload
     from paper_2409_08669_gb300.serve import Server
-    sizes = (6_000_000, 3_000_000, 1_000_000, 500_000)
-    params = [upload(S.cluster_scene(n=n, seed=31 + k), device=f"cuda:{local}") for k, n in enumerate(sizes)]
+    sizes = SERVE_SCENES
     st = S.Settings(mode=S.MODE_AABB)
-    srv = Server(max_slots=4, mem_budget_bytes=12 << 30, slot_pair_capacity=1 << 27,
-                 slot_max_gaussians=max(sizes), max_width=1920, max_height=1080, device=local)
+    srv = Server(max_slots=slots, mem_budget_bytes=24 << 30, slot_pair_capacity=1 << 27,
+                 slot_max_gaussians=max(sizes), max_width=1920, max_height=1080, device=local,
+                 max_batch=max_batch)
     ids = [srv.add_scene(p, st) for p in params]
     res = ((800, 800), (1280, 720), (1920, 1080))
     rng = np.random.default_rng(seed)
@@ -583,7 +588,7 @@ def serve_measure(local, n_requests=2000, warmup_requests=200, rate=200.0, seed=
     closed = srv.stats()
     burst_wall = time.perf_counter() - t0
     srv.close()
-    del params, bufs
+    del bufs
     torch.cuda.empty_cache()
     return {"workload": "serve-4scenes-poisson200",
             "scenes": list(sizes), "resolutions": [f"{w}x{h}" for w, h in res],
@@ -593,9 +598,23 @@ def serve_measure(local, n_requests=2000, warmup_requests=200, rate=200.0, seed=
             "max_inflight": int(open_loop["max_inflight"]),
             "admitted_while_busy": int(open_loop["admitted_while_busy"]),
             "capacity_errors": int(open_loop["capacity_errors"]),
+            "mean_batch": open_loop["mean_batch"],
             "saturation_frames_per_s": burst / burst_wall,
             "saturation_p50_ms": closed["p50_ms"], "saturation_p99_ms": closed["p99_ms"],
-            "failed_requests": len(failed), "slots": 4, "graphs": True}
+            "saturation_mean_batch": closed["mean_batch"],
+            "failed_requests": len(failed), "slots": slots, "max_batch": max_batch, "graphs": True}
+
+
+def serve_both(local):
+    """The serving measurement without and with batched frames, on the same
+    resident scenes and the same request streams (same seeds)."""
+    from paper_2409_08669_gb300.raster import upload
+    params = [upload(S.cluster_scene(n=n, seed=31 + k), device=f"cuda:{local}")
+              for k, n in enumerate(SERVE_SCENES)]
+    out = {"unbatched": serve_measure(local, max_batch=1, params=params),
+           "batched": serve_measure(local, max_batch=4, params=params)}
+    del params
+    return out
 
 
 def e2e_host(rast_ctx, scene, cams, st, steps, warmup):
@@ -770,7 +789,7 @@ def run_ours(args):
         result["train_step"] = train_step_rate(local)
         result["load_balance_finetune"] = finetune_measure(local)
     if not args.no_serve and world == 1:
-        result["serve"] = serve_measure(local)
+        result["serve"] = serve_both(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(scene, cams, st_adr, budget_s=args.cpu_budget)
     if rank == 0:
@@ -925,11 +944,17 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="heavy-3M-1080p")
     ap.add_argument("--quick", action="store_true",
                     help="time the AdR mode only (no plain/circle arms, e2e or baselines)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="only the serving measurement (unbatched and batched), one JSON line")
     args = ap.parse_args()
     select_workload(args.workload)
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serve": serve_both(0)}))
     else:
         run_ours(args)
 

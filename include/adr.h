@@ -282,6 +282,19 @@ adr_status adr_profile_read(adr_ctx *ctx, int32_t max_kernels, int32_t *kernel_i
                             double *total_ms, int32_t *launches, int32_t *num_kernels);
 const char *adr_profile_kernel_name(int32_t kernel_id);
 
+/* Per-tile tracing of Render (scheduling and load balance across tiles, the
+ * uneven load of Sec. 4.4).  While enabled (the first call allocates 32 bytes
+ * per tile of the largest image; disabling synchronises the device and frees
+ * them), every adr_render records for each tile the %globaltimer nanoseconds
+ * (low 32 bits) at which its CTA started and ended, the SM it ran on and the
+ * list positions it staged.  adr_read_tile_trace copies the last frame's
+ * record into `out` (device memory, uint32 [2, tiles_y * tiles_x, 4]: the
+ * first block for the whole list or depth slice 0, the second for depth slice
+ * 1, whose tiles that finished in slice 0 stay zero), enqueued on `stream`.
+ * ADR_ERR_INVALID if tracing is off or no frame was rendered. */
+adr_status adr_trace_tiles(adr_ctx *ctx, int32_t enable);
+adr_status adr_read_tile_trace(adr_ctx *ctx, uint32_t *out, void *stream);
+
 /* Waits for the context's work and reports device-side flags as a status;
  * clears them.  SYNCHRONISES.  In order of precedence: ADR_ERR_TIMEOUT (a
  * bounded lookback wait of the run scan gave up; that frame's later stages
@@ -368,26 +381,35 @@ adr_status adr_render_frame_noalloc(const float *means, const float *scales, con
  * = 12 * pairs + 150 * n + 32 * W * H, with pairs = 1.25 * (the scene's learned
  * pairs per pixel) * W * H, or slot_pair_capacity while the scene has no
  * completed frame; each slot's buffers are allocated once, at creation, so the
- * budget bounds the working set in flight, not the allocation.  With
- * use_graphs != 0 each (slot, scene, W, H) frame is captured once into a CUDA
- * graph and replayed after a one-thread kernel writes the request's camera
- * into the device copy the graph's kernels read.  A request's result equals that of adr_preprocess +
- * adr_sort + adr_render on its own (bit-identical image). */
+ * budget bounds the working set in flight, not the allocation.  Batching: the
+ * slots form max_slots / max_batch groups of max_batch; a free group takes the
+ * queue head together with later queued requests on the same scene (up to
+ * max_batch, each admitted only if the budget allows) and renders them as one
+ * batched frame: one Preprocess launch over all their cameras (the scene is
+ * read once), each camera's sort stages on its own stream, and one Render
+ * launch per depth slice over all their tiles.  With max_batch = 1 each slot
+ * renders one request at a time and frames of different requests only
+ * overlap.  With use_graphs != 0 each (group, scene, batch size, image sizes)
+ * frame is captured once into a CUDA graph and replayed after one-thread
+ * kernels write the requests' cameras into the device copies the graph's
+ * kernels read.  A request's result equals that of adr_preprocess + adr_sort +
+ * adr_render on its own (bit-identical image), batched or not. */
 typedef struct adr_server adr_server;
 
 typedef struct adr_serve_config {
-    int32_t max_slots;            /* 1..64 concurrent frames */
+    int32_t max_slots;            /* 1..64 concurrent frames (a multiple of max_batch) */
     int64_t mem_budget_bytes;     /* admission budget, > 0 */
     int64_t slot_pair_capacity;   /* Gaussian-tile pairs per slot, 1..2^30 */
     int64_t slot_max_gaussians;   /* largest scene, 1..2^29 */
     int32_t max_width, max_height;/* largest image, <= 4096 each */
     int32_t use_graphs;           /* 0: plain launches; else graph replay */
     int32_t device;               /* CUDA device ordinal */
+    int32_t max_batch;            /* 1..4 requests on one scene per batched frame */
 } adr_serve_config;
 
 /* Allocates every slot and starts the scheduler thread.  ADR_ERR_INVALID for
- * a configuration out of range, ADR_ERR_CUDA if an allocation fails (nothing
- * leaks). */
+ * a configuration out of range (including max_batch outside 1..4 or not
+ * dividing max_slots), ADR_ERR_CUDA if an allocation fails (nothing leaks). */
 adr_status adr_serve_create(adr_server **server, const adr_serve_config *config);
 /* Waits for frames in flight, stops the scheduler and frees everything.
  * Requests still queued are dropped.  NULL is a no-op. */
@@ -416,12 +438,13 @@ adr_status adr_serve_submit(adr_server *server, int32_t scene_id, const adr_came
  * releases the ticket.  ADR_ERR_INVALID for an unknown ticket or a negative
  * timeout_us (the ticket is left as it was). */
 adr_status adr_serve_poll(adr_server *server, uint64_t ticket, int64_t timeout_us);
-/* Statistics since creation, first min(n, 10) of: completed requests, p50
+/* Statistics since creation, first min(n, 13) of: completed requests, p50
  * latency ms, p99 latency ms, mean latency ms (submit to completion seen by
  * the scheduler), the largest number of frames in flight at once, requests
  * admitted while another was in flight, requests rejected by admission,
  * completed frames per second (first submit to last completion), requests
- * that ended with ADR_ERR_CAPACITY, graph replays. */
+ * that ended with ADR_ERR_CAPACITY, graph replays, batched frames launched,
+ * the largest batch, mean requests per batched frame. */
 adr_status adr_serve_stats(adr_server *server, double *out, int32_t n);
 /* Restarts the statistics (requests in flight still complete into the new
  * window). */

@@ -51,7 +51,8 @@ class adr_serve_config(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
                 ("slot_pair_capacity", ctypes.c_int64), ("slot_max_gaussians", ctypes.c_int64),
                 ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -88,6 +89,8 @@ _SIGNATURES = {
     "adr_set_depth_slices": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
+    "adr_trace_tiles": (_I32, [_P, _I32]),
+    "adr_read_tile_trace": (_I32, [_P, _P, _P]),
     "adr_serve_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(adr_serve_config)]),
     "adr_serve_destroy": (None, [_P]),
     "adr_serve_add_scene": (_I32, [_P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(adr_settings),

@@ -172,6 +172,7 @@ adr_status camera_to_dev(const adr_camera* cam, int max_w, int max_h, CamDev& d)
 adr_status settings_to_dev(const adr_settings* s, SetDev& d) { return make_settings(s, d); }
 
 void free_workspace(Workspace& w) {
+    if (w.tile_trace) cudaFree(w.tile_trace);
     if (w.prof) {
         for (int i = 0; i < w.prof->created; ++i) cudaEventDestroy(w.prof->ev[i]);
         delete w.prof;
@@ -604,6 +605,41 @@ adr_status adr_profile_enable(adr_ctx* c, int32_t enable) {
         delete c->ws.prof;
         c->ws.prof = nullptr;
     }
+    return ok();
+}
+
+adr_status adr_trace_tiles(adr_ctx* c, int32_t enable) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    if (enable && !c->ws.tile_trace) {
+        const size_t bytes = (size_t)2 * c->ws.max_tiles * sizeof(uint4);
+        cudaError_t e = cudaMalloc((void**)&c->ws.tile_trace, bytes);
+        if (e == cudaSuccess) e = cudaMemset(c->ws.tile_trace, 0, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (c->ws.tile_trace) cudaFree(c->ws.tile_trace);
+            c->ws.tile_trace = nullptr;
+            return fail(ADR_ERR_CUDA, "tile trace allocation: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!enable && c->ws.tile_trace) {
+        ADR_CUDA(cudaDeviceSynchronize());
+        cudaFree(c->ws.tile_trace);
+        c->ws.tile_trace = nullptr;
+    }
+    return ok();
+}
+
+adr_status adr_read_tile_trace(adr_ctx* c, uint32_t* out, void* stream) {
+    if (!c || !out) return fail(ADR_ERR_INVALID, "NULL argument");
+    if (!c->ws.tile_trace) return fail(ADR_ERR_INVALID, "tile tracing is not enabled");
+    if (!c->have_render) return fail(ADR_ERR_INVALID, "adr_read_tile_trace before adr_render");
+    DeviceGuard guard(c->device);
+    const size_t nt = (size_t)c->fs.num_tiles;
+    cudaStream_t strm = (cudaStream_t)stream;
+    ADR_CUDA(cudaMemcpyAsync(out, c->ws.tile_trace, nt * sizeof(uint4), cudaMemcpyDeviceToDevice, strm));
+    ADR_CUDA(cudaMemcpyAsync(out + 4 * nt, c->ws.tile_trace + nt, nt * sizeof(uint4),
+                             cudaMemcpyDeviceToDevice, strm));
     return ok();
 }
 

@@ -14,6 +14,7 @@ namespace adr {
 
 constexpr int kTile = ADR_TILE;          // 16x16 pixel tiles (Sec. 3.2)
 constexpr int kTilePixels = kTile * kTile;
+constexpr int kMaxBatch = 4;             // cameras of one batched frame (serving)
 
 // Camera as the kernels see it.
 struct CamDev {
@@ -156,6 +157,7 @@ struct Workspace {
     unsigned long long* lookback = nullptr;
     size_t lookback_words = 0;             // (max_n / kSortChunk + 2) * kRadix
     Profiler* prof = nullptr;              // non-null: time every launch
+    uint4* tile_trace = nullptr;           // non-null: [2 * max_tiles] Render's per-tile trace
     FrameParams* d_fp = nullptr;           // [1] camera + settings of the current frame
     uint32_t* d_stage = nullptr;           // [1] stage counter (see EpochRef)
     // Depth slices of the forward frame (slices.cu); all null: one slice.
@@ -223,13 +225,48 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
 void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream);
 void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
                     int32_t* load, cudaStream_t stream);
+// A batched frame: up to kMaxBatch cameras of one scene (same n, same
+// settings), each with its own workspace, rendered with one Preprocess and
+// one Render launch per phase for all of them; each camera's sort stages run
+// on its own stream of `bs` (forked from `stream` and joined back), or all on
+// `stream` when bs is null.
+struct BatchItem {
+    const Workspace* ws;
+    FrameState* fs;
+    std::atomic<uint32_t>* epoch;
+    float* img;
+    float* t_final;
+    int32_t* load;
+};
+struct BatchStreams {
+    cudaStream_t side[kMaxBatch];
+    cudaEvent_t fork;
+    cudaEvent_t join[kMaxBatch];
+};
+void enqueue_frame_batch(const BatchItem* items, int count, const float* means, const float* scales,
+                         const float* rots, const float* opac, const float* sh, cudaStream_t stream,
+                         const BatchStreams* bs, bool set_params);
 void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev& st);
 
 // Kernel launchers (each enqueues on `stream`; all pointers are device memory).
+// Preprocess and Render take a batch of up to kMaxBatch cameras of one scene
+// in one grid (the serving scheduler's batched frames; one camera otherwise).
+struct PreprocessOut {
+    const FrameParams* fp;   // the camera's frame parameters
+    uint32_t* stage;         // its workspace's stage counter (EpochRef)
+    float4* rec;
+    float4* aux;
+    uint32_t* depth_key;
+    uint32_t* gbox;
+};
+struct PreprocessBatch {
+    int count = 0;
+    PreprocessOut cam[kMaxBatch];
+};
+// grid = chunks of 256 Gaussians x count, the camera index fastest
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
-                       const float* opac, const float* sh, const FrameParams* fp,
-                       uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
-                       uint32_t* gbox, cudaStream_t stream);
+                       const float* opac, const float* sh, const PreprocessBatch& batch,
+                       cudaStream_t stream);
 
 // One stable 8-bit pass of the depth sort (sort.cu): keys (>> shift) & 255;
 // vals_in == nullptr means the values are 0..n-1.  counts: kRadix x grid
@@ -319,10 +356,33 @@ struct SliceState {
 #endif
 constexpr int kSliceDiv = ADR_SLICE_DIV;
 constexpr uint32_t kSliceProbe = 16;   // a context re-measures the slices every 16 frames
-void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
-                   const float4* rec, int lists, const FrameParams* fp, int num_tiles, float* img,
-                   float* t_final, int32_t* load, int32_t* last, int32_t* trav, float* tfin,
-                   int32_t* lstat, const SliceState& ss, cudaStream_t stream);
+// One camera's inputs and outputs of a Render launch.
+struct RenderCam {
+    const uint2* ranges = nullptr;        // per-tile lists (lists == kListsTiles)
+    const uint32_t* sorted_gauss = nullptr;
+    const uint2* runs = nullptr;          // column runs (lists == kListsColumns)
+    const float4* rec = nullptr;
+    const FrameParams* fp = nullptr;
+    float* img = nullptr;
+    float* t_final = nullptr;
+    int32_t* load = nullptr;
+    int32_t* last = nullptr;
+    int32_t* trav = nullptr;
+    float* tfin = nullptr;
+    int32_t* lstat = nullptr;
+    // Tracing (null: off): per tile, (start, end) of its CTA in %globaltimer
+    // nanoseconds (low 32 bits each), the SM it ran on and the positions it
+    // staged, at [tile] for phases 0 and 1 and at [num_tiles + tile] for phase 2.
+    uint4* trace = nullptr;
+    SliceState ss;
+};
+struct RenderBatch {
+    int count = 0;
+    int lists = kListsColumns;            // the same kind for every camera of the batch
+    int tile_begin[kMaxBatch + 1] = {0};  // camera b's tiles are blocks [tile_begin[b], tile_begin[b+1])
+    RenderCam cam[kMaxBatch];
+};
+void launch_render(const RenderBatch& batch, cudaStream_t stream);
 void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint32_t* c0,
                          cudaStream_t stream);
 void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,

@@ -64,19 +64,22 @@ void fill_frame_state(FrameState& fs, int64_t n, const CamDev& cam, const SetDev
     fs.sorted_gauss = nullptr;
 }
 
-void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
-                        const float* means, const float* scales, const float* rots,
-                        const float* opac, const float* sh, cudaStream_t stream,
-                        bool set_params) {
-    const int64_t n = fs.n;
+// Before Preprocess: the stage tag, the frame parameters and the counters.
+static void preprocess_head(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                            cudaStream_t stream, bool set_params) {
     count_stage(epoch, ws, stream);
     if (set_params) launch_set_frame_params(FrameParams{fs.cam, fs.st}, ws.d_fp, stream);
     cudaMemsetAsync(ws.counters, 0, kCntSlots * sizeof(uint32_t), stream);
     cudaMemsetAsync(ws.hist, 0, kHistWords * sizeof(uint32_t), stream);
-    // Stage 1: per-Gaussian projection, covariance, colour and early cull.
-    TIMED(ws, kKPreprocess, stream,
-          launch_preprocess((int)n, means, scales, rots, opac, sh, ws.d_fp, ws.d_stage, ws.rec,
-                            ws.aux, ws.depth_key, ws.gbox, stream));
+}
+
+static PreprocessOut preprocess_out(const Workspace& ws) {
+    return PreprocessOut{ws.d_fp, ws.d_stage, ws.rec, ws.aux, ws.depth_key, ws.gbox};
+}
+
+// After Preprocess: the Gaussians by view depth, then the run scan.
+static void preprocess_tail(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
+    const int64_t n = fs.n;
     // Gaussians by view depth: 4 stable 8-bit passes over the V Gaussians with
     // tiles (the first pass drops the others, key 0xFFFFFFFF, and counts the
     // V).  The last pass carries the packed rectangles into depth order.
@@ -99,6 +102,20 @@ void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_
     TIMED(ws, kKScanTiles, stream,
           launch_scan_tiles(ws.sorted_box, n, ws.capacity, ws.offsets, ws.chunk_first, ws.lookback,
                             ep, ws.counters, ws.status, ws.scan_grid, stream));
+}
+
+void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
+                        const float* means, const float* scales, const float* rots,
+                        const float* opac, const float* sh, cudaStream_t stream,
+                        bool set_params) {
+    preprocess_head(ws, fs, epoch, stream, set_params);
+    // Stage 1: per-Gaussian projection, covariance, colour and early cull.
+    PreprocessBatch pb;
+    pb.count = 1;
+    pb.cam[0] = preprocess_out(ws);
+    TIMED(ws, kKPreprocess, stream,
+          launch_preprocess((int)fs.n, means, scales, rots, opac, sh, pb, stream));
+    preprocess_tail(ws, fs, stream);
 }
 
 // Stage 4, pass 2 and stage 5: the pairs of the column runs grouped by tile
@@ -193,32 +210,54 @@ void enqueue_tile_lists(const Workspace& ws, FrameState& fs, cudaStream_t stream
     enqueue_tile_pass2(ws, fs, stream);
 }
 
-void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
-                    int32_t* load, cudaStream_t stream) {
-    // Stage 6.
-    SliceState ss;
-    ss.col_totals = ws.ttotals;
-    ss.capacity = ws.capacity;
-    if (!fs.sliced) {
-        ss.col_counters = ws.counters;
-        TIMED(ws, kKRender, stream,
-              launch_render(ws.ranges, fs.sorted_gauss, fs.runs, ws.rec, fs.lists, ws.d_fp,
-                            fs.num_tiles, img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss,
-                            stream));
-        return;
+// Render's inputs and outputs for one camera, in phase 0 (the whole list),
+// 1 (slice 0) or 2 (slice 1).
+static RenderCam render_cam(const Workspace& ws, const FrameState& fs, float* img, float* t_final,
+                            int32_t* load, int phase) {
+    RenderCam rc;
+    rc.ranges = ws.ranges;
+    rc.sorted_gauss = fs.sorted_gauss;
+    rc.runs = fs.runs;
+    rc.rec = ws.rec;
+    rc.fp = ws.d_fp;
+    rc.img = img;
+    rc.t_final = t_final;
+    rc.load = load;
+    rc.last = ws.last;
+    rc.trav = ws.trav;
+    rc.tfin = ws.tfin;
+    rc.lstat = ws.lstat;
+    rc.trace = ws.tile_trace;
+    rc.ss.col_totals = ws.ttotals;
+    rc.ss.capacity = ws.capacity;
+    rc.ss.phase = phase;
+    rc.ss.col_counters = phase == 0 ? ws.counters
+                                    : ws.slice_counters + (phase == 2 ? kCntSlots : 0);
+    if (phase != 0) {
+        rc.ss.pst = ws.pst;
+        rc.ss.pis = ws.pis;
+        rc.ss.tile_done = ws.tile_done;
+        rc.ss.tile_fbase = ws.tile_fbase;
     }
-    if (fs.runs_held != kRunsSlice0) enqueue_pass1(ws, fs, pair_source(ws, fs, 0), stream);
-    ss.pst = ws.pst;
-    ss.pis = ws.pis;
-    ss.tile_done = ws.tile_done;
-    ss.tile_fbase = ws.tile_fbase;
-    ss.col_counters = ws.slice_counters;
-    ss.phase = 1;
-    TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, kListsColumns, ws.d_fp, fs.num_tiles,
-                        img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss, stream));
-    // Slice 1: the Gaussians behind slice 0 that touch an unfinished tile,
-    // with their run offsets, then their column runs.
+    return rc;
+}
+
+// One Render launch over the items' cameras (all of the same list kind).
+static void render_launch(const BatchItem* items, int count, int phase, cudaStream_t stream) {
+    RenderBatch rb;
+    rb.count = count;
+    rb.lists = phase == 0 ? items[0].fs->lists : kListsColumns;
+    for (int b = 0; b < count; ++b) {
+        const BatchItem& it = items[b];
+        rb.cam[b] = render_cam(*it.ws, *it.fs, it.img, it.t_final, it.load, phase);
+        rb.tile_begin[b + 1] = rb.tile_begin[b] + it.fs->num_tiles;
+    }
+    TIMED(*items[0].ws, kKRender, stream, launch_render(rb, stream));
+}
+
+// Slice 1 of a sliced frame: the Gaussians behind slice 0 that touch an
+// unfinished tile, with their run offsets, then their column runs.
+static void slice1_runs(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
     uint32_t* c1 = ws.slice_counters + kCntSlots;
     TIMED(ws, kKSlice, stream,
           launch_survivors(ws.tile_done, fs.cam.tiles_x, fs.cam.tiles_y, ws.sat, ws.sorted_box,
@@ -227,11 +266,74 @@ void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_fi
                            ws.s_chunk_first, c1, ws.status, stream));
     enqueue_pass1(ws, fs, pair_source(ws, fs, 1), stream);
     fs.runs_held = kRunsSlice1;
-    ss.col_counters = c1;
-    ss.phase = 2;
-    TIMED(ws, kKRender, stream,
-          launch_render(ws.ranges, nullptr, fs.runs, ws.rec, kListsColumns, ws.d_fp, fs.num_tiles,
-                        img, t_final, load, ws.last, ws.trav, ws.tfin, ws.lstat, ss, stream));
+}
+
+// Runs fn(b, stream_b) for every item, on the item's own stream when a batch
+// has them (forked from and joined back into `stream` by events), else on
+// `stream`.
+template <class Fn>
+static void per_item(const BatchItem* items, int count, cudaStream_t stream, const BatchStreams* bs,
+                     Fn fn) {
+    if (!bs || count == 1) {
+        for (int b = 0; b < count; ++b) fn(b, stream);
+        return;
+    }
+    cudaEventRecord(bs->fork, stream);
+    for (int b = 0; b < count; ++b) {
+        cudaStreamWaitEvent(bs->side[b], bs->fork, 0);
+        fn(b, bs->side[b]);
+        cudaEventRecord(bs->join[b], bs->side[b]);
+    }
+    for (int b = 0; b < count; ++b) cudaStreamWaitEvent(stream, bs->join[b], 0);
+}
+
+static void render_items(const BatchItem* items, int count, cudaStream_t stream,
+                         const BatchStreams* bs) {
+    for (int b = 0; b < count; ++b)   // tracing: this frame's tiles only
+        if (items[b].ws->tile_trace)
+            cudaMemsetAsync(items[b].ws->tile_trace, 0, (size_t)2 * items[b].fs->num_tiles * sizeof(uint4),
+                            stream);
+    // Stage 6.
+    if (!items[0].fs->sliced) {
+        render_launch(items, count, 0, stream);
+        return;
+    }
+    per_item(items, count, stream, bs, [&](int b, cudaStream_t s) {
+        const BatchItem& it = items[b];
+        if (it.fs->runs_held != kRunsSlice0) enqueue_pass1(*it.ws, *it.fs, pair_source(*it.ws, *it.fs, 0), s);
+        it.fs->runs_held = kRunsSlice0;
+    });
+    render_launch(items, count, 1, stream);
+    per_item(items, count, stream, bs, [&](int b, cudaStream_t s) { slice1_runs(*items[b].ws, *items[b].fs, s); });
+    render_launch(items, count, 2, stream);
+}
+
+void enqueue_render(const Workspace& ws, FrameState& fs, float* img, float* t_final,
+                    int32_t* load, cudaStream_t stream) {
+    const BatchItem it{&ws, &fs, nullptr, img, t_final, load};
+    render_items(&it, 1, stream, nullptr);
+}
+
+void enqueue_frame_batch(const BatchItem* items, int count, const float* means, const float* scales,
+                         const float* rots, const float* opac, const float* sh, cudaStream_t stream,
+                         const BatchStreams* bs, bool set_params) {
+    if (count < 1 || count > kMaxBatch) return;
+    PreprocessBatch pb;
+    pb.count = count;
+    for (int b = 0; b < count; ++b) {
+        const BatchItem& it = items[b];
+        preprocess_head(*it.ws, *it.fs, *it.epoch, stream, set_params);
+        pb.cam[b] = preprocess_out(*it.ws);
+    }
+    // Stage 1 for every camera in one grid: the scene is read once.
+    TIMED(*items[0].ws, kKPreprocess, stream,
+          launch_preprocess((int)items[0].fs->n, means, scales, rots, opac, sh, pb, stream));
+    // Stages 2-5 per camera, side by side.
+    per_item(items, count, stream, bs, [&](int b, cudaStream_t s) {
+        preprocess_tail(*items[b].ws, *items[b].fs, s);
+        enqueue_sort(*items[b].ws, *items[b].fs, *items[b].epoch, s);
+    });
+    render_items(items, count, stream, bs);
 }
 
 void enqueue_backward(const Workspace& ws, const FrameState& fs, const float* means,

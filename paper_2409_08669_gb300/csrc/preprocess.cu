@@ -154,18 +154,25 @@ __device__ __forceinline__ bool tile_span_3dgs(float c, float r, int tiles, int&
 // (w1.d)^2 + (w2.d)^2 = (log2 e) * q / 2 and alpha = sigma * 2^-(...).
 constexpr float kHalfLog2e = 0.84932180028801907f;
 
+// One launch serves a batch of cameras of the same scene: block k handles the
+// Gaussians of chunk k / count for camera k % count, so the blocks of one
+// chunk run side by side and every camera after the first reads the chunk's
+// parameters from L2 rather than DRAM.
 __global__ void __launch_bounds__(256)
 k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ scales,
              const float* __restrict__ rots, const float* __restrict__ opac,
-             const float* __restrict__ sh, const FrameParams* __restrict__ fp,
-             uint32_t* __restrict__ stage, float4* __restrict__ rec,
-             float4* __restrict__ aux, uint32_t* __restrict__ depth_key,
-             uint32_t* __restrict__ gbox) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) atomicAdd(stage, 1u);   // new lookback tag for this call's passes
+             const float* __restrict__ sh, PreprocessBatch batch) {
+    const int b = (int)(blockIdx.x % (unsigned)batch.count);
+    const int i = (int)(blockIdx.x / (unsigned)batch.count) * blockDim.x + threadIdx.x;
+    const PreprocessOut& out = batch.cam[b];
+    if (i == 0) atomicAdd(out.stage, 1u);   // new lookback tag for this call's passes
     if (i >= n) return;
-    const CamDev cam = fp->cam;
-    const SetDev st = fp->st;
+    const CamDev cam = out.fp->cam;
+    const SetDev st = out.fp->st;
+    float4* __restrict__ rec = out.rec;
+    float4* __restrict__ aux = out.aux;
+    uint32_t* __restrict__ depth_key = out.depth_key;
+    uint32_t* __restrict__ gbox = out.gbox;
 
     const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
     // Sort depth: fixed evaluation order, each operation rounded separately.
@@ -301,13 +308,13 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
 }  // namespace
 
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
-                       const float* opac, const float* sh, const FrameParams* fp,
-                       uint32_t* stage, float4* rec, float4* aux, uint32_t* depth_key,
-                       uint32_t* gbox, cudaStream_t stream) {
-    if (n <= 0) return;
+                       const float* opac, const float* sh, const PreprocessBatch& batch,
+                       cudaStream_t stream) {
+    if (n <= 0 || batch.count < 1 || batch.count > kMaxBatch) return;
     const int threads = 256;
-    k_preprocess<<<(n + threads - 1) / threads, threads, 0, stream>>>(
-        n, means, scales, rots, opac, sh, fp, stage, rec, aux, depth_key, gbox);
+    const unsigned chunks = (unsigned)((n + threads - 1) / threads);
+    k_preprocess<<<chunks * (unsigned)batch.count, threads, 0, stream>>>(n, means, scales, rots,
+                                                                      opac, sh, batch);
 }
 
 }  // namespace adr

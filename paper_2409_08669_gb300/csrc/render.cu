@@ -57,15 +57,33 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
     return d;
 }
 
+// A launch renders a batch of cameras (the serving scheduler's batched
+// frames; one camera otherwise): blocks [tile_begin[b], tile_begin[b + 1])
+// are camera b's tiles.
 template <bool kRuns>
 __global__ void __launch_bounds__(kRenderThreads, 8)   // 8 CTAs per SM: <= 64 registers
-k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
-         const uint2* __restrict__ runs, const float4* __restrict__ rec,
-         const FrameParams* __restrict__ fp, float* __restrict__ img,
-         float* __restrict__ t_final, int32_t* __restrict__ load, int32_t* __restrict__ last_out,
-         int32_t* __restrict__ trav_out, float* __restrict__ tfin, int32_t* __restrict__ lstat,
-         SliceState ss) {
+k_render(const RenderBatch batch) {
     constexpr int kFill = kRuns ? kRunFill : kStage / kRenderThreads;
+    int cb = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && (int)blockIdx.x >= batch.tile_begin[q]) ? 1 : 0;
+    const RenderCam& rc = batch.cam[cb];
+    const int tile_index = (int)blockIdx.x - batch.tile_begin[cb];
+    const uint2* __restrict__ ranges = rc.ranges;
+    const uint32_t* __restrict__ sorted_gauss = rc.sorted_gauss;
+    const uint2* __restrict__ runs = rc.runs;
+    const float4* __restrict__ rec = rc.rec;
+    const FrameParams* __restrict__ fp = rc.fp;
+    float* __restrict__ img = rc.img;
+    float* __restrict__ t_final = rc.t_final;
+    int32_t* __restrict__ load = rc.load;
+    int32_t* __restrict__ last_out = rc.last;
+    int32_t* __restrict__ trav_out = rc.trav;
+    float* __restrict__ tfin = rc.tfin;
+    int32_t* __restrict__ lstat = rc.lstat;
+    const SliceState& ss = rc.ss;
+    uint32_t t_start = 0;
+    if (rc.trace && threadIdx.x == 0) asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_start));
     __shared__ float4 s_kl[kStage];    // k1, k2, log2(sigma), -
     __shared__ float4 s_nw[kStage];    // -w1x, -w2x, -w1y, -w2y
     __shared__ float4 s_rg[kStage];    // red, red, green, green
@@ -83,7 +101,7 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     const SetDev st = fp->st;
     // CTAs walk the tiles column by column: the tiles in flight at once share
     // a few columns' run lists and Gaussian records in L2.
-    const int ty = (int)(blockIdx.x % cam.tiles_y), tx = (int)(blockIdx.x / cam.tiles_y);
+    const int ty = tile_index % cam.tiles_y, tx = tile_index / cam.tiles_y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 8 + 2 * (lane >> 3);
     const int x = tx * kTile + lx, ya = ty * kTile + ly, yb = ya + 1;
@@ -268,6 +286,13 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
     stopped_b = stop_b != 0;
     // Traversal (positions evaluated): up to the stop, else the whole list seen.
     const int32_t trav_a = stopped_a ? stop_a : fbase, trav_b = stopped_b ? stop_b : fbase;
+    if (rc.trace && threadIdx.x == 0) {   // tracing: this tile's CTA
+        uint32_t t_end, smid;
+        asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_end));
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        const int ntiles = cam.tiles_x * cam.tiles_y;
+        rc.trace[(ss.phase == 2 ? ntiles : 0) + tile_rm] = make_uint4(t_start, t_end, smid, (uint32_t)fbase);
+    }
     if (ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
         const bool all_done = __syncthreads_count(done_a && done_b) == kRenderThreads;
         if (threadIdx.x == 0) {
@@ -313,20 +338,14 @@ k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_g
 
 }  // namespace
 
-void launch_render(const uint2* ranges, const uint32_t* sorted_gauss, const uint2* runs,
-                   const float4* rec, int lists, const FrameParams* fp, int num_tiles, float* img,
-                   float* t_final, int32_t* load, int32_t* last, int32_t* trav, float* tfin,
-                   int32_t* lstat, const SliceState& ss, cudaStream_t stream) {
-    const int tiles = num_tiles;
+void launch_render(const RenderBatch& batch, cudaStream_t stream) {
+    if (batch.count < 1 || batch.count > kMaxBatch) return;
+    const int tiles = batch.tile_begin[batch.count];
     if (tiles <= 0) return;
-    if (lists == kListsColumns)
-        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, fp, img,
-                                                             t_final, load, last, trav, tfin, lstat,
-                                                             ss);
+    if (batch.lists == kListsColumns)
+        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(batch);
     else
-        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(ranges, sorted_gauss, runs, rec, fp,
-                                                              img, t_final, load, last, trav, tfin,
-                                                              lstat, ss);
+        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(batch);
 }
 
 }  // namespace adr

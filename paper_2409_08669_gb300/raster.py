@@ -241,5 +241,21 @@ class Rasterizer:
     def profile_read(self):
         return _lib.adr_profile_read(self.ctx)
 
+    def trace_tiles(self, enable: bool):
+        """Per-tile Render tracing on or off (adr_trace_tiles)."""
+        _lib.check(_lib.load().adr_trace_tiles(self.ctx, 1 if enable else 0), "adr_trace_tiles")
+
+    def read_tile_trace(self, stream=None):
+        """The last frame's per-tile trace: uint32 numpy [2, tiles, 4] of
+        (start ns, end ns, SM, staged positions) for slice 0 (or the whole
+        list) and slice 1."""
+        cam = self.camera
+        nt = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
+        out = torch.empty((2, nt, 4), dtype=torch.int32, device=f"cuda:{self.device}")
+        _lib.check(_lib.load().adr_read_tile_trace(self.ctx, _ptr(out), _stream(stream)),
+                   "adr_read_tile_trace")
+        torch.cuda.synchronize(self.device)
+        return out.cpu().numpy().view(np.uint32)
+
     def sync_status(self):
         return _lib.adr_sync_status(self.ctx)

@@ -11,7 +11,8 @@ from . import _lib
 from .raster import check_params, check_tensor
 
 STAT_NAMES = ("completed", "p50_ms", "p99_ms", "mean_ms", "max_inflight", "admitted_while_busy",
-              "rejected", "frames_per_s", "capacity_errors", "graph_replays")
+              "rejected", "frames_per_s", "capacity_errors", "graph_replays", "batches",
+              "largest_batch", "mean_batch")
 
 
 class Server:
@@ -19,14 +20,15 @@ class Server:
 
     def __init__(self, max_slots=4, mem_budget_bytes=8 << 30, slot_pair_capacity=1 << 27,
                  slot_max_gaussians=1 << 22, max_width=1920, max_height=1080, use_graphs=True,
-                 device=None):
+                 device=None, max_batch=1):
         self._lib = _lib.load()
         dev = torch.cuda.current_device() if device is None else int(device)
         cfg = _lib.adr_serve_config(max_slots=max_slots, mem_budget_bytes=int(mem_budget_bytes),
                                     slot_pair_capacity=int(slot_pair_capacity),
                                     slot_max_gaussians=int(slot_max_gaussians),
                                     max_width=max_width, max_height=max_height,
-                                    use_graphs=1 if use_graphs else 0, device=dev)
+                                    use_graphs=1 if use_graphs else 0, device=dev,
+                                    max_batch=int(max_batch))
         h = ctypes.c_void_p()
         _lib.check(self._lib.adr_serve_create(ctypes.byref(h), ctypes.byref(cfg)), "adr_serve_create")
         self._h = h

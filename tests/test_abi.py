@@ -58,7 +58,7 @@ def test_binding_covers_every_declared_symbol(libpath):
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.adr_camera) == (16 + 4 + 1 + 3) * 4 + 2 * 4
     assert ctypes.sizeof(_lib.adr_settings) == 4 + 4 * 4 + 3 * 4 + 4 + 4 + 4
-    assert ctypes.sizeof(_lib.adr_serve_config) == 8 + 3 * 8 + 4 * 4
+    assert ctypes.sizeof(_lib.adr_serve_config) == 8 + 3 * 8 + 5 * 4 + 4   # + tail padding
 
 
 def test_version_and_error_without_gpu(libpath):
@@ -81,7 +81,7 @@ def test_scene_size_limit_rejected_without_gpu(libpath):
         assert not out.value
     cfg = _lib.adr_serve_config(max_slots=1, mem_budget_bytes=1 << 30, slot_pair_capacity=1 << 20,
                                 slot_max_gaussians=(1 << 29) + 1, max_width=256, max_height=256,
-                                use_graphs=1, device=0)
+                                use_graphs=1, device=0, max_batch=1)
     assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
     assert not out.value
 
@@ -90,12 +90,18 @@ def test_serve_config_rejected_without_gpu(libpath):
     lib = _lib.load()
     cfg = _lib.adr_serve_config(max_slots=0, mem_budget_bytes=1 << 30, slot_pair_capacity=1 << 20,
                                 slot_max_gaussians=1 << 16, max_width=256, max_height=256,
-                                use_graphs=1, device=0)
+                                use_graphs=1, device=0, max_batch=1)
     out = ctypes.c_void_p()
     assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
     assert not out.value
     cfg.max_slots, cfg.max_width = 2, 8192
     assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
+    # batches of 1..4 requests, the slots a whole number of batch groups
+    cfg.max_width = 256
+    for slots, batch in ((4, 0), (8, 5), (6, 4), (3, 2)):
+        cfg.max_slots, cfg.max_batch = slots, batch
+        assert lib.adr_serve_create(ctypes.byref(out), ctypes.byref(cfg)) == _lib.ADR_ERR_INVALID
+        assert not out.value
     assert lib.adr_serve_poll(None, 1, 0) == _lib.ADR_ERR_INVALID
 
 

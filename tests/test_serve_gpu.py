@@ -56,10 +56,13 @@ def _register(srv, env):
     return [srv.add_scene(p, st) for p, st in zip(env["params"], env["settings"])]
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_mix_equals_alone_bit_exact(env, use_graphs):
+@pytest.mark.parametrize("use_graphs,max_batch", [(True, 1), (False, 1), (True, 4), (False, 4)])
+def test_mix_equals_alone_bit_exact(env, use_graphs, max_batch):
+    """Batched (max_batch 4: two groups of four slots, each batch one
+    Preprocess and one Render launch per depth slice over its cameras) or not,
+    every served image equals its frame rendered alone."""
     from paper_2409_08669_gb300 import _lib
-    srv = _server(use_graphs=use_graphs)
+    srv = _server(use_graphs=use_graphs, max_batch=max_batch, max_slots=8 if max_batch > 1 else 4)
     ids = _register(srv, env)
     torch.cuda.synchronize()
     outs, tickets = [], []
@@ -77,7 +80,12 @@ def test_mix_equals_alone_bit_exact(env, use_graphs):
     assert st["completed"] == len(tickets)
     assert st["max_inflight"] > 1 and st["admitted_while_busy"] > 0, st
     if use_graphs:
-        assert st["graph_replays"] == len(tickets)
+        assert st["graph_replays"] == st["batches"]
+    if max_batch > 1:
+        assert st["largest_batch"] > 1 and st["mean_batch"] > 1.0, st
+        assert st["batches"] < len(tickets)
+    else:
+        assert st["largest_batch"] == 1 and st["batches"] == len(tickets)
     # second pass: graphs replayed from the cache for other cameras give the same images
     outs2 = [torch.empty_like(o) for o in outs]
     torch.cuda.synchronize()
@@ -185,13 +193,14 @@ def _near_tiles_mask(pre, width, height, pad=1):
     return m
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_served_images_match_the_oracle(env, use_graphs):
+@pytest.mark.parametrize("use_graphs,max_batch", [(True, 1), (False, 1), (True, 4)])
+def test_served_images_match_the_oracle(env, use_graphs, max_batch):
     """One request of each resident scene (AABB, PLAIN with a background,
-    CIRCLE), served while the other requests overlap with it, against the FP64
-    oracle on the same scene, camera and settings."""
+    CIRCLE), served while the other requests overlap with it (batched with
+    them when max_batch > 1), against the FP64 oracle on the same scene,
+    camera and settings."""
     from paper_2409_08669_gb300 import _lib
-    srv = _server(use_graphs=use_graphs)
+    srv = _server(use_graphs=use_graphs, max_batch=max_batch, max_slots=8 if max_batch > 1 else 4)
     ids = _register(srv, env)
     pick = {}
     for k, (sid, _) in enumerate(env["reqs"]):
