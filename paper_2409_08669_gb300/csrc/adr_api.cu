@@ -179,7 +179,7 @@ void free_workspace(Workspace& w) {
         w.prof = nullptr;
     }
     void* ptrs[] = {w.rec, w.aux, w.depth_key, w.offsets, w.gbox, w.sorted_box, w.gkeys[0],
-                    w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
+                    w.gkeys[1], w.gvals[0], w.gvals[1], w.pruns, w.prows, w.pgauss, w.tcounts, w.ttotals, w.tile_counts,
                     w.chunk_first, w.ranges, w.last, w.trav, w.tfin, w.lstat, w.g2d, w.load_sums,
                     w.hist, w.counters, w.status, w.lookback, w.d_fp, w.d_stage,
                     w.slice_counters, w.s_order, w.s_box, w.s_offsets, w.s_chunk_first,
@@ -195,7 +195,7 @@ size_t workspace_bytes(int64_t max_gaussians, int64_t pair_capacity, int32_t max
     const size_t pixels = (size_t)max_width * max_height;
     const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
     const size_t lb = ((N + kSortChunk - 1) / kSortChunk + 2) * kRadix * 8;
-    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36 + 12) + P * 12 +
+    return N * (kRecFloat4 * 16 + kAuxFloat4 * 16 + 4 * 4 + 8 + 16 + 36 + 12) + P * 14 +
            2 * (P / kSortChunk + 2) * 4 + tiles * 20 + pixels * 48 + lb +
            (size_t)kRadix * (kMaxTileGrid + 2) * 4 + 4096;
 }
@@ -239,6 +239,7 @@ adr_status alloc_workspace(Workspace& w, int64_t max_gaussians, int64_t pair_cap
         ALLOC(w.gvals[b], N * sizeof(uint32_t));
     }
     ALLOC(w.pruns, P * sizeof(uint2));
+    ALLOC(w.prows, (P + 8) * sizeof(uint16_t));   // + 16 bytes: Render reads whole 16-byte groups
     ALLOC(w.pgauss, P * sizeof(uint32_t));
     ALLOC(w.tile_counts, (size_t)w.max_tiles * sizeof(uint32_t));
     ALLOC(w.tcounts, (size_t)kRadix * kMaxTileGrid * sizeof(uint32_t));

@@ -139,6 +139,7 @@ struct Workspace {
     uint32_t* gkeys[2] = {nullptr, nullptr};   // [max_n] each
     uint32_t* gvals[2] = {nullptr, nullptr};   // [max_n] each
     uint2* pruns = nullptr;                // [capacity] column runs grouped by tile column
+    uint16_t* prows = nullptr;             // [capacity] their row intervals y0 | (h - 1) << 8
     uint32_t* pgauss = nullptr;            // [capacity] Gaussian ids of the pairs by (tile, depth)
     uint32_t* tcounts = nullptr;           // [kRadix * kMaxTileGrid] per-(digit, CTA) counts / starts
     uint32_t* ttotals = nullptr;           // [2 * kRadix] per-digit totals of the two tile passes
@@ -190,6 +191,7 @@ struct FrameState {
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
     const uint32_t* sorted_gauss = nullptr;  // list entries' Gaussians by (cell, depth)
     const uint2* runs = nullptr;             // column runs by (column, depth)
+    const uint16_t* rows = nullptr;          // their row intervals
     bool allow_slices = true;                // the caller's choice for the next sort
     bool sliced = false;                     // the frame renders in two depth slices
     int runs_held = 0;                       // which Gaussians' column runs ws.pruns holds
@@ -268,13 +270,11 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
                        const float* opac, const float* sh, const PreprocessBatch& batch,
                        cudaStream_t stream);
 
-// One stable 8-bit pass of the depth sort (sort.cu): keys (>> shift) & 255;
-// vals_in == nullptr means the values are 0..n-1.  counts: kRadix x grid
-// words; totals: kRadix words, zeroed before.  With pay_out, also writes
-// pay_out[i] = pay_in[vals_out[i]].
-// One stable 8-bit pass of the depth sort.  first: all n keys in, keys
-// 0xFFFFFFFF (no tiles) dropped and the kept ones counted into *kept; later
-// passes sort the *kept keys.
+// One stable 8-bit pass of the depth sort (sort.cu): keys (>> shift) & 255.
+// first: all n keys in, keys 0xFFFFFFFF (no tiles) dropped and the kept ones
+// counted into *kept; later passes sort the *kept keys; vals_in == nullptr
+// means the values are 0..n-1.  counts: kRadix x grid words; totals: kRadix
+// words, zeroed before.  With pay_out, also writes pay_out[i] = pay_in[vals_out[i]].
 void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                        uint32_t* vals_out, int64_t n, uint32_t* kept, bool first, int shift,
                        uint32_t* counts, uint32_t* totals, const uint32_t* pay_in,
@@ -307,7 +307,7 @@ int tile_scatter_blocks_per_sm();
 void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* totals,
                                uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
-                                 uint32_t* status, int grid, cudaStream_t stream);
+                                 uint16_t* rows_out, uint32_t* status, int grid, cudaStream_t stream);
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                             int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
                             uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream);
@@ -361,6 +361,7 @@ struct RenderCam {
     const uint2* ranges = nullptr;        // per-tile lists (lists == kListsTiles)
     const uint32_t* sorted_gauss = nullptr;
     const uint2* runs = nullptr;          // column runs (lists == kListsColumns)
+    const uint16_t* rows = nullptr;       // their row intervals, 16-byte aligned
     const float4* rec = nullptr;
     const FrameParams* fp = nullptr;
     float* img = nullptr;

@@ -48,7 +48,8 @@ constexpr size_t kOffSortedBox = align256(kOffGBox + kNaMaxGaussians * 4);
 constexpr size_t kOffGKeys = align256(kOffSortedBox + kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffGVals = align256(kOffGKeys + 2 * kNaMaxGaussians * 4);   // 2 buffers
 constexpr size_t kOffPRuns = align256(kOffGVals + 2 * kNaMaxGaussians * 4);
-constexpr size_t kOffPGauss = align256(kOffPRuns + kNaMaxPairs * 8);
+constexpr size_t kOffPRows = align256(kOffPRuns + kNaMaxPairs * 8);
+constexpr size_t kOffPGauss = align256(kOffPRows + (kNaMaxPairs + 8) * 2);
 constexpr size_t kOffChunkFirst = align256(kOffPGauss + kNaMaxPairs * 4);
 constexpr size_t kOffRanges = align256(kOffChunkFirst + (kNaMaxPairs / kSortChunk + 2) * 4);
 constexpr size_t kOffLast = align256(kOffRanges + kNaMaxTiles * 8);
@@ -114,6 +115,7 @@ adr_status setup(int dev, DeviceState*& out) {
             w.gvals[k] = reinterpret_cast<uint32_t*>(b + kOffGVals) + k * kNaMaxGaussians;
         }
         w.pruns = reinterpret_cast<uint2*>(b + kOffPRuns);
+        w.prows = reinterpret_cast<uint16_t*>(b + kOffPRows);
         w.pgauss = reinterpret_cast<uint32_t*>(b + kOffPGauss);
         w.tile_counts = reinterpret_cast<uint32_t*>(b + kOffTileCounts);
         w.tcounts = reinterpret_cast<uint32_t*>(b + kOffTCounts);

@@ -156,7 +156,7 @@ static void enqueue_pass1(const Workspace& ws, const FrameState& fs, const PairS
               launch_tile_count_columns(src, ws.tcounts, ws.ttotals, ws.status, G, stream));
         TIMED(ws, kKTileCountScan, stream, launch_tile_count_scan(ws.tcounts, ws.ttotals, G, stream));
         TIMED(ws, kKTileScatterColumns, stream,
-              launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.status, G, stream));
+              launch_tile_scatter_columns(src, ws.tcounts, ws.pruns, ws.prows, ws.status, G, stream));
     }
 }
 
@@ -185,6 +185,7 @@ void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& ep
                   cudaStream_t stream) {
     (void)epoch;   // the tile sort has no lookback words
     fs.runs = ws.pruns;
+    fs.rows = ws.prows;
     fs.sorted_gauss = nullptr;
     fs.lists = kListsColumns;
     fs.sliced = fs.allow_slices && ws.pst != nullptr && kSliceDiv > 0;
@@ -218,6 +219,7 @@ static RenderCam render_cam(const Workspace& ws, const FrameState& fs, float* im
     rc.ranges = ws.ranges;
     rc.sorted_gauss = fs.sorted_gauss;
     rc.runs = fs.runs;
+    rc.rows = fs.rows;
     rc.rec = ws.rec;
     rc.fp = ws.d_fp;
     rc.img = img;

@@ -158,7 +158,7 @@ constexpr float kHalfLog2e = 0.84932180028801907f;
 // Gaussians of chunk k / count for camera k % count, so the blocks of one
 // chunk run side by side and every camera after the first reads the chunk's
 // parameters from L2 rather than DRAM.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)   // 3 CTAs per SM: <= 80 registers
 k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ scales,
              const float* __restrict__ rots, const float* __restrict__ opac,
              const float* __restrict__ sh, PreprocessBatch batch) {

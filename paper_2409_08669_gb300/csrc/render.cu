@@ -35,7 +35,6 @@ constexpr int kRenderThreads = kTilePixels / 2;
 constexpr int kStage = kTilePixels;          // Gaussians staged per batch
 constexpr int kRenderWarps = kRenderThreads / 32;
 
-constexpr int kRunFill = 16;   // list entries each thread reads per batch (column runs)
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     float2 d;
@@ -63,7 +62,6 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
 template <bool kRuns>
 __global__ void __launch_bounds__(kRenderThreads, 8)   // 8 CTAs per SM: <= 64 registers
 k_render(const RenderBatch batch) {
-    constexpr int kFill = kRuns ? kRunFill : kStage / kRenderThreads;
     int cb = 0;
 #pragma unroll
     for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && (int)blockIdx.x >= batch.tile_begin[q]) ? 1 : 0;
@@ -72,6 +70,7 @@ k_render(const RenderBatch batch) {
     const uint2* __restrict__ ranges = rc.ranges;
     const uint32_t* __restrict__ sorted_gauss = rc.sorted_gauss;
     const uint2* __restrict__ runs = rc.runs;
+    const uint16_t* __restrict__ rows = rc.rows;
     const float4* __restrict__ rec = rc.rec;
     const FrameParams* __restrict__ fp = rc.fp;
     float* __restrict__ img = rc.img;
@@ -82,18 +81,18 @@ k_render(const RenderBatch batch) {
     float* __restrict__ tfin = rc.tfin;
     int32_t* __restrict__ lstat = rc.lstat;
     const SliceState& ss = rc.ss;
-    uint32_t t_start = 0;
-    if (rc.trace && threadIdx.x == 0) asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_start));
+    __shared__ uint32_t s_tstart;
+    if (rc.trace && threadIdx.x == 0) {
+        uint32_t t;
+        asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+        s_tstart = t;
+    }
     __shared__ float4 s_kl[kStage];    // k1, k2, log2(sigma), -
     __shared__ float4 s_nw[kStage];    // -w1x, -w2x, -w1y, -w2y
     __shared__ float4 s_rg[kStage];    // red, red, green, green
     __shared__ float2 s_bb[kStage];    // blue, blue
     __shared__ uint32_t s_gid[kStage];
-    __shared__ uint32_t s_cand[kFill][kRenderThreads];  // this batch's list entries' Gaussians
-    __shared__ uint32_t s_mask[kFill][kRenderWarps];    // kept entries per (k, warp), by lane
-    __shared__ uint32_t s_wcnt[kFill][kRenderWarps];    // their number
-    __shared__ uint32_t s_off[kFill * kRenderWarps];    // their exclusive prefix
-    __shared__ uint32_t s_total;
+    __shared__ uint32_t s_wsum[kRenderWarps];           // kept runs per warp
     __shared__ uint32_t s_next;
     __shared__ uint2 s_range;
 
@@ -152,79 +151,73 @@ k_render(const RenderBatch batch) {
         range = s_range;
     }
 
-    // Each batch reads kFill list entries per thread (list order: entry
-    // base + k * 128 + thread) and stages the first 256 kept ones; the list
-    // resumes at the first kept entry not staged.
+    // Each batch stages the first 256 kept entries of the next stretch of the
+    // list.  Column runs: thread t reads the packed row intervals of the 16
+    // consecutive runs from a0 + 16 t (a0 = the batch start rounded down to a
+    // 16-byte boundary: two 16-byte loads), keeps those covering the tile's
+    // row, and a block scan of the per-thread counts places them stably;
+    // only kept runs' Gaussian ids are fetched.  The list resumes at the
+    // first kept entry not staged.  Per-tile lists: every entry is kept.
     uint32_t base = range.x;
     while (base < range.y) {
         if (__syncthreads_count(done_a && done_b) == kRenderThreads) break;
-#pragma unroll 4
-        for (int k = 0; k < kFill; ++k) {
-            const uint32_t idx = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
-            bool keep = idx < range.y;
-            uint32_t g = 0;
-            if (keep) {
-                if (kRuns) {   // run record: Gaussian, y0 | (h - 1) << 8 | tx << 16
-                    const uint2 r = runs[idx];
-                    g = r.x;
-                    keep = (uint32_t)ty - (r.y & 0xFFu) <= ((r.y >> 8) & 0xFFu);
-                } else {
-                    g = sorted_gauss[idx];
+        uint32_t total, next;
+        if (kRuns) {
+            const uint32_t a0 = base & ~7u;
+            const uint32_t first = a0 + 16u * threadIdx.x;
+            uint32_t mask = 0;
+            const uint4* r4 = reinterpret_cast<const uint4*>(rows + first);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t g0 = first + 8u * (uint32_t)h;
+                if (g0 < range.y) {
+                    const uint4 q = r4[h];
+                    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t r = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;   // y0 | (h - 1) << 8
+                        const uint32_t idx = g0 + (uint32_t)e;
+                        const bool keep = idx >= base && idx < range.y &&
+                                          (uint32_t)ty - (r & 0xFFu) <= (r >> 8);
+                        mask |= keep ? (1u << (8 * h + e)) : 0u;
+                    }
                 }
             }
-            s_cand[k][threadIdx.x] = g;
-            // Stable compaction: one ballot per (k, warp), kept in shared
-            // memory; warp 0 scans their counts in list order (k-major).
-            const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) {
-                s_mask[k][warp] = mask;
-                s_wcnt[k][warp] = __popc(mask);
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {
-            constexpr int kN = kFill * kRenderWarps;
-            constexpr int kPer = (kN + 31) / 32;                 // counts per lane
-            uint32_t v[kPer], t = 0;
-#pragma unroll
-            for (int e = 0; e < kPer; ++e) {
-                const int i = lane * kPer + e;
-                v[e] = i < kN ? (&s_wcnt[0][0])[i] : 0u;
-                t += v[e];
-            }
-            uint32_t xs = t;
+            // block exclusive scan of the kept counts, in thread (= list) order
+            const uint32_t cnt = __popc(mask);
+            uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t yv = __shfl_up_sync(0xffffffffu, xs, o);
-                if (lane >= o) xs += yv;
+                const uint32_t yv = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += yv;
             }
-            uint32_t run = xs - t;
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            uint32_t before = incl - cnt;
+            total = 0;
 #pragma unroll
-            for (int e = 0; e < kPer; ++e) {
-                const int i = lane * kPer + e;
-                if (i < kN) s_off[i] = run;
-                run += v[e];
+            for (int q = 0; q < kRenderWarps; ++q) {
+                const uint32_t v = s_wsum[q];
+                before += q < warp ? v : 0u;
+                total += v;
             }
-            if (lane == 31) s_total = xs;
-        }
-        __syncthreads();
-        const uint32_t total = s_total;
-        const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-        for (int k = 0; k < kFill; ++k) {
-            const uint32_t mask = s_mask[k][warp];
-            if ((mask >> lane) & 1u) {
-                const uint32_t slot = s_off[k * kRenderWarps + warp] + __popc(mask & lt);
-                if (slot < (uint32_t)kStage) s_gid[slot] = s_cand[k][threadIdx.x];
-                else if (slot == (uint32_t)kStage)
-                    s_next = base + (uint32_t)(k * kRenderThreads) + threadIdx.x;
+            uint32_t slot = before;
+            while (mask) {
+                const int e = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                if (slot < (uint32_t)kStage) s_gid[slot] = runs[first + (uint32_t)e].x;
+                else if (slot == (uint32_t)kStage) s_next = first + (uint32_t)e;
+                ++slot;
             }
+            __syncthreads();
+            next = total > (uint32_t)kStage ? s_next : min(range.y, a0 + 16u * kRenderThreads);
+        } else {
+            total = min(range.y - base, (uint32_t)kStage);
+            for (uint32_t e = threadIdx.x; e < total; e += kRenderThreads) s_gid[e] = sorted_gauss[base + e];
+            __syncthreads();
+            next = base + total;
         }
         const int m = (int)min(total, (uint32_t)kStage);
-        __syncthreads();
-        const uint32_t next = total > (uint32_t)kStage
-                                  ? s_next
-                                  : min(range.y, base + (uint32_t)(kFill * kRenderThreads));
         for (int sl = threadIdx.x; sl < m; sl += kRenderThreads) {
             const uint32_t gi = s_gid[sl];
             const float4 r0 = rec[3 * (size_t)gi + 0];
@@ -291,7 +284,7 @@ k_render(const RenderBatch batch) {
         asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_end));
         asm("mov.u32 %0, %%smid;" : "=r"(smid));
         const int ntiles = cam.tiles_x * cam.tiles_y;
-        rc.trace[(ss.phase == 2 ? ntiles : 0) + tile_rm] = make_uint4(t_start, t_end, smid, (uint32_t)fbase);
+        rc.trace[(ss.phase == 2 ? ntiles : 0) + tile_rm] = make_uint4(s_tstart, t_end, smid, (uint32_t)fbase);
     }
     if (ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
         const bool all_done = __syncthreads_count(done_a && done_b) == kRenderThreads;

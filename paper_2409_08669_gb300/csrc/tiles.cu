@@ -320,6 +320,7 @@ __device__ __forceinline__ void generate_runs(const PairSource& src, const Span&
 
 __global__ void __launch_bounds__(kSortThreads, 3)
 k_scatter_columns(PairSource src, const uint32_t* __restrict__ starts, uint2* __restrict__ runs_out,
+                  uint16_t* __restrict__ rows_out,
                   int grid, uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColumnShared& sm = *reinterpret_cast<ColumnShared*>(smem_raw);
@@ -355,7 +356,10 @@ k_scatter_columns(PairSource src, const uint32_t* __restrict__ starts, uint2* __
         for (int s = tid; s < count; s += kSortThreads) {
             const uint32_t k = sm.u.kv.keys[s];
             const uint32_t g = sm.dst[min(run_tx(k), (uint32_t)kRadix - 1u)] + (uint32_t)s;
-            if ((int64_t)g < n) runs_out[g] = make_uint2(sm.u.kv.vals[s], k);
+            if ((int64_t)g < n) {
+                runs_out[g] = make_uint2(sm.u.kv.vals[s], k);
+                rows_out[g] = (uint16_t)(k & 0xFFFFu);   // y0 | (h - 1) << 8, what Render filters on
+            }
             else atomicOr(status, kErrRange);
         }
         __syncthreads();
@@ -625,8 +629,9 @@ void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t
 }
 
 void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
-                                 uint32_t* status, int grid, cudaStream_t stream) {
-    k_scatter_columns<<<grid, kSortThreads, kColumnSmem, stream>>>(src, starts, runs_out, grid, status);
+                                 uint16_t* rows_out, uint32_t* status, int grid, cudaStream_t stream) {
+    k_scatter_columns<<<grid, kSortThreads, kColumnSmem, stream>>>(src, starts, runs_out, rows_out, grid,
+                                                                  status);
 }
 
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
