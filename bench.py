@@ -931,6 +931,57 @@ def run_reference(args):
     }))
 
 
+def tile_trace_summary(cameras=(0, 12, 25)):
+    """Per-tile Render trace (adr_trace_tiles) of single frames of the selected
+    workload: for each depth slice, the span from the first tile's start to
+    the last tile's end, the mean and peak number of tiles in flight, how long
+    fewer than half of the peak were in flight at the end, per-tile duration
+    quantiles and the longest tiles (tx, ty, us, start us, positions staged)."""
+    import torch
+    from paper_2409_08669_gb300.raster import Rasterizer, upload
+    scene, cams = build_workload(0)
+    params = upload(scene)
+    rast = Rasterizer(max_gaussians=N_GAUSS, pair_capacity=PAIR_CAPACITY, max_width=WIDTH,
+                      max_height=HEIGHT)
+    rast.trace_tiles(True)
+    st = S.Settings(mode=S.MODE_AABB)
+    for k in range(6):
+        rast.forward(params, cams[k], st, want_aux=False)
+    tx = (WIDTH + 15) // 16
+    out = {"workload": WORKLOAD}
+    for k in cameras:
+        rast.forward(params, cams[k], st, want_aux=False)
+        torch.cuda.synchronize()
+        tr = rast.read_tile_trace().astype(np.int64)
+        rec = {}
+        for ph in (0, 1):
+            t = tr[ph]
+            used = (t[:, 0] != 0) | (t[:, 1] != 0)
+            if not used.any():
+                continue
+            s0 = t[used, 0]
+            base = s0.min()
+            s = (s0 - base) % (1 << 32)
+            e = (t[used, 1] - base) % (1 << 32)
+            d = e - s
+            bins = np.zeros(int(e.max()) // 1000 + 2)
+            for a, b in zip(s // 1000, e // 1000):
+                bins[a:b + 1] += 1
+            half = np.nonzero(bins >= 0.5 * bins.max())[0]
+            idx = np.nonzero(used)[0]
+            top = np.argsort(-d)[:5]
+            rec["slice0" if ph == 0 else "slice1"] = {
+                "tiles": int(used.sum()), "span_us": float(e.max()) / 1e3,
+                "mean_in_flight": float(bins.mean()), "peak_in_flight": int(bins.max()),
+                "tail_below_half_us": int(len(bins) - 1 - half[-1]) if half.size else 0,
+                "tile_us_p50": float(np.median(d)) / 1e3, "tile_us_p99": float(np.percentile(d, 99)) / 1e3,
+                "longest": [[int(idx[i] % tx), int(idx[i] // tx), round(float(d[i]) / 1e3, 1),
+                             round(float(s[i]) / 1e3, 1), int(t[idx[i], 3])] for i in top]}
+        out[f"camera{k}"] = rec
+    rast.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -946,11 +997,17 @@ def main():
                     help="time the AdR mode only (no plain/circle arms, e2e or baselines)")
     ap.add_argument("--serve-only", action="store_true",
                     help="only the serving measurement (unbatched and batched), one JSON line")
+    ap.add_argument("--tile-trace", action="store_true",
+                    help="only the per-tile Render trace of three frames of the workload, one JSON line")
     args = ap.parse_args()
     select_workload(args.workload)
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.tile_trace:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(tile_trace_summary()))
     elif args.serve_only:
         import torch
         torch.cuda.set_device(0)
