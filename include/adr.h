@@ -191,7 +191,7 @@ adr_status adr_render(adr_ctx *ctx, float *img, float *t_final, int32_t *load, v
  * dL/dload [H,W] (may be NULL; it reaches the opacities through the reading
  * of d l_i / d alpha_ik that the frame's settings->load_grad selects, see
  * adr_load_grad), writes dL/d means [n,3], scales [n,3],
- * rots [n,4] (w,x,y,z; 16-byte aligned), opac [n] and sh [n,16,3] (coefficients
+ * rots [n,4] (w,x,y,z; 16-byte aligned), opac [n] and sh [n,16,3] (16-byte aligned; coefficients
  * above sh_degree get 0).  The parameter arrays must be the ones passed to
  * adr_preprocess for this frame, unchanged.  Gradient buffers are overwritten.
  * Per tile, each pixel walks its blended Gaussians back to front recovering

@@ -540,8 +540,8 @@ adr_status adr_render_backward(adr_ctx* c, const float* means, const float* scal
     if (!dl_dimg) return fail(ADR_ERR_INVALID, "dl_dimg is NULL");
     if (c->fs.n > 0 && (!g_means || !g_scales || !g_rots || !g_opac || !g_sh))
         return fail(ADR_ERR_INVALID, "a gradient output pointer is NULL");
-    if (c->fs.n > 0 && !aligned(g_rots, 16))
-        return fail(ADR_ERR_INVALID, "g_rots must be 16-byte aligned");
+    if (c->fs.n > 0 && (!aligned(g_rots, 16) || !aligned(g_sh, 16)))
+        return fail(ADR_ERR_INVALID, "g_rots and g_sh must be 16-byte aligned");
     DeviceGuard guard(c->device);
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;

@@ -19,13 +19,29 @@ namespace {
 
 constexpr int kBwdThreads = kTilePixels;
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum over the warp of nine per-lane values, as a reduce-scatter over 16
+// slots (slots 9-15 zero) by recursive halving: at distance 16, 8, 4, 2 each
+// lane keeps half of its slots (the half bit 4, 3, 2, 1 of its lane selects)
+// and adds its partner's copy of them, then pairs (lane, lane ^ 1) add; 16
+// shuffles instead of 45.  Lanes 2s and 2s + 1 end with the total of slot s.
+__device__ __forceinline__ float reduce_scatter9(const float (&v)[9], int lane) {
+    float a[16];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 16; ++i) a[i] = i < 9 ? v[i] : 0.f;
+#pragma unroll
+    for (int half = 8, dist = 16; half >= 1; half >>= 1, dist >>= 1) {
+        const bool up = (lane & dist) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = up ? a[i] : a[i + half];
+            const float keep = up ? a[i + half] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, dist);
+        }
+    }
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 5)   // 5 CTAs per SM: <= 48 registers
 k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__ sorted_gauss,
                   const float4* __restrict__ rec, const float4* __restrict__ aux,
                   const FrameParams* __restrict__ fp, const int32_t* __restrict__ last_pos,
@@ -33,6 +49,7 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                   const float* __restrict__ dl_dimg, const float* __restrict__ dl_dload,
                   float* __restrict__ g2d) {
     __shared__ float2 s_xy[kBwdThreads];
+    __shared__ float2 s_k[kBwdThreads];       // quad_k of the Gaussian at this tile
     __shared__ float4 s_w[kBwdThreads];
     __shared__ float4 s_c[kBwdThreads];
     __shared__ float4 s_conic[kBwdThreads];   // conic a, b, c, sigma
@@ -75,9 +92,9 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
     const float e_low = st.e_low;   // alpha >= alpha_low as 2^e >= alpha_low, decided on e
 
     if (range.x < range.y) {
-        // The longest prefix any pixel of the tile needs.
-        int max_last = last;
-        max_last = __reduce_max_sync(0xffffffffu, max_last);
+        // The longest prefix any pixel of the warp, and of the tile, needs.
+        const int warp_last = __reduce_max_sync(0xffffffffu, last);
+        const int max_last = warp_last;
         __shared__ int s_max[kBwdThreads / 32];
         if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = max_last;
         __syncthreads();
@@ -91,15 +108,19 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
             if (pos < bend) {
                 const uint32_t g = sorted_gauss[range.x + pos];
                 const float4 r0 = rec[3 * (size_t)g + 0];
-                s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
-                                                __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
-                s_w[threadIdx.x] = rec[3 * (size_t)g + 1];
+                const float2 c = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
+                                             __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
+                const float4 w = rec[3 * (size_t)g + 1];
+                s_xy[threadIdx.x] = c;
+                s_k[threadIdx.x] = quad_k(c, w);
+                s_w[threadIdx.x] = w;
                 s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
                 s_conic[threadIdx.x] = aux[2 * (size_t)g + 0];
                 s_g[threadIdx.x] = g;
             }
             __syncthreads();
-            for (int p = bend - 1; p >= bstart; --p) {
+            // this warp's positions: none of its pixels blended one past warp_last
+            for (int p = min(bend, warp_last) - 1; p >= bstart; --p) {
                 const int j = p - bstart;
                 bool contrib = false;
                 float d_px = 0.f, d_py = 0.f, d_ca = 0.f, d_cb = 0.f, d_cc = 0.f, d_sig = 0.f;
@@ -110,7 +131,7 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                     const float4 w = s_w[j];
                     const float4 col = s_c[j];
                     const float dx = c.x - fx, dy = c.y - fy;
-                    const float e = quad_exponent(quad_k(c, w), w, col.w, fx, fy);
+                    const float e = quad_exponent(s_k[j], w, col.w, fx, fy);
                     if (e >= e_low) {
                         const float raw = ex2_approx(e);
                         const float alpha = fminf(0.99f, raw);
@@ -139,17 +160,11 @@ k_render_backward(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-                    d_px = warp_sum(d_px); d_py = warp_sum(d_py);
-                    d_ca = warp_sum(d_ca); d_cb = warp_sum(d_cb); d_cc = warp_sum(d_cc);
-                    d_sig = warp_sum(d_sig);
-                    d_r = warp_sum(d_r); d_g = warp_sum(d_g); d_b = warp_sum(d_b);
-                    if ((threadIdx.x & 31) == 0) {
-                        float* o = g2d + (size_t)s_g[j] * 9;
-                        atomicAdd(o + 0, d_px); atomicAdd(o + 1, d_py);
-                        atomicAdd(o + 2, d_ca); atomicAdd(o + 3, d_cb); atomicAdd(o + 4, d_cc);
-                        atomicAdd(o + 5, d_sig);
-                        atomicAdd(o + 6, d_r); atomicAdd(o + 7, d_g); atomicAdd(o + 8, d_b);
-                    }
+                    const int lane = threadIdx.x & 31;
+                    const float v[9] = {d_px, d_py, d_ca, d_cb, d_cc, d_sig, d_r, d_g, d_b};
+                    const float tot = reduce_scatter9(v, lane);
+                    const int slot = (lane >> 1) & 15;   // the slot lane's total belongs to
+                    if (!(lane & 1) && slot < 9) atomicAdd(g2d + (size_t)s_g[j] * 9 + slot, tot);
                 }
             }
         }
@@ -195,7 +210,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16],
     dY[15][0] = -kY3a * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * kY3a * x * y; dY[15][2] = 0.f;
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 5)   // 5 CTAs per SM: <= 96 registers, no local memory
 k_preprocess_backward(int n, const float* __restrict__ means, const float* __restrict__ scales,
                       const float* __restrict__ rots, const float* __restrict__ opac,
                       const float* __restrict__ sh, const FrameParams* __restrict__ fp,
@@ -209,9 +224,12 @@ k_preprocess_backward(int n, const float* __restrict__ means, const float* __res
     const SetDev st = fp->st;
     float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float go = 0.f;
-    float* gsh = g_sh + (size_t)i * 48;
+    // SH coefficients and their gradient move as 12 float4 per Gaussian (both
+    // arrays 16-byte aligned, 192 B per Gaussian).
+    float4* gsh4 = reinterpret_cast<float4*>(g_sh) + (size_t)i * 12;
     if (gbox[i] == 0xFFFFFFFFu) {   // no tiles
-        for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) gsh4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
         const float* G = g2d + (size_t)i * 9;
         const float gpx = G[0], gpy = G[1], gca = G[2], gcb = G[3], gcc = G[4];
@@ -224,24 +242,46 @@ k_preprocess_backward(int n, const float* __restrict__ means, const float* __res
         float Y[16], dY[16][3];
         sh_basis(dx, dy, dz, Y, dY);
         const int nb = (st.sh_degree + 1) * (st.sh_degree + 1);
-        const float* s = sh + (size_t)i * 48;
+        const float4* s4 = reinterpret_cast<const float4*>(sh) + (size_t)i * 12;
+        // Every loop is unrolled over the 48 coefficient slots (slot e holds
+        // coefficient e / 3 of channel e % 3), so all indices are static.
         float raw[3] = {0.5f, 0.5f, 0.5f};
-        for (int k = 0; k < nb; ++k)
-            for (int c = 0; c < 3; ++c) raw[c] = fmaf(s[3 * k + c], Y[k], raw[c]);
-        float grgb[3];
-        for (int c = 0; c < 3; ++c) grgb[c] = raw[c] > 0.f ? G[6 + c] : 0.f;
-        float gdir[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < 16; ++k) {
-            float sk = 0.f;
-            for (int c = 0; c < 3; ++c) {
-                const float v = k < nb ? Y[k] * grgb[c] : 0.f;
-                gsh[3 * k + c] = v;
-                if (k < nb) sk = fmaf(s[3 * k + c], grgb[c], sk);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            const float4 q = s4[j];
+            const float v[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * j + u, k = e / 3, c = e % 3;
+                if (k < nb) raw[c] = fmaf(v[u], Y[k], raw[c]);
             }
+        }
+        float grgb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) grgb[c] = raw[c] > 0.f ? G[6 + c] : 0.f;
+        float sk[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sk[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            const float4 q = s4[j];   // L1-resident since the loop above
+            const float v[4] = {q.x, q.y, q.z, q.w};
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * j + u, k = e / 3, c = e % 3;
+                o[u] = k < nb ? Y[k] * grgb[c] : 0.f;
+                if (k < nb) sk[k] = fmaf(v[u], grgb[c], sk[k]);
+            }
+            gsh4[j] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        float gdir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
             if (k < nb) {
-                gdir[0] = fmaf(sk, dY[k][0], gdir[0]);
-                gdir[1] = fmaf(sk, dY[k][1], gdir[1]);
-                gdir[2] = fmaf(sk, dY[k][2], gdir[2]);
+                gdir[0] = fmaf(sk[k], dY[k][0], gdir[0]);
+                gdir[1] = fmaf(sk[k], dY[k][1], gdir[1]);
+                gdir[2] = fmaf(sk[k], dY[k][2], gdir[2]);
             }
         }
         // through the normalisation: d(d)/dv = (I - d d^T) / |v|
