@@ -29,8 +29,10 @@ namespace {
 // w_iy fy advance together in one paired FP32 FMA (fma.rn.f32x2, each lane
 // rounding as the scalar fmaf does), the fx-term is formed once for both
 // pixels, and the blend of the two pixels is one paired sequence without
-// branches: every pixel takes exactly the decisions of quad_exponent's scalar
-// evaluation, which the backward uses too.
+// branches (weight alpha T, then T - alpha T, which is T (1 - alpha) of Eq. 3
+// with one rounding fewer): every pixel takes exactly the decisions of
+// quad_exponent's scalar evaluation, which the backward uses too.  The loop
+// is not unrolled (unrolling by two measured slower).
 constexpr int kRenderThreads = kTilePixels / 2;
 constexpr int kStage = kTilePixels;          // Gaussians staged per batch
 constexpr int kRenderWarps = kRenderThreads / 32;
@@ -51,6 +53,16 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
     asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
         "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
         "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
         : "=f"(d.x), "=f"(d.y)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return d;
@@ -234,6 +246,9 @@ k_render(const RenderBatch batch) {
         }
         __syncthreads();
         if (!__all_sync(0xffffffffu, done_a && done_b)) {   // warp-uniform: the loop votes
+            // A pixel becomes done only where it stops, so the loop leaves
+            // there once every pixel of the warp is done.
+#pragma unroll 1
             for (int j = 0; j < m; ++j) {
                 const float4 kl = s_kl[j];
                 const float4 nw = s_nw[j];
@@ -246,28 +261,28 @@ k_render(const RenderBatch batch) {
                 const float ea = fmaf(-ua.x, ua.x, fmaf(-ua.y, ua.y, kl.z));
                 const float eb = fmaf(-ub.x, ub.x, fmaf(-ub.y, ub.y, kl.z));
                 bool la = !done_a && ea >= e_low, lb = !done_b && eb >= e_low;
-                if (!__any_sync(0xffffffffu, la || lb)) {   // no pixel of the warp reaches alpha_low
-                    if (__all_sync(0xffffffffu, done_a && done_b)) break;
-                    continue;
-                }
+                if (!__any_sync(0xffffffffu, la || lb)) continue;   // no pixel of the warp reaches alpha_low
                 // Front-to-back step (Eq. 3), both pixels at once: a pixel that
                 // skips has alpha 0 here, so T and C stay as they are.
-                float2 alpha = make_float2(la ? fminf(0.99f, ex2_approx(ea)) : 0.f,
+                const float2 alpha = make_float2(la ? fminf(0.99f, ex2_approx(ea)) : 0.f,
                                            lb ? fminf(0.99f, ex2_approx(eb)) : 0.f);
-                float2 test_T = fmul2(T, ffma2(alpha, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
-                const int32_t pos = fbase + j + 1;
-                const bool sa = test_T.x < t_min, sb = test_T.y < t_min;
-                if (__any_sync(0xffffffffu, sa || sb)) {
+                // T (1 - alpha) = T - alpha T
+                float2 wgt = fmul2(alpha, T);
+                float2 test_T = fsub2(T, wgt);
+                // a done pixel keeps T >= t_min, so only a pixel stopping here can vote
+                if (__any_sync(0xffffffffu, fminf(test_T.x, test_T.y) < t_min)) {
                     // rare: a pixel stops before this Gaussian, which it does not blend
-                    if (sa) { alpha.x = 0.f; test_T.x = T.x; la = false; stop_a = pos; done_a = true; }
-                    if (sb) { alpha.y = 0.f; test_T.y = T.y; lb = false; stop_b = pos; done_b = true; }
+                    const int32_t pos = fbase + j + 1;
+                    if (test_T.x < t_min) { wgt.x = 0.f; test_T.x = T.x; la = false; stop_a = pos; done_a = true; }
+                    if (test_T.y < t_min) { wgt.y = 0.f; test_T.y = T.y; lb = false; stop_b = pos; done_b = true; }
+                    if (__all_sync(0xffffffffu, done_a && done_b)) break;   // nothing blends this Gaussian
                 }
-                const float2 wgt = fmul2(alpha, T);
                 const float4 rg = s_rg[j];
                 C0 = ffma2(make_float2(rg.x, rg.y), wgt, C0);
                 C1 = ffma2(make_float2(rg.z, rg.w), wgt, C1);
                 C2 = ffma2(s_bb[j], wgt, C2);
                 T = test_T;
+                const int32_t pos = fbase + j + 1;
                 if (la) { ++cnt_a; last_a = pos; }
                 if (lb) { ++cnt_b; last_b = pos; }
             }

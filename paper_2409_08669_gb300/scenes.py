@@ -227,6 +227,22 @@ def heavy_scene(n=3_000_000, seed=2, dense_fraction=0.3, dense_std=0.22) -> Scen
     return _pack(means[perm], *(a[perm] for a in attrs))
 
 
+def deep_scene(n=20_000, seed=9, z_eye=-3.0, near=0.25, far=40_000.0) -> Scene:
+    """Gaussians in front of a camera at (0, 0, z_eye) looking along +z, at
+    view depths log-uniform in [near, far] (17 octaves), inside the 60-degree
+    frustum, with scales proportional to the depth (a few pixels each).  The
+    depth keys of the visible Gaussians then span more than 2^27."""
+    rng = np.random.default_rng(seed)
+    d = np.exp(rng.uniform(np.log(near), np.log(far), size=n))
+    half = np.tan(np.radians(30.0))
+    x = rng.uniform(-0.9, 0.9, size=n) * half * d
+    y = rng.uniform(-0.9, 0.9, size=n) * half * d
+    means = np.stack([x, y, z_eye + d], axis=1)
+    scales, rots, opac, sh = _attributes(rng, n)
+    scales = scales / np.exp(-4.0) * 0.004 * d[:, None]
+    return _pack(means, scales, rots, opac, sh)
+
+
 def perturbed_scene(scene: Scene, seed=4, mean_std=0.01, logit_std=0.3) -> Scene:
     """Training target: means + N(0, 0.01), opacity logits + N(0, 0.3)."""
     rng = np.random.default_rng(seed)

@@ -100,6 +100,18 @@ def test_3dgs_rect_rule_parity(rast, mode):
     _check_frame(rast, scene, cam, st, f"rect3dgs/{S.MODE_NAMES[mode]}")
 
 
+def test_wide_depth_span_sort_parity(rast):
+    """Visible depths over 17 octaves (depth keys spanning more than 2^27, so
+    every byte of the key varies and all four depth passes reorder); pairs
+    and image against the oracle."""
+    scene = S.deep_scene()
+    cam = S.look_at((0, 0, -3), width=320, height=240)
+    ref = oracle.render(scene, cam, S.Settings(mode=S.MODE_AABB))
+    keys = ref["pre"]["depth"][ref["pre"]["tiles"] > 0].astype(np.float32).view(np.uint32)
+    assert int(keys.max()) - (int(keys.min()) & ~511) >= 1 << 27
+    _check_frame(rast, scene, cam, S.Settings(mode=S.MODE_AABB), "deep/aabb")
+
+
 def test_cluster_scene_1080p_subset(rast):
     """A 200k-Gaussian draw of the clustered scene at 1920x1080 (tile grid 120x68)."""
     scene = S.cluster_scene(n=200_000, seed=1)
