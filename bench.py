@@ -67,10 +67,10 @@ EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation i
 KERNELS_PER_FRAME = 30
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
-# its two launches of one frame, 63.5 MB) and the per-tile list pass
+# its two launches of one frame, 57.6 MB) and the per-tile list pass
 # (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md, 128.34 + 576.92 MB over
 # P = 1.5958e8 pairs, scaled by the measured P).
-TRAFFIC_BYTES_PER_FRAME = {"render": (11.10e6 + 8.57e6) + (43.41e6 + 0.40e6)}
+TRAFFIC_BYTES_PER_FRAME = {"render": (10.48e6 + 11.72e6) + (35.35e6 + 0.08e6)}
 TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 
@@ -733,15 +733,26 @@ def run_ours(args):
     with ClockSampler(local, window) as clk:
         t_adr, stages, kernels = time_mode(rast, params, cams, st_adr, args.steps, args.warmup,
                                            stream, pg, kernel_times=True, clock=clk)
+        status = rast.sync_status()
+        if status != 0:
+            raise SystemExit(f"device status {status} after the timed region")
+        # The PLAIN and circle legs: a leg whose frames hold more pairs than the
+        # context's pair capacity (PLAIN at 4K exceeds the 2^30 maximum) renders
+        # incomplete images, so it is reported as over capacity, not timed.
+        leg_status = {}
         if not args.quick:
             t_plain, stages_plain, _ = time_mode(rast, params, cams, st_plain, args.steps,
                                                  args.warmup, stream, pg)
+            leg_status["plain"] = rast.sync_status()
             t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup,
                                        stream, pg, with_stages=False)
+            leg_status["circle"] = rast.sync_status()
     clocks = clk.summary()
-    status = rast.sync_status()
-    if status != 0:
-        raise SystemExit(f"device status {status} after the timed region")
+    for leg, code in leg_status.items():
+        if code not in (0, 2):   # 2: ADR_ERR_CAPACITY
+            raise SystemExit(f"device status {code} after the {leg} leg")
+    plain_ok = leg_status.get("plain") == 0
+    circle_ok = leg_status.get("circle") == 0
     if args.quick:
         rast.close()
         fps, _ = aggregate_fps(pg, t_adr, args.steps, world)
@@ -758,7 +769,8 @@ def run_ours(args):
     nu = min(args.steps, 5)
     ucams = [cams[(args.warmup + k) % len(cams)] for k in range(nu)]
     units_adr = frame_units(rast, params, ucams, st_adr, stream, nu)
-    units_plain = frame_units(rast, params, ucams, st_plain, stream, nu)
+    units_plain = frame_units(rast, params, ucams, st_plain, stream, nu) if plain_ok else None
+    over_cap = f"over the pair capacity ({PAIR_CAPACITY} pairs) at this workload"
     u_mean = {k: statistics.mean(u[k] for u in units_adr) for k in units_adr[0]}
     hbm_gbs, sm_max_mhz, peak_src = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -795,7 +807,8 @@ def run_ours(args):
     alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12
     render_alu = u_mean["evals"] * EVAL_FP32_OPS / (render_ms / 1e3) / 1e12
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
-    stage_ms_plain = {k: statistics.mean(v) for k, v in stages_plain.items()}
+    stage_ms_plain = ({k: statistics.mean(v) for k, v in stages_plain.items()} if plain_ok
+                      else over_cap)
 
     e2e_fps, h2d, d2h = e2e_host(rast.ctx, scene, cams, st_adr, max(3, min(args.steps, 10)), 2)
 
@@ -820,16 +833,19 @@ def run_ours(args):
                           if scene_fits_l2() else
                           f"inputs larger than L2 ({N_GAUSS * 236 / 1e6:.0f} MB scene, "
                           f"{N_GAUSS * 48 / 1e6:.0f} MB render records); no flush")},
-        "plain_fps": frames / t_plain,
-        "circle_fps": frames / t_circle,
-        "speedup_vs_plain": t_plain / t_adr,
+        "plain_fps": frames / t_plain if plain_ok else over_cap,
+        "circle_fps": frames / t_circle if circle_ok else over_cap,
+        "speedup_vs_plain": t_plain / t_adr if plain_ok else None,
         "stages_ms": stage_ms,
         "stages_ms_plain": stage_ms_plain,
         "pairs_per_frame": {"adr_aabb": u_mean["pairs"],
-                            "plain": statistics.mean(u["pairs"] for u in units_plain)},
+                            "plain": (statistics.mean(u["pairs"] for u in units_plain)
+                                      if plain_ok else over_cap)},
         "evals_per_frame": {"adr_aabb": u_mean["evals"],
-                            "plain": statistics.mean(u["evals"] for u in units_plain)},
-        "culled_pair_fraction": 1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain),
+                            "plain": (statistics.mean(u["evals"] for u in units_plain)
+                                      if plain_ok else None)},
+        "culled_pair_fraction": (1.0 - u_mean["pairs"] / statistics.mean(u["pairs"] for u in units_plain)
+                                 if plain_ok else None),
         # What the sorting kernels move: the depth sort orders the V Gaussians
         # with tiles (4 passes); tile pass 1 groups the column runs it builds
         # (both depth slices' runs when sliced) by tile column.  The pairs
