@@ -322,12 +322,26 @@ adr_status adr_sync_status(adr_ctx *ctx);
  * of range. */
 adr_status adr_test_lookback_expiry(int32_t withheld_chunk, int32_t spin_limit);
 
-/* End-to-end frame from HOST memory: copies the scene arrays (HOST pointers,
- * ideally pinned) into the context's device staging buffers, runs
- * preprocess, sort and render, and copies img [3,H,W] (and t_final, load if
- * non-NULL; all HOST pointers) back.  The first call allocates the staging
- * buffers (max_gaussians * 236 bytes + image buffers).  SYNCHRONISES
- * `stream` before returning. */
+/* End-to-end frame from HOST memory: the scene arrays and img [3,H,W] (and
+ * t_final, load if non-NULL) are HOST pointers.  Runs preprocess, sort and
+ * render and SYNCHRONISES `stream` before returning.
+ * With ADR_HOST_READ_MAPPED (the default), if every one of those buffers is
+ * pinned memory mapped into the device's address space (cudaHostAlloc /
+ * cudaHostRegister, e.g. torch pin_memory; rots and sh 16-byte aligned),
+ * Preprocess reads the scene in place over the host link (44 bytes of each
+ * Gaussian plus the 192 bytes of SH of the Gaussians with tiles) and Render
+ * writes the outputs in place: nothing is copied.  Otherwise, and always with
+ * ADR_HOST_READ_COPY, the arrays are copied into device staging buffers,
+ * allocated by the first such call (max_gaussians * 236 bytes + image
+ * buffers), and the outputs copied back.  The host buffers must not change
+ * until the call returns. */
+/* How adr_render_host reaches its HOST buffers (see there).  ADR_ERR_INVALID
+ * for an unknown mode. */
+typedef enum adr_host_read {
+    ADR_HOST_READ_COPY = 0, ADR_HOST_READ_MAPPED = 1
+} adr_host_read;
+adr_status adr_set_host_reads(adr_ctx *ctx, int32_t mode);
+
 adr_status adr_render_host(adr_ctx *ctx, const float *means, const float *scales,
                            const float *rots, const float *opac, const float *sh, int64_t n,
                            const adr_camera *camera, const adr_settings *settings,

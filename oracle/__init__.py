@@ -153,7 +153,7 @@ def tile_ranges(keys, width, height):
     return ranges
 
 
-def render_tiled(pre, ranges, vals, settings, tol_alpha=1e-5, tol_t=1e-4):
+def render_tiled(pre, ranges, vals, settings, tol_alpha=1e-4, tol_t=1e-4):
     """Stage 6: per-pixel front-to-back blending over the tile's sorted list
     (Eq. 2-3) with the per-pixel load l_i (Eq. 12)."""
     w, h = pre["width"], pre["height"]
@@ -196,7 +196,7 @@ def load_std(load) -> float:
     return _load().orc_load_std(load.shape[0], _p(load))
 
 
-def render(scene, camera, settings, tol_rel=1e-6, tol_alpha=1e-5, tol_t=1e-4):
+def render(scene, camera, settings, tol_rel=1e-6, tol_alpha=1e-4, tol_t=1e-4):
     """The whole forward path: preprocess, pairs, sort, ranges, tiled render."""
     pre = preprocess(scene, camera, settings, tol_rel)
     keys, vals = emit_pairs(pre)

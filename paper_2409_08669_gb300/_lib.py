@@ -87,6 +87,7 @@ _SIGNATURES = {
                               _P, _P]),
     "adr_profile_enable": (_I32, [_P, _I32]),
     "adr_set_depth_slices": (_I32, [_P, _I32]),
+    "adr_set_host_reads": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
     "adr_trace_tiles": (_I32, [_P, _I32]),
@@ -252,6 +253,13 @@ def adr_image_loss(img, ref, channels, height, width, w_l1, w_ssim, stats, dl_di
 
 def adr_set_depth_slices(ctx, mode):
     return check(load().adr_set_depth_slices(ctx, int(mode)), "adr_set_depth_slices")
+
+
+HOST_READ_COPY, HOST_READ_MAPPED = 0, 1
+
+
+def adr_set_host_reads(ctx, mode):
+    return check(load().adr_set_host_reads(ctx, int(mode)), "adr_set_host_reads")
 
 
 def adr_profile_enable(ctx, enable):

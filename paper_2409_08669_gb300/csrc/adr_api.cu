@@ -60,6 +60,19 @@ struct DeviceGuard {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// The device address of HOST memory the current device can access in place
+// (pinned memory mapped into its address space), or nullptr for any other
+// pointer.
+const float* mapped_host(const float* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();   // not an error for this call: clear it
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<const float*>(a.devicePointer) : nullptr;
+}
+
 adr_status make_cam(int max_w, int max_h, const adr_camera* cam, CamDev& d) {
     if (!cam) return fail(ADR_ERR_INVALID, "camera is NULL");
     if (cam->width <= 0 || cam->height <= 0 || cam->width > max_w || cam->height > max_h)
@@ -144,6 +157,7 @@ struct adr_ctx {
     bool slices_pay = true;
     uint32_t frames = 0;
     int32_t slice_mode = ADR_SLICES_ADAPTIVE;
+    int32_t host_reads = ADR_HOST_READ_MAPPED;   // adr_render_host: read mapped host buffers in place
     // host-path staging (adr_render_host), allocated on its first use
     float* stage = nullptr;
     float* stage_img = nullptr;
@@ -588,6 +602,14 @@ adr_status adr_image_loss(const float* img, const float* ref, int32_t channels, 
     return check_launch("adr_image_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
 }
 
+adr_status adr_set_host_reads(adr_ctx* c, int32_t mode) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (mode != ADR_HOST_READ_COPY && mode != ADR_HOST_READ_MAPPED)
+        return fail(ADR_ERR_INVALID, "unknown host read mode %d", (int)mode);
+    c->host_reads = mode;
+    return ok();
+}
+
 adr_status adr_set_depth_slices(adr_ctx* c, int32_t mode) {
     if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
     if (mode != ADR_SLICES_NEVER && mode != ADR_SLICES_ALWAYS && mode != ADR_SLICES_ADAPTIVE)
@@ -689,6 +711,33 @@ adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, 
     if (!camera) return fail(ADR_ERR_INVALID, "camera is NULL");
     DeviceGuard guard(c->device);
     cudaStream_t strm = (cudaStream_t)stream;
+    const size_t hw = (size_t)camera->width * camera->height;
+    // Pinned host memory mapped into the device's address space is read (and
+    // the image written) in place over the host link: Preprocess then moves
+    // only what it reads -- 44 bytes of every Gaussian and the 192 bytes of
+    // SH of the Gaussians with tiles -- instead of a copy of every array.
+    if (c->host_reads == ADR_HOST_READ_MAPPED) {
+        const float* dm = mapped_host(means);
+        const float* ds = mapped_host(scales);
+        const float* dr = mapped_host(rots);
+        const float* dop = mapped_host(opac);
+        const float* dsh = mapped_host(sh);
+        float* di = const_cast<float*>(mapped_host(img));
+        float* dt = t_final ? const_cast<float*>(mapped_host(t_final)) : nullptr;
+        int32_t* dl = load ? reinterpret_cast<int32_t*>(const_cast<float*>(
+                                 mapped_host(reinterpret_cast<const float*>(load))))
+                           : nullptr;
+        const bool inputs = n == 0 || (dm && ds && dr && dop && dsh && aligned(dr, 16) && aligned(dsh, 16));
+        const bool outputs = di && (!t_final || dt) && (!load || dl);
+        if (inputs && outputs) {
+            adr_status s = adr_preprocess(c, dm, ds, dr, dop, dsh, n, camera, settings, stream);
+            if (s != ADR_OK) return s;
+            if ((s = adr_sort(c, stream)) != ADR_OK) return s;
+            if ((s = adr_render(c, di, dt, dl, stream)) != ADR_OK) return s;
+            ADR_CUDA(cudaStreamSynchronize(strm));
+            return ok();
+        }
+    }
     const size_t N = (size_t)c->ws.max_n;
     const size_t per = 3 + 3 + 4 + 1 + 48;   // floats per Gaussian
     if (!c->stage) {   // all three staging buffers, or none (a later call retries)
@@ -725,7 +774,6 @@ adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, 
     adr_status s = adr_preprocess(c, d_means, d_scales, d_rots, d_opac, d_sh, n, camera, settings, stream);
     if (s != ADR_OK) return s;
     if ((s = adr_sort(c, stream)) != ADR_OK) return s;
-    const size_t hw = (size_t)camera->width * camera->height;
     float* d_img = c->stage_img;
     float* d_t = d_img + 3 * hw;
     if ((s = adr_render(c, d_img, d_t, c->stage_load, stream)) != ADR_OK) return s;
