@@ -376,7 +376,8 @@ def kernel_bytes(name, n, u, hw):
     depends on the depth slices' sizes, which the frame does not report."""
     P, V = u["pairs"], u["visible"]
     return {
-        "preprocess": 44 * n + 192 * V + 104 * n,  # params (+SH of kept) in; records, key, box out
+        # params (+SH of kept) in; records of kept (64 B), radii/depth, key, box out
+        "preprocess": 44 * n + 192 * V + 40 * n + 64 * V,
         # 4 passes: the first reads the n keys twice and writes the V kept keys +
         # values; the others count, read and write V keys + values; the last
         # also gathers and writes the V packed rectangles

@@ -253,7 +253,8 @@ adr_status adr_read_pairs(adr_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t 
 
 /* Inspection: per-Gaussian Preprocess results for the last adr_preprocess.
  *   geom [n, ADR_GEOM_FLOATS]: px, py, conic_a, conic_b, conic_c, opacity,
- *        r_x, r_y, red, green, blue, depth
+ *        r_x, r_y, red, green, blue, depth (for a Gaussian without tiles only
+ *        r_x, r_y and depth; the other fields read 0)
  *   rect [n,4] int32 tile rectangle tx0, ty0, tx1, ty1 (exclusive ends)
  *   tiles [n] int32 number of tiles (0 = culled) */
 adr_status adr_read_gaussians(adr_ctx *ctx, float *geom, int32_t *rect, int32_t *tiles,

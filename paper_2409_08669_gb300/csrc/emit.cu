@@ -208,15 +208,18 @@ k_read_gaussians(const float4* __restrict__ rec, const float4* __restrict__ aux,
                  int32_t* __restrict__ rect_out, int32_t* __restrict__ tiles_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 r0 = rec[3 * i + 0], r2 = rec[3 * i + 2];
-    const float4 a0 = aux[2 * i + 0], a1 = aux[2 * i + 1];
+    const uint32_t box = gbox[i];
+    const bool has = box != 0xFFFFFFFFu;
+    // Preprocess writes the records of Gaussians with tiles only: the others
+    // report zeros except their radii and depth.
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 r0 = has ? rec[3 * i + 0] : z4, r2 = has ? rec[3 * i + 2] : z4;
+    const float4 a0 = has ? aux[2 * i + 0] : z4, a1 = aux[2 * i + 1];
     if (geom) {
         float* o = geom + (size_t)i * ADR_GEOM_FLOATS;
         o[0] = r0.x; o[1] = r0.y; o[2] = a0.x; o[3] = a0.y; o[4] = a0.z; o[5] = a0.w;
         o[6] = a1.x; o[7] = a1.y; o[8] = r2.x; o[9] = r2.y; o[10] = r2.z; o[11] = a1.z;
     }
-    const uint32_t box = gbox[i];
-    const bool has = box != 0xFFFFFFFFu;
     const int32_t x0 = has ? (int32_t)(box & 0xFFu) : 0, y0 = has ? (int32_t)((box >> 8) & 0xFFu) : 0;
     const int32_t w = has ? (int32_t)((box >> 16) & 0xFFu) + 1 : 0, h = has ? (int32_t)(box >> 24) + 1 : 0;
     if (rect_out) {

@@ -293,10 +293,14 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
             a1 = make_float4(rx, ry, depth, lam);
         }
     }
-    rec[3 * i + 0] = r0;
-    rec[3 * i + 1] = r1;
-    rec[3 * i + 2] = r2;
-    aux[2 * i + 0] = a0;
+    // Render and the backward read the records of Gaussians with tiles only;
+    // the others keep just a1 (radii, depth) for inspection.
+    if (ntiles) {
+        rec[3 * i + 0] = r0;
+        rec[3 * i + 1] = r1;
+        rec[3 * i + 2] = r2;
+        aux[2 * i + 0] = a0;
+    }
     aux[2 * i + 1] = a1;
     depth_key[i] = key;
     // packed rectangle x0 | y0 << 8 | (w-1) << 16 | (h-1) << 24, all ones if no tiles

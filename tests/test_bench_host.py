@@ -60,7 +60,7 @@ def test_clock_summary_without_samples():
 def test_algorithmic_bytes_table():
     u = {"pairs": 1000, "visible": 100, "runs": 50, "evals": 0, "loaded": 10}
     hw = 1920 * 1080
-    assert bench.kernel_bytes("preprocess", 200, u, hw) == 44 * 200 + 192 * 100 + 104 * 200
+    assert bench.kernel_bytes("preprocess", 200, u, hw) == 44 * 200 + 192 * 100 + 40 * 200 + 64 * 100
     assert bench.kernel_bytes("tile_scatter_rows", 200, u, hw) == 8 * 50 + 4 * 1000
     assert bench.kernel_bytes("render", 200, u, hw) == 52 * 10 + 12 * hw
     assert bench.kernel_bytes("slice", 200, u, hw) is None       # depends on the slices' sizes
