@@ -6,11 +6,40 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
 
 #include "adr.h"
 #include "status_bits.h"   // device-side error word bits and their adr_status
 
 namespace adr {
+
+// Programmatic dependent launch.  The frame's kernels follow one another on
+// one stream; each is launched with programmatic stream serialization, so it
+// is scheduled as soon as every block of the kernel before it has started
+// (pdl_prologue's trigger) instead of after that kernel has drained, and its
+// blocks then wait in pdl_prologue until the kernel before has completed and
+// its writes are visible.  pdl_prologue() is the first statement of every
+// kernel launched this way; on a normal launch both instructions are no-ops.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args&&... args) {
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 constexpr int kTile = ADR_TILE;          // 16x16 pixel tiles (Sec. 3.2)
 constexpr int kTilePixels = kTile * kTile;

@@ -88,6 +88,7 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
              uint32_t* __restrict__ offsets, uint32_t* __restrict__ chunk_first,
              unsigned long long* __restrict__ lookback, EpochRef eref,
              uint32_t* __restrict__ counters, uint32_t* __restrict__ status, LookbackTest lt) {
+    pdl_prologue();
     const uint32_t epoch = (*eref.stage) * 8u + eref.pass;
     // The depth sort kept only the Gaussians with tiles: scan those.
     const int64_t n = min(n_host, (int64_t)counters[kCntDepthKept]);
@@ -171,6 +172,7 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
 // work as after an overflow, and only kErrLookback reports it.
 __global__ void k_finish_pairs(uint32_t* __restrict__ counters, int64_t capacity,
                                uint32_t* __restrict__ status) {
+    pdl_prologue();
     const unsigned long long p = *reinterpret_cast<const unsigned long long*>(counters + kCntPairs64);
     if (counters[kCntScanFailed] != 0u) {
         counters[kCntPairs] = kSat;
@@ -242,10 +244,10 @@ void launch_scan_tiles(const uint32_t* sorted_box, int64_t n, int64_t capacity, 
                        uint32_t* chunk_first, unsigned long long* lookback, EpochRef epoch,
                        uint32_t* counters, uint32_t* status, int grid, cudaStream_t stream) {
     if (n > 0)
-        k_scan_tiles<<<grid, kScanThreads, 0, stream>>>(sorted_box, n, capacity, offsets, chunk_first,
+        launch_pdl(k_scan_tiles, grid, kScanThreads, 0, stream, sorted_box, n, capacity, offsets, chunk_first,
                                                         lookback, epoch, counters, status,
                                                         lookback_test());
-    k_finish_pairs<<<1, 1, 0, stream>>>(counters, capacity, status);
+    launch_pdl(k_finish_pairs, 1, 1, 0, stream, counters, capacity, status);
 }
 
 void launch_copy_ranges(const uint2* ranges, int num_tiles, uint2* out, cudaStream_t stream) {

@@ -38,11 +38,12 @@ void Profiler::end(cudaStream_t s) {
     } while (0)
 
 namespace {
-__global__ void k_set_frame_params(FrameParams p, FrameParams* __restrict__ out) { *out = p; }
+__global__ void k_set_frame_params(FrameParams p, FrameParams* __restrict__ out) {
+    pdl_prologue(); *out = p; }
 }  // namespace
 
 void launch_set_frame_params(const FrameParams& p, FrameParams* d_fp, cudaStream_t stream) {
-    k_set_frame_params<<<1, 1, 0, stream>>>(p, d_fp);
+    launch_pdl(k_set_frame_params, 1, 1, 0, stream, p, d_fp);
 }
 
 const void* set_frame_params_kernel() { return reinterpret_cast<const void*>(&k_set_frame_params); }

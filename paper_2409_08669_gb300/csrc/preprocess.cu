@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256, 3)   // 3 CTAs per SM: <= 80 registers
 k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ scales,
              const float* __restrict__ rots, const float* __restrict__ opac,
              const float* __restrict__ sh, PreprocessBatch batch) {
+    pdl_prologue();
     const int b = (int)(blockIdx.x % (unsigned)batch.count);
     const int i = (int)(blockIdx.x / (unsigned)batch.count) * blockDim.x + threadIdx.x;
     const PreprocessOut& out = batch.cam[b];
@@ -317,7 +318,7 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
     if (n <= 0 || batch.count < 1 || batch.count > kMaxBatch) return;
     const int threads = 256;
     const unsigned chunks = (unsigned)((n + threads - 1) / threads);
-    k_preprocess<<<chunks * (unsigned)batch.count, threads, 0, stream>>>(n, means, scales, rots,
+    launch_pdl(k_preprocess, chunks * (unsigned)batch.count, threads, 0, stream, n, means, scales, rots,
                                                                       opac, sh, batch);
 }
 

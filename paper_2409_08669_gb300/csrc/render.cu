@@ -74,6 +74,7 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
 template <bool kRuns>
 __global__ void __launch_bounds__(kRenderThreads, 8)   // 8 CTAs per SM: <= 64 registers
 k_render(const RenderBatch batch) {
+    pdl_prologue();
     int cb = 0;
 #pragma unroll
     for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && (int)blockIdx.x >= batch.tile_begin[q]) ? 1 : 0;
@@ -351,9 +352,9 @@ void launch_render(const RenderBatch& batch, cudaStream_t stream) {
     const int tiles = batch.tile_begin[batch.count];
     if (tiles <= 0) return;
     if (batch.lists == kListsColumns)
-        k_render<true><<<tiles, kRenderThreads, 0, stream>>>(batch);
+        launch_pdl(k_render<true>, tiles, kRenderThreads, 0, stream, batch);
     else
-        k_render<false><<<tiles, kRenderThreads, 0, stream>>>(batch);
+        launch_pdl(k_render<false>, tiles, kRenderThreads, 0, stream, batch);
 }
 
 }  // namespace adr

@@ -33,6 +33,7 @@ __device__ __forceinline__ uint32_t slice0_count(uint32_t visible) {
 
 __global__ void k_slice0_setup(const uint32_t* __restrict__ counters,
                                const uint32_t* __restrict__ offsets, uint32_t* __restrict__ c0) {
+    pdl_prologue();
     const uint32_t V = counters[kCntVisible];
     const uint32_t K0 = slice0_count(V);
     c0[kCntPairs] = counters[kCntPairs];
@@ -57,6 +58,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 constexpr int kSatChunks = (kRadix + 1 + 31) / 32;
 __global__ void __launch_bounds__(kSurvThreads)
 k_sat_rows(const uint32_t* __restrict__ tile_done, int tiles_x, int tiles_y, uint32_t* __restrict__ sat) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     const int y = (int)(blockIdx.x * (kSurvThreads / 32) + (threadIdx.x >> 5));
     const int W = tiles_x + 1;
@@ -80,6 +82,7 @@ k_sat_rows(const uint32_t* __restrict__ tile_done, int tiles_x, int tiles_y, uin
 // Column pass: one warp per column.
 __global__ void __launch_bounds__(kSurvThreads)
 k_sat_cols(int tiles_x, int tiles_y, uint32_t* __restrict__ sat) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     const int x = (int)(blockIdx.x * (kSurvThreads / 32) + (threadIdx.x >> 5));
     const int W = tiles_x + 1, H = tiles_y + 1;
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(kSurvThreads)
 k_surv_count(const uint32_t* __restrict__ sorted_box, const uint32_t* __restrict__ counters,
              const uint32_t* __restrict__ sat, int tiles_x, int grid, uint32_t* __restrict__ cnt,
              uint8_t* __restrict__ keep_flag) {
+    pdl_prologue();
     __shared__ uint32_t s_w[2][kSurvThreads / 32];
     uint32_t a, e;
     surv_span(counters, grid, a, e);
@@ -166,6 +170,7 @@ k_surv_count(const uint32_t* __restrict__ sorted_box, const uint32_t* __restrict
 __global__ void __launch_bounds__(kMaxTileGrid / 8)
 k_surv_scan(uint32_t* __restrict__ cnt, int grid, const uint32_t* __restrict__ counters,
             uint32_t* __restrict__ c1) {
+    pdl_prologue();
     constexpr int kT = kMaxTileGrid / 8, kPer = 8;
     __shared__ uint32_t s_w[kT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -216,6 +221,7 @@ k_surv_scatter(const uint32_t* __restrict__ sorted_box, const uint32_t* __restri
                uint32_t* __restrict__ s_order, uint32_t* __restrict__ s_box,
                uint32_t* __restrict__ s_offsets, uint32_t* __restrict__ s_chunk_first,
                uint32_t* __restrict__ status) {
+    pdl_prologue();
     __shared__ uint32_t s_w[2][kSurvThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t a, e;
@@ -266,7 +272,7 @@ k_surv_scatter(const uint32_t* __restrict__ sorted_box, const uint32_t* __restri
 
 void launch_slice0_setup(const uint32_t* counters, const uint32_t* offsets, uint32_t* c0,
                          cudaStream_t stream) {
-    k_slice0_setup<<<1, 1, 0, stream>>>(counters, offsets, c0);
+    launch_pdl(k_slice0_setup, 1, 1, 0, stream, counters, offsets, c0);
 }
 
 void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint32_t* sat,
@@ -275,13 +281,13 @@ void launch_survivors(const uint32_t* tile_done, int tiles_x, int tiles_y, uint3
                       uint32_t* s_order, uint32_t* s_box, uint32_t* s_offsets,
                       uint32_t* s_chunk_first, uint32_t* c1, uint32_t* status, cudaStream_t stream) {
     const int warps = kSurvThreads / 32;
-    k_sat_rows<<<(tiles_y + 1 + warps - 1) / warps, kSurvThreads, 0, stream>>>(tile_done, tiles_x,
+    launch_pdl(k_sat_rows, (tiles_y + 1 + warps - 1) / warps, kSurvThreads, 0, stream, tile_done, tiles_x,
                                                                                tiles_y, sat);
-    k_sat_cols<<<(tiles_x + 1 + warps - 1) / warps, kSurvThreads, 0, stream>>>(tiles_x, tiles_y, sat);
-    k_surv_count<<<grid, kSurvThreads, 0, stream>>>(sorted_box, counters, sat, tiles_x, grid, cnt,
+    launch_pdl(k_sat_cols, (tiles_x + 1 + warps - 1) / warps, kSurvThreads, 0, stream, tiles_x, tiles_y, sat);
+    launch_pdl(k_surv_count, grid, kSurvThreads, 0, stream, sorted_box, counters, sat, tiles_x, grid, cnt,
                                                     keep_flag);
-    k_surv_scan<<<1, kMaxTileGrid / 8, 0, stream>>>(cnt, grid, counters, c1);
-    k_surv_scatter<<<grid, kSurvThreads, 0, stream>>>(sorted_box, order, counters, keep_flag, grid,
+    launch_pdl(k_surv_scan, 1, kMaxTileGrid / 8, 0, stream, cnt, grid, counters, c1);
+    launch_pdl(k_surv_scatter, grid, kSurvThreads, 0, stream, sorted_box, order, counters, keep_flag, grid,
                                                       cnt, n_max, chunk_max, s_order, s_box,
                                                       s_offsets, s_chunk_first, status);
 }

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kSortThreads)
 k_digit_counts(const uint32_t* __restrict__ keys, int64_t n_host, const uint32_t* __restrict__ n_dev,
                bool drop, int shift, int grid, uint32_t* __restrict__ counts,
                uint32_t* __restrict__ totals, uint32_t* __restrict__ kept_total) {
+    pdl_prologue();
     __shared__ uint32_t s_cnt[kRadix + 1];   // + the dropped keys
     const int tid = threadIdx.x;
     const int64_t n = pass_items(n_host, n_dev);
@@ -100,6 +101,7 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
                 const uint32_t* __restrict__ starts, int grid,
                 const uint32_t* __restrict__ pay_in, uint32_t* __restrict__ pay_out,
                 uint32_t* __restrict__ status) {
+    pdl_prologue();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortShared& sm = *reinterpret_cast<SortShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -214,10 +216,10 @@ void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
     // First pass: all n keys in, the kept ones counted into *kept.  Later
     // passes: the *kept keys.
     const uint32_t* n_dev = first ? nullptr : kept;
-    k_digit_counts<<<grid, kSortThreads, 0, stream>>>(keys_in, n, n_dev, first, shift, grid, counts,
+    launch_pdl(k_digit_counts, grid, kSortThreads, 0, stream, keys_in, n, n_dev, first, shift, grid, counts,
                                                       totals, first ? kept : nullptr);
     launch_tile_count_scan(counts, totals, grid, stream);
-    k_digit_scatter<<<grid, kSortThreads, kSortSmem, stream>>>(keys_in, vals_in, keys_out, vals_out, n,
+    launch_pdl(k_digit_scatter, grid, kSortThreads, kSortSmem, stream, keys_in, vals_in, keys_out, vals_out, n,
                                                               n_dev, first, shift, counts, grid,
                                                               pay_in, pay_out, status);
 }

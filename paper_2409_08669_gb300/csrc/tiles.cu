@@ -230,6 +230,7 @@ __device__ __forceinline__ bool gauss_span(const PairSource& src, const Span& sp
 __global__ void __launch_bounds__(kSortThreads)
 k_count_columns(PairSource src, int grid, uint32_t* __restrict__ counts, uint32_t* __restrict__ totals,
                 uint32_t* __restrict__ status) {
+    pdl_prologue();
     __shared__ int s_diff[kRadix + 1];
     __shared__ uint32_t s_wsum[kWarps];
     const int tid = threadIdx.x;
@@ -322,6 +323,7 @@ __global__ void __launch_bounds__(kSortThreads, 3)
 k_scatter_columns(PairSource src, const uint32_t* __restrict__ starts, uint2* __restrict__ runs_out,
                   uint16_t* __restrict__ rows_out,
                   int grid, uint32_t* __restrict__ status) {
+    pdl_prologue();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColumnShared& sm = *reinterpret_cast<ColumnShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -380,6 +382,7 @@ k_count_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counte
              int grid, int tiles_x, int num_tiles, uint32_t* __restrict__ counts,
              uint32_t* __restrict__ totals, uint32_t* __restrict__ tile_counts,
              uint32_t* __restrict__ status) {
+    pdl_prologue();
     __shared__ int s_diff[kRadix + 1];
     __shared__ int s_col[kColSlots][kRadix + 1];
     __shared__ uint32_t s_wsum[kWarps];
@@ -448,6 +451,7 @@ constexpr int kRangeThreads = 1024;
 __global__ void __launch_bounds__(kRangeThreads)
 k_tile_ranges(const uint32_t* __restrict__ tile_counts, int num_tiles,
               const uint32_t* __restrict__ counters, int64_t capacity, uint2* __restrict__ ranges) {
+    pdl_prologue();
     __shared__ uint32_t s_w[kRangeThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool overflow = (int64_t)counters[kCntPairs] > capacity;
@@ -484,6 +488,7 @@ __global__ void __launch_bounds__(kSortThreads, 8)   // 8 CTAs per SM: 32 regist
 k_scatter_rows(const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                int64_t capacity, const uint32_t* __restrict__ starts, uint32_t* __restrict__ gauss_out,
                int grid, int tiles_y, uint32_t* __restrict__ status) {
+    pdl_prologue();
     __shared__ RowShared sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Span sp = cta_span(run_count(counters, capacity), grid);
@@ -576,6 +581,7 @@ static_assert(kScanPerThread * kScanCtaThreads == kMaxTileGrid, "scan covers the
 
 __global__ void __launch_bounds__(kScanCtaThreads)
 k_count_scan(uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals, int grid) {
+    pdl_prologue();
     __shared__ uint32_t s_w[kScanCtaThreads / 32];
     __shared__ uint32_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -625,37 +631,37 @@ int tile_scatter_blocks_per_sm() {
 
 void launch_tile_count_columns(const PairSource& src, uint32_t* counts, uint32_t* totals,
                                uint32_t* status, int grid, cudaStream_t stream) {
-    k_count_columns<<<grid, kSortThreads, 0, stream>>>(src, grid, counts, totals, status);
+    launch_pdl(k_count_columns, grid, kSortThreads, 0, stream, src, grid, counts, totals, status);
 }
 
 void launch_tile_scatter_columns(const PairSource& src, const uint32_t* starts, uint2* runs_out,
                                  uint16_t* rows_out, uint32_t* status, int grid, cudaStream_t stream) {
-    k_scatter_columns<<<grid, kSortThreads, kColumnSmem, stream>>>(src, starts, runs_out, rows_out, grid,
+    launch_pdl(k_scatter_columns, grid, kSortThreads, kColumnSmem, stream, src, starts, runs_out, rows_out, grid,
                                                                   status);
 }
 
 void launch_tile_count_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                             int tiles_x, int num_tiles, uint32_t* counts, uint32_t* totals,
                             uint32_t* tile_counts, uint32_t* status, int grid, cudaStream_t stream) {
-    k_count_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, grid, tiles_x, num_tiles,
+    launch_pdl(k_count_rows, grid, kSortThreads, 0, stream, runs, counters, capacity, grid, tiles_x, num_tiles,
                                                     counts, totals, tile_counts, status);
 }
 
 void launch_tile_ranges(const uint32_t* tile_counts, int num_tiles, const uint32_t* counters,
                         int64_t capacity, uint2* ranges, cudaStream_t stream) {
     if (num_tiles <= 0) return;
-    k_tile_ranges<<<1, kRangeThreads, 0, stream>>>(tile_counts, num_tiles, counters, capacity, ranges);
+    launch_pdl(k_tile_ranges, 1, kRangeThreads, 0, stream, tile_counts, num_tiles, counters, capacity, ranges);
 }
 
 void launch_tile_scatter_rows(const uint2* runs, const uint32_t* counters, int64_t capacity,
                               const uint32_t* starts, uint32_t* gauss_out, uint32_t* status,
                               int grid, int tiles_y, cudaStream_t stream) {
-    k_scatter_rows<<<grid, kSortThreads, 0, stream>>>(runs, counters, capacity, starts, gauss_out,
+    launch_pdl(k_scatter_rows, grid, kSortThreads, 0, stream, runs, counters, capacity, starts, gauss_out,
                                                       grid, tiles_y, status);
 }
 
 void launch_tile_count_scan(uint32_t* counts, const uint32_t* totals, int grid, cudaStream_t stream) {
-    k_count_scan<<<kRadix, kScanCtaThreads, 0, stream>>>(counts, totals, grid);
+    launch_pdl(k_count_scan, kRadix, kScanCtaThreads, 0, stream, counts, totals, grid);
 }
 
 }  // namespace adr
