@@ -830,10 +830,13 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 10))
     e2e_fps, d2h = e2e_host(rast.ctx, scene, cams, st_adr, e2e_steps, 2, L.HOST_READ_MAPPED)
     e2e_copy_fps, _ = e2e_host(rast.ctx, scene, cams, st_adr, e2e_steps, 2, L.HOST_READ_COPY)
-    # bytes that cross the host link each step: Preprocess reads 44 B of every
-    # Gaussian (means, scales, rots, opacity) and the 192 B of SH of the
-    # Gaussians with tiles in place; the copy path moves every array
-    h2d = int(44 * N_GAUSS + 192 * u_mean["visible"])
+    # bytes that cross the host link each step: Preprocess reads at most 44 B
+    # of every Gaussian (means, scales, rots, opacity) in place, and the colour
+    # kernels 204 B (SH + mean) of each Gaussian a Render launch blends; the
+    # copy path moves every array
+    blended = (math.ceil(u_mean["visible"] / 16) + u_mean["visible_slice1"]
+               if u_mean["sliced"] else u_mean["visible"])
+    h2d = int(44 * N_GAUSS + 204 * blended)
     h2d_copy = sum(a.nbytes for a in scene.arrays())
 
     result = {
@@ -886,8 +889,9 @@ def run_ours(args):
                                     "frac": (render["gbs"] / hbm_gbs) if render else None}},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "how": ("adr_render_host with pinned host buffers: Preprocess reads the scene "
-                        "in place over the host link and Render writes the image in place"),
+                "how": ("adr_render_host with pinned host buffers: Preprocess and the colour "
+                        "kernels read the scene in place over the host link and Render writes "
+                        "the image in place"),
                 "copy_path": {"value": e2e_copy_fps, "unit": "frames/s",
                               "h2d_bytes_per_step": h2d_copy, "d2h_bytes_per_step": d2h}},
         "gpu_launches": KERNELS_PER_FRAME * args.steps,

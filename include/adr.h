@@ -254,7 +254,9 @@ adr_status adr_read_pairs(adr_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t 
 /* Inspection: per-Gaussian Preprocess results for the last adr_preprocess.
  *   geom [n, ADR_GEOM_FLOATS]: px, py, conic_a, conic_b, conic_c, opacity,
  *        r_x, r_y, red, green, blue, depth (for a Gaussian without tiles only
- *        r_x, r_y and depth; the other fields read 0)
+ *        r_x, r_y and depth; the other fields read 0).  After adr_render_host
+ *        with mapped host buffers only the Gaussians the frame blended have
+ *        their colour (see there; the others read 0)
  *   rect [n,4] int32 tile rectangle tx0, ty0, tx1, ty1 (exclusive ends)
  *   tiles [n] int32 number of tiles (0 = culled) */
 adr_status adr_read_gaussians(adr_ctx *ctx, float *geom, int32_t *rect, int32_t *tiles,
@@ -329,9 +331,11 @@ adr_status adr_test_lookback_expiry(int32_t withheld_chunk, int32_t spin_limit);
  * With ADR_HOST_READ_MAPPED (the default), if every one of those buffers is
  * pinned memory mapped into the device's address space (cudaHostAlloc /
  * cudaHostRegister, e.g. torch pin_memory; rots and sh 16-byte aligned),
- * Preprocess reads the scene in place over the host link (44 bytes of each
- * Gaussian plus the 192 bytes of SH of the Gaussians with tiles) and Render
- * writes the outputs in place: nothing is copied.  Otherwise, and always with
+ * Preprocess reads the scene in place over the host link (at most 44 bytes
+ * of each Gaussian), the SH colours are computed just before each Render
+ * launch for the Gaussians it blends only (192 bytes of SH each; with depth
+ * slices, far fewer than the Gaussians with tiles), and Render writes the
+ * outputs in place: nothing is copied.  Otherwise, and always with
  * ADR_HOST_READ_COPY, the arrays are copied into device staging buffers,
  * allocated by the first such call (max_gaussians * 236 bytes + image
  * buffers), and the outputs copied back.  The host buffers must not change

@@ -158,6 +158,7 @@ struct adr_ctx {
     uint32_t frames = 0;
     int32_t slice_mode = ADR_SLICES_ADAPTIVE;
     int32_t host_reads = ADR_HOST_READ_MAPPED;   // adr_render_host: read mapped host buffers in place
+    bool defer_colors = false;   // the next adr_preprocess leaves the SH colours to adr_render
     // host-path staging (adr_render_host), allocated on its first use
     float* stage = nullptr;
     float* stage_img = nullptr;
@@ -387,7 +388,8 @@ adr_status adr_preprocess(adr_ctx* c, const float* means, const float* scales, c
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
     fill_frame_state(c->fs, n, cam, st);
-    enqueue_preprocess(c->ws, c->fs, c->epoch, means, scales, rots, opac, sh, strm);
+    enqueue_preprocess(c->ws, c->fs, c->epoch, means, scales, rots, opac, sh, strm, true,
+                       c->defer_colors);
     if ((s = check_launch("adr_preprocess")) != ADR_OK) return s;
     c->have_frame = true;
     c->have_sort = c->have_render = false;
@@ -514,6 +516,11 @@ adr_status adr_read_gaussians(adr_ctx* c, float* geom, int32_t* rect, int32_t* t
     if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
     if (!c->have_frame) return fail(ADR_ERR_INVALID, "adr_read_gaussians before adr_preprocess");
     DeviceGuard guard(c->device);
+    // A frame computes the SH colours of the Gaussians it blends only; the
+    // inspection reports every Gaussian with tiles, from the frame's SH array.
+    if (geom && c->fs.defer_colors && c->fs.sh && c->fs.order && c->fs.n > 0)
+        launch_colors(c->fs.order, c->ws.counters + kCntVisible, c->fs.means, c->fs.sh, c->ws.d_fp,
+                      c->ws.rec, c->ws.sm_count, (cudaStream_t)stream);
     launch_read_gaussians(c->ws.rec, c->ws.aux, c->ws.gbox, (int)c->fs.n, geom, rect,
                           tiles, (cudaStream_t)stream);
     return check_launch("adr_read_gaussians") == ADR_OK ? ok() : ADR_ERR_CUDA;
@@ -730,11 +737,16 @@ adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, 
         const bool inputs = n == 0 || (dm && ds && dr && dop && dsh && aligned(dr, 16) && aligned(dsh, 16));
         const bool outputs = di && (!t_final || dt) && (!load || dl);
         if (inputs && outputs) {
+            // The colours come from host memory too: only those of the
+            // Gaussians each Render phase blends are read.
+            c->defer_colors = true;
             adr_status s = adr_preprocess(c, dm, ds, dr, dop, dsh, n, camera, settings, stream);
+            c->defer_colors = false;
             if (s != ADR_OK) return s;
             if ((s = adr_sort(c, stream)) != ADR_OK) return s;
             if ((s = adr_render(c, di, dt, dl, stream)) != ADR_OK) return s;
             ADR_CUDA(cudaStreamSynchronize(strm));
+            c->fs.means = c->fs.sh = nullptr;   // the caller's buffers: not read after the call
             return ok();
         }
     }

@@ -141,7 +141,7 @@ enum Counter : int {
 enum KernelId : int {
     kKPreprocess = 0, kKDepthPass, kKScanTiles, kKTileRanges, kKTileCountColumns,
     kKTileScatterColumns, kKTileCountRows, kKTileScatterRows, kKTileCountScan, kKRender,
-    kKRenderBackward, kKPreprocessBackward, kKSlice, kKernelCount
+    kKRenderBackward, kKPreprocessBackward, kKSlice, kKColors, kKernelCount
 };
 const char* kernel_name(int id);
 struct Profiler {
@@ -218,6 +218,12 @@ struct FrameState {
     SetDev st{};
     int num_tiles = 0;
     const uint32_t* order = nullptr;         // Gaussians by depth (the first V have tiles)
+    // Deferred colours (frames whose parameters sit in host memory): Preprocess
+    // skips the SH colour and each Render phase first computes it for the
+    // Gaussians it blends, from these arrays (nullptr once they may be gone).
+    bool defer_colors = false;
+    const float* means = nullptr;
+    const float* sh = nullptr;
     const uint32_t* sorted_gauss = nullptr;  // list entries' Gaussians by (cell, depth)
     const uint2* runs = nullptr;             // column runs by (column, depth)
     const uint16_t* rows = nullptr;          // their row intervals
@@ -248,7 +254,7 @@ const void* set_frame_params_kernel();
 void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                         const float* means, const float* scales, const float* rots,
                         const float* opac, const float* sh, cudaStream_t stream,
-                        bool set_params = true);
+                        bool set_params = true, bool defer_colors = false);
 void enqueue_sort(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                   cudaStream_t stream);
 // Builds per-tile lists (from every Gaussian's column runs) if the last sort
@@ -295,6 +301,7 @@ struct PreprocessBatch {
     PreprocessOut cam[kMaxBatch];
 };
 // grid = chunks of 256 Gaussians x count, the camera index fastest
+// sh == nullptr defers the SH colours to launch_colors.
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
                        const float* opac, const float* sh, const PreprocessBatch& batch,
                        cudaStream_t stream);
@@ -308,6 +315,13 @@ void launch_depth_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
                        uint32_t* vals_out, int64_t n, uint32_t* kept, bool first, int shift,
                        uint32_t* counts, uint32_t* totals, const uint32_t* pay_in,
                        uint32_t* pay_out, uint32_t* status, int grid, cudaStream_t stream);
+
+// SH colours (Sec. 3.2.1, stage 1's view-dependent colour) of the Gaussians
+// ids[0 .. *count) into their render records (rec[3 i + 2].xyz), on demand:
+// a frame with deferred colours computes them only for the Gaussians a Render
+// launch blends.
+void launch_colors(const uint32_t* ids, const uint32_t* count, const float* means, const float* sh,
+                   const FrameParams* fp, float4* rec, int sm_count, cudaStream_t stream);
 
 // Inputs of the tile passes.
 struct PairSource {

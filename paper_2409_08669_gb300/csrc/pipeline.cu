@@ -9,7 +9,7 @@ const char* kernel_name(int id) {
     static const char* names[kKernelCount] = {
         "preprocess", "depth_pass", "scan_tiles", "tile_ranges",
         "tile_count_columns", "tile_scatter_columns", "tile_count_rows", "tile_scatter_rows",
-        "tile_count_scan", "render", "render_backward", "preprocess_backward", "slice"};
+        "tile_count_scan", "render", "render_backward", "preprocess_backward", "slice", "colors"};
     return (id >= 0 && id < kKernelCount) ? names[id] : "?";
 }
 
@@ -108,14 +108,19 @@ static void preprocess_tail(const Workspace& ws, FrameState& fs, cudaStream_t st
 void enqueue_preprocess(const Workspace& ws, FrameState& fs, std::atomic<uint32_t>& epoch,
                         const float* means, const float* scales, const float* rots,
                         const float* opac, const float* sh, cudaStream_t stream,
-                        bool set_params) {
+                        bool set_params, bool defer_colors) {
     preprocess_head(ws, fs, epoch, stream, set_params);
-    // Stage 1: per-Gaussian projection, covariance, colour and early cull.
+    fs.defer_colors = defer_colors;
+    fs.means = means;
+    fs.sh = sh;
+    // Stage 1: per-Gaussian projection, covariance, early cull and (unless
+    // deferred to Render) the SH colour.
     PreprocessBatch pb;
     pb.count = 1;
     pb.cam[0] = preprocess_out(ws);
     TIMED(ws, kKPreprocess, stream,
-          launch_preprocess((int)fs.n, means, scales, rots, opac, sh, pb, stream));
+          launch_preprocess((int)fs.n, means, scales, rots, opac, defer_colors ? nullptr : sh, pb,
+                            stream));
     preprocess_tail(ws, fs, stream);
 }
 
@@ -245,6 +250,18 @@ static RenderCam render_cam(const Workspace& ws, const FrameState& fs, float* im
     return rc;
 }
 
+// The SH colours of the Gaussians a Render phase blends: phase 0 every
+// Gaussian with tiles, phase 1 the nearest K0 (slice 0), phase 2 slice 1's.
+static void enqueue_colors(const Workspace& ws, const FrameState& fs, int phase, cudaStream_t stream) {
+    if (!fs.defer_colors || fs.n <= 0 || !fs.order || !fs.sh) return;
+    const uint32_t* ids = phase == 2 ? ws.s_order : fs.order;
+    const uint32_t* count = phase == 0   ? ws.counters + kCntVisible
+                            : phase == 1 ? ws.slice_counters + kCntVisible
+                                         : ws.slice_counters + kCntSlots + kCntVisible;
+    TIMED(ws, kKColors, stream,
+          launch_colors(ids, count, fs.means, fs.sh, ws.d_fp, ws.rec, ws.sm_count, stream));
+}
+
 // One Render launch over the items' cameras (all of the same list kind).
 static void render_launch(const BatchItem* items, int count, int phase, cudaStream_t stream) {
     RenderBatch rb;
@@ -298,6 +315,8 @@ static void render_items(const BatchItem* items, int count, cudaStream_t stream,
                             stream);
     // Stage 6.
     if (!items[0].fs->sliced) {
+        per_item(items, count, stream, bs,
+                 [&](int b, cudaStream_t s) { enqueue_colors(*items[b].ws, *items[b].fs, 0, s); });
         render_launch(items, count, 0, stream);
         return;
     }
@@ -305,9 +324,13 @@ static void render_items(const BatchItem* items, int count, cudaStream_t stream,
         const BatchItem& it = items[b];
         if (it.fs->runs_held != kRunsSlice0) enqueue_pass1(*it.ws, *it.fs, pair_source(*it.ws, *it.fs, 0), s);
         it.fs->runs_held = kRunsSlice0;
+        enqueue_colors(*it.ws, *it.fs, 1, s);
     });
     render_launch(items, count, 1, stream);
-    per_item(items, count, stream, bs, [&](int b, cudaStream_t s) { slice1_runs(*items[b].ws, *items[b].fs, s); });
+    per_item(items, count, stream, bs, [&](int b, cudaStream_t s) {
+        slice1_runs(*items[b].ws, *items[b].fs, s);
+        enqueue_colors(*items[b].ws, *items[b].fs, 2, s);
+    });
     render_launch(items, count, 2, stream);
 }
 
@@ -326,6 +349,9 @@ void enqueue_frame_batch(const BatchItem* items, int count, const float* means, 
     for (int b = 0; b < count; ++b) {
         const BatchItem& it = items[b];
         preprocess_head(*it.ws, *it.fs, *it.epoch, stream, set_params);
+        it.fs->defer_colors = false;
+        it.fs->means = means;
+        it.fs->sh = sh;
         pb.cam[b] = preprocess_out(*it.ws);
     }
     // Stage 1 for every camera in one grid: the scene is read once.

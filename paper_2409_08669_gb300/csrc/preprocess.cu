@@ -281,11 +281,16 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
                 rc = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1,
                                   (unsigned short)ty1);
                 key = __float_as_uint(depth);
-                // SH colour, d = normalise(X0 - cam_pos).
-                float dx = mx - cam.cam_pos[0], dy = my - cam.cam_pos[1], dz = mz - cam.cam_pos[2];
-                const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                dx *= dn; dy *= dn; dz *= dn;
-                const float3 rgb = sh_to_rgb(sh + (size_t)i * 48, st.sh_degree, dx, dy, dz);
+                // SH colour, d = normalise(X0 - cam_pos); with sh == nullptr
+                // (deferred colours) k_colors fills .xyz in for the Gaussians
+                // a Render launch blends.
+                float3 rgb = make_float3(0.f, 0.f, 0.f);
+                if (sh) {
+                    float dx = mx - cam.cam_pos[0], dy = my - cam.cam_pos[1], dz = mz - cam.cam_pos[2];
+                    const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    dx *= dn; dy *= dn; dz *= dn;
+                    rgb = sh_to_rgb(sh + (size_t)i * 48, st.sh_degree, dx, dy, dz);
+                }
                 r2 = make_float4(rgb.x, rgb.y, rgb.z, log2f(sigma));
             }
             r0 = make_float4(px, py, pxf.lo, pyf.lo);
@@ -310,6 +315,33 @@ k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ s
                      : 0xFFFFFFFFu;
 }
 
+// Stage 1's view-dependent colour, rgb = max(0, sum_k sh_k Y_k(d) + 0.5) with
+// d = normalise(X0 - cam_pos), for the Gaussians ids[0 .. *count) (one per
+// thread, grid-stride): written into .xyz of their third render record.
+constexpr int kColorThreads = 256;
+__global__ void __launch_bounds__(kColorThreads)
+k_colors(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ count,
+         const float* __restrict__ means, const float* __restrict__ sh,
+         const FrameParams* __restrict__ fp, float4* __restrict__ rec) {
+    pdl_prologue();
+    const uint32_t m = *count;
+    const CamDev cam = fp->cam;
+    const int degree = fp->st.sh_degree;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const uint32_t i = ids[k];
+        const float mx = means[3 * (size_t)i + 0], my = means[3 * (size_t)i + 1], mz = means[3 * (size_t)i + 2];
+        float dx = mx - cam.cam_pos[0], dy = my - cam.cam_pos[1], dz = mz - cam.cam_pos[2];
+        const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        dx *= dn; dy *= dn; dz *= dn;
+        const float3 rgb = sh_to_rgb(sh + (size_t)i * 48, degree, dx, dy, dz);
+        float4 r2 = rec[3 * (size_t)i + 2];
+        r2.x = rgb.x;
+        r2.y = rgb.y;
+        r2.z = rgb.z;
+        rec[3 * (size_t)i + 2] = r2;
+    }
+}
+
 }  // namespace
 
 void launch_preprocess(int n, const float* means, const float* scales, const float* rots,
@@ -319,7 +351,13 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
     const int threads = 256;
     const unsigned chunks = (unsigned)((n + threads - 1) / threads);
     launch_pdl(k_preprocess, chunks * (unsigned)batch.count, threads, 0, stream, n, means, scales, rots,
-                                                                      opac, sh, batch);
+               opac, sh, batch);
+}
+
+void launch_colors(const uint32_t* ids, const uint32_t* count, const float* means, const float* sh,
+                   const FrameParams* fp, float4* rec, int sm_count, cudaStream_t stream) {
+    launch_pdl(k_colors, (sm_count > 0 ? sm_count : 1) * 8, kColorThreads, 0, stream, ids, count,
+               means, sh, fp, rec);
 }
 
 }  // namespace adr
