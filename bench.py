@@ -734,7 +734,7 @@ def run_ours(args):
     rast.num_pairs()
 
     window = ("warm-up and timed AdR frames, the instrumented AdR pass" +
-              ("" if args.quick else ", then the plain and circle legs"))
+              ("" if args.quick else ", then the plain, circle and tile-split legs"))
     with ClockSampler(local, window) as clk:
         # The headline: the frames alone, with no event inside the timed region.
         t_adr, _, _ = time_mode(rast, params, cams, st_adr, args.steps, args.warmup, stream, pg,
@@ -763,6 +763,13 @@ def run_ours(args):
             t_circle, _, _ = time_mode(rast, params, cams, st_circle, args.steps, args.warmup,
                                        stream, pg, with_stages=False)
             leg_status["circle"] = rast.sync_status()
+            # f2: the last depth slice's tiles as pixel halves on two CTAs each
+            from paper_2409_08669_gb300 import _lib as L
+            rast.set_tile_split(L.TILE_SPLIT_LAST_SLICE)
+            t_split, _, _ = time_mode(rast, params, cams, st_adr, args.steps, args.warmup, stream, pg,
+                                      with_stages=False)
+            rast.set_tile_split(L.TILE_SPLIT_OFF)
+            leg_status["tile_split"] = rast.sync_status()
     clocks = clk.summary()
     for leg, code in leg_status.items():
         if code not in (0, 2):   # 2: ADR_ERR_CAPACITY
@@ -863,6 +870,7 @@ def run_ours(args):
                           f"{N_GAUSS * 48 / 1e6:.0f} MB render records); no flush")},
         "plain_fps": frames / t_plain if plain_ok else over_cap,
         "circle_fps": frames / t_circle if circle_ok else over_cap,
+        "tile_split_fps": frames / max_over_ranks(pg, t_split),
         "speedup_vs_plain": t_plain / t_adr if plain_ok else None,
         "stages_ms": stage_ms,
         "stages_ms_plain": stage_ms_plain,

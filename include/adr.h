@@ -159,6 +159,20 @@ typedef enum adr_slice_mode {
  * for an unknown mode. */
 adr_status adr_set_depth_slices(adr_ctx *ctx, int32_t mode);
 
+/* Heavy tiles across CTAs (the uneven load across tiles, Sec. 4.4): with
+ * ADR_TILE_SPLIT_LAST_SLICE, the last depth slice renders every unfinished
+ * tile as two CTAs of one pixel per thread (the tile's top and bottom 8
+ * rows), so each tile runs on twice the warps; every pixel's arithmetic is
+ * unchanged and the frames are bit-identical to ADR_TILE_SPLIT_OFF (the
+ * default, faster on the measured workloads).  A tile's list is not split:
+ * front-to-back blending stops at a transmittance that depends on the whole
+ * prefix.  Applies to adr_render of this context from the next call;
+ * ADR_ERR_INVALID for an unknown mode. */
+typedef enum adr_tile_split {
+    ADR_TILE_SPLIT_OFF = 0, ADR_TILE_SPLIT_LAST_SLICE = 1
+} adr_tile_split;
+adr_status adr_set_tile_split(adr_ctx *ctx, int32_t mode);
+
 /* Stages 4-5: the tile lists, ordered by (tile, depth, index) (the Gaussians
  * are already in depth order).  The pairs are grouped by column of tiles:
  * each Gaussian contributes one run per tile column of its rectangle (its

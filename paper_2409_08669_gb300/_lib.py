@@ -88,6 +88,7 @@ _SIGNATURES = {
     "adr_profile_enable": (_I32, [_P, _I32]),
     "adr_set_depth_slices": (_I32, [_P, _I32]),
     "adr_set_host_reads": (_I32, [_P, _I32]),
+    "adr_set_tile_split": (_I32, [_P, _I32]),
     "adr_profile_read": (_I32, [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]),
     "adr_profile_kernel_name": (ctypes.c_char_p, [_I32]),
     "adr_trace_tiles": (_I32, [_P, _I32]),
@@ -260,6 +261,13 @@ HOST_READ_COPY, HOST_READ_MAPPED = 0, 1
 
 def adr_set_host_reads(ctx, mode):
     return check(load().adr_set_host_reads(ctx, int(mode)), "adr_set_host_reads")
+
+
+TILE_SPLIT_OFF, TILE_SPLIT_LAST_SLICE = 0, 1
+
+
+def adr_set_tile_split(ctx, mode):
+    return check(load().adr_set_tile_split(ctx, int(mode)), "adr_set_tile_split")
 
 
 def adr_profile_enable(ctx, enable):

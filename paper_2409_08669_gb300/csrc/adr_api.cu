@@ -159,6 +159,7 @@ struct adr_ctx {
     int32_t slice_mode = ADR_SLICES_ADAPTIVE;
     int32_t host_reads = ADR_HOST_READ_MAPPED;   // adr_render_host: read mapped host buffers in place
     bool defer_colors = false;   // the next adr_preprocess leaves the SH colours to adr_render
+    int32_t tile_split = ADR_TILE_SPLIT_OFF;   // adr_set_tile_split
     // host-path staging (adr_render_host), allocated on its first use
     float* stage = nullptr;
     float* stage_img = nullptr;
@@ -432,6 +433,7 @@ adr_status adr_render(adr_ctx* c, float* img, float* t_final, int32_t* load, voi
     DeviceGuard guard(c->device);
     cudaStream_t strm = (cudaStream_t)stream;
     c->last_stream = strm;
+    c->fs.split_last_slice = c->tile_split == ADR_TILE_SPLIT_LAST_SLICE;
     enqueue_render(c->ws, c->fs, img, t_final, load, strm);
     if (c->fs.sliced && !c->slice_probe) {
         // Runs of every Gaussian, of slice 0 and of slice 1, back to the host.
@@ -607,6 +609,14 @@ adr_status adr_image_loss(const float* img, const float* ref, int32_t channels, 
     launch_image_loss(img, ref, channels, height, width, win, w_l1, w_ssim, stats, dl_dimg,
                       scratch, (cudaStream_t)stream);
     return check_launch("adr_image_loss") == ADR_OK ? ok() : ADR_ERR_CUDA;
+}
+
+adr_status adr_set_tile_split(adr_ctx* c, int32_t mode) {
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (mode != ADR_TILE_SPLIT_OFF && mode != ADR_TILE_SPLIT_LAST_SLICE)
+        return fail(ADR_ERR_INVALID, "unknown tile split mode %d", (int)mode);
+    c->tile_split = mode;
+    return ok();
 }
 
 adr_status adr_set_host_reads(adr_ctx* c, int32_t mode) {

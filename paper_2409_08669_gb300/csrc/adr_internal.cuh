@@ -229,6 +229,7 @@ struct FrameState {
     const uint16_t* rows = nullptr;          // their row intervals
     bool allow_slices = true;                // the caller's choice for the next sort
     bool sliced = false;                     // the frame renders in two depth slices
+    bool split_last_slice = false;           // slice 1 renders tiles by pixel halves (f2)
     int runs_held = 0;                       // which Gaussians' column runs ws.pruns holds
     int lists = -1;                          // a ListKind; -1 before the first sort
 };
@@ -423,6 +424,7 @@ struct RenderCam {
 struct RenderBatch {
     int count = 0;
     int lists = kListsColumns;            // the same kind for every camera of the batch
+    int split = 0;                        // phase 2: k_render_half (tiles by pixel halves)
     int tile_begin[kMaxBatch + 1] = {0};  // camera b's tiles are blocks [tile_begin[b], tile_begin[b+1])
     RenderCam cam[kMaxBatch];
 };

@@ -267,6 +267,7 @@ static void render_launch(const BatchItem* items, int count, int phase, cudaStre
     RenderBatch rb;
     rb.count = count;
     rb.lists = phase == 0 ? items[0].fs->lists : kListsColumns;
+    rb.split = phase == 2 && items[0].fs->split_last_slice ? 1 : 0;
     for (int b = 0; b < count; ++b) {
         const BatchItem& it = items[b];
         rb.cam[b] = render_cam(*it.ws, *it.fs, it.img, it.t_final, it.load, phase);

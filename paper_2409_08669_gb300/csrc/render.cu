@@ -68,6 +68,103 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
     return d;
 }
 
+// Column tx's run range [start, end) in its pass's column lists (empty after
+// a pair overflow); warp 0 writes it to *out, the caller synchronises.
+__device__ __forceinline__ void column_range(const SliceState& ss, int tx, int lane, int warp,
+                                             uint2* out) {
+    if (warp != 0) return;
+    uint32_t before = 0;
+    for (int c = lane; c < tx; c += 32) before += ss.col_totals[c];
+    before = __reduce_add_sync(0xffffffffu, before);
+    if (lane == 0) {
+        const bool overflow = (int64_t)ss.col_counters[kCntPairs] > ss.capacity;
+        *out = overflow ? make_uint2(0u, 0u) : make_uint2(before, before + ss.col_totals[tx]);
+    }
+}
+
+// One batch of a tile's list from its column's runs [base, end): thread t
+// reads the packed row intervals of the 16 consecutive runs from a0 + 16 t
+// (a0 = base rounded down to a 16-byte boundary: two 16-byte loads), keeps
+// those covering row ty, and a block scan of the per-thread counts places
+// the first kStage kept ones' Gaussian ids stably in s_gid.  Returns the
+// kept count; *next is where the list resumes (the first kept run not
+// staged).  Ends with a block barrier.
+__device__ __forceinline__ uint32_t stage_column_batch(uint32_t base, uint32_t end, int ty,
+                                                       const uint16_t* __restrict__ rows,
+                                                       const uint2* __restrict__ runs,
+                                                       uint32_t* s_gid, uint32_t* s_wsum,
+                                                       uint32_t* s_next, int lane, int warp,
+                                                       uint32_t* next) {
+    const uint32_t a0 = base & ~7u;
+    const uint32_t first = a0 + 16u * threadIdx.x;
+    uint32_t mask = 0;
+    const uint4* r4 = reinterpret_cast<const uint4*>(rows + first);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t g0 = first + 8u * (uint32_t)h;
+        if (g0 < end) {
+            const uint4 q = r4[h];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t r = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;   // y0 | (h - 1) << 8
+                const uint32_t idx = g0 + (uint32_t)e;
+                const bool keep = idx >= base && idx < end && (uint32_t)ty - (r & 0xFFu) <= (r >> 8);
+                mask |= keep ? (1u << (8 * h + e)) : 0u;
+            }
+        }
+    }
+    // block exclusive scan of the kept counts, in thread (= list) order
+    const uint32_t cnt = __popc(mask);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yv = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += yv;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t before = incl - cnt, total = 0;
+#pragma unroll
+    for (int q = 0; q < kRenderWarps; ++q) {
+        const uint32_t v = s_wsum[q];
+        before += q < warp ? v : 0u;
+        total += v;
+    }
+    uint32_t slot = before;
+    while (mask) {
+        const int e = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (slot < (uint32_t)kStage) s_gid[slot] = runs[first + (uint32_t)e].x;
+        else if (slot == (uint32_t)kStage) *s_next = first + (uint32_t)e;
+        ++slot;
+    }
+    __syncthreads();
+    *next = total > (uint32_t)kStage ? *s_next : min(end, a0 + 16u * kRenderThreads);
+    return total;
+}
+
+// The m staged Gaussians' terms, the centre taken relative to the tile origin
+// (ox, oy): (hi - origin) is exact, one rounding for lo.  Ends with a barrier.
+__device__ __forceinline__ void stage_records(int m, const uint32_t* s_gid, const float4* __restrict__ rec,
+                                              float ox, float oy, float4* s_kl, float4* s_nw,
+                                              float4* s_rg, float2* s_bb) {
+    for (int sl = threadIdx.x; sl < m; sl += kRenderThreads) {
+        const uint32_t gi = s_gid[sl];
+        const float4 r0 = rec[3 * (size_t)gi + 0];
+        const float4 w = rec[3 * (size_t)gi + 1];
+        const float4 col = rec[3 * (size_t)gi + 2];
+        const float2 c = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
+                                     __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
+        const float2 k = quad_k(c, w);
+        s_kl[sl] = make_float4(k.x, k.y, col.w, 0.f);   // k1, k2, log2(sigma), -
+        s_nw[sl] = make_float4(-w.x, -w.z, -w.y, -w.w);  // -w1x, -w2x, -w1y, -w2y
+        s_rg[sl] = make_float4(col.x, col.x, col.y, col.y);
+        s_bb[sl] = make_float2(col.z, col.z);
+    }
+    __syncthreads();
+}
+
 // A launch renders a batch of cameras (the serving scheduler's batched
 // frames; one camera otherwise): blocks [tile_begin[b], tile_begin[b + 1])
 // are camera b's tiles.
@@ -150,16 +247,7 @@ k_render(const RenderBatch batch) {
         fbase = ss.tile_fbase[tile_rm];
     }
     if (kRuns) {   // column tx's runs start after the runs of the columns before it
-        if (warp == 0) {
-            uint32_t before = 0;
-            for (int c = lane; c < tx; c += 32) before += ss.col_totals[c];
-            before = __reduce_add_sync(0xffffffffu, before);
-            if (lane == 0) {
-                const bool overflow = (int64_t)ss.col_counters[kCntPairs] > ss.capacity;
-                s_range = overflow ? make_uint2(0u, 0u)
-                                   : make_uint2(before, before + ss.col_totals[tx]);
-            }
-        }
+        column_range(ss, tx, lane, warp, &s_range);
         __syncthreads();
         range = s_range;
     }
@@ -176,54 +264,8 @@ k_render(const RenderBatch batch) {
         if (__syncthreads_count(done_a && done_b) == kRenderThreads) break;
         uint32_t total, next;
         if (kRuns) {
-            const uint32_t a0 = base & ~7u;
-            const uint32_t first = a0 + 16u * threadIdx.x;
-            uint32_t mask = 0;
-            const uint4* r4 = reinterpret_cast<const uint4*>(rows + first);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t g0 = first + 8u * (uint32_t)h;
-                if (g0 < range.y) {
-                    const uint4 q = r4[h];
-                    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t r = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;   // y0 | (h - 1) << 8
-                        const uint32_t idx = g0 + (uint32_t)e;
-                        const bool keep = idx >= base && idx < range.y &&
-                                          (uint32_t)ty - (r & 0xFFu) <= (r >> 8);
-                        mask |= keep ? (1u << (8 * h + e)) : 0u;
-                    }
-                }
-            }
-            // block exclusive scan of the kept counts, in thread (= list) order
-            const uint32_t cnt = __popc(mask);
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t yv = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += yv;
-            }
-            if (lane == 31) s_wsum[warp] = incl;
-            __syncthreads();
-            uint32_t before = incl - cnt;
-            total = 0;
-#pragma unroll
-            for (int q = 0; q < kRenderWarps; ++q) {
-                const uint32_t v = s_wsum[q];
-                before += q < warp ? v : 0u;
-                total += v;
-            }
-            uint32_t slot = before;
-            while (mask) {
-                const int e = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                if (slot < (uint32_t)kStage) s_gid[slot] = runs[first + (uint32_t)e].x;
-                else if (slot == (uint32_t)kStage) s_next = first + (uint32_t)e;
-                ++slot;
-            }
-            __syncthreads();
-            next = total > (uint32_t)kStage ? s_next : min(range.y, a0 + 16u * kRenderThreads);
+            total = stage_column_batch(base, range.y, ty, rows, runs, s_gid, s_wsum, &s_next, lane,
+                                       warp, &next);
         } else {
             total = min(range.y - base, (uint32_t)kStage);
             for (uint32_t e = threadIdx.x; e < total; e += kRenderThreads) s_gid[e] = sorted_gauss[base + e];
@@ -231,21 +273,7 @@ k_render(const RenderBatch batch) {
             next = base + total;
         }
         const int m = (int)min(total, (uint32_t)kStage);
-        for (int sl = threadIdx.x; sl < m; sl += kRenderThreads) {
-            const uint32_t gi = s_gid[sl];
-            const float4 r0 = rec[3 * (size_t)gi + 0];
-            const float4 w = rec[3 * (size_t)gi + 1];
-            const float4 col = rec[3 * (size_t)gi + 2];
-            // centre relative to the tile origin: (hi - origin) is exact, one rounding for lo
-            const float2 c = make_float2(__fadd_rn(__fsub_rn(r0.x, ox), r0.z),
-                                         __fadd_rn(__fsub_rn(r0.y, oy), r0.w));
-            const float2 k = quad_k(c, w);
-            s_kl[sl] = make_float4(k.x, k.y, col.w, 0.f);
-            s_nw[sl] = make_float4(-w.x, -w.z, -w.y, -w.w);
-            s_rg[sl] = make_float4(col.x, col.x, col.y, col.y);
-            s_bb[sl] = make_float2(col.z, col.z);
-        }
-        __syncthreads();
+        stage_records(m, s_gid, rec, ox, oy, s_kl, s_nw, s_rg, s_bb);
         if (!__all_sync(0xffffffffu, done_a && done_b)) {   // warp-uniform: the loop votes
             // A pixel becomes done only where it stops, so the loop leaves
             // there once every pixel of the warp is done.
@@ -345,13 +373,132 @@ k_render(const RenderBatch batch) {
     }
 }
 
+
+// f2, heavy tiles across CTAs: the last depth slice with every unfinished
+// tile split by pixel halves, two CTAs of 128 threads per tile, CTA h
+// rendering rows 8h..8h+7 with one pixel per thread, so each tile runs on
+// twice the warps (phase 2, column runs; selected with adr_set_tile_split).
+// Each pixel takes exactly the operations of k_render's paired lanes, so the
+// image, l_i and every per-pixel output are bit-identical to k_render's.
+__global__ void __launch_bounds__(kRenderThreads, 8)
+k_render_half(const RenderBatch batch) {
+    pdl_prologue();
+    const int blk = (int)(blockIdx.x >> 1), half = (int)(blockIdx.x & 1u);
+    int cb = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && blk >= batch.tile_begin[q]) ? 1 : 0;
+    const RenderCam& rc = batch.cam[cb];
+    const int tile_index = blk - batch.tile_begin[cb];
+    const SliceState& ss = rc.ss;
+    __shared__ uint32_t s_tstart;
+    if (rc.trace && threadIdx.x == 0) {
+        uint32_t t;
+        asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+        s_tstart = t;
+    }
+    __shared__ float4 s_kl[kStage];
+    __shared__ float4 s_nw[kStage];
+    __shared__ float4 s_rg[kStage];
+    __shared__ float2 s_bb[kStage];
+    __shared__ uint32_t s_gid[kStage];
+    __shared__ uint32_t s_wsum[kRenderWarps];
+    __shared__ uint32_t s_next;
+    __shared__ uint2 s_range;
+
+    const CamDev cam = rc.fp->cam;
+    const SetDev st = rc.fp->st;
+    const int ty = tile_index % cam.tiles_y, tx = tile_index / cam.tiles_y;
+    const int tile_rm = ty * cam.tiles_x + tx;
+    if (ss.tile_done[tile_rm]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp w: the 8x4 block (w mod 2, w div 2) of the half; lane l: (l mod 8, l div 8)
+    const int lx = (warp & 1) * 8 + (lane & 7), ly = half * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const int x = tx * kTile + lx, y = ty * kTile + ly;
+    const bool in_p = x < cam.width && y < cam.height;
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const float fx = (float)lx, fy = (float)ly;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    int32_t cnt = 0, last = 0, stop = 0;
+    bool done = !in_p;
+    const float e_low = st.e_low, t_min = st.t_min;
+    const size_t pix = in_p ? (size_t)y * cam.width + x : 0;
+    if (in_p) {   // resume the state slice 0 left
+        const float4 a = ss.pst[pix];
+        const int4 b = ss.pis[pix];
+        T = a.x; C0 = a.y; C1 = a.z; C2 = a.w;
+        cnt = b.x; last = b.y; done = b.w != 0; stop = done ? b.z : 0;
+    }
+    int32_t fbase = ss.tile_fbase[tile_rm];
+    column_range(ss, tx, lane, warp, &s_range);
+    __syncthreads();
+    const uint2 range = s_range;
+    uint32_t base = range.x;
+    while (base < range.y) {
+        if (__syncthreads_count(done) == kRenderThreads) break;
+        uint32_t next;
+        const uint32_t total = stage_column_batch(base, range.y, ty, rc.rows, rc.runs, s_gid, s_wsum,
+                                                  &s_next, lane, warp, &next);
+        const int m = (int)min(total, (uint32_t)kStage);
+        stage_records(m, s_gid, rc.rec, ox, oy, s_kl, s_nw, s_rg, s_bb);
+        if (!__all_sync(0xffffffffu, done)) {
+#pragma unroll 1
+            for (int j = 0; j < m; ++j) {
+                const float4 kl = s_kl[j];
+                const float4 nw = s_nw[j];
+                const float u1 = fmaf(nw.z, fy, fmaf(nw.x, fx, kl.x));
+                const float u2 = fmaf(nw.w, fy, fmaf(nw.y, fx, kl.y));
+                const float e = fmaf(-u1, u1, fmaf(-u2, u2, kl.z));
+                bool l = !done && e >= e_low;
+                if (!__any_sync(0xffffffffu, l)) continue;
+                const float alpha = l ? fminf(0.99f, ex2_approx(e)) : 0.f;
+                float wgt = __fmul_rn(alpha, T);
+                float test_T = __fsub_rn(T, wgt);
+                if (__any_sync(0xffffffffu, test_T < t_min)) {
+                    if (test_T < t_min) { wgt = 0.f; test_T = T; l = false; stop = fbase + j + 1; done = true; }
+                    if (__all_sync(0xffffffffu, done)) break;
+                }
+                const float4 rg = s_rg[j];
+                C0 = fmaf(rg.x, wgt, C0);
+                C1 = fmaf(rg.z, wgt, C1);
+                C2 = fmaf(s_bb[j].x, wgt, C2);
+                T = test_T;
+                if (l) { ++cnt; last = fbase + j + 1; }
+            }
+        }
+        fbase += m;
+        base = next;
+    }
+    const bool stopped = stop != 0;
+    const int32_t trav = stopped ? stop : fbase;
+    if (rc.trace && threadIdx.x == 0 && half == 0) {   // tracing: the tile's first half
+        uint32_t t_end, smid;
+        asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_end));
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        rc.trace[cam.tiles_x * cam.tiles_y + tile_rm] = make_uint4(s_tstart, t_end, smid, (uint32_t)fbase);
+    }
+    if (in_p) {
+        const size_t hw = (size_t)cam.width * cam.height;
+        rc.img[pix] = C0 + T * st.bg[0];
+        rc.img[hw + pix] = C1 + T * st.bg[1];
+        rc.img[2 * hw + pix] = C2 + T * st.bg[2];
+        if (rc.t_final) rc.t_final[pix] = T;
+        if (rc.load) rc.load[pix] = cnt;
+        if (rc.last) rc.last[pix] = last;
+        if (rc.trav) rc.trav[pix] = trav;
+        if (rc.tfin) rc.tfin[pix] = T;
+        if (rc.lstat) rc.lstat[pix] = cnt | (stopped ? (int32_t)0x80000000u : 0);
+    }
+}
+
 }  // namespace
 
 void launch_render(const RenderBatch& batch, cudaStream_t stream) {
     if (batch.count < 1 || batch.count > kMaxBatch) return;
     const int tiles = batch.tile_begin[batch.count];
     if (tiles <= 0) return;
-    if (batch.lists == kListsColumns)
+    if (batch.lists == kListsColumns && batch.split && batch.cam[0].ss.phase == 2)
+        launch_pdl(k_render_half, 2 * tiles, kRenderThreads, 0, stream, batch);
+    else if (batch.lists == kListsColumns)
         launch_pdl(k_render<true>, tiles, kRenderThreads, 0, stream, batch);
     else
         launch_pdl(k_render<false>, tiles, kRenderThreads, 0, stream, batch);

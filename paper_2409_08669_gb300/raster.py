@@ -153,6 +153,11 @@ class Rasterizer:
 
     SLICES_NEVER, SLICES_ALWAYS, SLICES_ADAPTIVE = 0, 1, 2
 
+    def set_tile_split(self, mode):
+        """TILE_SPLIT_OFF (default) or TILE_SPLIT_LAST_SLICE: the last depth slice
+        renders every unfinished tile as two half-tile CTAs (see adr.h)."""
+        _lib.adr_set_tile_split(self.ctx, mode)
+
     def set_depth_slices(self, mode):
         """Depth slices of the frame: SLICES_NEVER, SLICES_ALWAYS or SLICES_ADAPTIVE
         (default); the images are the same, only the time differs."""

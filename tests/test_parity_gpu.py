@@ -276,27 +276,39 @@ def test_depth_slice_modes_render_identical_frames(rast):
 def test_heavy_cluster_frame_parity(rast):
     """A camera facing the heavy scene's dense cluster at 1080p: many tiles
     are still unfinished after depth slice 0 and their pixels blend ~900
-    Gaussians each.  The sliced frame is bit-identical to the unsliced one
-    (image, T, l_i, last and traversed positions), and the whole image keeps
-    parity with the oracle."""
+    Gaussians each.  The sliced frame, with the last slice's tiles rendered
+    whole or split into pixel halves across two CTAs (heavy tiles across
+    CTAs), is bit-identical to the unsliced one (image, T, l_i, last and
+    traversed positions), and the whole image keeps parity with the oracle
+    in both."""
+    from paper_2409_08669_gb300 import _lib
     from paper_2409_08669_gb300.raster import Rasterizer, upload
     scene = S.heavy_scene(n=300_000, seed=2)
     cam = S.orbit_cameras(50, width=1920, height=1080)[0]
     st = S.Settings(mode=S.MODE_AABB)
     params = upload(scene)
     out = []
-    for mode in (Rasterizer.SLICES_NEVER, Rasterizer.SLICES_ALWAYS):
+    for mode, split in ((Rasterizer.SLICES_NEVER, _lib.TILE_SPLIT_OFF),
+                        (Rasterizer.SLICES_ALWAYS, _lib.TILE_SPLIT_OFF),
+                        (Rasterizer.SLICES_ALWAYS, _lib.TILE_SPLIT_LAST_SLICE)):
         rast.set_depth_slices(mode)
+        rast.set_tile_split(split)
         img, t_final, load = rast.forward(params, cam, st)
         torch.cuda.synchronize()
         last, trav = rast.read_pixel_stats()
         fc = rast.frame_counts()
         out.append((img.cpu().numpy(), t_final.cpu().numpy(), load.cpu().numpy(), last, trav))
-    assert fc["sliced"] == 1 and fc["visible_slice1"] > 0
-    for a, b in zip(*out):
-        np.testing.assert_array_equal(a, b)
+        if mode == Rasterizer.SLICES_ALWAYS:
+            assert fc["sliced"] == 1 and fc["visible_slice1"] > 0
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            np.testing.assert_array_equal(a, b)
+    _check_frame(rast, scene, cam, st, "heavy300k-1080p/sliced/split")
+    rast.set_tile_split(_lib.TILE_SPLIT_OFF)
     _check_frame(rast, scene, cam, st, "heavy300k-1080p/sliced")
     rast.set_depth_slices(Rasterizer.SLICES_ADAPTIVE)
+    with pytest.raises(_lib.AdrError):
+        rast.set_tile_split(3)
 
 
 def test_degenerate_gaussians_are_culled(rast):
