@@ -346,10 +346,10 @@ adr_status adr_test_lookback_expiry(int32_t withheld_chunk, int32_t spin_limit);
  * pinned memory mapped into the device's address space (cudaHostAlloc /
  * cudaHostRegister, e.g. torch pin_memory; rots and sh 16-byte aligned),
  * Preprocess reads the scene in place over the host link (at most 44 bytes
- * of each Gaussian), the SH colours are computed just before each Render
- * launch for the Gaussians it blends only (192 bytes of SH each; with depth
- * slices, far fewer than the Gaussians with tiles), and Render writes the
- * outputs in place: nothing is copied.  Otherwise, and always with
+ * of each Gaussian), the SH colours (192 bytes each) are read for the
+ * Gaussians with tiles -- or, in a frame with depth slices, just before each
+ * Render launch for the Gaussians it blends only, far fewer -- and Render
+ * writes the outputs in place: nothing is copied.  Otherwise, and always with
  * ADR_HOST_READ_COPY, the arrays are copied into device staging buffers,
  * allocated by the first such call (max_gaussians * 236 bytes + image
  * buffers), and the outputs copied back.  The host buffers must not change

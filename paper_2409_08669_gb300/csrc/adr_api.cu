@@ -397,13 +397,10 @@ adr_status adr_preprocess(adr_ctx* c, const float* means, const float* scales, c
     return ok();
 }
 
-adr_status adr_sort(adr_ctx* c, void* stream) {
-    NvtxRange range_("adr_sort");
-    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
-    if (!c->have_frame) return fail(ADR_ERR_INVALID, "adr_sort before adr_preprocess");
-    DeviceGuard guard(c->device);
-    cudaStream_t strm = (cudaStream_t)stream;
-    c->last_stream = strm;
+// Whether the context's next adr_sort builds depth slices: always, never, or
+// (adaptive) when the last sliced frame's run counts, read back without
+// waiting, showed they pay, and every kSliceProbe-th frame to measure again.
+static bool next_frame_slices(adr_ctx* c) {
     if (c->slice_probe) {   // the last sliced frame's run counts, if they are back
         const cudaError_t q = cudaEventQuery(c->slice_ev);
         if (q == cudaSuccess) {
@@ -414,9 +411,18 @@ adr_status adr_sort(adr_ctx* c, void* stream) {
             cudaGetLastError();   // not an error: clear it
         }
     }
-    c->fs.allow_slices = c->slice_mode == ADR_SLICES_ALWAYS ||
-                         (c->slice_mode == ADR_SLICES_ADAPTIVE &&
-                          (c->slices_pay || (c->frames % kSliceProbe) == 0));
+    return c->slice_mode == ADR_SLICES_ALWAYS ||
+           (c->slice_mode == ADR_SLICES_ADAPTIVE && (c->slices_pay || (c->frames % kSliceProbe) == 0));
+}
+
+adr_status adr_sort(adr_ctx* c, void* stream) {
+    NvtxRange range_("adr_sort");
+    if (!c) return fail(ADR_ERR_INVALID, "ctx is NULL");
+    if (!c->have_frame) return fail(ADR_ERR_INVALID, "adr_sort before adr_preprocess");
+    DeviceGuard guard(c->device);
+    cudaStream_t strm = (cudaStream_t)stream;
+    c->last_stream = strm;
+    c->fs.allow_slices = next_frame_slices(c);
     ++c->frames;
     enqueue_sort(c->ws, c->fs, c->epoch, strm);
     adr_status s;
@@ -747,9 +753,11 @@ adr_status adr_render_host(adr_ctx* c, const float* means, const float* scales, 
         const bool inputs = n == 0 || (dm && ds && dr && dop && dsh && aligned(dr, 16) && aligned(dsh, 16));
         const bool outputs = di && (!t_final || dt) && (!load || dl);
         if (inputs && outputs) {
-            // The colours come from host memory too: only those of the
-            // Gaussians each Render phase blends are read.
-            c->defer_colors = true;
+            // The colours come from host memory too: a sliced frame reads
+            // only those of the Gaussians each Render phase blends; an
+            // unsliced frame blends every Gaussian with tiles and reads them
+            // in Preprocess, in index order.
+            c->defer_colors = next_frame_slices(c);
             adr_status s = adr_preprocess(c, dm, ds, dr, dop, dsh, n, camera, settings, stream);
             c->defer_colors = false;
             if (s != ADR_OK) return s;

@@ -43,14 +43,20 @@ def test_host_frames_match_device_frame(rast):
     scene = S.cluster_scene(n=150_000, seed=3)
     cam = S.orbit_cameras(50, width=1280, height=720)[11]
     st = S.Settings(mode=S.MODE_AABB)
+    from paper_2409_08669_gb300.raster import Rasterizer
     img, t_final, load = rast.forward(upload(scene), cam, st)
     torch.cuda.synchronize()
     ref = (img.cpu().numpy(), t_final.cpu().numpy(), load.cpu().numpy())
     frames = {}
-    for mode in (_lib.HOST_READ_MAPPED, _lib.HOST_READ_COPY):
-        _lib.adr_set_host_reads(rast.ctx, mode)
-        for pinned in (True, False):
-            frames[(mode, pinned)] = _host_frame(rast, scene, cam, st, pinned)
+    # with depth slices the mapped path defers the SH colours to each Render
+    # launch; without, Preprocess reads them
+    for slices in (Rasterizer.SLICES_ALWAYS, Rasterizer.SLICES_NEVER):
+        rast.set_depth_slices(slices)
+        for mode in (_lib.HOST_READ_MAPPED, _lib.HOST_READ_COPY):
+            _lib.adr_set_host_reads(rast.ctx, mode)
+            for pinned in (True, False):
+                frames[(slices, mode, pinned)] = _host_frame(rast, scene, cam, st, pinned)
+    rast.set_depth_slices(Rasterizer.SLICES_ADAPTIVE)
     _lib.adr_set_host_reads(rast.ctx, _lib.HOST_READ_MAPPED)
     for key, out in frames.items():
         for a, b in zip(out, ref):
