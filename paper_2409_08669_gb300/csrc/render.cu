@@ -97,6 +97,17 @@ __device__ __forceinline__ uint32_t stage_column_batch(uint32_t base, uint32_t e
                                                        uint32_t* next) {
     const uint32_t a0 = base & ~7u;
     const uint32_t first = a0 + 16u * threadIdx.x;
+    // the thread's runs inside [base, end) as bits 0..15 (first > base only
+    // for thread 0, by at most 7)
+    const uint32_t lo = base > first ? base - first : 0u;
+    const uint32_t hi = end > first ? min(16u, end - first) : 0u;
+    const uint32_t in_range = hi > lo ? (0xFFFFu >> (16u - hi)) & (0xFFFFu << lo) : 0u;
+    // Row test of two runs per 32-bit word, one per 16-bit lane holding
+    // y0 | (h - 1) << 8: a run covers row ty iff y0 <= ty and ty - y0 <= h - 1.
+    // Per lane x = ty + 256 - y0 and then (256 + h - 1) - (x mod 256) stay in
+    // 1..511, so no lane borrows from the next; bit 8 of x is set iff
+    // y0 <= ty, and bit 8 of the second iff ty - y0 <= h - 1.
+    const uint32_t t2 = (uint32_t)ty * 0x00010001u + 0x01000100u;
     uint32_t mask = 0;
     const uint4* r4 = reinterpret_cast<const uint4*>(rows + first);
 #pragma unroll
@@ -106,14 +117,15 @@ __device__ __forceinline__ uint32_t stage_column_batch(uint32_t base, uint32_t e
             const uint4 q = r4[h];
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint32_t r = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;   // y0 | (h - 1) << 8
-                const uint32_t idx = g0 + (uint32_t)e;
-                const bool keep = idx >= base && idx < end && (uint32_t)ty - (r & 0xFFu) <= (r >> 8);
-                mask |= keep ? (1u << (8 * h + e)) : 0u;
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = t2 - (w[j] & 0x00FF00FFu);                   // ty + 256 - y0
+                const uint32_t z = ((w[j] >> 8) & 0x00FF00FFu) | 0x01000100u;   // 256 + h - 1
+                const uint32_t b = (z - (x & 0x00FF00FFu)) & x & 0x01000100u;  // bits 8, 24
+                mask |= (((b >> 8) | (b >> 23)) & 3u) << (8 * h + 2 * j);
             }
         }
     }
+    mask &= in_range;
     // block exclusive scan of the kept counts, in thread (= list) order
     const uint32_t cnt = __popc(mask);
     uint32_t incl = cnt;
