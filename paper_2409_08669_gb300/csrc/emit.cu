@@ -17,7 +17,11 @@ namespace adr {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
+#ifndef ADR_SCAN_ITEMS
+#define ADR_SCAN_ITEMS 16
+#endif
+constexpr int kScanItems = ADR_SCAN_ITEMS;   // a multiple of 4
+static_assert(kScanItems % 4 == 0, "16-byte loads and stores");
 constexpr int kScanChunk = kScanThreads * kScanItems;
 constexpr uint32_t kSat = 0x7FFFFFFFu;   // running sums saturate here (> any capacity)
 constexpr unsigned long long kScanInc = 1ull << 31;
@@ -103,13 +107,26 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
         const uint32_t chunk = s_chunk;
         const int64_t base = (int64_t)chunk * kScanChunk;
         if (base >= n) break;
-        // Blocked arrangement: thread t owns items base + t*16 .. +15.
+        // Blocked arrangement: thread t owns items base + t*kScanItems and the
+        // kScanItems after it, read with 16-byte loads where all are in range.
+        const int64_t i0 = base + (int64_t)tid * kScanItems;
+        const bool full = i0 + kScanItems <= n;
         uint32_t w[kScanItems];
+        if (full) {
+            const uint4* b4 = reinterpret_cast<const uint4*>(sorted_box + i0);
+#pragma unroll
+            for (int k = 0; k < kScanItems / 4; ++k) {
+                const uint4 q = b4[k];
+                w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) w[k] = i0 + k < n ? sorted_box[i0 + k] : 0xFFFFFFFFu;
+        }
         uint32_t tsum = 0, psum = 0, nonzero = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int64_t i = base + tid * kScanItems + k;
-            const uint32_t box = i < n ? sorted_box[i] : 0xFFFFFFFFu;   // all ones: no tiles
+            const uint32_t box = w[k];   // all ones: no tiles
             const bool has = box != 0xFFFFFFFFu;
             w[k] = has ? ((box >> 16) & 0xFFu) + 1u : 0u;
             const uint32_t t = has ? w[k] * ((box >> 24) + 1u) : 0u;
@@ -147,11 +164,18 @@ k_scan_tiles(const uint32_t* __restrict__ sorted_box, int64_t n_host, int64_t ca
         if (lane == 0 && nz) atomicAdd(counters + kCntVisible, nz);
         __syncthreads();
         uint32_t run = sat_add(s_prefix, texcl);
+        uint32_t quad[4];
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int64_t i = base + tid * kScanItems + k;
+            const int64_t i = i0 + k;
             const uint32_t t = w[k];
-            if (i < n) offsets[i] = run;
+            quad[k & 3] = run;
+            if (full) {
+                if ((k & 3) == 3)
+                    reinterpret_cast<uint4*>(offsets + i0)[k >> 2] = make_uint4(quad[0], quad[1], quad[2], quad[3]);
+            } else if (i < n) {
+                offsets[i] = run;
+            }
             if (t != 0 && (int64_t)run < capacity) {
                 // run chunks start inside [run, run + t)
                 const uint64_t c_lo = ((uint64_t)run + kSortChunk - 1) / kSortChunk;

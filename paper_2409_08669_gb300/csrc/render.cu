@@ -180,89 +180,98 @@ __device__ __forceinline__ void stage_records(int m, const uint32_t* s_gid, cons
 // A launch renders a batch of cameras (the serving scheduler's batched
 // frames; one camera otherwise): blocks [tile_begin[b], tile_begin[b + 1])
 // are camera b's tiles.
-template <bool kRuns>
-__global__ void __launch_bounds__(kRenderThreads, 8)   // 8 CTAs per SM: <= 64 registers
+// The tile's constants, kept in shared memory so that the blend loop holds
+// only its own state in registers: with them, and the pixels' stop positions,
+// out of the registers and the single-camera launch indexing no camera array,
+// the column-run kernel of one camera fits 56 registers without spilling,
+// i.e. 9 CTAs (36 warps) per SM.
+struct TileInfo {
+    int width, height, tiles_x, tiles_y, tx, ty;
+};
+
+#ifndef ADR_RENDER_CTAS
+#define ADR_RENDER_CTAS 9   // CTAs per SM: 56 registers, no spills (10: 48 with spills)
+#endif
+// kBatched: blocks of several cameras (the serving scheduler's batched frames).
+template <bool kRuns, bool kBatched>
+__global__ void __launch_bounds__(kRenderThreads, ADR_RENDER_CTAS)
 k_render(const RenderBatch batch) {
     pdl_prologue();
     int cb = 0;
+    if (kBatched) {
 #pragma unroll
-    for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && (int)blockIdx.x >= batch.tile_begin[q]) ? 1 : 0;
-    const RenderCam& rc = batch.cam[cb];
-    const int tile_index = (int)blockIdx.x - batch.tile_begin[cb];
-    const uint2* __restrict__ ranges = rc.ranges;
-    const uint32_t* __restrict__ sorted_gauss = rc.sorted_gauss;
-    const uint2* __restrict__ runs = rc.runs;
-    const uint16_t* __restrict__ rows = rc.rows;
-    const float4* __restrict__ rec = rc.rec;
-    const FrameParams* __restrict__ fp = rc.fp;
-    float* __restrict__ img = rc.img;
-    float* __restrict__ t_final = rc.t_final;
-    int32_t* __restrict__ load = rc.load;
-    int32_t* __restrict__ last_out = rc.last;
-    int32_t* __restrict__ trav_out = rc.trav;
-    float* __restrict__ tfin = rc.tfin;
-    int32_t* __restrict__ lstat = rc.lstat;
-    const SliceState& ss = rc.ss;
-    __shared__ uint32_t s_tstart;
-    if (rc.trace && threadIdx.x == 0) {
-        uint32_t t;
-        asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
-        s_tstart = t;
+        for (int q = 1; q < kMaxBatch; ++q) cb += (q < batch.count && (int)blockIdx.x >= batch.tile_begin[q]) ? 1 : 0;
     }
+    __shared__ uint32_t s_tstart;
+    __shared__ TileInfo s_ti;
     __shared__ float4 s_kl[kStage];    // k1, k2, log2(sigma), -
     __shared__ float4 s_nw[kStage];    // -w1x, -w2x, -w1y, -w2y
     __shared__ float4 s_rg[kStage];    // red, red, green, green
     __shared__ float2 s_bb[kStage];    // blue, blue
     __shared__ uint32_t s_gid[kStage];
+    __shared__ int2 s_stop[kRenderThreads];             // each thread's stop positions (0: none)
     __shared__ uint32_t s_wsum[kRenderWarps];           // kept runs per warp
     __shared__ uint32_t s_next;
     __shared__ uint2 s_range;
-
-    const CamDev cam = fp->cam;
-    const SetDev st = fp->st;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Warp w renders the 8x8 quadrant (w mod 2, w div 2); lane l the pixels
+    // (l mod 8, 2 (l div 8)) and (l mod 8, 2 (l div 8) + 1) of it.
+    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 8 + 2 * (lane >> 3);
+    // Values used before the blend loop only; after it they are read back
+    // from s_ti.
+    const int tile_index = (int)blockIdx.x - (kBatched ? batch.tile_begin[cb] : 0);
+    const CamDev cam = batch.cam[cb].fp->cam;
     // CTAs walk the tiles column by column: the tiles in flight at once share
     // a few columns' run lists and Gaussian records in L2.
-    const int ty = tile_index % cam.tiles_y, tx = tile_index / cam.tiles_y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 8 + 2 * (lane >> 3);
-    const int x = tx * kTile + lx, ya = ty * kTile + ly, yb = ya + 1;
-    const bool in_a = x < cam.width && ya < cam.height, in_b = x < cam.width && yb < cam.height;
-    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const int ty0 = tile_index % cam.tiles_y, tx0 = tile_index / cam.tiles_y;
+    if (threadIdx.x == 0) {
+        s_ti = TileInfo{cam.width, cam.height, cam.tiles_x, cam.tiles_y, tx0, ty0};
+        if (batch.cam[cb].trace) {
+            uint32_t t;
+            asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+            s_tstart = t;
+        }
+    }
+    const int x0 = tx0 * kTile + lx, ya0 = ty0 * kTile + ly;
+    bool done_a = !(x0 < cam.width && ya0 < cam.height);
+    bool done_b = !(x0 < cam.width && ya0 + 1 < cam.height);
+    const int tile_rm0 = ty0 * cam.tiles_x + tx0;
+    uint2 range = kRuns ? make_uint2(0u, 0u) : batch.cam[cb].ranges[tile_rm0];
     const float2 fx2 = make_float2((float)lx, (float)lx);
     const float2 fya2 = make_float2((float)ly, (float)ly), fyb2 = make_float2((float)(ly + 1), (float)(ly + 1));
-
-    uint2 range = kRuns ? make_uint2(0u, 0u) : ranges[ty * cam.tiles_x + tx];
-    // Per-pixel blend state: pixel a in .x, pixel b in .y.
+    // Per-pixel blend state: pixel a in .x, pixel b in .y.  A pixel's stop
+    // position (0 while it blends) lives in s_stop.
     float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
-    int32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, stop_a = 0, stop_b = 0;
-    bool done_a = !in_a, done_b = !in_b, stopped_a = false, stopped_b = false;
-    const float e_low = st.e_low, t_min = st.t_min;
+    int32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0;
+    int2 stop = make_int2(0, 0);
+    const float e_low = batch.cam[cb].fp->st.e_low, t_min = batch.cam[cb].fp->st.t_min;
     int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
-    const int tile_rm = ty * cam.tiles_x + tx;
-    const size_t pixa = in_a ? (size_t)ya * cam.width + x : 0;
-    const size_t pixb = in_b ? (size_t)yb * cam.width + x : 0;
-    if (ss.phase == 2) {   // last slice: resume the tiles the first slice left unfinished
-        if (ss.tile_done[tile_rm]) return;
+    if (batch.cam[cb].ss.phase == 2) {   // last slice: resume the tiles the first slice left unfinished
+        const SliceState& ss = batch.cam[cb].ss;
+        if (ss.tile_done[tile_rm0]) return;
+        const size_t pixa = (size_t)ya0 * cam.width + x0;
         // a pixel that stopped keeps its traversal as its stop position
-        if (in_a) {
+        if (!done_a) {
             const float4 a = ss.pst[pixa];
             const int4 b = ss.pis[pixa];
             T.x = a.x; C0.x = a.y; C1.x = a.z; C2.x = a.w;
-            cnt_a = b.x; last_a = b.y; stopped_a = done_a = b.w != 0; stop_a = stopped_a ? b.z : 0;
+            cnt_a = b.x; last_a = b.y; done_a = b.w != 0; stop.x = done_a ? b.z : 0;
         }
-        if (in_b) {
+        if (!done_b) {
+            const size_t pixb = pixa + (size_t)cam.width;
             const float4 a = ss.pst[pixb];
             const int4 b = ss.pis[pixb];
             T.y = a.x; C0.y = a.y; C1.y = a.z; C2.y = a.w;
-            cnt_b = b.x; last_b = b.y; stopped_b = done_b = b.w != 0; stop_b = stopped_b ? b.z : 0;
+            cnt_b = b.x; last_b = b.y; done_b = b.w != 0; stop.y = done_b ? b.z : 0;
         }
-        fbase = ss.tile_fbase[tile_rm];
+        fbase = ss.tile_fbase[tile_rm0];
     }
+    s_stop[threadIdx.x] = stop;
     if (kRuns) {   // column tx's runs start after the runs of the columns before it
-        column_range(ss, tx, lane, warp, &s_range);
-        __syncthreads();
-        range = s_range;
+        column_range(batch.cam[cb].ss, tx0, lane, warp, &s_range);
     }
+    __syncthreads();
+    if (kRuns) range = s_range;
 
     // Each batch stages the first 256 kept entries of the next stretch of the
     // list.  Column runs: thread t reads the packed row intervals of the 16
@@ -272,20 +281,24 @@ k_render(const RenderBatch batch) {
     // only kept runs' Gaussian ids are fetched.  The list resumes at the
     // first kept entry not staged.  Per-tile lists: every entry is kept.
     uint32_t base = range.x;
-    while (base < range.y) {
+    const uint32_t end = range.y;
+    while (base < end) {
         if (__syncthreads_count(done_a && done_b) == kRenderThreads) break;
+        const int tx = s_ti.tx, ty = s_ti.ty;
         uint32_t total, next;
         if (kRuns) {
-            total = stage_column_batch(base, range.y, ty, rows, runs, s_gid, s_wsum, &s_next, lane,
-                                       warp, &next);
+            total = stage_column_batch(base, end, ty, batch.cam[cb].rows, batch.cam[cb].runs, s_gid,
+                                       s_wsum, &s_next, lane, warp, &next);
         } else {
-            total = min(range.y - base, (uint32_t)kStage);
+            const uint32_t* __restrict__ sorted_gauss = batch.cam[cb].sorted_gauss;
+            total = min(end - base, (uint32_t)kStage);
             for (uint32_t e = threadIdx.x; e < total; e += kRenderThreads) s_gid[e] = sorted_gauss[base + e];
             __syncthreads();
             next = base + total;
         }
         const int m = (int)min(total, (uint32_t)kStage);
-        stage_records(m, s_gid, rec, ox, oy, s_kl, s_nw, s_rg, s_bb);
+        stage_records(m, s_gid, batch.cam[cb].rec, (float)(tx * kTile), (float)(ty * kTile), s_kl, s_nw,
+                      s_rg, s_bb);
         if (!__all_sync(0xffffffffu, done_a && done_b)) {   // warp-uniform: the loop votes
             // A pixel becomes done only where it stops, so the loop leaves
             // there once every pixel of the warp is done.
@@ -314,8 +327,8 @@ k_render(const RenderBatch batch) {
                 if (__any_sync(0xffffffffu, fminf(test_T.x, test_T.y) < t_min)) {
                     // rare: a pixel stops before this Gaussian, which it does not blend
                     const int32_t pos = fbase + j + 1;
-                    if (test_T.x < t_min) { wgt.x = 0.f; test_T.x = T.x; la = false; stop_a = pos; done_a = true; }
-                    if (test_T.y < t_min) { wgt.y = 0.f; test_T.y = T.y; lb = false; stop_b = pos; done_b = true; }
+                    if (test_T.x < t_min) { wgt.x = 0.f; test_T.x = T.x; la = false; s_stop[threadIdx.x].x = pos; done_a = true; }
+                    if (test_T.y < t_min) { wgt.y = 0.f; test_T.y = T.y; lb = false; s_stop[threadIdx.x].y = pos; done_b = true; }
                     if (__all_sync(0xffffffffu, done_a && done_b)) break;   // nothing blends this Gaussian
                 }
                 const float4 rg = s_rg[j];
@@ -331,18 +344,25 @@ k_render(const RenderBatch batch) {
         fbase += m;
         base = next;
     }
-    stopped_a = stop_a != 0;
-    stopped_b = stop_b != 0;
+    stop = s_stop[threadIdx.x];
+    const TileInfo ti = s_ti;
+    const int x = ti.tx * kTile + lx, ya = ti.ty * kTile + ly;
+    const bool in_a = x < ti.width && ya < ti.height, in_b = x < ti.width && ya + 1 < ti.height;
+    const int tile_rm = ti.ty * ti.tiles_x + ti.tx;
+    const bool stopped_a = stop.x != 0, stopped_b = stop.y != 0;
     // Traversal (positions evaluated): up to the stop, else the whole list seen.
-    const int32_t trav_a = stopped_a ? stop_a : fbase, trav_b = stopped_b ? stop_b : fbase;
+    const int32_t trav_a = stopped_a ? stop.x : fbase, trav_b = stopped_b ? stop.y : fbase;
+    const RenderCam& rc = batch.cam[cb];
     if (rc.trace && threadIdx.x == 0) {   // tracing: this tile's CTA
         uint32_t t_end, smid;
         asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t_end));
         asm("mov.u32 %0, %%smid;" : "=r"(smid));
-        const int ntiles = cam.tiles_x * cam.tiles_y;
-        rc.trace[(ss.phase == 2 ? ntiles : 0) + tile_rm] = make_uint4(s_tstart, t_end, smid, (uint32_t)fbase);
+        const int ntiles = ti.tiles_x * ti.tiles_y;
+        rc.trace[(rc.ss.phase == 2 ? ntiles : 0) + tile_rm] = make_uint4(s_tstart, t_end, smid, (uint32_t)fbase);
     }
-    if (ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
+    const size_t pixa = (size_t)ya * ti.width + x, pixb = pixa + (size_t)ti.width;
+    if (rc.ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
+        const SliceState& ss = rc.ss;
         const bool all_done = __syncthreads_count(done_a && done_b) == kRenderThreads;
         if (threadIdx.x == 0) {
             ss.tile_done[tile_rm] = all_done ? 1u : 0u;
@@ -360,28 +380,29 @@ k_render(const RenderBatch batch) {
             return;
         }
     }
-    const size_t hw = (size_t)cam.width * cam.height;
+    const float bg0 = rc.fp->st.bg[0], bg1 = rc.fp->st.bg[1], bg2 = rc.fp->st.bg[2];
+    const size_t hw = (size_t)ti.width * ti.height;
     if (in_a) {
-        img[pixa] = C0.x + T.x * st.bg[0];
-        img[hw + pixa] = C1.x + T.x * st.bg[1];
-        img[2 * hw + pixa] = C2.x + T.x * st.bg[2];
-        if (t_final) t_final[pixa] = T.x;
-        if (load) load[pixa] = cnt_a;
-        if (last_out) last_out[pixa] = last_a;
-        if (trav_out) trav_out[pixa] = trav_a;
-        if (tfin) tfin[pixa] = T.x;
-        if (lstat) lstat[pixa] = cnt_a | (stopped_a ? (int32_t)0x80000000u : 0);
+        rc.img[pixa] = C0.x + T.x * bg0;
+        rc.img[hw + pixa] = C1.x + T.x * bg1;
+        rc.img[2 * hw + pixa] = C2.x + T.x * bg2;
+        if (rc.t_final) rc.t_final[pixa] = T.x;
+        if (rc.load) rc.load[pixa] = cnt_a;
+        if (rc.last) rc.last[pixa] = last_a;
+        if (rc.trav) rc.trav[pixa] = trav_a;
+        if (rc.tfin) rc.tfin[pixa] = T.x;
+        if (rc.lstat) rc.lstat[pixa] = cnt_a | (stopped_a ? (int32_t)0x80000000u : 0);
     }
     if (in_b) {
-        img[pixb] = C0.y + T.y * st.bg[0];
-        img[hw + pixb] = C1.y + T.y * st.bg[1];
-        img[2 * hw + pixb] = C2.y + T.y * st.bg[2];
-        if (t_final) t_final[pixb] = T.y;
-        if (load) load[pixb] = cnt_b;
-        if (last_out) last_out[pixb] = last_b;
-        if (trav_out) trav_out[pixb] = trav_b;
-        if (tfin) tfin[pixb] = T.y;
-        if (lstat) lstat[pixb] = cnt_b | (stopped_b ? (int32_t)0x80000000u : 0);
+        rc.img[pixb] = C0.y + T.y * bg0;
+        rc.img[hw + pixb] = C1.y + T.y * bg1;
+        rc.img[2 * hw + pixb] = C2.y + T.y * bg2;
+        if (rc.t_final) rc.t_final[pixb] = T.y;
+        if (rc.load) rc.load[pixb] = cnt_b;
+        if (rc.last) rc.last[pixb] = last_b;
+        if (rc.trav) rc.trav[pixb] = trav_b;
+        if (rc.tfin) rc.tfin[pixb] = T.y;
+        if (rc.lstat) rc.lstat[pixb] = cnt_b | (stopped_b ? (int32_t)0x80000000u : 0);
     }
 }
 
@@ -511,9 +532,11 @@ void launch_render(const RenderBatch& batch, cudaStream_t stream) {
     if (batch.lists == kListsColumns && batch.split && batch.cam[0].ss.phase == 2)
         launch_pdl(k_render_half, 2 * tiles, kRenderThreads, 0, stream, batch);
     else if (batch.lists == kListsColumns)
-        launch_pdl(k_render<true>, tiles, kRenderThreads, 0, stream, batch);
+        launch_pdl(batch.count > 1 ? k_render<true, true> : k_render<true, false>, tiles, kRenderThreads, 0,
+                   stream, batch);
     else
-        launch_pdl(k_render<false>, tiles, kRenderThreads, 0, stream, batch);
+        launch_pdl(batch.count > 1 ? k_render<false, true> : k_render<false, false>, tiles, kRenderThreads,
+                   0, stream, batch);
 }
 
 }  // namespace adr
