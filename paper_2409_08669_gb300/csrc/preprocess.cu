@@ -158,15 +158,30 @@ constexpr float kHalfLog2e = 0.84932180028801907f;
 // Gaussians of chunk k / count for camera k % count, so the blocks of one
 // chunk run side by side and every camera after the first reads the chunk's
 // parameters from L2 rather than DRAM.
-__global__ void __launch_bounds__(256, 3)   // 3 CTAs per SM: <= 80 registers
+constexpr int kPreThreads = 256;
+constexpr int kPreCtasPerSm = 3;
+__global__ void __launch_bounds__(kPreThreads, kPreCtasPerSm)   // <= 80 registers
 k_preprocess(int n, const float* __restrict__ means, const float* __restrict__ scales,
              const float* __restrict__ rots, const float* __restrict__ opac,
-             const float* __restrict__ sh, PreprocessBatch batch) {
+             const float* __restrict__ sh, PreprocessBatch batch, int64_t ahead) {
     pdl_prologue();
     const int b = (int)(blockIdx.x % (unsigned)batch.count);
     const int i = (int)(blockIdx.x / (unsigned)batch.count) * blockDim.x + threadIdx.x;
     const PreprocessOut& out = batch.cam[b];
     if (i == 0) atomicAdd(out.stage, 1u);   // new lookback tag for this call's passes
+    // Lane 0 of each warp asks L2 for the parameters (44 B per Gaussian) of
+    // the warp that runs one wave of CTAs later (`ahead` Gaussians on), so
+    // that warp's first loads hit L2 instead of waiting on DRAM.  Bulk
+    // prefetches: 16-byte aligned, sizes multiples of 16.
+    if ((threadIdx.x & 31) == 0 && b == 0 && ahead > 0) {
+        const int64_t g = (int64_t)i + ahead;
+        if (g + 32 <= n) {
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 384;" ::"l"(means + 3 * g) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 384;" ::"l"(scales + 3 * g) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 512;" ::"l"(rots + 4 * g) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 128;" ::"l"(opac + g) : "memory");
+        }
+    }
     if (i >= n) return;
     const CamDev cam = out.fp->cam;
     const SetDev st = out.fp->st;
@@ -348,10 +363,22 @@ void launch_preprocess(int n, const float* means, const float* scales, const flo
                        const float* opac, const float* sh, const PreprocessBatch& batch,
                        cudaStream_t stream) {
     if (n <= 0 || batch.count < 1 || batch.count > kMaxBatch) return;
-    const int threads = 256;
+    const int threads = kPreThreads;
     const unsigned chunks = (unsigned)((n + threads - 1) / threads);
+    // One wave of resident CTAs, in Gaussians of one camera (a multiple of
+    // 32): the prefetch distance.  Parameters in device memory only; host
+    // buffers mapped into the device's address space are read without it.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;
+    cudaPointerAttributes pa;
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, means);
+    if (pe != cudaSuccess) (void)cudaGetLastError();   // this query's own error only
+    const bool on_device = pe == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+    const int64_t ahead = on_device ? ((int64_t)sms * kPreCtasPerSm * threads / batch.count) & ~(int64_t)31 : 0;
     launch_pdl(k_preprocess, chunks * (unsigned)batch.count, threads, 0, stream, n, means, scales, rots,
-               opac, sh, batch);
+               opac, sh, batch, ahead);
 }
 
 void launch_colors(const uint32_t* ids, const uint32_t* count, const float* means, const float* sh,
