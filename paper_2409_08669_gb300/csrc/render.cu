@@ -32,10 +32,11 @@ namespace {
 // branches (weight alpha T, then T - alpha T, which is T (1 - alpha) of Eq. 3
 // with one rounding fewer): every pixel takes exactly the decisions of
 // quad_exponent's scalar evaluation, which the backward uses too.  The loop
-// is unrolled by two.
+// is unrolled by four.
 constexpr int kRenderThreads = kTilePixels / 2;
 constexpr int kStage = kTilePixels;          // Gaussians staged per batch
 constexpr int kRenderWarps = kRenderThreads / 32;
+constexpr float kInf = __builtin_huge_valf();
 
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -233,8 +234,9 @@ k_render(const RenderBatch batch) {
         }
     }
     const int x0 = tx0 * kTile + lx, ya0 = ty0 * kTile + ly;
-    bool done_a = !(x0 < cam.width && ya0 < cam.height);
-    bool done_b = !(x0 < cam.width && ya0 + 1 < cam.height);
+    const float e_low0 = batch.cam[cb].fp->st.e_low;
+    float2 elim = make_float2((x0 < cam.width && ya0 < cam.height) ? e_low0 : kInf,
+                              (x0 < cam.width && ya0 + 1 < cam.height) ? e_low0 : kInf);
     const int tile_rm0 = ty0 * cam.tiles_x + tx0;
     uint2 range = kRuns ? make_uint2(0u, 0u) : batch.cam[cb].ranges[tile_rm0];
     const float2 fx2 = make_float2((float)lx, (float)lx);
@@ -251,18 +253,20 @@ k_render(const RenderBatch batch) {
         if (ss.tile_done[tile_rm0]) return;
         const size_t pixa = (size_t)ya0 * cam.width + x0;
         // a pixel that stopped keeps its traversal as its stop position
-        if (!done_a) {
+        if (elim.x != kInf) {
             const float4 a = ss.pst[pixa];
             const int4 b = ss.pis[pixa];
             T.x = a.x; C0.x = a.y; C1.x = a.z; C2.x = a.w;
-            cnt_a = b.x; last_a = b.y; done_a = b.w != 0; stop.x = done_a ? b.z : 0;
+            cnt_a = b.x; last_a = b.y;
+            if (b.w != 0) { elim.x = kInf; stop.x = b.z; }
         }
-        if (!done_b) {
+        if (elim.y != kInf) {
             const size_t pixb = pixa + (size_t)cam.width;
             const float4 a = ss.pst[pixb];
             const int4 b = ss.pis[pixb];
             T.y = a.x; C0.y = a.y; C1.y = a.z; C2.y = a.w;
-            cnt_b = b.x; last_b = b.y; done_b = b.w != 0; stop.y = done_b ? b.z : 0;
+            cnt_b = b.x; last_b = b.y;
+            if (b.w != 0) { elim.y = kInf; stop.y = b.z; }
         }
         fbase = ss.tile_fbase[tile_rm0];
     }
@@ -283,7 +287,7 @@ k_render(const RenderBatch batch) {
     uint32_t base = range.x;
     const uint32_t end = range.y;
     while (base < end) {
-        if (__syncthreads_count(done_a && done_b) == kRenderThreads) break;
+        if (__syncthreads_count(fminf(elim.x, elim.y) == kInf) == kRenderThreads) break;
         const int tx = s_ti.tx, ty = s_ti.ty;
         uint32_t total, next;
         if (kRuns) {
@@ -299,9 +303,10 @@ k_render(const RenderBatch batch) {
         const int m = (int)min(total, (uint32_t)kStage);
         stage_records(m, s_gid, batch.cam[cb].rec, (float)(tx * kTile), (float)(ty * kTile), s_kl, s_nw,
                       s_rg, s_bb);
-        if (!__all_sync(0xffffffffu, done_a && done_b)) {   // warp-uniform: the loop votes
-            // A pixel becomes done only where it stops, so the loop leaves
-            // there once every pixel of the warp is done.  The batch goes in
+        if (!__all_sync(0xffffffffu, fminf(elim.x, elim.y) == kInf)) {   // warp-uniform: the loop votes
+            // A pixel becomes done only where it stops (its exponent limit
+            // then becomes +inf, so no later Gaussian reaches it), and the
+            // loop leaves there once every pixel of the warp is done.  The batch goes in
             // windows of 32 positions: bit k of bits_a / bits_b records that
             // pixel a / b blended position j0 + k, and each window's bits are
             // folded into l_i (their count) and the last blended position
@@ -311,7 +316,7 @@ k_render(const RenderBatch batch) {
             for (int j0 = 0; j0 < m && !warp_done; j0 += 32) {
                 const int len = min(32, m - j0);
                 uint32_t bits_a = 0u, bits_b = 0u;
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < len; ++k) {
                     const int j = j0 + k;
                     const float4 kl = s_kl[j];
@@ -324,12 +329,12 @@ k_render(const RenderBatch batch) {
                     // reaches alpha_low iff e >= e_low
                     const float ea = fmaf(-ua.x, ua.x, fmaf(-ua.y, ua.y, kl.z));
                     const float eb = fmaf(-ub.x, ub.x, fmaf(-ub.y, ub.y, kl.z));
-                    bool la = !done_a && ea >= e_low, lb = !done_b && eb >= e_low;
+                    const bool la = ea >= elim.x, lb = eb >= elim.y;
                     if (!__any_sync(0xffffffffu, la || lb)) continue;   // no pixel of the warp reaches alpha_low
                     // Front-to-back step (Eq. 3), both pixels at once: a pixel
                     // that skips has alpha 0 here, so T and C stay as they are.
-                    const float2 alpha = make_float2(la ? fminf(0.99f, ex2_approx(ea)) : 0.f,
-                                                     lb ? fminf(0.99f, ex2_approx(eb)) : 0.f);
+                    float2 alpha = make_float2(la ? fminf(0.99f, ex2_approx(ea)) : 0.f,
+                                               lb ? fminf(0.99f, ex2_approx(eb)) : 0.f);
                     // T (1 - alpha) = T - alpha T
                     float2 wgt = fmul2(alpha, T);
                     float2 test_T = fsub2(T, wgt);
@@ -337,9 +342,9 @@ k_render(const RenderBatch batch) {
                     if (__any_sync(0xffffffffu, fminf(test_T.x, test_T.y) < t_min)) {
                         // rare: a pixel stops before this Gaussian, which it does not blend
                         const int32_t pos = fbase + j + 1;
-                        if (test_T.x < t_min) { wgt.x = 0.f; test_T.x = T.x; la = false; s_stop[threadIdx.x].x = pos; done_a = true; }
-                        if (test_T.y < t_min) { wgt.y = 0.f; test_T.y = T.y; lb = false; s_stop[threadIdx.x].y = pos; done_b = true; }
-                        if (__all_sync(0xffffffffu, done_a && done_b)) {   // nothing blends this Gaussian
+                        if (test_T.x < t_min) { alpha.x = wgt.x = 0.f; test_T.x = T.x; s_stop[threadIdx.x].x = pos; elim.x = kInf; }
+                        if (test_T.y < t_min) { alpha.y = wgt.y = 0.f; test_T.y = T.y; s_stop[threadIdx.x].y = pos; elim.y = kInf; }
+                        if (__all_sync(0xffffffffu, fminf(elim.x, elim.y) == kInf)) {   // nothing blends this Gaussian
                             warp_done = true;
                             break;
                         }
@@ -350,8 +355,9 @@ k_render(const RenderBatch batch) {
                     C2 = ffma2(s_bb[j], wgt, C2);
                     T = test_T;
                     const uint32_t bit = 1u << k;
-                    if (la) bits_a |= bit;
-                    if (lb) bits_b |= bit;
+                    // blended: alpha >= alpha_low (> 0) and the pixel did not stop here
+                    if (alpha.x > 0.f) bits_a |= bit;
+                    if (alpha.y > 0.f) bits_b |= bit;
                 }
                 cnt_a += __popc(bits_a);
                 cnt_b += __popc(bits_b);
@@ -381,7 +387,7 @@ k_render(const RenderBatch batch) {
     const size_t pixa = (size_t)ya * ti.width + x, pixb = pixa + (size_t)ti.width;
     if (rc.ss.phase == 1) {   // first slice: finish the tile, or keep its state for the last one
         const SliceState& ss = rc.ss;
-        const bool all_done = __syncthreads_count(done_a && done_b) == kRenderThreads;
+        const bool all_done = __syncthreads_count(fminf(elim.x, elim.y) == kInf) == kRenderThreads;
         if (threadIdx.x == 0) {
             ss.tile_done[tile_rm] = all_done ? 1u : 0u;
             if (!all_done) ss.tile_fbase[tile_rm] = fbase;

@@ -187,6 +187,31 @@ def test_single_gaussian_footprint_closed_form(rast, theta, op):
     np.testing.assert_array_equal(load[ref["near"] == 0], ref["load"][ref["near"] == 0])
 
 
+def test_opaque_stack_with_zero_t_min_counts_every_blend(rast):
+    """t_min = 0 (no early termination): behind a few dozen Gaussians of alpha
+    near 0.99 the FP32 transmittance of the central pixels underflows to 0, yet every
+    later Gaussian that reaches alpha_low there is still blended (with zero
+    weight) and counted in l_i (Eq. 12), as in the FP64 oracle, where T never
+    reaches 0."""
+    from paper_2409_08669_gb300.raster import upload
+    k = 100
+    means = np.zeros((k, 3))
+    means[:, 2] = np.linspace(0.0, 1.2, k)
+    rgb = np.stack([np.linspace(0.1, 0.9, k), np.full(k, 0.5), np.linspace(0.9, 0.1, k)], axis=1)
+    sh = np.zeros((k, 16, 3))
+    sh[:, 0, :] = (rgb - 0.5) / 0.28209479177387814   # DC band: colour = Y00 * c + 0.5
+    scene = S._pack(means, np.tile([0.2, 0.15, 0.01], (k, 1)), np.tile([1.0, 0.0, 0.0, 0.0], (k, 1)),
+                    np.full(k, 0.995), sh)
+    cam = S.look_at((0, 0, -3), width=64, height=48)
+    st = S.Settings(t_min=0.0)
+    img, t_final, load = gpu_forward(rast, upload(scene), cam, st)
+    ref = oracle.render(scene, cam, st)
+    keep = ref["near"] == 0
+    assert ref["load"].max() == k and np.all(load[keep] == ref["load"][keep])
+    assert np.count_nonzero(t_final[keep & (ref["load"] == k)] == 0.0) >= 8   # the underflow tested
+    np.testing.assert_allclose(img[:, keep], ref["img"][:, keep], atol=1e-4)
+
+
 def test_empty_scene_and_all_culled(rast):
     from paper_2409_08669_gb300.raster import upload
     cam = S.look_at((0, 0, -3), width=40, height=24)
