@@ -67,10 +67,10 @@ EVAL_FP32_OPS = 15        # FP32 lane operations per Gaussian-pixel evaluation i
 KERNELS_PER_FRAME = 30
 # DRAM bytes (read + write) of one launch from one-pass ncu captures at the
 # heavy 3M-Gaussian 1080p frame: Render (profiles/render_heavy-3M-1080p_traffic.md,
-# its two launches of one frame, 57.6 MB) and the per-tile list pass
+# its two launches of one frame, 54.8 MB) and the per-tile list pass
 # (profiles/tile_scatter_rows_heavy-3M-1080p_traffic.md, 128.34 + 576.92 MB over
 # P = 1.5958e8 pairs, scaled by the measured P).
-TRAFFIC_BYTES_PER_FRAME = {"render": (10.48e6 + 11.72e6) + (35.35e6 + 0.08e6)}
+TRAFFIC_BYTES_PER_FRAME = {"render": (10479616 + 8927232) + (35350528 + 17920)}
 TRAFFIC_BYTES_PER_PAIR = {"tile_scatter_rows": (128.34e6 + 576.92e6) / 1.5958e8}
 
 
