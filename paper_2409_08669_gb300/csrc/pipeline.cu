@@ -1,6 +1,8 @@
 // Stage orchestration shared by every entry point: enqueues the kernels of
 // the six-stage rasterizer (Sec. 3.2.1) on one stream for a Workspace,
 // wherever its buffers come from.
+#include <algorithm>
+
 #include "adr_internal.cuh"
 
 namespace adr {
@@ -280,9 +282,13 @@ static void render_launch(const BatchItem* items, int count, int phase, cudaStre
 // unfinished tile, with their run offsets, then their column runs.
 static void slice1_runs(const Workspace& ws, FrameState& fs, cudaStream_t stream) {
     uint32_t* c1 = ws.slice_counters + kCntSlots;
+    // The survivor selection walks the Gaussians behind slice 0 in 256-item steps,
+    // each CTA its own range: ~1024 Gaussians per CTA keeps each CTA's chain of
+    // steps short (2048 CTAs at 3M Gaussians: 1.49 -> 1.52 k frames/s).
+    const int surv_grid = (int)std::min<int64_t>(kMaxTileGrid, std::max<int64_t>(ws.sort_grid, fs.n / 1024));
     TIMED(ws, kKSlice, stream,
           launch_survivors(ws.tile_done, fs.cam.tiles_x, fs.cam.tiles_y, ws.sat, ws.sorted_box,
-                           fs.order, ws.counters, ws.sort_grid, ws.surv_cnt, ws.surv_flag, ws.max_n,
+                           fs.order, ws.counters, surv_grid, ws.surv_cnt, ws.surv_flag, ws.max_n,
                            ws.capacity / kSortChunk + 2, ws.s_order, ws.s_box, ws.s_offsets,
                            ws.s_chunk_first, c1, ws.status, stream));
     enqueue_pass1(ws, fs, pair_source(ws, fs, 1), stream);
