@@ -3,12 +3,12 @@
 // alpha < alpha_low skip, early termination and the per-pixel load l_i
 // (Sec. 4.4, Eq. 12).
 //
-// One CTA of 256 threads per 16x16 tile.  The tile reads a depth-ordered list
-// that holds its own list as a subsequence -- the column runs of its column of
-// tiles (kRuns) -- or its own list.  Each batch reads up to 2048 runs (8 per
-// thread), keeps those whose rows hold the tile's row, compacts the first 256
-// kept ones stably into shared memory with their records, and every pixel
-// blends them.  Pixels stop early (transmittance below t_min), so a tile
+// One CTA of 128 threads per 16x16 tile, two pixels per thread.  The tile
+// reads a depth-ordered list that holds its own list as a subsequence -- the
+// column runs of its column of tiles (kRuns) -- or its own list.  Each batch
+// reads up to 2048 runs (16 per thread), keeps those whose rows hold the
+// tile's row, compacts the first 256 kept ones stably into shared memory with
+// their records, and every pixel blends them.  Pixels stop early (transmittance below t_min), so a tile
 // usually reads only the front of its list; the CTA leaves as soon as every
 // pixel has terminated (__syncthreads_count).  Pixel offsets are taken
 // relative to the tile origin so the float-float centre collapses to one
@@ -234,9 +234,12 @@ k_render(const RenderBatch batch) {
         }
     }
     const int x0 = tx0 * kTile + lx, ya0 = ty0 * kTile + ly;
-    const float e_low0 = batch.cam[cb].fp->st.e_low;
-    float2 elim = make_float2((x0 < cam.width && ya0 < cam.height) ? e_low0 : kInf,
-                              (x0 < cam.width && ya0 + 1 < cam.height) ? e_low0 : kInf);
+    // Each pixel's limit on the exponent: a Gaussian reaches it iff e >= limit.
+    // e_low while the pixel blends; +inf for a pixel outside the image or
+    // one that stopped (done), so the skip test needs no separate flag.
+    const float e_low = batch.cam[cb].fp->st.e_low, t_min = batch.cam[cb].fp->st.t_min;
+    float2 elim = make_float2((x0 < cam.width && ya0 < cam.height) ? e_low : kInf,
+                              (x0 < cam.width && ya0 + 1 < cam.height) ? e_low : kInf);
     const int tile_rm0 = ty0 * cam.tiles_x + tx0;
     uint2 range = kRuns ? make_uint2(0u, 0u) : batch.cam[cb].ranges[tile_rm0];
     const float2 fx2 = make_float2((float)lx, (float)lx);
@@ -246,7 +249,6 @@ k_render(const RenderBatch batch) {
     float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
     int32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0;
     int2 stop = make_int2(0, 0);
-    const float e_low = batch.cam[cb].fp->st.e_low, t_min = batch.cam[cb].fp->st.t_min;
     int32_t fbase = 0;   // position in the tile's own list of this batch's first entry
     if (batch.cam[cb].ss.phase == 2) {   // last slice: resume the tiles the first slice left unfinished
         const SliceState& ss = batch.cam[cb].ss;
