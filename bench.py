@@ -237,6 +237,18 @@ def build_workload(rank=0):
 L2_BYTES = 129 * 1024 * 1024
 
 
+def workload_config(world):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+            "cameras": N_CAMERAS, "mode": "adr_aabb", "sh_degree": 3,
+            "parallelism": f"replicas x{world}",
+            "l2": (f"inputs smaller than L2 ({N_GAUSS * 236 / 1e6:.1f} MB scene): a 256 MB "
+                   "buffer is written before every timed frame, which is timed on its own"
+                   if scene_fits_l2() else
+                   f"inputs larger than L2 ({N_GAUSS * 236 / 1e6:.0f} MB scene, "
+                   f"{N_GAUSS * 48 / 1e6:.0f} MB render records); no flush")}
+
+
 def scene_fits_l2():
     """Whether the workload's inputs fit the 129 MB L2 (then every timed frame
     starts after an L2 flush)."""
@@ -860,14 +872,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": f"synthetic (seeded {WORKLOADS[WORKLOAD][0]} scene; no dataset or trained model)",
-        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
-                   "cameras": N_CAMERAS, "mode": "adr_aabb", "sh_degree": 3,
-                   "parallelism": f"replicas x{world}",
-                   "l2": (f"inputs smaller than L2 ({N_GAUSS * 236 / 1e6:.1f} MB scene): a 256 MB "
-                          "buffer is written before every timed frame, which is timed on its own"
-                          if scene_fits_l2() else
-                          f"inputs larger than L2 ({N_GAUSS * 236 / 1e6:.0f} MB scene, "
-                          f"{N_GAUSS * 48 / 1e6:.0f} MB render records); no flush")},
+        "config": workload_config(world),
         "plain_fps": frames / t_plain if plain_ok else over_cap,
         "circle_fps": frames / t_circle if circle_ok else over_cap,
         "tile_split_fps": frames / max_over_ranks(pg, t_split),
@@ -972,6 +977,7 @@ class OracleFrame:
         o.render_tiled(full, ranges, svals, st)
         t_render = time.perf_counter() - t1
         self.last_split = (t_pre * self.g_div, t_render * tile_scale)
+        self.last_raw = t_pre + t_render   # wall seconds of the sample itself
         return t_pre * self.g_div + t_render * tile_scale
 
 
@@ -1035,17 +1041,27 @@ def run_reference(args):
     warmup = max(args.warmup, 3)
     for k in range(warmup):
         of.frame_seconds(cams[k % ncam], st, key=k % ncam)
-    secs = [of.frame_seconds(cams[(warmup + k) % ncam], st, key=(warmup + k) % ncam)
-            for k in range(args.steps)]
+    secs, raw = [], []
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        secs.append(of.frame_seconds(cams[(warmup + k) % ncam], st, key=(warmup + k) % ncam))
+        raw.append(of.last_raw)
+    t_wall = time.perf_counter() - t_wall
     total = sum(secs)
     fps = args.steps / total
+    # A step is the bounded sample: ms_per_step is its wall time, and `value`
+    # scales each step's sample to a full frame of the workload.
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
         "n_gpus": world, "steps": args.steps, "warmup": warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * t_wall / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
-                   "cameras": N_CAMERAS, "mode": "adr_aabb"},
+        "config": workload_config(world),
+        "step": ("a bounded sample of one frame: preprocess, emission and sort of 1/64 of the "
+                 "Gaussians and the tiled render of 1/256 of the tiles, each scaled to the full "
+                 "frame for `value`"),
+        "sample_ms_per_step": 1e3 * sum(raw) / args.steps,
+        "scaled_ms_per_frame": 1e3 * total / args.steps,
         "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": "per step: 1/64 Gaussian sample (preprocess, emit, sort) and "
                                    "1/256 tile sample (render), scaled to a full frame; "
