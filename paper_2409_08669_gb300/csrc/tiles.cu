@@ -24,9 +24,9 @@
 //      (per-digit totals are summed with atomics while counting),
 //   3. CTA b walks its chunks in order, ranks each chunk's items stably,
 //      groups them by digit in shared memory and writes every digit's run
-//      contiguously from its running offset.  Pass 1 ranks with warp
-//      match_any; pass 2 from per-warp row counts and a walk over the runs
-//      (see k_scatter_rows).
+//      contiguously from its running offset.  Pass 1 ranks with a warp
+//      ballot per digit bit; pass 2 from per-warp row counts and a walk over
+//      the runs (see k_scatter_rows).
 // No CTA ever waits for another one: the passes need no co-residency and no
 // spin-waits.
 #include <cstddef>
@@ -179,7 +179,15 @@ __device__ __forceinline__ void rank_chunk(Shared& sm, const uint32_t (&dig)[kSo
 #pragma unroll
     for (int q = 0; q < kSortItems; ++q) {
         const uint32_t d = dig[q];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // The lanes with the same digit (0..kRadix): one ballot per bit of the
+        // 9-bit value, every bit agreeing (match_any's result, without its
+        // cost growing with the number of distinct digits).
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= kRadixBits; ++b) {
+            const uint32_t ones = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? ones : ~ones;
+        }
         const uint32_t before = sm.warp_cnt[warp][d];
         rank[q] = before + __popc(peers & lanemask_lt());
         __syncwarp();
