@@ -115,3 +115,26 @@ def test_sort_throughput_counts_what_the_kernels_move():
     assert out["depth_sort_gaussians_per_s"] == 1_000_000 / 1e-4
     assert abs(out["tile_pass1_runs_per_s"] - 500_000 / 5e-5) < 1e-3 * 1e10
     assert out["runs_built_per_frame"] == 500_000
+
+
+def test_reference_arm_line_shares_the_config_and_times_its_steps(capsys, monkeypatch):
+    """`--impl reference` on the tiny workload: one JSON line whose config is
+    our arm's, whose ms_per_step is the wall time of a step as run (the
+    bounded sample) and whose value is frames/s of full frames (each step's
+    sample scaled up, so slower than the sample's own rate)."""
+    import argparse
+    import json
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.select_workload("tiny-10k-256")
+    try:
+        bench.run_reference(argparse.Namespace(steps=2, warmup=3, gpus=1))
+        d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+        assert d["impl"] == "reference" and d["unit"] == "frames/s" and d["steps"] == 2
+        assert d["config"] == bench.workload_config(1)
+        assert abs(d["ms_per_step"] - d["sample_ms_per_step"]) < 0.5 * d["ms_per_step"] + 50.0
+        assert d["scaled_ms_per_frame"] > d["sample_ms_per_step"]
+        assert abs(d["value"] - 1e3 / d["scaled_ms_per_frame"]) < 1e-9 * max(1.0, d["value"])
+        assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["value"] == d["value"]
+    finally:
+        bench.select_workload("heavy-3M-1080p")   # the module's default
